@@ -1,0 +1,489 @@
+"""Accuracy-controlled factorization of an H^2 matrix, its explicit inverse,
+and forward / backward substitution (oracle side, plain complex128 numpy).
+
+Follows Sec. III (Algorithms 1-4, eqs. 4-35) and Sec. IV (Algorithms 5-6):
+
+  for l = L .. l0:                                   (Algorithm 1)
+    for every cluster i at level l, in the elimination order:
+      Step 0  basis update from the stored fill-ins, eqs. (16)-(18) / (25)-(27)
+      Step 1  complement basis, Q~_i = [V~_i^perp  V~_i], eqs. (4), (19), (28)
+      Step 2  Z_cur <- Q_i^H Z_cur conj(Q_i) on row / column i, eq. (5), Alg. 3
+      Step 3  partial LU of the first #i - k unknowns, eqs. (9)-(15), Alg. 4
+    update couplings (eqs. 20-22, 33), pad transfers (eq. 23), merge (Fig. 2h)
+  LU of the final block (Algorithm 1, last line)
+
+Block store.  Every block of the current matrix is kept in the current
+coordinates of its row and column clusters: all n_c unknowns before cluster c
+is processed at this level, the Q~_c coordinates afterwards, of which only the
+trailing k~_c ("kept") stay in Z_cur.  Inadmissible blocks are dense; an
+admissible block carries its original coupling S (in the level's incoming
+bases) plus one summed fill-in F (eq. 15 and the paragraph after it).
+
+Readings of the paper (each listed in the design doc):
+  R1 one cluster basis per cluster serves rows and columns (eq. 2); for a
+     general, non-symmetric matrix Step 0 adds the column fill-ins
+     F_{k,i}^T conj(F_{k,i}) to the row Gram of eq. (16).
+  R2 truncation: keep eigenpairs of G_i with lambda > (eps * nu_i)^2, where
+     nu_i^2 = sum ||S||_F^2 over the admissible blocks of row and column i at
+     this level plus trace(sum F F^H + sum F^T conj(F)).
+  R3 a fill-in landing on a pair that the level's partition does not hold
+     (it lies inside an ancestor's admissible block) is stored like an
+     admissible fill-in ("pushed" block); after the level its kept part is
+     carried into the parent pair's fill-in, up to the ancestor level where
+     eq. (33) folds it into the coupling.
+  R4 Step 1 keeps V~_i verbatim as the last k columns (Householder QR gives
+     the complement), so eqs. (7)-(8) hold to round-off.
+  R5 partial pivoting inside the m_i x m_i block (largest |z|, lowest row).
+  R6 clusters of one colour of the near-field graph are processed as one
+     batch (the 'colored' order); 'natural' is the paper's left-to-right sweep.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+from . import dense
+from .tree import elimination_order
+
+
+class ClusterFactor:
+    """Factor data of one cluster at one level (the non-identity parts of
+    Q_i^l, L_i^l and U_i^l in eq. 34)."""
+
+    __slots__ = ("n", "kt", "m", "Q", "LU", "piv", "Up", "Lp")
+
+
+class LevelFactor:
+    __slots__ = ("l", "order", "n", "kt", "cl", "stats")
+
+
+class Factorization:
+    pass
+
+
+def _linv_p(LU, piv, X):
+    """L^{-1} P X with unit lower L from a packed LU."""
+    return sla.solve_triangular(LU, X[piv], lower=True, unit_diagonal=True)
+
+
+def _uinv(LU, X):
+    return sla.solve_triangular(LU, X, lower=False)
+
+
+def _x_uinv(X, LU):
+    """X U^{-1} = (U^{-T} X^T)^T."""
+    return sla.solve_triangular(LU, X.T, lower=False, trans="T").T
+
+
+def _round(X, dtype):
+    return X if dtype == np.complex128 else X.astype(dtype).astype(np.complex128)
+
+
+def factorize(H, eps, ordering="colored", bulk=np.complex128):
+    """Factorize Z_H2 (Algorithm 1).  `bulk`=np.complex64 rounds the Schur /
+    LU / transform products to FP32 complex, emulating the mixed-precision
+    path; rank decisions (Step 0/1) always run in FP64."""
+    tree, part, L, l0 = H.tree, H.part, H.L, H.l0
+    Fz = Factorization()
+    Fz.H, Fz.eps, Fz.ordering = H, eps, ordering
+    Fz.levels = []
+    # level-L state
+    n = np.array(tree.size[L], dtype=np.int64)
+    B = {c: H.V[c].copy() for c in range(2 ** L)}
+    near = {p: H.D[p].copy() for p in part.inad[L]}
+    fill = {}
+    for l in range(L, l0 - 1, -1):
+        near_set = set(part.inad[l])
+        adm_set = set(part.adm[l])
+        nbrs = part.near_lists(l)
+        order = elimination_order(nbrs, ordering)
+        nc = 2 ** l
+        k0 = np.array([B[c].shape[1] for c in range(nc)], dtype=np.int64)
+        # sum of ||S||_F^2 over admissible blocks of row and column c (R2)
+        snorm2 = np.zeros(nc)
+        for (t, s), S in H.S[l].items():
+            v = float(np.sum(np.abs(S) ** 2))
+            snorm2[t] += v
+            snorm2[s] += v
+        kt = k0.copy()
+        m = np.zeros(nc, dtype=np.int64)
+        done = np.zeros(nc, dtype=bool)
+        lev = LevelFactor()
+        lev.l, lev.order, lev.n = l, order, n.copy()
+        lev.cl = {}
+        stats = dict(pushed_blocks=0, fill_blocks=0, rank_growth=0)
+        fill_rows = {c: [] for c in range(nc)}
+        fill_cols = {c: [] for c in range(nc)}
+        for (a, b) in fill:
+            fill_rows[a].append(b)
+            fill_cols[b].append(a)
+
+        def act(c):
+            return slice(int(m[c]), int(n[c])) if done[c] else slice(0, int(n[c]))
+
+        for i in order:
+            ni = int(n[i])
+            Bi = B[i]
+            ki = Bi.shape[1]
+            # ---- Step 0: update the cluster basis from stored fill-ins ----
+            # The complement of the incoming basis, from a Householder QR of
+            # B_i, gives G_i of eq. (16)/(25) in complement coordinates:
+            # G_i = Vp (Vp^H M Vp) Vp^H with M = sum F F^H (+ column side, R1),
+            # because I - B B^H = Vp Vp^H.  Its eigenvectors Vp U are then
+            # orthogonal to B_i by construction.
+            if ki == 0:
+                Vp = np.eye(ni, dtype=np.complex128)
+            else:
+                Qf, _ = np.linalg.qr(Bi, mode="complete")
+                Vp = Qf[:, ki:]
+            rows = [(k, fill[(i, k)]) for k in fill_rows[i]]
+            cols = [(k, fill[(k, i)]) for k in fill_cols[i]]
+            Vadd = np.zeros((ni, 0), dtype=np.complex128)
+            Vrest = Vp
+            if (rows or cols) and ni > ki:
+                M = np.zeros((ni, ni), dtype=np.complex128)
+                for k, Fm in rows:
+                    Fa = Fm[:, act(k)]
+                    M += Fa @ Fa.conj().T                       # eq. (16) inner sum
+                for k, Fm in cols:
+                    Fa = Fm[act(k), :]
+                    M += Fa.T @ Fa.conj()                       # column side (R1)
+                Gc = Vp.conj().T @ M @ Vp                       # eq. (16)/(25)
+                Gc = 0.5 * (Gc + Gc.conj().T)
+                w, U = np.linalg.eigh(Gc)                       # eq. (17)/(26)
+                nu2 = snorm2[i] + float(np.real(np.trace(M)))
+                thr = eps * eps * nu2
+                r = int(np.sum(w > thr))
+                if r:
+                    Vadd = Vp @ U[:, ::-1][:, :r]               # descending eigenvalues
+                    Vrest = Vp @ U[:, ::-1][:, r:]
+                    stats["rank_growth"] += r
+            Bi = np.hstack([Bi, Vadd])                          # eq. (18)/(27)
+            k = Bi.shape[1]
+            kt[i] = k
+            mi = ni - k
+            # ---- Step 1: complement, Q~_i = [V~^perp, V~] (eq. 19, R4) ----
+            Q = np.hstack([Vrest, Bi])
+            B[i] = Bi
+            # ---- Step 2: Z_cur <- Q_i^H Z_cur conj(Q_i) (eq. 5, Alg. 3) ----
+            Qh, Qb = Q.conj().T, Q.conj()
+            for j in nbrs[i]:
+                if j == i:
+                    near[(i, i)] = _round(Qh @ near[(i, i)] @ Qb, bulk)
+                else:
+                    cj = act(j)
+                    X = near[(i, j)]
+                    X[:, cj] = _round(Qh @ X[:, cj], bulk)
+                    X = near[(j, i)]
+                    X[cj, :] = _round(X[cj, :] @ Qb, bulk)
+            for kk in fill_rows[i]:
+                X = fill[(i, kk)]
+                ck = act(kk)
+                X[:, ck] = _round(Qh @ X[:, ck], bulk)
+            for kk in fill_cols[i]:
+                X = fill[(kk, i)]
+                ck = act(kk)
+                X[ck, :] = _round(X[ck, :] @ Qb, bulk)
+            # ---- Step 3: partial LU of the first m_i unknowns (Alg. 4) ----
+            cf = ClusterFactor()
+            cf.n, cf.kt, cf.m, cf.Q = ni, k, mi, Q
+            cf.Up, cf.Lp = {}, {}
+            cf.LU, cf.piv = None, None
+            if mi > 0:
+                LU, piv = dense.lu(near[(i, i)][:mi, :mi])     # eq. (11)
+                LU = _round(LU, bulk)
+                cf.LU, cf.piv = LU, piv
+                ps = {}
+                for j in nbrs[i]:
+                    cs = slice(mi, ni) if j == i else act(j)
+                    Uj = _round(_linv_p(LU, piv, near[(i, j)][:mi, cs]), bulk)   # Alg. 4 l.2
+                    Lj = _round(_x_uinv(near[(j, i)][cs, :mi], LU), bulk)       # Alg. 4 l.3
+                    cf.Up[j] = (Uj, cs)
+                    cf.Lp[j] = (Lj, cs)
+                    ps[j] = cs
+                for j in nbrs[i]:                               # Alg. 4 l.4, eq. (12)
+                    Lj, rs = cf.Lp[j]
+                    for kk in nbrs[i]:
+                        Uk, cs = cf.Up[kk]
+                        upd = _round(Lj @ Uk, bulk)
+                        if (j, kk) in near_set:
+                            near[(j, kk)][rs, cs] -= upd
+                        else:                                   # eq. (15): store F_jk
+                            if (j, kk) not in fill:
+                                fill[(j, kk)] = np.zeros((int(n[j]), int(n[kk])), dtype=np.complex128)
+                                fill_rows[j].append(kk)
+                                fill_cols[kk].append(j)
+                                stats["fill_blocks"] += 1
+                                if (j, kk) not in adm_set:
+                                    stats["pushed_blocks"] += 1
+                            fill[(j, kk)][rs, cs] -= upd
+            m[i] = mi
+            done[i] = True
+            lev.cl[i] = cf
+        lev.kt = kt.copy()
+        stats["kt_max"] = int(kt.max()) if nc else 0
+        stats["n_max"] = int(n.max()) if nc else 0
+        lev.stats = stats
+        Fz.levels.append(lev)
+
+        def kept(a, b):
+            """Kept (trailing) part of pair (a,b) after the level: the merged
+            block of Fig. 2(h); admissible blocks give pad(S) + F (eqs. 20-22)."""
+            if (a, b) in near_set:
+                return near[(a, b)][m[a]:, m[b]:].copy()
+            X = np.zeros((int(kt[a]), int(kt[b])), dtype=np.complex128)
+            if (a, b) in adm_set:
+                S = H.S[l][(a, b)]
+                X[:S.shape[0], :S.shape[1]] = S                 # eq. (20)
+            if (a, b) in fill:
+                X += fill[(a, b)][m[a]:, m[b]:]                 # eq. (22)/(33)
+            return X
+
+        if l > l0:
+            # ---- merge to level l-1 (eq. 23, eq. 24, Fig. 2 g-i) ----
+            npar = np.array([kt[2 * p] + kt[2 * p + 1] for p in range(2 ** (l - 1))], dtype=np.int64)
+            Bn = {}
+            for p in range(2 ** (l - 1)):
+                Tp = H.T[l - 1][p]
+                c1, c2 = 2 * p, 2 * p + 1
+                k1 = int(k0[c1])
+                Tn = np.zeros((int(npar[p]), Tp.shape[1]), dtype=np.complex128)
+                Tn[:k1] = Tp[:k1]                               # eq. (23) zero padding
+                Tn[kt[c1]:kt[c1] + int(k0[c2])] = Tp[k1:]
+                Bn[p] = Tn
+            near_n = {}
+            for p, q in part.inad[l - 1]:
+                top = np.hstack([kept(2 * p, 2 * q), kept(2 * p, 2 * q + 1)])
+                bot = np.hstack([kept(2 * p + 1, 2 * q), kept(2 * p + 1, 2 * q + 1)])
+                near_n[(p, q)] = np.vstack([top, bot])
+            near_par = set(part.inad[l - 1])
+            fill_n = {}
+            for (a, b), Fm in fill.items():
+                if (a, b) in adm_set:
+                    continue
+                pa, pb = a // 2, b // 2
+                assert (pa, pb) not in near_par
+                if (pa, pb) not in fill_n:
+                    fill_n[(pa, pb)] = np.zeros((int(npar[pa]), int(npar[pb])), dtype=np.complex128)
+                ro = 0 if a % 2 == 0 else int(kt[a - 1])
+                co = 0 if b % 2 == 0 else int(kt[b - 1])
+                fill_n[(pa, pb)][ro:ro + kt[a], co:co + kt[b]] += Fm[m[a]:, m[b]:]
+            n, B, near, fill = npar, Bn, near_n, fill_n
+        else:
+            # ---- final block: all pairs at level l0 (Alg. 1, last line) ----
+            off = np.concatenate([[0], np.cumsum(kt)])
+            R = np.zeros((off[-1], off[-1]), dtype=np.complex128)
+            for a in range(nc):
+                for b in range(nc):
+                    assert (a, b) in near_set or (a, b) in adm_set
+                    R[off[a]:off[a + 1], off[b]:off[b + 1]] = kept(a, b)
+            Fz.root_size = int(off[-1])
+            Fz.root_off = off
+            if off[-1] > 0:
+                Fz.root_LU, Fz.root_piv = dense.lu(R)
+                Fz.root_LU = _round(Fz.root_LU, bulk)
+            else:
+                Fz.root_LU, Fz.root_piv = np.zeros((0, 0), dtype=np.complex128), np.zeros(0, dtype=np.int64)
+            Fz.root = R
+    return Fz
+
+
+# --------------------------------------------------------------------------
+# Solve: Algorithm 5 (forward), root, Algorithm 6 (backward)
+# --------------------------------------------------------------------------
+
+def _leaf_split(Fz, v):
+    tree, L = Fz.H.tree, Fz.H.L
+    return {c: v[tree.start[L][c]:tree.start[L][c] + tree.size[L][c]].copy() for c in range(2 ** L)}
+
+
+def _merge(lev, vec):
+    nc = len(lev.n)
+    return {p: np.concatenate([vec[2 * p][lev.n[2 * p] - lev.kt[2 * p]:],
+                               vec[2 * p + 1][lev.n[2 * p + 1] - lev.kt[2 * p + 1]:]])
+            for p in range(nc // 2)}
+
+
+def _scatter(lev_child, vec_child, vec_par):
+    for p, vp in vec_par.items():
+        for c in (2 * p, 2 * p + 1):
+            k = int(lev_child.kt[c])
+            m = int(lev_child.n[c]) - k
+            o = 0 if c % 2 == 0 else int(lev_child.kt[c - 1])
+            vec_child[c][m:] = vp[o:o + k]
+
+
+def _root_split(Fz, lev, y):
+    off = Fz.root_off
+    out = {}
+    for c in range(len(lev.n)):
+        out[c] = y[off[c]:off[c + 1]]
+    return out
+
+
+def solve(Fz, b, inverse=None):
+    """x = Z^{-1} b via L y = b (Alg. 5, eqs. 36-39) and U x = y (Alg. 6,
+    eqs. 40-42); b in tree order (N or N x nrhs).  With `inverse` (from
+    `invert`) the same traversal uses the explicit inverse blocks of eq. (35)."""
+    b = np.asarray(b, dtype=np.complex128)
+    one = b.ndim == 1
+    if one:
+        b = b[:, None]
+    vec = _leaf_split(Fz, b)
+    saved = []
+    for li, lev in enumerate(Fz.levels):
+        for i in lev.order:
+            cf = lev.cl[i]
+            vec[i] = cf.Q.conj().T @ vec[i]                      # Alg. 5 l.3
+            if cf.m > 0:
+                if inverse is None:
+                    bi = _linv_p(cf.LU, cf.piv, vec[i][:cf.m])   # Alg. 5 l.4, eq. (39)
+                else:
+                    bi = inverse.Linv[li][i] @ vec[i][:cf.m]
+                vec[i][:cf.m] = bi
+                for j, (Lj, rs) in cf.Lp.items():
+                    vec[j][rs] -= Lj @ bi
+        saved.append(vec)
+        if li + 1 < len(Fz.levels):
+            vec = _merge(lev, vec)                              # P_l
+    top = Fz.levels[-1]
+    r = np.concatenate([vec[c][top.n[c] - top.kt[c]:] for c in range(len(top.n))]) if Fz.root_size else np.zeros((0, b.shape[1]), dtype=np.complex128)
+    if Fz.root_size:
+        if inverse is None:
+            y = dense.lu_solve(Fz.root_LU, Fz.root_piv, r)
+        else:
+            y = inverse.Rinv @ r
+    else:
+        y = r
+    par = _root_split(Fz, top, y)
+    for li in range(len(Fz.levels) - 1, -1, -1):
+        lev = Fz.levels[li]
+        vec = saved[li]
+        for c, vp in par.items():                               # P_l^T
+            k = int(lev.kt[c])
+            vec[c][int(lev.n[c]) - k:] = vp
+        for i in reversed(lev.order):
+            cf = lev.cl[i]
+            if cf.m > 0:
+                if inverse is None:
+                    t = vec[i][:cf.m].copy()
+                    for k_, (Uk, cs) in cf.Up.items():
+                        t -= Uk @ vec[k_][cs]
+                    vec[i][:cf.m] = _uinv(cf.LU, t)             # Alg. 6 l.5
+                else:
+                    t = inverse.Uinv[li][i] @ vec[i][:cf.m]
+                    for k_, (Ub, cs) in inverse.Ub[li][i].items():
+                        t += Ub @ vec[k_][cs]
+                    vec[i][:cf.m] = t
+            vec[i] = cf.Q.conj() @ vec[i]                        # Alg. 6 l.6
+        if li > 0:
+            child = Fz.levels[li - 1]
+            par = {}
+            for p in range(len(lev.n)):
+                v = vec[p]
+                k1 = int(child.kt[2 * p])
+                par[2 * p] = v[:k1]
+                par[2 * p + 1] = v[k1:]
+    x = np.concatenate([vec[c] for c in range(len(Fz.levels[0].n))])
+    return x[:, 0] if one else x
+
+
+def solve_adjoint(Fz, r):
+    """lambda = Z^{-H} r from the same factors: the adjoints of the solve's
+    elementary operations applied in reverse order (U^H then L^H of eq. 34)."""
+    r = np.asarray(r, dtype=np.complex128)
+    one = r.ndim == 1
+    if one:
+        r = r[:, None]
+    vec = _leaf_split(Fz, r)
+    saved = []
+    for li, lev in enumerate(Fz.levels):
+        for i in lev.order:
+            cf = lev.cl[i]
+            vec[i] = cf.Q.T @ vec[i]                              # (conj Q)^H
+            if cf.m > 0:
+                t = sla.solve_triangular(cf.LU, vec[i][:cf.m], lower=False, trans="C")
+                vec[i][:cf.m] = t
+                for k_, (Uk, cs) in cf.Up.items():
+                    vec[k_][cs] -= Uk.conj().T @ t
+        saved.append(vec)
+        if li + 1 < len(Fz.levels):
+            vec = _merge(lev, vec)
+    top = Fz.levels[-1]
+    if Fz.root_size:
+        z = np.concatenate([vec[c][top.n[c] - top.kt[c]:] for c in range(len(top.n))])
+        z = sla.solve_triangular(Fz.root_LU, z, lower=False, trans="C")
+        z = sla.solve_triangular(Fz.root_LU, z, lower=True, unit_diagonal=True, trans="C")
+        y = np.empty_like(z)
+        y[Fz.root_piv] = z
+    else:
+        y = np.zeros((0, r.shape[1]), dtype=np.complex128)
+    par = _root_split(Fz, top, y)
+    for li in range(len(Fz.levels) - 1, -1, -1):
+        lev = Fz.levels[li]
+        vec = saved[li]
+        for c, vp in par.items():
+            k = int(lev.kt[c])
+            vec[c][int(lev.n[c]) - k:] = vp
+        for i in reversed(lev.order):
+            cf = lev.cl[i]
+            if cf.m > 0:
+                t = vec[i][:cf.m].copy()
+                for j, (Lj, rs) in cf.Lp.items():
+                    t -= Lj.conj().T @ vec[j][rs]
+                t = sla.solve_triangular(cf.LU, t, lower=True, unit_diagonal=True, trans="C")
+                u = np.empty_like(t)
+                u[cf.piv] = t                                   # P^T
+                vec[i][:cf.m] = u
+            vec[i] = cf.Q @ vec[i]
+        if li > 0:
+            child = Fz.levels[li - 1]
+            par = {}
+            for p in range(len(lev.n)):
+                v = vec[p]
+                k1 = int(child.kt[2 * p])
+                par[2 * p] = v[:k1]
+                par[2 * p + 1] = v[k1:]
+    x = np.concatenate([vec[c] for c in range(len(Fz.levels[0].n))])
+    return x[:, 0] if one else x
+
+
+class Inverse:
+    pass
+
+
+def invert(Fz):
+    """Explicit factor-form inverse of eq. (35): (L_i'i')^{-1} P, (U_i'i')^{-1},
+    -(U_i'i')^{-1} U_i'c panels and the inverse of the final block, so that
+    applying Z^{-1} needs matrix-vector products only."""
+    inv = Inverse()
+    inv.Linv, inv.Uinv, inv.Ub = [], [], []
+    for lev in Fz.levels:
+        Li, Ui, Ubl = {}, {}, {}
+        for i, cf in lev.cl.items():
+            if cf.m == 0:
+                continue
+            I = np.eye(cf.m, dtype=np.complex128)
+            Li[i] = _linv_p(cf.LU, cf.piv, I)
+            Ui[i] = _uinv(cf.LU, I)
+            Ubl[i] = {k: (-Ui[i] @ Uk, cs) for k, (Uk, cs) in cf.Up.items()}
+        inv.Linv.append(Li)
+        inv.Uinv.append(Ui)
+        inv.Ub.append(Ubl)
+    inv.Rinv = dense.lu_solve(Fz.root_LU, Fz.root_piv, np.eye(Fz.root_size, dtype=np.complex128)) if Fz.root_size else None
+    return inv
+
+
+def refine(Fz, b, tol=1e-6, max_iter=20, solve_fn=None):
+    """Iterative refinement x += Z^{-1}(b - Z_H2 x) with an FP64 H^2 matvec."""
+    from .h2 import matvec
+    solve_fn = solve_fn or (lambda v: solve(Fz, v))
+    x = solve_fn(b)
+    nb = np.linalg.norm(b)
+    hist = []
+    for _ in range(max_iter + 1):
+        r = b - matvec(Fz.H, x)
+        rel = np.linalg.norm(r) / nb
+        hist.append(rel)
+        if rel <= tol or len(hist) > max_iter:
+            break
+        x = x + solve_fn(r)
+    return x, hist
