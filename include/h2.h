@@ -1,0 +1,207 @@
+/*
+ * h2.h - C ABI of libh2, a GB300 (sm_103a) implementation of the
+ * accuracy-controlled direct solver for general H^2 matrices of
+ * Ma & Jiao (2017): level-by-level factorization with cluster-basis update
+ * from the fill-ins, its explicit inverse, forward / backward substitution,
+ * and the H^2 matrix-vector product.
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im) pairs: complex128 = 2 doubles.
+ *   - Vectors are N x nrhs, column-major, in the GLOBAL point order that the
+ *     caller used for the points (the library applies its tree permutation).
+ *   - Every call returns an h2_status; nothing throws across the ABI.  After
+ *     an error, h2_last_error(ctx) holds a message; a context whose
+ *     factorization failed stays valid for h2_matvec, h2_stats and
+ *     h2_destroy (its factors are dropped).
+ *   - Device pointers must be CUDA device (or managed) memory of the current
+ *     device unless the H2_HOST flag says they are host memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     work of a call is enqueued on it; calls return after it finished.
+ *   - The caller owns every buffer it passes in; the library copies what it
+ *     keeps.  The context owns all of its device arenas.
+ */
+#ifndef H2_H
+#define H2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h2_ctx h2_ctx;
+
+typedef enum {
+  H2_OK = 0,
+  H2_EINVAL = -1,     /* bad argument (sizes, NULL, flags)                  */
+  H2_ENOMEM = -2,     /* device or host allocation failed, or arena cap hit */
+  H2_ESINGULAR = -3,  /* zero pivot in a partial LU or in the final LU      */
+  H2_ENOCONV = -4,    /* refinement did not reach the tolerance             */
+  H2_ETIMEOUT = -5,   /* a bounded device-side wait ran out                 */
+  H2_ECUDA = -6,      /* a CUDA runtime call failed                         */
+  H2_EINTERNAL = -7,  /* broken internal invariant (message says which)     */
+  H2_ESTATE = -8      /* call out of order (e.g. solve before factorize)    */
+} h2_status;
+
+/* Precision of the factorization bulk (Steps 2-3, fill-ins, factors, solve).
+ * Rank decisions (Step 0-1: Gram, eigen-decomposition, complement) and the
+ * H^2 matvec always run in FP64. */
+typedef enum { H2_FP64 = 0, H2_MIXED = 1 /* complex64 bulk */ } h2_prec;
+
+/* Elimination order inside a level (Sec. III: "from the left to the right
+ * across all the clusters"). COLORED processes the colour classes of the
+ * near-field graph in increasing colour, each class as one batch. */
+typedef enum { H2_ORDER_COLORED = 0, H2_ORDER_NATURAL = 1 } h2_order;
+
+/* Flags of h2_solve / h2_matvec. */
+#define H2_ADJOINT 1u      /* solve A^H x = b / multiply by A^H              */
+#define H2_REFINE 2u       /* iterative refinement against the FP64 matvec   */
+#define H2_USE_INVERSE 4u  /* apply the explicit inverse of h2_invert        */
+#define H2_HOST 8u         /* b / x (or x / y) are HOST pointers             */
+
+typedef struct {
+  int leafsize;          /* cluster tree leaf size (default 64)             */
+  double eta;            /* admissibility ||c_t-c_s|| >= eta (r_t+r_s) (1.0) */
+  double sign;           /* s in A = I + s K D_chi (default +1)             */
+  int ordering;          /* h2_order (default H2_ORDER_COLORED)             */
+  int proxy_min;         /* minimum proxy points per sphere (default 64)    */
+  double proxy_radius;   /* proxy sphere radius / cluster radius (3.0)      */
+  size_t arena_cap_bytes;/* 0 = unlimited; else H2_ENOMEM beyond it         */
+  int host_only;         /* 1: h2_build keeps the representation on the host
+                            only (no GPU needed); such a context allows
+                            h2_export, h2_stats and h2_destroy only         */
+} h2_opts;
+
+/* Fill `o` with the defaults listed above. */
+void h2_default_opts(h2_opts* o);
+
+/*
+ * h2_build - H^2 representation of the scalar volume-integral-equation
+ * matrix A = I + s K D_chi on the points (Sec. II, eqs. 1-3; the paper
+ * builds its H^2 matrices with its refs. [14],[15], not described there):
+ *   K_ij = k^2 h^3 exp(-j k r_ij)/(4 pi r_ij) (i != j),
+ *   K_ii = (1 + j k a) exp(-j k a) - 1,  a = (3/(4 pi))^(1/3) h.
+ * The library factorizes the complex-symmetric Z = D^{1/2} A D^{-1/2}
+ * (chi_i > 0 required) and maps A x = b onto Z (D^{1/2} x) = D^{1/2} b.
+ *
+ *   pts     HOST, N x 3 row-major doubles (x, y, z per point)
+ *   k, h    wavenumber and cell size
+ *   chi     HOST, chi_len doubles: chi_len == N (per cell) or 1 (uniform)
+ *   eps     construction accuracy (relative, per cluster sample)
+ *   opts    NULL = defaults
+ *   stream  cudaStream_t for the uploads
+ *   out     receives the new context (NULL on error)
+ */
+h2_status h2_build(const double* pts, int64_t N, double k, double h,
+                   const double* chi, int64_t chi_len, double eps,
+                   const h2_opts* opts, void* stream, h2_ctx** out);
+
+/*
+ * h2_load - import an explicit H^2 matrix (e.g. from another constructor).
+ * All arrays are HOST memory; complex arrays are complex128, column-major.
+ *   N, L, l0     size, leaf depth, first level with admissible blocks; the
+ *                cluster tree is complete: level l has 2^l clusters, cluster
+ *                c has children 2c, 2c+1; leaves are contiguous in tree order
+ *   perm         N int64: perm[p] = global index of tree position p
+ *   leaf_size    2^L int64 point counts of the leaves
+ *   rank         ranks k_c of all clusters at levels l0..L, level-major
+ *                (level l0 first), 2^l entries per level
+ *   V            leaf bases, concatenated: leaf c is size_c x k_c
+ *   T            stacked transfers of levels l0..L-1 (level-major, cluster
+ *                order): (k_2c + k_2c+1) x k_c each
+ *   n_adm        admissible pair counts per level l0..L (L-l0+1 entries)
+ *   adm          pairs (t, s) per level, concatenated, 2 int64 each
+ *   S            couplings k_t x k_s in the same order (Z_ts = V_t S V_s^T)
+ *   n_near       number of dense leaf blocks; near: pairs (t, s), 2 int64
+ *   D            dense blocks size_t x size_s in the same order
+ *   dscale       N doubles (global order) or NULL: the context represents
+ *                A = diag(dscale)^{-1} Z diag(dscale) (NULL = identity)
+ * The pairs must partition the matrix (every entry in exactly one block).
+ */
+h2_status h2_load(int64_t N, int L, int l0, const int64_t* perm,
+                  const int64_t* leaf_size, const int64_t* rank,
+                  const double* V, const double* T, const int64_t* n_adm,
+                  const int64_t* adm, const double* S, int64_t n_near,
+                  const int64_t* near, const double* D, const double* dscale,
+                  const h2_opts* opts, void* stream, h2_ctx** out);
+
+/*
+ * h2_factorize - Algorithm 1 of the paper (Steps 0-3 per cluster, eqs.
+ * 4-33; coupling / transfer update and merge per level; LU of the final
+ * block), giving Z = LU in the product form of eq. (34).
+ *   eps_fill  truncation of the fill-in basis update, eqs. (17)/(26)
+ *   prec      h2_prec
+ * Replaces any earlier factorization of the context.  H2_ESINGULAR on a zero
+ * pivot.  Runs on the context's build stream.
+ */
+h2_status h2_factorize(h2_ctx* ctx, double eps_fill, int prec);
+
+/*
+ * h2_invert - explicit factor-form inverse of eq. (35): inverts every
+ * partial-LU diagonal block and the final block and pre-multiplies the U
+ * panels, so that H2_USE_INVERSE solves use matrix-vector products only.
+ * Requires a factorization (H2_ESTATE otherwise).
+ */
+h2_status h2_invert(h2_ctx* ctx);
+
+/*
+ * h2_solve - x = A^{-1} b by forward substitution (Algorithm 5, eqs. 36-39),
+ * the final block, and backward substitution (Algorithm 6, eqs. 40-42).
+ *   b, x       N x nrhs complex128, column-major, global order; x may alias b
+ *   flags      H2_ADJOINT (x = A^{-H} b, the adjoint traversal of the same
+ *              factors), H2_REFINE, H2_USE_INVERSE, H2_HOST
+ *   tol        H2_REFINE: stop at ||b - A x|| / ||b|| <= tol (per column max)
+ *   max_iter   H2_REFINE: maximum correction steps
+ *   iters      out (may be NULL): refinement steps taken
+ *   resid      out (may be NULL): final relative residual (max over columns)
+ * H2_ENOCONV if refinement stops above tol (x holds the last iterate).
+ */
+h2_status h2_solve(h2_ctx* ctx, const void* b, void* x, int nrhs,
+                   unsigned flags, double tol, int max_iter, int* iters,
+                   double* resid, void* stream);
+
+/*
+ * h2_matvec - y = A x (or A^H x with H2_ADJOINT) with the H^2 representation
+ * in FP64: upward pass through the nested bases (eq. 3), couplings (eq. 2),
+ * downward pass and the dense near field.  x, y: N x nrhs complex128,
+ * column-major, global order; must not alias.
+ */
+h2_status h2_matvec(h2_ctx* ctx, const void* x, void* y, int nrhs,
+                    unsigned flags, void* stream);
+
+/*
+ * h2_export - copy the H^2 representation out in the h2_load layout (HOST
+ * arrays, caller-allocated).  Call h2_export_sizes first: it returns the
+ * element counts (complex entries for V, T, S, D; pairs for adm / near).
+ */
+h2_status h2_export_sizes(const h2_ctx* ctx, int64_t* N, int* L, int* l0,
+                          int64_t* nV, int64_t* nT, int64_t* nS,
+                          int64_t* n_adm_total, int64_t* n_near, int64_t* nD);
+h2_status h2_export(const h2_ctx* ctx, int64_t* perm, int64_t* leaf_size,
+                    int64_t* rank, double* V, double* T, int64_t* n_adm,
+                    int64_t* adm, double* S, int64_t* near, double* D,
+                    double* dscale);
+
+/*
+ * h2_stats - JSON object with per-level sizes, ranks before / after the
+ * basis update, block counts (near, admissible, fill-in, pushed), colours,
+ * algorithmic flops and bytes, kernel launches, device bytes and timings of
+ * the last factorization / solve.  Returns H2_EINVAL if `cap` is too small
+ * (the JSON is truncated); `cap` >= 64 KiB is always enough.
+ */
+h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap);
+
+/* Last error message of the context ("" if none); valid until next call. */
+const char* h2_last_error(const h2_ctx* ctx);
+
+/* Message for a status code. */
+const char* h2_status_string(int status);
+
+/* Frees the context and all of its device memory. NULL is a no-op. */
+void h2_destroy(h2_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2_H */

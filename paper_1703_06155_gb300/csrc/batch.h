@@ -1,0 +1,73 @@
+// Host-side builders for the batched task lists and their launch helpers.
+#pragma once
+#include <algorithm>
+
+#include "h2_host.h"
+
+namespace h2 {
+
+inline size_t esz(int prec) { return prec == h2k::P64 ? sizeof(h2k::cd) : sizeof(h2k::cf); }
+
+// C = alpha * sum op(A) op(B) + beta * C, tiled 64 x 64
+struct GemmBatch {
+  std::vector<h2k::GemmTask> t;
+  std::vector<h2k::GemmPair> p;
+  std::vector<h2k::GemmTile> tl;
+  double flops = 0;
+  void task(void* C, int ldc, int M, int N, double alpha, double beta) {
+    t.push_back(h2k::GemmTask{C, ldc, M, N, (int)p.size(), 0, alpha, beta});
+  }
+  void pair(const void* A, int lda, int opA, const void* B, int ldb, int opB, int K) {
+    if (K <= 0) return;
+    p.push_back(h2k::GemmPair{A, B, lda, ldb, K, opA, opB});
+    t.back().np++;
+    flops += 8.0 * t.back().M * (double)t.back().N * K;
+  }
+  void close() {
+    h2k::GemmTask& g = t.back();
+    if (g.M <= 0 || g.N <= 0 || (g.np == 0 && g.beta == 1.0)) {
+      p.resize(g.p0);
+      t.pop_back();
+      return;
+    }
+    const int ti = (int)t.size() - 1;
+    const int bm = h2k::gemm_tile_m(0), bn = h2k::gemm_tile_n(0);
+    for (int tn = 0; tn * bn < g.N; ++tn)
+      for (int tm = 0; tm * bm < g.M; ++tm) tl.push_back(h2k::GemmTile{ti, tm, tn});
+  }
+  bool empty() const { return tl.empty(); }
+  void clear() { t.clear(); p.clear(); tl.clear(); flops = 0; }
+};
+
+// in-place X <- op(A) X (left) or X <- X op(A) (right)
+struct ApplyBatch {
+  std::vector<h2k::ApplyTask> t;
+  int maxp = 0;
+  double flops = 0;
+  void add(const void* A, int lda, int op, void* X, int ldx, int p, int w, int lo) {
+    if (p <= 0 || w <= 0 || lo >= p) return;
+    t.push_back(h2k::ApplyTask{A, X, lda, ldx, p, w, lo, op});
+    maxp = std::max(maxp, p);
+    flops += 8.0 * (double)(p - lo) * p * w;
+  }
+  bool empty() const { return t.empty(); }
+  void clear() { t.clear(); maxp = 0; flops = 0; }
+};
+
+struct CopyBatch {
+  std::vector<h2k::CopyTask> t;
+  // dst[0:rows,0:cols] (=|+=) src[0:srows,0:scols] zero-padded
+  void add(const void* src, int sprec, int lds, int srows, int scols, void* dst, int dprec, int ldd, int rows,
+           int cols, int mode = 0, double alpha = 1.0) {
+    if (rows <= 0 || cols <= 0) return;
+    t.push_back(h2k::CopyTask{src, dst, lds, ldd, rows, cols, srows, scols, sprec, dprec, mode, 0, alpha});
+  }
+  bool empty() const { return t.empty(); }
+  void clear() { t.clear(); }
+};
+
+void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what);
+void run_apply(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what);
+void run_copy(Ctx& c, CopyBatch& b, const char* what);
+
+}  // namespace h2

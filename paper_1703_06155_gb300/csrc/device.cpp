@@ -1,0 +1,124 @@
+// Device memory, task staging, and the FP64 device copy of the H^2 matrix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "h2_host.h"
+
+namespace h2 {
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+[[noreturn]] void fail(h2_status st, const std::string& msg) { throw Err{st, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(H2_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (b.bytes >= bytes) return b.p;
+  const size_t old = b.bytes;
+  const size_t want = std::max(bytes, old + old / 4);
+  if (c.opts.arena_cap_bytes && c.dev_bytes - old + want > c.opts.arena_cap_bytes)
+    fail(H2_ENOMEM, "device arena cap exceeded");
+  // the old contents are not kept: grow-only scratch / per-factorization arenas
+  if (b.p) {
+    ck(cudaStreamSynchronize(c.stream), "sync before realloc");
+    cudaFree(b.p);
+    b.p = nullptr;
+    c.dev_bytes -= old;
+    b.bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    fail(H2_ENOMEM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+  }
+  b.p = p;
+  b.bytes = want;
+  c.dev_bytes += want;
+  c.dev_peak = std::max(c.dev_peak, c.dev_bytes);
+  return p;
+}
+
+Stager::~Stager() {
+  if (pinned) cudaFreeHost(pinned);
+}
+
+void Stager::upload(Ctx& c) {
+  if (uploaded >= host.size()) return;
+  if (cap < host.size()) {
+    // everything uploaded so far has been consumed by launches already in
+    // the stream: wait for them, grow, and upload the whole range again
+    ck(cudaStreamSynchronize(c.stream), "stager sync");
+    if (pinned) cudaFreeHost(pinned);
+    pinned = nullptr;
+    cap = std::max(host.size() * 2, (size_t)1 << 20);
+    ck(cudaMallocHost(&pinned, cap), "cudaMallocHost");
+    dev_ensure(c, dev, cap);
+    uploaded = 0;
+  }
+  std::memcpy((unsigned char*)pinned + uploaded, host.data() + uploaded, host.size() - uploaded);
+  ck(cudaMemcpyAsync((unsigned char*)dev.p + uploaded, (unsigned char*)pinned + uploaded, host.size() - uploaded,
+                     cudaMemcpyHostToDevice, c.stream),
+     "task upload");
+  uploaded = host.size();
+}
+
+template <class T>
+static void upload_vec(Ctx& c, DevBuf& b, const std::vector<T>& v) {
+  dev_ensure(c, b, v.size() * sizeof(T));
+  if (!v.empty()) ck(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c.stream), "upload");
+  ck(cudaStreamSynchronize(c.stream), "upload sync");
+}
+
+void upload_h2(Ctx& c) {
+  H2Host& H = c.H;
+  const int L = H.L, l0 = H.l0;
+  std::vector<cplx> buf;
+  // leaf bases
+  c.V_off.assign(size_t(1) << L, 0);
+  for (int t = 0; t < (1 << L); ++t) {
+    c.V_off[t] = buf.size();
+    buf.insert(buf.end(), H.V[t].begin(), H.V[t].end());
+  }
+  upload_vec(c, c.dV, buf);
+  buf.clear();
+  c.T_off.assign(L + 1, {});
+  for (int l = l0; l < L; ++l) {
+    c.T_off[l].assign(size_t(1) << l, 0);
+    for (int t = 0; t < (1 << l); ++t) {
+      c.T_off[l][t] = buf.size();
+      buf.insert(buf.end(), H.T[l][t].begin(), H.T[l][t].end());
+    }
+  }
+  upload_vec(c, c.dT, buf);
+  buf.clear();
+  c.S_off.assign(L + 1, {});
+  c.adm_id.assign(L + 1, {});
+  for (int l = l0; l <= L; ++l) {
+    c.S_off[l].assign(H.part.adm[l].size(), 0);
+    for (size_t q = 0; q < H.part.adm[l].size(); ++q) {
+      c.S_off[l][q] = buf.size();
+      buf.insert(buf.end(), H.S[l][q].begin(), H.S[l][q].end());
+      c.adm_id[l][pkey(H.part.adm[l][q].first, H.part.adm[l][q].second)] = (int)q;
+    }
+  }
+  upload_vec(c, c.dS, buf);
+  buf.clear();
+  c.D_off.assign(H.part.inad[L].size(), 0);
+  for (size_t q = 0; q < H.part.inad[L].size(); ++q) {
+    c.D_off[q] = buf.size();
+    buf.insert(buf.end(), H.D[q].begin(), H.D[q].end());
+  }
+  upload_vec(c, c.dD, buf);
+  upload_vec(c, c.dperm, H.tree.perm);
+  upload_vec(c, c.dscale, H.dscale);
+}
+
+}  // namespace h2

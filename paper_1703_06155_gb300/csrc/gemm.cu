@@ -1,0 +1,143 @@
+// Batched variable-size complex sum-GEMM:  C = alpha * sum_p op(A_p) op(B_p) + beta * C
+//
+// One CTA computes one BM x BN tile of one task.  The host lists the tiles,
+// so a single launch covers every product of a colour class (Schur updates
+// grouped by target block, Step-0 Grams, H^2 matvec stages ...).  Operands
+// are staged through shared memory as split real / imaginary planes; each
+// thread owns a 4 x 4 complex micro-tile (rows ty + 16 i, columns tx + 16 j),
+// which keeps the shared-memory reads conflict-free.
+#include "h2_kernels.h"
+
+namespace h2k {
+namespace {
+
+template <class E> struct RealOf;
+template <> struct RealOf<cd> { using T = double; };
+template <> struct RealOf<cf> { using T = float; };
+
+template <class E, class R>
+__device__ __forceinline__ void load_op(const E* base, int ld, int op, int r, int c, R& re, R& im) {
+  // element (r, c) of op(X)
+  const E v = (op == OP_N || op == OP_C) ? base[(size_t)r + (size_t)c * ld] : base[(size_t)c + (size_t)r * ld];
+  re = (R)v.re;
+  im = (op == OP_C || op == OP_H) ? -(R)v.im : (R)v.im;
+}
+
+template <class E, class R>
+__device__ __forceinline__ void store_val(E* p, R re, R im) {
+  E v;
+  v.re = (decltype(v.re))re;
+  v.im = (decltype(v.im))im;
+  *p = v;
+}
+
+constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
+
+template <class EI, class R, class EO>
+__global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
+                                            const GemmPair* __restrict__ pairs,
+                                            const GemmTile* __restrict__ tiles) {
+  __shared__ R As_r[BK][BM], As_i[BK][BM];
+  __shared__ R Bs_r[BK][BN], Bs_i[BK][BN];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask tk = tasks[tl.task];
+  const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  R acc_r[4][4], acc_i[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc_r[i][j] = acc_i[i][j] = (R)0;
+
+  for (int pi = tk.p0; pi < tk.p0 + tk.np; ++pi) {
+    const GemmPair pr = pairs[pi];
+    const EI* A = (const EI*)pr.A;
+    const EI* B = (const EI*)pr.B;
+    const bool at = (pr.opA == OP_T || pr.opA == OP_H);
+    const bool bt = (pr.opB == OP_T || pr.opB == OP_H);
+    for (int k0 = 0; k0 < pr.K; k0 += BK) {
+      // A tile: BM x BK of op(A)
+#pragma unroll
+      for (int r = 0; r < (BM * BK) / NT; ++r) {
+        const int l = tid + r * NT;
+        int i, k;
+        if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
+        R re = 0, im = 0;
+        if (m0 + i < tk.M && k0 + k < pr.K) load_op<EI, R>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
+        As_r[k][i] = re;
+        As_i[k][i] = im;
+      }
+      // B tile: BK x BN of op(B)
+#pragma unroll
+      for (int r = 0; r < (BK * BN) / NT; ++r) {
+        const int l = tid + r * NT;
+        int k, j;
+        if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
+        R re = 0, im = 0;
+        if (n0 + j < tk.N && k0 + k < pr.K) load_op<EI, R>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
+        Bs_r[k][j] = re;
+        Bs_i[k][j] = im;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        R ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc_r[i][j] = fma(ar[i], br[j], fma(-ai[i], bi[j], acc_r[i][j]));
+            acc_i[i][j] = fma(ar[i], bi[j], fma(ai[i], br[j], acc_i[i][j]));
+          }
+      }
+      __syncthreads();
+    }
+  }
+  EO* C = (EO*)tk.C;
+  const R al = (R)tk.alpha, be = (R)tk.beta;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= tk.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= tk.N) continue;
+      EO* p = C + (size_t)m + (size_t)n * tk.ldc;
+      R re = al * acc_r[i][j], im = al * acc_i[i][j];
+      if (tk.beta != 0.0) {
+        const EO c = *p;
+        re = fma(be, (R)c.re, re);
+        im = fma(be, (R)c.im, im);
+      }
+      store_val<EO, R>(p, re, im);
+    }
+  }
+}
+
+}  // namespace
+
+int gemm_tile_m(int) { return BM; }
+int gemm_tile_n(int) { return BN; }
+
+cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
+                 int pin, int pout, int pacc, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (pin == P64 && pacc == P64 && pout == P64)
+    k_gemm<cd, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+  else if (pin == P32 && pacc == P32 && pout == P32)
+    k_gemm<cf, float, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+  else if (pin == P32 && pacc == P64 && pout == P64)
+    k_gemm<cf, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+  else if (pin == P64 && pacc == P64 && pout == P32)
+    k_gemm<cd, double, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace h2k

@@ -1,0 +1,192 @@
+// Host-side data structures of libh2: cluster tree, block partition, the H^2
+// representation (FP64, tree order) and the per-context device state.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/h2.h"
+#include "h2_kernels.h"
+
+namespace h2 {
+
+using cplx = std::complex<double>;
+using Pair = std::pair<int, int>;
+
+inline int64_t pkey(int a, int b) { return ((int64_t)a << 32) | (uint32_t)b; }
+
+// Complete binary cluster tree (Sec. II): level l has 2^l clusters; cluster c
+// covers tree positions [start, start+size); children are 2c, 2c+1.
+struct Tree {
+  int64_t N = 0;
+  int L = 0;
+  std::vector<int64_t> perm;                 // tree position -> global index
+  std::vector<std::vector<int64_t>> start, size;
+  std::vector<std::vector<double>> centre;   // 3 per cluster
+  std::vector<std::vector<double>> radius;
+};
+
+// Admissible / inadmissible same-level pairs (eq. 1), sorted per level.
+struct Partition {
+  std::vector<std::vector<Pair>> adm, inad;
+  int l0 = 0;
+};
+
+void build_tree(const double* pts, int64_t N, int leafsize, Tree& t);
+void build_partition(const Tree& t, double eta, Partition& p);
+std::vector<std::vector<int>> near_lists(const Partition& p, int l);
+std::vector<int> greedy_colours(const std::vector<std::vector<int>>& nbrs);
+
+// H^2 representation in FP64, tree order, levels l0..L.
+struct H2Host {
+  Tree tree;
+  Partition part;
+  int L = 0, l0 = 0;
+  std::vector<std::vector<int>> rank;                // [l][c]
+  std::vector<std::vector<cplx>> V;                  // leaf bases, size x k
+  std::vector<std::vector<std::vector<cplx>>> T;     // [l][c] (k1+k2) x k
+  std::vector<std::vector<std::vector<cplx>>> S;     // [l][adm idx] kt x ks
+  std::vector<std::vector<cplx>> D;                  // [inad[L] idx]
+  std::vector<double> dscale;                        // global order (size N)
+};
+
+// Host H^2 construction (proxy + interpolative decomposition), h2_build.
+std::string build_h2(const double* pts, int64_t N, double k, double h, const double* chi, int64_t chi_len,
+                     double eps, const h2_opts& o, H2Host& H);
+
+// ------------------------------------------------------------------------
+// Device memory: grow-only buffers owned by the context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release();
+};
+
+struct Ctx;
+
+// Error carried out of the host planners as an exception inside the library
+// (converted to an h2_status at the ABI boundary).
+struct Err {
+  h2_status st;
+  std::string msg;
+};
+[[noreturn]] void fail(h2_status st, const std::string& msg);
+void ck(cudaError_t e, const char* what);
+
+// Grow-only device buffer allocation with arena accounting.
+void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes);
+
+// Task staging: host task arrays are appended into one growing byte buffer,
+// copied into pinned memory and uploaded with cudaMemcpyAsync just before the
+// launch that reads them.  Uploaded ranges are never overwritten until
+// begin(), which the caller issues only while the stream is idle.
+struct Stager {
+  std::vector<unsigned char> host;
+  size_t uploaded = 0;
+  void* pinned = nullptr;
+  size_t cap = 0;
+  DevBuf dev;
+  std::vector<size_t> offs;
+  ~Stager();
+  void begin() { host.clear(); offs.clear(); uploaded = 0; }
+  template <class T>
+  int add(const std::vector<T>& v) {
+    size_t o = (host.size() + 255) & ~(size_t)255;
+    host.resize(o + v.size() * sizeof(T) + 1);
+    if (!v.empty()) std::memcpy(host.data() + o, v.data(), v.size() * sizeof(T));
+    offs.push_back(o);
+    return (int)offs.size() - 1;
+  }
+  void upload(Ctx& c);
+  template <class T>
+  const T* ptr(int i) const { return (const T*)((const unsigned char*)dev.p + offs[i]); }
+};
+
+// Factor data of one level.
+struct LevelF {
+  int l = 0, nc = 0;
+  std::vector<int> n, k0, kt, m;
+  std::vector<std::vector<int>> nbrs;          // near lists incl. self
+  std::vector<std::vector<int>> batches;       // elimination batches
+  std::vector<int> batch_of;
+  std::vector<Pair> near_pairs;                // == part.inad[l]
+  std::unordered_map<int64_t, int> near_id;
+  std::vector<size_t> near_off;                // element offsets
+  std::vector<Pair> fill_pairs;
+  std::unordered_map<int64_t, int> fill_id;
+  std::vector<size_t> fill_off;
+  std::vector<char> fill_live;
+  std::vector<char> fill_is_adm;
+  std::vector<size_t> B_off, Q_off, inv_off, piv_off;
+  std::vector<double> snorm2;
+  DevBuf near_buf, fill_buf, B_buf, Q_buf, inv_buf, piv_buf, Ub_buf;
+  std::vector<size_t> Ub_off;                  // per (cluster, nbr) for eq. 35
+  std::vector<int> nbr_first;                  // first (cluster, nbr) index
+  // solve-time vector layout
+  std::vector<int64_t> voff;                   // cluster offsets in level vector
+  int64_t vlen = 0;
+};
+
+// Blocked LU of the final block (Algorithm 1, last line).
+struct RootF {
+  int n = 0, nb = 32;
+  DevBuf R, piv, Linv, Uinv, Rinv;  // R packed LU; per-panel inverses
+  std::vector<int> kt;               // kept sizes of the level-l0 clusters
+};
+
+struct Stats {
+  double t_factor_ms = 0, t_solve_ms = 0, t_build_ms = 0;
+  double flops_factor = 0;
+  int64_t launches_factor = 0, launches_solve = 0;
+  int refine_iters = 0;
+  double refine_resid = 0;
+  std::vector<std::string> level_json;
+};
+
+struct Ctx {
+  H2Host H;
+  cudaStream_t stream = nullptr;
+  h2_opts opts;
+  std::string err;
+  size_t dev_bytes = 0, dev_peak = 0;
+  // device copy of the H^2 (FP64)
+  DevBuf dV, dT, dS, dD, dperm, dscale;
+  std::vector<size_t> V_off;                        // per leaf
+  std::vector<std::vector<size_t>> T_off, S_off;    // [l][c] / [l][adm idx]
+  std::vector<size_t> D_off;                        // per inad[L] pair
+  std::vector<std::unordered_map<int64_t, int>> adm_id;  // [l] pair -> idx
+  // factorization
+  bool factored = false, inverted = false;
+  int prec = 0;
+  double eps_fill = 0;
+  std::vector<LevelF> lev;  // lev[0] = leaf level L, ..., last = l0
+  RootF root;
+  // scratch
+  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf;
+  Stager st;
+  Stats stats;
+  int64_t launches = 0;
+};
+
+void upload_h2(Ctx& c);
+void factorize(Ctx& c, double eps, int prec);
+void invert(Ctx& c);
+// x (tree order, bulk precision vector of length N*nrhs) <- Z^{-1} x in place
+void solve_tree(Ctx& c, void* x, int nrhs, bool adjoint, bool use_inverse);
+// y = Z_H2 x, FP64, tree order
+void matvec_tree(Ctx& c, const h2k::cd* x, h2k::cd* y, int nrhs, bool adjoint);
+
+}  // namespace h2

@@ -1,0 +1,159 @@
+// Device-side building blocks of libh2 and the task descriptors the host
+// planner fills for them.  Every batched kernel takes a flat array of tasks
+// (and, where output is tiled, a flat array of tiles), so one launch covers
+// all clusters of a colour class / level.  Sizes are exact (the host reads the
+// ranks back after each colour's basis update), so no kernel sees a dynamic
+// shape.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace h2k {
+
+// Interleaved complex numbers, the storage of every complex arena.
+struct __align__(16) cd { double re, im; };
+struct __align__(8) cf { float re, im; };
+
+enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 /* conj */, OP_H = 3 /* conj-transpose */ };
+enum Prec : int { P64 = 0, P32 = 1 };
+
+// ---- batched sum-GEMM:  C = alpha * sum_p op(A_p) op(B_p) + beta * C -----
+struct GemmPair {
+  const void* A;
+  const void* B;
+  int lda, ldb, K, opA, opB;
+};
+struct GemmTask {
+  void* C;
+  int ldc, M, N;
+  int p0, np;       // pairs [p0, p0+np)
+  double alpha, beta;
+};
+struct GemmTile { int task, tm, tn; };
+
+// ---- in-place apply of a small square matrix to a panel -------------------
+//  left : X[r_lo:p, 0:w] = op(A)[r_lo:p, 0:p] * X[0:p, 0:w]
+//  right: X[0:h, c_lo:p] = X[0:h, 0:p] * op(A)[0:p, c_lo:p]
+struct ApplyTask {
+  const void* A;
+  void* X;
+  int lda, ldx;
+  int p;       // order of A
+  int w;       // left: columns of X; right: rows of X
+  int lo;      // first output row (left) / column (right)
+  int opA;
+};
+struct ApplyTile { int task, t0; };  // t0: first column (left) / row (right)
+
+// ---- batched 2-D copy / accumulate ---------------------------------------
+//  dst[0:rows, 0:cols] (=|+=) alpha * op(src) ; src NULL -> zero fill
+struct CopyTask {
+  const void* src;
+  void* dst;
+  int lds, ldd, rows, cols;
+  int srows, scols;        // source extent; entries outside it read as zero
+  int src_prec, dst_prec;  // Prec of each side (complex64 or complex128)
+  int mode;                // 0 assign, 1 accumulate
+  int transpose;           // 1: dst = src^T (src is cols x rows)
+  double alpha;
+};
+
+// ---- Householder complement of an orthonormal basis ----------------------
+//  B (n x k, FP64) -> Vp (n x (n-k)), orthonormal, orthogonal to B.
+struct HhTask {
+  const cd* B;
+  cd* W;      // n x k scratch
+  cd* Vp;     // n x (n-k) output (ld n)
+  int n, k;
+};
+
+// ---- Hermitian Jacobi eigen-decomposition (FP64) -------------------------
+//  A (p x p, ld p) is destroyed; U (p x p) gets eigenvectors sorted by
+//  decreasing eigenvalue, lam the eigenvalues (decreasing).
+struct EigTask {
+  cd* A;
+  cd* U;
+  double* lam;
+  int p;
+};
+
+// ---- partial-pivoting LU of one m x m block + explicit triangular inverses
+struct LuTask {
+  void* A;        // m x m in place (ld lda)
+  void* Linv;     // m x m out: L^{-1} P (ld m)
+  void* Uinv;     // m x m out: U^{-1}   (ld m)
+  int* piv;       // m out: piv[r] = original row now at r
+  int lda, m;
+};
+
+// ---- Step 0 rank selection: r = #{lambda_j > eps^2 (snorm2 + trace(M))} ---
+struct SelTask {
+  const cd* M;        // n x n Gram (trace), may be NULL (trace 0)
+  const double* lam;  // p eigenvalues, decreasing
+  int* out;           // r
+  int n, p;
+  double snorm2, eps2;
+};
+
+// ---- blocked LU of the final block: one tall panel with partial pivoting --
+//  A[row0:row0+nrows, col0:col0+kb] factorized in place, ipiv[j] = absolute
+//  row swapped with row0+j, Linv = (unit lower L11)^{-1}, Uinv = U11^{-1}.
+struct PanelTask {
+  void* A;
+  void* Linv;
+  void* Uinv;
+  int* ipiv;
+  int lda, row0, col0, nrows, kb;
+};
+
+// ---- launches (all on `s`, return cudaGetLastError()) ---------------------
+// Element precision of A, B (inputs) and C (output), and the precision the
+// products are accumulated in.
+cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
+                 const GemmTile* d_tiles, int ntiles, int pin, int pout,
+                 int pacc, cudaStream_t s);
+int gemm_tile_m(int pacc);
+int gemm_tile_n(int pacc);
+
+cudaError_t apply_left(const ApplyTask* d_tasks, const ApplyTile* d_tiles,
+                       int ntiles, int prec, int maxp, int tw, cudaStream_t s);
+cudaError_t apply_right(const ApplyTask* d_tasks, const ApplyTile* d_tiles,
+                        int ntiles, int prec, int maxp, int th, cudaStream_t s);
+int apply_tile_width(int prec, int maxp);
+
+cudaError_t copy2d(const CopyTask* d_tasks, int ntasks, cudaStream_t s);
+
+cudaError_t householder_complement(const HhTask* d_tasks, int ntasks,
+                                   cudaStream_t s);
+cudaError_t jacobi_eig(const EigTask* d_tasks, int ntasks, int maxp,
+                       int* d_status, cudaStream_t s);
+cudaError_t lu_small(const LuTask* d_tasks, int ntasks, int prec,
+                     int* d_status, cudaStream_t s);
+cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
+cudaError_t lu_panel(const PanelTask* d_task, int prec, int* d_status,
+                     cudaStream_t s);
+// apply the row interchanges ipiv[0:kb] (rows row0+j <-> ipiv[j]) to the
+// columns [c0, c1) of A (ld lda), in order (forward) or reversed
+cudaError_t swap_rows(void* A, int lda, const int* ipiv, int row0, int kb,
+                      int c0, int c1, int prec, int reverse, cudaStream_t s);
+
+// A[i, i] = v for i < n (other entries untouched)
+cudaError_t set_diag(void* A, int lda, int n, int prec, double v, cudaStream_t s);
+
+// Vector helpers: y[perm-gathered] etc.
+//  gather : out[p + col*N] = scale(in[perm[p] + col*ldi]) * in[...]
+cudaError_t permute_scale(const void* in, void* out, const int64_t* d_perm,
+                          const double* d_scale, int64_t N, int nrhs,
+                          int in_prec, int out_prec, int inverse, int conj,
+                          cudaStream_t s);
+// column-wise squared norms (FP64) of an N x nrhs complex128 matrix
+cudaError_t col_norms2(const cd* x, int64_t N, int nrhs, double* d_out,
+                       cudaStream_t s);
+// y = a - b   (complex128, N x nrhs contiguous)
+cudaError_t axpby(const cd* a, const cd* b, cd* y, int64_t n, double alpha,
+                  double beta, cudaStream_t s);
+// convert complex128 <-> complex64 (contiguous)
+cudaError_t convert(const void* in, int in_prec, void* out, int out_prec,
+                    int64_t n, cudaStream_t s);
+
+}  // namespace h2k

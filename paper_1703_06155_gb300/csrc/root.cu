@@ -1,0 +1,203 @@
+// Rank selection of Step 0 and the panel kernels of the blocked LU of the
+// final block (Algorithm 1, last line).
+#include "h2_kernels.h"
+
+namespace h2k {
+namespace {
+
+constexpr int NT = 256;
+
+template <class E> struct RealOf;
+template <> struct RealOf<cd> { using T = double; };
+template <> struct RealOf<cf> { using T = float; };
+
+// Keep lambda_j > eps^2 nu^2 with nu^2 = snorm2 + trace(M): snorm2 is the sum
+// of ||S||_F^2 over the admissible blocks of the cluster's row and column,
+// trace(M) the squared Frobenius norm of its fill-ins (eqs. 17 / 26).
+__global__ void __launch_bounds__(NT) k_select(const SelTask* __restrict__ tasks) {
+  __shared__ double red[NT];
+  __shared__ int cnt[NT];
+  const SelTask t = tasks[blockIdx.x];
+  double tr = 0;
+  if (t.M)
+    for (int i = threadIdx.x; i < t.n; i += NT) tr += t.M[i + (size_t)i * t.n].re;
+  red[threadIdx.x] = tr;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double thr = t.eps2 * (t.snorm2 + red[0]);
+  int c = 0;
+  for (int j = threadIdx.x; j < t.p; j += NT) c += t.lam[j] > thr;
+  cnt[threadIdx.x] = c;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) cnt[threadIdx.x] += cnt[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *t.out = cnt[0];
+}
+
+template <class E>
+__global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ task, int* status) {
+  using R = typename RealOf<E>::T;
+  __shared__ R redv[NT];
+  __shared__ int redi[NT];
+  const PanelTask t = *task;
+  E* A = (E*)t.A;
+  const int ld = t.lda, kb = t.kb;
+  auto at = [&](int r, int c) -> E& { return A[(size_t)(t.row0 + r) + (size_t)(t.col0 + c) * ld]; };
+  for (int j = 0; j < kb; ++j) {
+    R best = -1;
+    int bi = t.nrows;
+    for (int i = j + threadIdx.x; i < t.nrows; i += NT) {
+      const E v = at(i, j);
+      const R a = (R)v.re * (R)v.re + (R)v.im * (R)v.im;
+      if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+    }
+    redv[threadIdx.x] = best;
+    redi[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        const R o = redv[threadIdx.x + s];
+        const int oi = redi[threadIdx.x + s];
+        if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
+          redv[threadIdx.x] = o;
+          redi[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const int pr = redi[0];
+    const R pv = redv[0];
+    __syncthreads();
+    if (!(pv > (R)0)) {
+      if (threadIdx.x == 0 && status) atomicMax(status, 1);
+      return;
+    }
+    if (threadIdx.x == 0) t.ipiv[j] = t.row0 + pr;
+    if (pr != j)
+      for (int c = threadIdx.x; c < kb; c += NT) {
+        const E a = at(j, c);
+        at(j, c) = at(pr, c);
+        at(pr, c) = a;
+      }
+    __syncthreads();
+    const E d = at(j, j);
+    const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
+    const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
+    for (int i = j + 1 + threadIdx.x; i < t.nrows; i += NT) {
+      E v = at(i, j);
+      const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
+      v.re = vr;
+      v.im = vi;
+      at(i, j) = v;
+    }
+    __syncthreads();
+    const int rem_r = t.nrows - j - 1, rem_c = kb - j - 1;
+    for (int idx = threadIdx.x; idx < rem_r * rem_c; idx += NT) {
+      const int i = j + 1 + idx % rem_r, c = j + 1 + idx / rem_r;
+      const E l = at(i, j), u = at(j, c);
+      E v = at(i, c);
+      v.re = (R)v.re - ((R)l.re * (R)u.re - (R)l.im * (R)u.im);
+      v.im = (R)v.im - ((R)l.re * (R)u.im + (R)l.im * (R)u.re);
+      at(i, c) = v;
+    }
+    __syncthreads();
+  }
+  // (unit lower L11)^{-1}
+  E* X = (E*)t.Linv;
+  for (int idx = threadIdx.x; idx < kb * kb; idx += NT) {
+    E v;
+    v.re = (idx % kb == idx / kb) ? 1 : 0;
+    v.im = 0;
+    X[idx] = v;
+  }
+  __syncthreads();
+  for (int tt = 0; tt < kb - 1; ++tt) {
+    const int rem = kb - tt - 1;
+    for (int idx = threadIdx.x; idx < rem * kb; idx += NT) {
+      const int i = tt + 1 + idx % rem, c = idx / rem;
+      const E l = at(i, tt), x = X[tt + (size_t)c * kb];
+      E v = X[i + (size_t)c * kb];
+      v.re = (R)v.re - ((R)l.re * (R)x.re - (R)l.im * (R)x.im);
+      v.im = (R)v.im - ((R)l.re * (R)x.im + (R)l.im * (R)x.re);
+      X[i + (size_t)c * kb] = v;
+    }
+    __syncthreads();
+  }
+  // U11^{-1}
+  E* Y = (E*)t.Uinv;
+  for (int idx = threadIdx.x; idx < kb * kb; idx += NT) {
+    E v;
+    v.re = (idx % kb == idx / kb) ? 1 : 0;
+    v.im = 0;
+    Y[idx] = v;
+  }
+  __syncthreads();
+  for (int tt = kb - 1; tt >= 0; --tt) {
+    const E d = at(tt, tt);
+    const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
+    const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
+    for (int c = threadIdx.x; c < kb; c += NT) {
+      E v = Y[tt + (size_t)c * kb];
+      const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
+      v.re = vr;
+      v.im = vi;
+      Y[tt + (size_t)c * kb] = v;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < tt * kb; idx += NT) {
+      const int i = idx % tt, c = idx / tt;
+      const E u = at(i, tt), y = Y[tt + (size_t)c * kb];
+      E v = Y[i + (size_t)c * kb];
+      v.re = (R)v.re - ((R)u.re * (R)y.re - (R)u.im * (R)y.im);
+      v.im = (R)v.im - ((R)u.re * (R)y.im + (R)u.im * (R)y.re);
+      Y[i + (size_t)c * kb] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <class E>
+__global__ void k_swap_rows(E* A, int lda, const int* ipiv, int row0, int kb, int c0, int c1, int reverse) {
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x) {
+    for (int q = 0; q < kb; ++q) {
+      const int j = reverse ? kb - 1 - q : q;
+      const int r1 = row0 + j, r2 = ipiv[j];
+      if (r1 != r2) {
+        const E a = A[(size_t)r1 + (size_t)c * lda];
+        A[(size_t)r1 + (size_t)c * lda] = A[(size_t)r2 + (size_t)c * lda];
+        A[(size_t)r2 + (size_t)c * lda] = a;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t select_rank(const SelTask* d, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_select<<<n, NT, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t lu_panel(const PanelTask* d, int prec, int* st, cudaStream_t s) {
+  if (prec == P64) k_lu_panel<cd><<<1, NT, 0, s>>>(d, st);
+  else k_lu_panel<cf><<<1, NT, 0, s>>>(d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t swap_rows(void* A, int lda, const int* ipiv, int row0, int kb, int c0, int c1, int prec, int reverse,
+                      cudaStream_t s) {
+  if (c1 <= c0) return cudaSuccess;
+  const int n = c1 - c0;
+  const int g = (n + 127) / 128;
+  if (prec == P64) k_swap_rows<cd><<<g, 128, 0, s>>>((cd*)A, lda, ipiv, row0, kb, c0, c1, reverse);
+  else k_swap_rows<cf><<<g, 128, 0, s>>>((cf*)A, lda, ipiv, row0, kb, c0, c1, reverse);
+  return cudaGetLastError();
+}
+
+}  // namespace h2k

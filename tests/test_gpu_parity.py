@@ -1,0 +1,161 @@
+"""GPU path vs the CPU oracle on the same seeded H^2 matrices (C ABI via the
+ctypes binding).  The oracle's H^2 representation is handed to h2_load, so
+both sides factorize exactly the same matrix.
+
+Tolerances (floating point, complex128 unless stated):
+  * matvec: 1e-13 relative (same arithmetic, different summation order);
+  * eps_fill = 0: the factorization is an exact block LU of Z_H2, so the
+    solution matches a dense solve to 1e-10;
+  * eps_fill = eps: GPU and oracle keep fill-in directions by the same rule,
+    but at a threshold tie a direction can be kept by one side only (ranks
+    +-1), which perturbs the solution by O(eps).  Bound: 10 eps relative to
+    the oracle's solution, as long as the oracle's own residual is <= eps.
+"""
+import numpy as np
+import pytest
+
+from oracle import factor
+from oracle import h2 as oh2
+from paper_1703_06155_gb300 import inputs
+
+from _h2io import from_tree, oracle_to_rep, to_tree
+from _problems import factorization, h2_dense, h2_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1703_06155_gb300 import lib
+    lib()
+    return torch.device("cuda:0")
+
+
+def gpu_ctx(H, **kw):
+    from paper_1703_06155_gb300 import H2
+    return H2.load(oracle_to_rep(H), **kw)
+
+
+def oracle_solve(Fz, b_global, adjoint=False):
+    H = Fz.H
+    if adjoint:
+        return from_tree(H, factor.solve_adjoint(Fz, to_tree(H, b_global)))
+    return from_tree(H, factor.solve(Fz, to_tree(H, b_global)))
+
+
+@pytest.mark.parametrize("n", [12, 16])
+def test_matvec_parity(dev, n):
+    H = h2_problem(n, 64, 1e-6)
+    A = gpu_ctx(H)
+    x = inputs.rhs_gaussian(H.tree.N, 3, 5)
+    y_ref = from_tree(H, oh2.matvec(H, to_tree(H, x)))
+    y = A.matvec(torch.from_numpy(x).to(dev)).cpu().numpy()
+    assert rel(y, y_ref) < 1e-13
+    yh = A.matvec(x)  # host buffers
+    assert rel(yh, y_ref) < 1e-13
+    # adjoint product against the dense conjugate transpose
+    Zd = h2_dense(n, 64, 1e-6)
+    ya = A.matvec(x, adjoint=True)
+    ya_ref = from_tree(H, Zd.conj().T @ to_tree(H, x))
+    assert rel(ya, ya_ref) < 1e-13
+
+
+@pytest.mark.parametrize("ordering", ["colored", "natural"])
+def test_exact_block_lu(dev, ordering):
+    H = h2_problem(12, 64, 1e-6)
+    A = gpu_ctx(H, ordering=ordering)
+    A.factorize(0.0, "fp64")
+    Zd = h2_dense(12, 64, 1e-6)
+    b = inputs.rhs_gaussian(H.tree.N, 2, 11)
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b)))
+    x = A.solve(torch.from_numpy(b).to(dev)).cpu().numpy()
+    assert rel(x, xe) < 1e-10
+    xa = A.solve(b, adjoint=True)
+    xae = from_tree(H, np.linalg.solve(Zd.conj().T, to_tree(H, b)))
+    assert rel(xa, xae) < 1e-10
+
+
+@pytest.mark.parametrize("n,eps", [(12, 1e-6), (16, 1e-6), (12, 1e-4)])
+def test_fp64_parity(dev, n, eps):
+    H = h2_problem(n, 64, eps)
+    Fz = factorization(n, 64, eps, eps, "colored")
+    A = gpu_ctx(H)
+    A.factorize(eps, "fp64")
+    b = inputs.rhs_gaussian(H.tree.N, 1, 0)[:, 0]
+    x_orc = oracle_solve(Fz, b)
+    Zd = h2_dense(n, 64, eps)
+    res_orc = np.linalg.norm(Zd @ to_tree(H, x_orc) - to_tree(H, b)) / np.linalg.norm(b)
+    x = A.solve(b)
+    res_gpu = np.linalg.norm(Zd @ to_tree(H, x) - to_tree(H, b)) / np.linalg.norm(b)
+    assert res_orc <= eps and res_gpu <= 10 * eps, (res_orc, res_gpu)
+    assert rel(x, x_orc) <= 10 * eps, rel(x, x_orc)
+    # ranks: per level, the largest kept rank agrees within a few directions
+    st = A.stats()
+    for lev, olev in zip(st["levels"], Fz.levels):
+        assert abs(lev["kt_max"] - int(olev.kt.max())) <= 2, (lev, olev.kt.max())
+    # after refinement both solutions agree with the exact H^2 solution
+    xr = A.solve(b, refine=True, tol=1e-13, max_iter=10)
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b)))
+    assert rel(xr, xe) < 1e-11
+
+
+def test_inverse_and_adjoint(dev):
+    eps = 1e-6
+    H = h2_problem(12, 64, eps)
+    Fz = factorization(12, 64, eps, eps, "colored")
+    A = gpu_ctx(H)
+    A.factorize(eps, "fp64")
+    b = inputs.rhs_gaussian(H.tree.N, 4, 9)
+    bt = torch.from_numpy(b).to(dev)
+    x = A.solve(bt).cpu().numpy()
+    A.invert()
+    xi = A.solve(bt, use_inverse=True).cpu().numpy()
+    assert rel(xi, x) < 1e-12
+    xa = A.solve(bt, adjoint=True).cpu().numpy()
+    xa_orc = oracle_solve(Fz, b, adjoint=True)
+    assert rel(xa, xa_orc) <= 10 * eps
+    # <A^H y, x> = <y, A x> with the GPU adjoint solve and matvec
+    y = inputs.rhs_gaussian(H.tree.N, 1, 3)[:, 0]
+    u = A.solve(y, adjoint=True)
+    v = b[:, 0]
+    lhs = np.vdot(u, A.matvec(A.solve(v)))
+    rhs = np.vdot(A.matvec(u, adjoint=True), A.solve(v))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-10
+
+
+def test_mixed_precision_refinement(dev):
+    eps = 1e-6
+    H = h2_problem(12, 64, eps)
+    A = gpu_ctx(H)
+    A.factorize(eps, "mixed")
+    b = inputs.rhs_gaussian(H.tree.N, 2, 1)
+    Zd = h2_dense(12, 64, eps)
+    x = A.solve(b, refine=True, tol=1e-10, max_iter=30)
+    assert A.last_solve["resid"] <= 1e-10
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b)))
+    assert rel(x, xe) < 1e-8
+
+
+def test_singular_pivot_reports_status(dev):
+    # a leaf diagonal block that is exactly zero where the partial LU pivots
+    from paper_1703_06155_gb300 import H2Error
+    H = h2_problem(12, 64, 1e-6)
+    rep = oracle_to_rep(H)
+    n0 = int(rep["leaf_size"][0])
+    rep["D"] = rep["D"].copy()
+    rep["D"][: n0 * n0] = 0  # first near block is (0, 0)
+    A = gpu_ctx_rep(rep)
+    with pytest.raises(H2Error) as ei:
+        A.factorize(1e-6, "fp64")
+    assert ei.value.status == -3
+
+
+def gpu_ctx_rep(rep):
+    from paper_1703_06155_gb300 import H2
+    return H2.load(rep)
