@@ -1,0 +1,279 @@
+"""Benchmark of the accuracy-controlled H^2 direct solver on one GB300.
+
+Workload (default): 32^3 = 32,768-point regular grid, cube side 2 wavelengths
+(k = 2 pi, h = 1/16), uniform contrast chi = 3 (eps_r = 4), leaf 64,
+admissibility 1.0, eps_build = eps_fill = 1e-6, 16 complex Gaussian RHS
+(seed 1).  A "step" is one pass of the hot path on resident inputs:
+h2_factorize (mixed precision: complex64 bulk, FP64 rank decisions) followed
+by h2_solve of the 16 RHS with FP64-matvec iterative refinement to a relative
+residual of 1e-6.  value = N / (step time) unknowns/s; the FP64 factorization
+is timed beside it.  The H^2 construction (h2_build) is not timed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (plain FP64 numpy) on a bounded sample
+of the same workload: the 16^3 sub-grid with the same h, chi and eps.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K = 2.0 * math.pi
+H = 1.0 / 16.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, default=32)
+    p.add_argument("--eps", type=float, default=1e-6)
+    p.add_argument("--chi", type=float, default=3.0)
+    p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--json-extra", action="store_true", help="print per-level stats")
+    p.add_argument("--profile-step", action="store_true",
+                   help="build, then exactly one factorize + refined solve (for profiler captures)")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=" + q, "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                f = [x.strip() for x in out.split(",")]
+                if len(f) >= 7:
+                    self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# --------------------------------------------------------------- oracle ---
+
+def oracle_sample(args, repeat=1):
+    """Oracle (CPU, FP64) build + factorize + solve on the 16^3 sub-grid."""
+    from oracle import factor, h2
+    from paper_1703_06155_gb300 import inputs
+    n = min(args.grid, 16)
+    pts = inputs.grid_points(n, H)
+    N = len(pts)
+    chi = inputs.chi_uniform(N, args.chi)
+    Hm = h2.build(pts, chi, K, H, leafsize=64, eps=args.eps)
+    b = inputs.rhs_gaussian(N, args.nrhs, args.seed)
+    bt = b[Hm.tree.perm]
+    times = []
+    for _ in range(repeat):
+        t0 = time.perf_counter()
+        Fz = factor.factorize(Hm, args.eps, "colored", bulk=np.complex64 if args.prec == "mixed" else np.complex128)
+        x, hist = factor.refine(Fz, bt, tol=args.tol, max_iter=20)
+        times.append(time.perf_counter() - t0)
+    return N, times, hist[-1]
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N, times, res = oracle_sample(args, repeat=args.warmup + args.steps)
+    t = times[args.warmup:] if len(times) > args.warmup else times
+    step = float(np.mean(t))
+    v = N / step
+    line = {
+        "impl": "reference", "metric": "H2 factorize+solve unknowns/s (rel. residual 1e-6)", "value": v,
+        "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if args.prec == "fp64" else "c64+c128", "data": "synthetic",
+        "config": {"workload": "grid%d_chi%g_eps%g_nrhs%d (oracle sample: 16^3 sub-grid, N=%d)" % (
+            args.grid, args.chi, args.eps, args.nrhs, N)},
+        "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "oracle factorize + refined solve of the 16^3 sub-grid (N=%d)" % N},
+        "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "final_residual": res,
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU ---
+
+def run_ours(args):
+    import torch
+    from paper_1703_06155_gb300 import H2, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    pts = inputs.grid_points(args.grid, H)
+    N = len(pts)
+    t0 = time.perf_counter()
+    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream)
+    t_build = time.perf_counter() - t0
+    b_host = inputs.rhs_gaussian(N, args.nrhs, args.seed + rank)  # independent instance per rank
+    b = torch.from_numpy(b_host).to("cuda")
+    if args.profile_step:
+        A.factorize(args.eps, args.prec)
+        A.solve(b, refine=True, tol=args.tol, max_iter=30)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "stats": A.stats()}))
+        return
+
+    def step(prec):
+        A.factorize(args.eps, prec)
+        x = A.solve(b, refine=True, tol=args.tol, max_iter=30)
+        return x
+
+    for _ in range(args.warmup):
+        step(args.prec)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler() as cs:
+        ev0.record(stream)
+        fac_ms = []
+        for _ in range(args.steps):
+            f0 = time.perf_counter()
+            A.factorize(args.eps, args.prec)
+            fac_ms.append((time.perf_counter() - f0) * 1e3)
+            x = A.solve(b, refine=True, tol=args.tol, max_iter=30)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = A.stats()
+    solve_info = dict(A.last_solve)
+    # residual of the result against the H^2 matrix (FP64 matvec)
+    r = A.matvec(x) - b
+    res = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+    # FP64 comparison run (not part of the metric)
+    f0 = time.perf_counter()
+    A.factorize(args.eps, "fp64")
+    fp64_fac_ms = (time.perf_counter() - f0) * 1e3
+    s0 = time.perf_counter()
+    A.solve(b, refine=True, tol=args.tol, max_iter=30)
+    fp64_solve_ms = (time.perf_counter() - s0) * 1e3
+    fp64_iters = A.last_solve["iters"]
+    # e2e: same step through the public API with HOST buffers
+    A.factorize(args.eps, args.prec)
+    e0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        A.factorize(args.eps, args.prec)
+        xh = A.solve(b_host, refine=True, tol=args.tol, max_iter=30)
+    e_ms = (time.perf_counter() - e0) * 1e3 / max(1, args.steps // 2)
+    value = world * N / (ms / 1e3)
+    line = {
+        "metric": "H2 factorize+solve unknowns/s (rel. residual 1e-6)", "value": value, "unit": "unknowns/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 bulk + c128 rank/refine" if args.prec == "mixed" else "c128",
+        "data": "synthetic",
+        "config": {"workload": "grid%d (N=%d), chi=%g, eps=%g, nrhs=%d, leaf 64, eta 1" % (
+            args.grid, N, args.chi, args.eps, args.nrhs), "precision": args.prec,
+            "l2": "inputs larger than L2 (near-field arena %.0f MB)" % (st.get("dev_bytes", 0) / 1e6)},
+        "factorize_ms": float(np.mean(fac_ms)), "solve_iters": solve_info.get("iters"),
+        "final_residual": res, "fp64": {"factorize_ms": fp64_fac_ms, "solve_ms": fp64_solve_ms,
+                                       "solve_iters": fp64_iters,
+                                       "factorize_unknowns_per_s": N / (fp64_fac_ms / 1e3)},
+        "factorize_unknowns_per_s": N / (float(np.mean(fac_ms)) / 1e3),
+        "build_s": t_build, "gpu_launches": int(st["launches_factor"] + st["launches_solve"]),
+        "e2e": {"value": world * N / (e_ms / 1e3), "unit": "unknowns/s",
+                "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
+        "clocks": cs.summary(),
+    }
+    if args.json_extra:
+        line["stats"] = st
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        Nc, times, _ = oracle_sample(args, repeat=1)
+        line["cpu_baseline"] = {"value": Nc / times[0], "unit": "unknowns/s", "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": "oracle factorize + refined solve of the 16^3 sub-grid (N=%d)" % Nc}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

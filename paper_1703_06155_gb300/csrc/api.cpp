@@ -17,6 +17,7 @@ using namespace h2k;
 struct h2_ctx {
   Ctx c;
   DevBuf tA, tB, tC, tR, hb, hx, invscale;
+  DevBuf bpts, bsq, bflat, bG;  // construction scratch
 };
 
 namespace {
@@ -87,6 +88,60 @@ std::vector<double> col_norms(h2_ctx* x, const cd* v, int nrhs) {
   return h;
 }
 
+// Far-field sample Grams of one level on the GPU (kgram.cu).
+void gpu_gram(h2_ctx* x, double k, double w, const std::vector<std::vector<int64_t>>& rows,
+              const std::vector<std::vector<int64_t>>& ranges, std::vector<std::vector<cplx>>& G) {
+  Ctx& c = x->c;
+  const H2Host& H = c.H;
+  const int64_t N = H.tree.N;
+  const int nc = (int)rows.size();
+  std::vector<int64_t> flat;
+  std::vector<size_t> roff(nc), goff(nc);
+  size_t gtot = 0;
+  for (int t = 0; t < nc; ++t) {
+    roff[t] = flat.size();
+    flat.insert(flat.end(), rows[t].begin(), rows[t].end());
+    flat.insert(flat.end(), ranges[t].begin(), ranges[t].end());
+    goff[t] = gtot;
+    gtot += rows[t].size() * rows[t].size();
+  }
+  G.assign(nc, {});
+  if (gtot == 0) return;
+  int64_t* dflat = (int64_t*)dev_ensure(c, x->bflat, flat.size() * sizeof(int64_t));
+  ck(cudaMemcpy(dflat, flat.data(), flat.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "gram rows");
+  cd* dG = (cd*)dev_ensure(c, x->bG, gtot * sizeof(cd));
+  std::vector<KGramTask> tasks;
+  std::vector<KGramTile> tiles;
+  std::vector<int> owner;
+  for (int t = 0; t < nc; ++t) {
+    const int nr = (int)rows[t].size();
+    if (nr == 0) continue;
+    tasks.push_back(KGramTask{dflat + roff[t], dflat + roff[t] + nr, dG + goff[t], nr, (int)ranges[t].size() / 2});
+    owner.push_back(t);
+    const int nt = (nr + 63) / 64;
+    for (int tn = 0; tn < nt; ++tn)
+      for (int tm = 0; tm <= tn; ++tm) tiles.push_back(KGramTile{(int)tasks.size() - 1, tm, tn});
+  }
+  ck(cudaStreamSynchronize(c.stream), "sync");
+  c.st.begin();
+  const int i0 = c.st.add(tasks), i1 = c.st.add(tiles);
+  c.st.upload(c);
+  ck(kernel_gram(c.st.ptr<KGramTask>(i0), c.st.ptr<KGramTile>(i1), (int)tiles.size(), (const double*)x->bpts.p,
+                 (const double*)x->bsq.p, k, w, c.stream),
+     "kernel gram");
+  std::vector<cplx> hG(gtot);
+  ck(cudaMemcpyAsync(hG.data(), dG, gtot * sizeof(cd), cudaMemcpyDeviceToHost, c.stream), "gram D2H");
+  ck(cudaStreamSynchronize(c.stream), "gram sync");
+  for (int t : owner) {
+    const int nr = (int)rows[t].size();
+    std::vector<cplx> g(hG.begin() + goff[t], hG.begin() + goff[t] + (size_t)nr * nr);
+    for (int j = 0; j < nr; ++j)
+      for (int i = j + 1; i < nr; ++i)
+        if (i / 64 > j / 64) g[(size_t)i + (size_t)j * nr] = std::conj(g[(size_t)j + (size_t)i * nr]);
+    G[t] = std::move(g);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -138,9 +193,44 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   }
   const h2_status st = guard(x, [&]() {
     const auto t0 = std::chrono::steady_clock::now();
-    const std::string e = build_h2(pts, N, k, h, chi, chi_len, eps, x->c.opts, x->c.H);
+    Ctx& c = x->c;
+    c.stream = (cudaStream_t)stream;
+    const double w = k * k * h * h * h / (4.0 * M_PI);
+    std::vector<double> pts_tree, sq_tree;
+    auto tree_arrays = [&]() {
+      if (!pts_tree.empty()) return;
+      const int64_t n = c.H.tree.N;
+      pts_tree.resize(3 * n);
+      sq_tree.resize(n);
+      for (int64_t p = 0; p < n; ++p) {
+        const int64_t g = c.H.tree.perm[p];
+        for (int d = 0; d < 3; ++d) pts_tree[3 * p + d] = pts[3 * g + d];
+        sq_tree[p] = c.H.dscale[g];
+      }
+    };
+    GramFn gram = [&](int, const std::vector<std::vector<int64_t>>& rows,
+                      const std::vector<std::vector<int64_t>>& ranges, std::vector<std::vector<cplx>>& G) {
+      tree_arrays();
+      if (c.opts.host_only) {
+        host_gram(pts_tree.data(), sq_tree.data(), k, w, rows, ranges, G);
+        return;
+      }
+      if (!x->bpts.p) {
+        dev_ensure(c, x->bpts, pts_tree.size() * sizeof(double));
+        dev_ensure(c, x->bsq, sq_tree.size() * sizeof(double));
+        ck(cudaMemcpy(x->bpts.p, pts_tree.data(), pts_tree.size() * sizeof(double), cudaMemcpyHostToDevice), "pts");
+        ck(cudaMemcpy(x->bsq.p, sq_tree.data(), sq_tree.size() * sizeof(double), cudaMemcpyHostToDevice), "sq");
+      }
+      gpu_gram(x, k, w, rows, ranges, G);
+    };
+    const std::string e = build_h2(pts, N, k, h, chi, chi_len, eps, x->c.opts, x->c.H, gram);
     if (!e.empty()) fail(H2_EINVAL, e);
+    x->c.H.symmetric = true;  // Z = I + s D^{1/2} K D^{1/2}
     if (!x->c.opts.host_only) finish_setup(x, stream);
+    x->bpts.release();
+    x->bsq.release();
+    x->bflat.release();
+    x->bG.release();
     x->c.stats.t_build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
   if (st != H2_OK) {
@@ -310,6 +400,43 @@ h2_status h2_load(int64_t N, int L, int l0, const int64_t* perm, const int64_t* 
             fail(H2_EINVAL, "pair both admissible and inadmissible");
       for (int l = 0; l < l0; ++l)
         if (!H.part.adm[l].empty()) fail(H2_EINVAL, "admissible pair above l0");
+    }
+    // symmetric iff every admissible and near block equals the transpose of
+    // its mirror block
+    {
+      bool sym = true;
+      for (int l = l0; l <= L && sym; ++l)
+        for (size_t q = 0; q < H.part.adm[l].size() && sym; ++q) {
+          const auto [t, u] = H.part.adm[l][q];
+          const auto it = std::lower_bound(H.part.adm[l].begin(), H.part.adm[l].end(), Pair{u, t});
+          if (it == H.part.adm[l].end() || *it != Pair{u, t}) { sym = false; break; }
+          const auto& A = H.S[l][q];
+          const auto& B = H.S[l][it - H.part.adm[l].begin()];
+          const int kt = H.rank[l][t], ku = H.rank[l][u];
+          double nrm = 0, dif = 0;
+          for (int i = 0; i < kt; ++i)
+            for (int j = 0; j < ku; ++j) {
+              nrm += std::norm(A[(size_t)i + (size_t)j * kt]);
+              dif += std::norm(A[(size_t)i + (size_t)j * kt] - B[(size_t)j + (size_t)i * ku]);
+            }
+          if (dif > 1e-24 * nrm) sym = false;
+        }
+      for (size_t q = 0; q < H.part.inad[L].size() && sym; ++q) {
+        const auto [t, u] = H.part.inad[L][q];
+        const auto it = std::lower_bound(H.part.inad[L].begin(), H.part.inad[L].end(), Pair{u, t});
+        if (it == H.part.inad[L].end() || *it != Pair{u, t}) { sym = false; break; }
+        const auto& A = H.D[q];
+        const auto& B = H.D[it - H.part.inad[L].begin()];
+        const int nt = (int)tr.size[L][t], nu = (int)tr.size[L][u];
+        double nrm = 0, dif = 0;
+        for (int i = 0; i < nt; ++i)
+          for (int j = 0; j < nu; ++j) {
+            nrm += std::norm(A[(size_t)i + (size_t)j * nt]);
+            dif += std::norm(A[(size_t)i + (size_t)j * nt] - B[(size_t)j + (size_t)i * nu]);
+          }
+        if (dif > 1e-24 * nrm) sym = false;
+      }
+      H.symmetric = sym;
     }
     H.dscale.assign(N, 1.0);
     if (dscale)
@@ -537,7 +664,7 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
     << ",\"t_solve_ms\":" << c.stats.t_solve_ms << ",\"flops_factor\":" << c.stats.flops_factor
     << ",\"launches_factor\":" << c.stats.launches_factor << ",\"launches_solve\":" << c.stats.launches_solve
     << ",\"refine_iters\":" << c.stats.refine_iters << ",\"refine_resid\":" << c.stats.refine_resid
-    << ",\"dev_bytes\":" << c.dev_bytes << ",\"dev_peak\":" << c.dev_peak << ",\"root_n\":" << c.root.n
+    << ",\"symmetric\":" << (c.H.symmetric ? 1 : 0) << ",\"dev_bytes\":" << c.dev_bytes << ",\"dev_peak\":" << c.dev_peak << ",\"root_n\":" << c.root.n
     << ",\"build_rank_max\":[";
   for (int l = c.H.l0; l <= c.H.L; ++l) {
     int mx = 0;
@@ -562,7 +689,9 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
     o << (li ? "," : "") << "{\"l\":" << F.l << ",\"clusters\":" << F.nc << ",\"n_max\":" << nmax
       << ",\"k0_max\":" << k0max << ",\"kt_max\":" << ktmax << ",\"eliminated\":" << msum
       << ",\"batches\":" << F.batches.size() << ",\"near\":" << F.near_pairs.size()
-      << ",\"adm\":" << c.H.part.adm[F.l].size() << ",\"fill_live\":" << live << ",\"pushed_live\":" << pushed << "}";
+      << ",\"adm\":" << c.H.part.adm[F.l].size() << ",\"fill_live\":" << live << ",\"pushed_live\":" << pushed
+      << ",\"ritz_max\":" << F.st_ritz_max << ",\"ritz_mean\":" << (F.st_ritz_n ? (double)F.st_ritz_sum / F.st_ritz_n : 0.0)
+      << ",\"jacobi_sweeps_max\":" << F.st_sweeps_max << "}";
   }
   o << "]}";
   const std::string s = o.str();

@@ -15,7 +15,7 @@ struct GemmBatch {
   std::vector<h2k::GemmTile> tl;
   double flops = 0;
   void task(void* C, int ldc, int M, int N, double alpha, double beta) {
-    t.push_back(h2k::GemmTask{C, ldc, M, N, (int)p.size(), 0, alpha, beta});
+    t.push_back(h2k::GemmTask{C, ldc, M, N, (int)p.size(), 0, alpha, beta, 1, 0, 0, 0});
   }
   void pair(const void* A, int lda, int opA, const void* B, int ldb, int opB, int K) {
     if (K <= 0) return;
@@ -23,19 +23,53 @@ struct GemmBatch {
     t.back().np++;
     flops += 8.0 * t.back().M * (double)t.back().N * K;
   }
+  // mark the open task's C as Hermitian (square, sum of X X^H products)
+  void hermitian() { t.back().herm = 1; }
   void close() {
     h2k::GemmTask& g = t.back();
     if (g.M <= 0 || g.N <= 0 || (g.np == 0 && g.beta == 1.0)) {
       p.resize(g.p0);
       t.pop_back();
-      return;
     }
-    const int ti = (int)t.size() - 1;
-    const int bm = h2k::gemm_tile_m(0), bn = h2k::gemm_tile_n(0);
-    for (int tn = 0; tn * bn < g.N; ++tn)
-      for (int tm = 0; tm * bm < g.M; ++tm) tl.push_back(h2k::GemmTile{ti, tm, tn});
   }
-  bool empty() const { return tl.empty(); }
+  // Tile list; tasks whose K is long compared with the number of output tiles
+  // are split along K (deterministic two-pass sum) so that a launch keeps the
+  // SMs busy.  Returns the split-K workspace size in accumulator elements.
+  int64_t plan(int target_ctas = 4 * 152) {
+    tl.clear();
+    const int bm = h2k::gemm_tile_m(0), bn = h2k::gemm_tile_n(0);
+    auto ntile = [&](const h2k::GemmTask& g) {
+      const int64_t a = (g.M + bm - 1) / bm, b = (g.N + bn - 1) / bn;
+      return g.herm ? a * (a + 1) / 2 : a * b;
+    };
+    int64_t tiles0 = 0;
+    for (auto& g : t) tiles0 += ntile(g);
+    int64_t ws = 0;
+    for (size_t ti = 0; ti < t.size(); ++ti) {
+      h2k::GemmTask& g = t[ti];
+      int64_t K = 0;
+      for (int q = g.p0; q < g.p0 + g.np; ++q) K += p[q].K;
+      int nk = 1;
+      if (tiles0 < target_ctas && K >= 128) {
+        nk = (int)std::min<int64_t>((target_ctas + tiles0 - 1) / tiles0, K / 64);
+        nk = std::max(1, std::min(nk, 64));
+      }
+      g.nk = nk;
+      g.ksz = nk > 1 ? (int)(((K + nk - 1) / nk + 7) / 8 * 8) : 0;
+      if (nk > 1) {
+        nk = (int)((K + g.ksz - 1) / g.ksz);
+        g.nk = nk;
+        g.ws_off = ws;
+        ws += (int64_t)nk * g.M * g.N;
+      }
+      for (int kc = 0; kc < g.nk; ++kc)
+        for (int tn = 0; tn * bn < g.N; ++tn)
+          for (int tm = 0; tm * bm < g.M; ++tm)
+            if (!g.herm || tm <= tn) tl.push_back(h2k::GemmTile{(int)ti, tm, tn, kc});
+    }
+    return ws;
+  }
+  bool empty() const { return t.empty(); }
   void clear() { t.clear(); p.clear(); tl.clear(); flops = 0; }
 };
 

@@ -1,19 +1,18 @@
-// h2_build: H^2 representation of Z = I + s D^{1/2} K D^{1/2} by proxy
-// sampling and nested interpolative decompositions (host, multi-threaded).
+// h2_build: H^2 representation of Z = I + s D^{1/2} K D^{1/2} by nested
+// interpolative decompositions of exact far-field samples.
 //
 // The paper builds its H^2 matrices with the method of its refs. [14], [15]
 // and does not describe it (Sec. VI).  This construction, for each level from
 // the leaves up and each cluster t:
 //   rows_t   the points of t (leaf) or the skeletons of its two children
-//   sample   Z(rows_t, cols) with cols = every point of t's far field
-//            (clusters admissible with t or an ancestor of t) inside a sphere
-//            of radius proxy_radius * r_t around c_t, plus, if some far point
-//            lies outside it, single- and double-layer sources on that sphere
-//            (Fibonacci points): by Green's representation formula they span
-//            the field of every far source outside the sphere.
-//   ID       column-pivoted Householder QR of sample^T, stopped when the
-//            largest remaining column norm <= eps * the first one; the pivots
-//            are the skeleton rows, P_t interpolates the other rows.
+//   sample   Z(rows_t, F*(t)), F*(t) = every point of the clusters admissible
+//            with t or with an ancestor of t (all of t's far field); only its
+//            Gram G_t = Z Z^H is formed (GPU kernel, O(N^2 k) FP64 work)
+//   ID       pivoted Cholesky of G_t (the column-pivoted QR of Z^H in Gram
+//            form): pivot = largest remaining diagonal, stop when it is
+//            <= eps^2 times the first; the pivots are the skeleton rows and
+//            P_t = L(rest) L(skel)^{-1} interpolates the others, so that
+//            Z(rows_t, F*) ~= P_t Z(skel_t, F*)
 //   basis    P_t = Q R (leaf: V_t = Q) or diag(R_t1, R_t2) P_t = Q R
 //            (non-leaf: T_t = Q), so the bases are orthonormal and nested
 //            (eq. 3); couplings S_ts = R_t Z(skel_t, skel_s) R_s^T (eq. 2,
@@ -29,10 +28,10 @@ namespace h2 {
 namespace {
 
 struct KernelCtx {
-  const double* pts;
-  const double* sq;   // sqrt(chi), global index
+  const double* pts;  // global order
+  const double* sq;   // sqrt(chi), global order
   const double* chi;
-  double k, h, sign, self_re, self_im, w;  // w = k^2 h^3 / (4 pi)
+  double k, sign, self_re, self_im, w;  // w = k^2 h^3 / (4 pi)
 };
 
 inline cplx zentry(const KernelCtx& K, int64_t i, int64_t j) {
@@ -42,18 +41,6 @@ inline cplx zentry(const KernelCtx& K, int64_t i, int64_t j) {
   const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
   const double a = K.sign * K.sq[i] * K.sq[j] * K.w / r;
   return cplx(a * std::cos(K.k * r), -a * std::sin(K.k * r));
-}
-
-// Green's function G = e^{-jkr}/(4 pi r) scaled by k^2 h^3 (single layer) and
-// its derivative along the outward sphere normal at the source (double layer)
-inline void proxy_entry(const KernelCtx& K, int64_t i, const double* z, const double* nz, cplx& g, cplx& dg) {
-  const double dx = K.pts[3 * i] - z[0], dy = K.pts[3 * i + 1] - z[1], dz = K.pts[3 * i + 2] - z[2];
-  const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
-  const cplx e = std::exp(cplx(0, -K.k * r));
-  g = K.sq[i] * K.w * e / r;
-  // d/dn_z of e^{-jkr}/r with r = |x - z|: (jk r + 1) e^{-jkr} / r^2 * ((x-z).n / r)
-  const double cosn = (dx * nz[0] + dy * nz[1] + dz * nz[2]) / r;
-  dg = K.sq[i] * K.w * cplx(1.0, K.k * r) * e / (r * r) * cosn;
 }
 
 // column-major helpers
@@ -87,62 +74,50 @@ cplx householder(cplx* x, int n, double* beta) {
   return tau;
 }
 
-// Row interpolative decomposition of M (nr x nc): skeleton rows and P (nr x k)
-// with M ~= P M(skel, :).
-void row_id(const Mat& M, double eps, std::vector<int>& skel, Mat& P) {
-  const int nr = M.m, nc = M.n;
-  // A = M^T (nc x nr), pivot over its columns (= rows of M)
-  Mat A(nc, nr);
-  for (int j = 0; j < nr; ++j)
-    for (int i = 0; i < nc; ++i) A(i, j) = M(j, i);
+// Row interpolative decomposition from the Gram G = M M^H (nr x nr):
+// skeleton rows and P (nr x k) with M ~= P M(skel, :).
+void row_id_gram(const Mat& G, double eps, std::vector<int>& skel, Mat& P) {
+  const int nr = G.m;
+  std::vector<double> d(nr);
+  for (int i = 0; i < nr; ++i) d[i] = G(i, i).real();
   std::vector<int> piv(nr);
-  for (int j = 0; j < nr; ++j) piv[j] = j;
-  std::vector<double> cn(nr);
-  const int kmax = std::min(nr, nc);
+  for (int i = 0; i < nr; ++i) piv[i] = i;
+  Mat Lm(nr, nr);  // row = original index, column = step
   double first = -1;
   int k = 0;
-  for (int j = 0; j < kmax; ++j) {
+  for (int j = 0; j < nr; ++j) {
     int best = j;
-    double bv = -1;
-    for (int c = j; c < nr; ++c) {
-      double s = 0;
-      for (int i = j; i < nc; ++i) s += std::norm(A(i, c));
-      cn[c] = s;
-      if (s > bv) { bv = s; best = c; }
+    for (int i = j + 1; i < nr; ++i)
+      if (d[piv[i]] > d[piv[best]]) best = i;
+    const double dv = d[piv[best]];
+    if (j == 0) first = dv;
+    if (!(dv > eps * eps * first) || dv <= 0.0) break;
+    std::swap(piv[j], piv[best]);
+    const int p = piv[j];
+    const double sd = std::sqrt(dv);
+    for (int q = j; q < nr; ++q) {
+      const int i = piv[q];
+      cplx v = G(i, p);
+      for (int t = 0; t < j; ++t) v -= Lm(i, t) * std::conj(Lm(p, t));
+      Lm(i, j) = v / sd;
     }
-    const double bn = std::sqrt(bv);
-    if (j == 0) first = bn;
-    if (bn <= eps * first || bn == 0.0) break;
-    if (best != j) {
-      for (int i = 0; i < nc; ++i) std::swap(A(i, j), A(i, best));
-      std::swap(piv[j], piv[best]);
-    }
-    double beta;
-    const cplx tau = householder(&A(j, j), nc - j, &beta);
-    // apply H^H = I - conj(tau) v v^H to A(j:, j+1:)
-    for (int c = j + 1; c < nr; ++c) {
-      cplx d = 0;
-      for (int i = j; i < nc; ++i) d += std::conj(A(i, j)) * A(i, c);
-      d *= std::conj(tau);
-      for (int i = j; i < nc; ++i) A(i, c) -= A(i, j) * d;
-    }
-    A(j, j) = beta;
+    for (int q = j + 1; q < nr; ++q) d[piv[q]] -= std::norm(Lm(piv[q], j));
     k = j + 1;
-  }
-  // X = R11^{-1} R12  (k x (nr-k)); R11 upper triangular in A(0:k, 0:k)
-  Mat X(k, nr - k);
-  for (int c = 0; c < nr - k; ++c) {
-    for (int i = k - 1; i >= 0; --i) {
-      cplx v = A(i, k + c);
-      for (int t = i + 1; t < k; ++t) v -= A(i, t) * X(t, c);
-      X(i, c) = v / A(i, i);
-    }
   }
   skel.assign(piv.begin(), piv.begin() + k);
   P = Mat(nr, k);
   for (int j = 0; j < k; ++j) P(piv[j], j) = 1.0;
-  for (int c = 0; c < nr - k; ++c)
-    for (int j = 0; j < k; ++j) P(piv[k + c], j) = X(j, c);
+  // other rows: x L_s = L_r(i, :) with L_s = L(skel, :) lower triangular
+  std::vector<cplx> x(k);
+  for (int q = k; q < nr; ++q) {
+    const int i = piv[q];
+    for (int j = k - 1; j >= 0; --j) {
+      cplx v = Lm(i, j);
+      for (int t = j + 1; t < k; ++t) v -= x[t] * Lm(piv[t], j);
+      x[j] = v / Lm(piv[j], j);
+    }
+    for (int j = 0; j < k; ++j) P(i, j) = x[j];
+  }
 }
 
 // thin QR by Householder: P (m x k) = Q R, Q orthonormal (m x k), R (k x k)
@@ -194,8 +169,64 @@ void parallel_for(int n, F f) {
 
 }  // namespace
 
+// Orthonormal complement of the orthonormal columns of B (n x k): the last
+// n - k columns of the Householder Q of B (Step 1, eq. 4, computed once when
+// the H^2 matrix is set up: the paper notes V^perp may be stored then).
+std::vector<cplx> host_complement(const std::vector<cplx>& B, int n, int k) {
+  Mat A(n, k);
+  A.a = B;
+  std::vector<cplx> tau(k);
+  for (int j = 0; j < k; ++j) {
+    double beta;
+    tau[j] = householder(&A(j, j), n - j, &beta);
+    for (int c = j + 1; c < k; ++c) {
+      cplx d = 0;
+      for (int i = j; i < n; ++i) d += std::conj(A(i, j)) * A(i, c);
+      d *= std::conj(tau[j]);
+      for (int i = j; i < n; ++i) A(i, c) -= A(i, j) * d;
+    }
+  }
+  const int q = n - k;
+  Mat E(n, q);
+  for (int c = 0; c < q; ++c) E(k + c, c) = 1.0;
+  for (int j = k - 1; j >= 0; --j)
+    for (int c = 0; c < q; ++c) {
+      cplx d = E(j, c);
+      for (int i = j + 1; i < n; ++i) d += std::conj(A(i, j)) * E(i, c);
+      d *= tau[j];
+      E(j, c) -= d;
+      for (int i = j + 1; i < n; ++i) E(i, c) -= A(i, j) * d;
+    }
+  return E.a;
+}
+
+void host_gram(const double* pts, const double* sq, double k, double w, const std::vector<std::vector<int64_t>>& rows,
+               const std::vector<std::vector<int64_t>>& ranges, std::vector<std::vector<cplx>>& G) {
+  G.assign(rows.size(), {});
+  parallel_for((int)rows.size(), [&](int t) {
+    const int nr = (int)rows[t].size();
+    std::vector<cplx> g((size_t)nr * nr, 0.0), z(nr);
+    for (size_t q = 0; q + 1 < ranges[t].size(); q += 2)
+      for (int64_t c = ranges[t][q]; c < ranges[t][q] + ranges[t][q + 1]; ++c) {
+        for (int i = 0; i < nr; ++i) {
+          const int64_t p = rows[t][i];
+          const double dx = pts[3 * p] - pts[3 * c], dy = pts[3 * p + 1] - pts[3 * c + 1],
+                       dz = pts[3 * p + 2] - pts[3 * c + 2];
+          const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+          const double a = w * sq[p] * sq[c] / r;
+          z[i] = cplx(a * std::cos(k * r), -a * std::sin(k * r));
+        }
+        for (int j = 0; j < nr; ++j) {
+          const cplx zj = std::conj(z[j]);
+          for (int i = 0; i < nr; ++i) g[(size_t)i + (size_t)j * nr] += z[i] * zj;
+        }
+      }
+    G[t] = std::move(g);
+  });
+}
+
 std::string build_h2(const double* pts, int64_t N, double k, double h, const double* chi, int64_t chi_len,
-                     double eps, const h2_opts& o, H2Host& H) {
+                     double eps, const h2_opts& o, H2Host& H, const GramFn& gram) {
   std::vector<double> chiv(N), sq(N);
   for (int64_t i = 0; i < N; ++i) {
     chiv[i] = chi_len == 1 ? chi[0] : chi[i];
@@ -212,9 +243,8 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
   H.dscale = sq;
   const double a = std::cbrt(3.0 / (4.0 * M_PI)) * h;
   const cplx self = (1.0 + cplx(0, k * a)) * std::exp(cplx(0, -k * a)) - 1.0;
-  KernelCtx K{pts, sq.data(), chiv.data(), k, h, o.sign, self.real(), self.imag(), k * k * h * h * h / (4.0 * M_PI)};
+  KernelCtx K{pts, sq.data(), chiv.data(), k, o.sign, self.real(), self.imag(), k * k * h * h * h / (4.0 * M_PI)};
 
-  // admissible partners per level and cluster
   std::vector<std::vector<std::vector<int>>> admp(L + 1);
   for (int l = 0; l <= L; ++l) {
     admp[l].assign(size_t(1) << l, {});
@@ -224,7 +254,7 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
   H.V.assign(size_t(1) << L, {});
   H.T.assign(L + 1, {});
   H.S.assign(L + 1, {});
-  std::vector<std::vector<std::vector<int64_t>>> skel(L + 1);  // global indices
+  std::vector<std::vector<std::vector<int64_t>>> skel(L + 1);  // tree positions
   std::vector<std::vector<Mat>> Rm(L + 1);
 
   for (int l = L; l >= l0; --l) {
@@ -233,75 +263,35 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
     Rm[l].assign(nc, Mat());
     H.rank[l].assign(nc, 0);
     if (l < L) H.T[l].assign(nc, {});
-    parallel_for(nc, [&](int t) {
-      std::vector<int64_t> rows;
+    std::vector<std::vector<int64_t>> rows(nc), ranges(nc);
+    for (int t = 0; t < nc; ++t) {
       if (l == L) {
-        for (int64_t p = T.start[l][t]; p < T.start[l][t] + T.size[l][t]; ++p) rows.push_back(T.perm[p]);
+        for (int64_t p = T.start[l][t]; p < T.start[l][t] + T.size[l][t]; ++p) rows[t].push_back(p);
       } else {
-        rows = skel[l + 1][2 * t];
-        rows.insert(rows.end(), skel[l + 1][2 * t + 1].begin(), skel[l + 1][2 * t + 1].end());
+        rows[t] = skel[l + 1][2 * t];
+        rows[t].insert(rows[t].end(), skel[l + 1][2 * t + 1].begin(), skel[l + 1][2 * t + 1].end());
       }
-      const double* c = &T.centre[l][3 * t];
-      const double rho = o.proxy_radius * T.radius[l][t];
-      // far-field points inside the proxy sphere
-      std::vector<int64_t> inside;
-      bool any_far = false, any_outside = false;
-      for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1) {
+      for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
         for (int s : admp[lv][anc]) {
-          any_far = true;
-          const double* cs = &T.centre[lv][3 * s];
-          const double dc = std::sqrt((c[0] - cs[0]) * (c[0] - cs[0]) + (c[1] - cs[1]) * (c[1] - cs[1]) +
-                                      (c[2] - cs[2]) * (c[2] - cs[2]));
-          if (dc >= rho + T.radius[lv][s]) {
-            any_outside = true;
-            continue;
-          }
-          for (int64_t p = T.start[lv][s]; p < T.start[lv][s] + T.size[lv][s]; ++p) {
-            const int64_t g = T.perm[p];
-            double d2 = 0;
-            for (int q = 0; q < 3; ++q) d2 += (pts[3 * g + q] - c[q]) * (pts[3 * g + q] - c[q]);
-            if (d2 < rho * rho) inside.push_back(g);
-            else any_outside = true;
-          }
+          ranges[t].push_back(T.start[lv][s]);
+          ranges[t].push_back(T.size[lv][s]);
         }
-      }
-      const int nr = (int)rows.size();
-      if (!any_far || nr == 0) {
-        skel[l][t].clear();
-        Rm[l][t] = Mat(0, 0);
-        H.rank[l][t] = 0;
-        if (l == L) H.V[t].clear();
-        else H.T[l][t].clear();
-        return;
-      }
-      const double kr = k * rho;
-      // proxy layers only represent far sources outside the sphere
-      int np = (int)std::ceil((kr + 16.0) * (kr + 16.0));
-      np = std::max(np, o.proxy_min);
-      if (!any_outside) np = 0;
-      Mat M(nr, 2 * np + (int)inside.size());
-      const double ga = M_PI * (3.0 - std::sqrt(5.0));
-      for (int q = 0; q < np; ++q) {
-        const double zc = 1.0 - (2.0 * q + 1.0) / np;
-        const double rr = std::sqrt(std::max(0.0, 1.0 - zc * zc));
-        const double th = ga * q;
-        const double nz[3] = {rr * std::cos(th), rr * std::sin(th), zc};
-        const double z[3] = {c[0] + rho * nz[0], c[1] + rho * nz[1], c[2] + rho * nz[2]};
-        for (int i = 0; i < nr; ++i) {
-          cplx g, dg;
-          proxy_entry(K, rows[i], z, nz, g, dg);
-          M(i, 2 * q) = g;
-          M(i, 2 * q + 1) = dg * rho;  // scale the double layer to the single layer
-        }
-      }
-      for (size_t q = 0; q < inside.size(); ++q)
-        for (int i = 0; i < nr; ++i) M(i, 2 * np + (int)q) = zentry(K, rows[i], inside[q]);
+      if (ranges[t].empty()) rows[t].clear();  // no far field: rank 0
+    }
+    std::vector<std::vector<cplx>> G;
+    gram(l, rows, ranges, G);
+    parallel_for(nc, [&](int t) {
+      const int nr = (int)rows[t].size();
       std::vector<int> sk;
-      Mat P;
-      row_id(M, eps, sk, P);
+      Mat P(nr, 0);
+      if (nr > 0) {
+        Mat Gm(nr, nr);
+        Gm.a = G[t];
+        row_id_gram(Gm, eps, sk, P);
+      }
       const int kk = (int)sk.size();
       std::vector<int64_t> sg(kk);
-      for (int j = 0; j < kk; ++j) sg[j] = rows[sk[j]];
+      for (int j = 0; j < kk; ++j) sg[j] = rows[t][sk[j]];
       skel[l][t] = sg;
       H.rank[l][t] = kk;
       Mat Q, R;
@@ -313,18 +303,19 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
         const Mat& R2 = Rm[l + 1][2 * t + 1];
         const int k1 = R1.m, k2 = R2.m;
         Mat Pm(k1 + k2, kk);
-        for (int j = 0; j < kk; ++j) {
-          for (int i = 0; i < k1; ++i) {
-            cplx v = 0;
-            for (int q = i; q < k1; ++q) v += R1(i, q) * P(q, j);
-            Pm(i, j) = v;
+        if (nr > 0)
+          for (int j = 0; j < kk; ++j) {
+            for (int i = 0; i < k1; ++i) {
+              cplx v = 0;
+              for (int q = i; q < k1; ++q) v += R1(i, q) * P(q, j);
+              Pm(i, j) = v;
+            }
+            for (int i = 0; i < k2; ++i) {
+              cplx v = 0;
+              for (int q = i; q < k2; ++q) v += R2(i, q) * P(k1 + q, j);
+              Pm(k1 + i, j) = v;
+            }
           }
-          for (int i = 0; i < k2; ++i) {
-            cplx v = 0;
-            for (int q = i; q < k2; ++q) v += R2(i, q) * P(k1 + q, j);
-            Pm(k1 + i, j) = v;
-          }
-        }
         thin_qr(Pm, Q, R);
         H.T[l][t] = Q.a;
       }
@@ -342,7 +333,7 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
       const int kt = (int)st.size(), ks = (int)ss.size();
       Mat Zs(kt, ks);
       for (int j = 0; j < ks; ++j)
-        for (int i = 0; i < kt; ++i) Zs(i, j) = zentry(K, st[i], ss[j]);
+        for (int i = 0; i < kt; ++i) Zs(i, j) = zentry(K, T.perm[st[i]], T.perm[ss[j]]);
       const Mat& Rt = Rm[l][t];
       const Mat& Rs = Rm[l][s];
       Mat Y(kt, ks);  // Rt Zs

@@ -192,10 +192,10 @@ __global__ void __launch_bounds__(NT) k_jacobi(const EigTask* __restrict__ tasks
   double fro = 0;
   for (int idx = threadIdx.x; idx < p * p; idx += NT) fro += A[idx].re * A[idx].re + A[idx].im * A[idx].im;
   fro = block_sum(fro, red);
-  // rotations whose off-diagonal entry is below 1e-18 ||A||_F (or 1e-17 of
+  // rotations whose off-diagonal entry is below 4e-16 ||A||_F (or 1e-17 of
   // the geometric mean of the two diagonal entries) are skipped; the sweep
   // loop ends after a sweep without any rotation.
-  const double gmin = fmax(1e-300, 1e-18 * sqrt(fro));
+  const double gmin = fmax(1e-300, 4e-16 * sqrt(fro));
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (threadIdx.x == 0) any_rot = 0;
@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const EigTask* __restrict__ tasks
     if (!any_rot) break;
   }
   if (sweep == kMaxSweeps && threadIdx.x == 0 && status) atomicMax(status, 2);
+  if (threadIdx.x == 0 && t.sweeps) *t.sweeps = sweep;
   // sort eigenvalues in decreasing order (ties: lower index first); the
   // rank of each eigenvalue goes to shared memory (pa/pb hold >= p ints)
   int* rks = pa;
@@ -454,6 +455,12 @@ __device__ void copy_body(const CopyTask& t) {
   for (int idx = threadIdx.x + blockIdx.y * NT; idx < n; idx += NT * gridDim.y) {
     const int r = idx % t.rows, c = idx / t.rows;
     ED v;
+    if (t.mode == 2) {
+      v.re = (r == c) ? 1 : 0;
+      v.im = 0;
+      D[(size_t)r + (size_t)c * t.ldd] = v;
+      continue;
+    }
     if (S && r < t.srows && c < t.scols) {
       const ES s = t.transpose ? S[(size_t)c + (size_t)r * t.lds] : S[(size_t)r + (size_t)c * t.lds];
       cvt(s, v, t.alpha);

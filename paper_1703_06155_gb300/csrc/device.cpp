@@ -117,6 +117,28 @@ void upload_h2(Ctx& c) {
     buf.insert(buf.end(), H.D[q].begin(), H.D[q].end());
   }
   upload_vec(c, c.dD, buf);
+  // complements of the leaf bases and of the transfer matrices (Step 1)
+  buf.clear();
+  c.Vp_off.assign(size_t(1) << L, 0);
+  for (int t = 0; t < (1 << L); ++t) {
+    c.Vp_off[t] = buf.size();
+    const int n = (int)H.tree.size[L][t], k = H.rank[L][t];
+    const std::vector<cplx> E = host_complement(H.V[t], n, k);
+    buf.insert(buf.end(), E.begin(), E.end());
+  }
+  upload_vec(c, c.dVp, buf);
+  buf.clear();
+  c.Tp_off.assign(L + 1, {});
+  for (int l = l0; l < L; ++l) {
+    c.Tp_off[l].assign(size_t(1) << l, 0);
+    for (int t = 0; t < (1 << l); ++t) {
+      c.Tp_off[l][t] = buf.size();
+      const int n = H.rank[l + 1][2 * t] + H.rank[l + 1][2 * t + 1], k = H.rank[l][t];
+      const std::vector<cplx> E = host_complement(H.T[l][t], n, k);
+      buf.insert(buf.end(), E.begin(), E.end());
+    }
+  }
+  upload_vec(c, c.dTp, buf);
   upload_vec(c, c.dperm, H.tree.perm);
   upload_vec(c, c.dscale, H.dscale);
 }

@@ -38,12 +38,30 @@ using namespace h2k;
 
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what) {
   if (b.empty()) return;
+  const int64_t ws = b.plan();
+  if (b.tl.empty()) return;
+  void* wsp = nullptr;
+  if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
   c.st.upload(c);
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
-          c.stream),
+          wsp, c.stream),
      what);
   c.launches++;
+  if (ws > 0) {
+    int maxmn = 0;
+    for (auto& g : b.t)
+      if (g.nk > 1) maxmn = std::max(maxmn, g.M * g.N);
+    ck(gemm_reduce(c.st.ptr<GemmTask>(i0), (int)b.t.size(), maxmn, pout, pacc, wsp, c.stream), what);
+    c.launches++;
+  }
+  int maxh = 0;
+  for (auto& g : b.t)
+    if (g.herm) maxh = std::max(maxh, g.M * g.N);
+  if (maxh > 0) {
+    ck(gemm_mirror(c.st.ptr<GemmTask>(i0), (int)b.t.size(), maxh, pout, c.stream), what);
+    c.launches++;
+  }
 }
 
 void run_apply(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
@@ -79,7 +97,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   {
     // keep the device arenas of an earlier factorization (grow-only)
     DevBuf b1 = std::move(F.near_buf), b2 = std::move(F.fill_buf), b3 = std::move(F.B_buf), b4 = std::move(F.Q_buf),
-           b5 = std::move(F.inv_buf), b6 = std::move(F.piv_buf), b7 = std::move(F.Ub_buf);
+           b5 = std::move(F.inv_buf), b6 = std::move(F.piv_buf), b7 = std::move(F.Ub_buf), b8 = std::move(F.Vp_buf);
     F = LevelF();
     F.near_buf = std::move(b1);
     F.fill_buf = std::move(b2);
@@ -88,6 +106,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.inv_buf = std::move(b5);
     F.piv_buf = std::move(b6);
     F.Ub_buf = std::move(b7);
+    F.Vp_buf = std::move(b8);
   }
   F.l = l;
   F.nc = nc;
@@ -141,7 +160,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   dev_ensure(c, F.fill_buf, tot * es);
   if (tot) ck(cudaMemsetAsync(F.fill_buf.p, 0, tot * es, c.stream), "fill memset");
   // bases (FP64), Q (bulk), L^{-1}P and U^{-1} (bulk), pivots
-  size_t tb = 0, tq = 0, ti = 0, tp = 0;
+  size_t tb = 0, tq = 0, ti = 0, tp = 0, tvp = 0;
   F.voff.assign(nc, 0);
   F.vlen = 0;
   for (int i = 0; i < nc; ++i) {
@@ -156,6 +175,8 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     ti += 2 * (size_t)n[i] * n[i];
     F.piv_off.push_back(tp);
     tp += n[i];
+    F.Vp_off.push_back(tvp);
+    tvp += (size_t)n[i] * (n[i] - F.k0[i]);
     F.voff[i] = F.vlen;
     F.vlen += n[i];
   }
@@ -163,6 +184,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   dev_ensure(c, F.Q_buf, tq * es);
   dev_ensure(c, F.inv_buf, ti * es);
   dev_ensure(c, F.piv_buf, tp * sizeof(int));
+  dev_ensure(c, F.Vp_buf, tvp * sizeof(cd));
   // sum of ||S||_F^2 over the admissible blocks of each row and column
   F.snorm2.assign(nc, 0.0);
   for (size_t q = 0; q < H.part.adm[l].size(); ++q) {
@@ -198,10 +220,12 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
   std::set<int> inb(bt.begin(), bt.end());
 
   // ------------------------------ Phase A (FP64) ---------------------------
+  // Vp: complement of the incoming basis (stored with the level); G' = Vp^H M
+  // Vp is the Gram of eq. (16) in complement coordinates.
   struct Info {
-    int i, n, k0, p;
+    int i, n, k0, p, rp = 0;
     bool fill;
-    size_t W, Vp, M, T1, G, U, Y, lam;
+    size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1;
     std::vector<int> rowf, colf;
   };
   std::vector<Info> info;
@@ -218,44 +242,41 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
       if (F.fill_pairs[q].second == i) f.colf.push_back((int)q);
     }
     f.fill = (!f.rowf.empty() || !f.colf.empty()) && f.p > 0;
-    f.W = sc;
-    sc += (size_t)f.n * std::max(f.k0, 1);
-    f.Vp = sc;
-    sc += (size_t)f.n * std::max(f.p, 1);
     if (f.fill) {
-      f.M = sc;
-      sc += (size_t)f.n * f.n;
-      f.T1 = sc;
-      sc += (size_t)f.n * f.p;
-      f.G = sc;
-      sc += (size_t)f.p * f.p;
-      f.U = sc;
-      sc += (size_t)f.p * f.p;
-      f.Y = sc;
-      sc += (size_t)f.n * f.p;
-      f.lam = sc;
-      sc += (size_t)(f.p + 1) / 2 + 1;
+      const size_t n = f.n, p = f.p;
+      auto take = [&](size_t cnt) { const size_t o = sc; sc += cnt; return o; };
+      f.M = take(n * n);
+      f.T1 = take(n * p);
+      f.G = take(p * p);
+      f.L = take(p * p);
+      f.T = take(p * p);
+      f.W = take(p * p);
+      f.Qx = take(p * p);
+      f.Z1 = take(p * p);
+      f.Gh = take(p * p);
+      f.U = take(p * p);
+      f.lam = take(p / 2 + 1);
+      f.W1 = take(n * p);
+      f.W2 = take(n * p);
+      f.Yf = take(n * p);
+      f.Y1 = take(n * p);
     }
     info.push_back(f);
   }
   cd* S = (cd*)dev_ensure(c, c.scratch, (sc + 1) * sizeof(cd));
-  // r per cluster (device ints)
-  int* d_r = (int*)dev_ensure(c, c.normbuf, bt.size() * sizeof(int) + 64);
-  ck(cudaMemsetAsync(d_r, 0, bt.size() * sizeof(int), c.stream), "memset r");
-  {
-    std::vector<HhTask> hh;
-    for (auto& f : info) hh.push_back(HhTask{P.B + F.B_off[f.i], S + f.W, S + f.Vp, f.n, f.k0});
-    const int i0 = c.st.add(hh);
-    c.st.upload(c);
-    ck(householder_complement(c.st.ptr<HhTask>(i0), (int)hh.size(), c.stream), "householder");
-    c.launches++;
-  }
+  int* d_r = (int*)dev_ensure(c, c.normbuf, 3 * bt.size() * sizeof(int) + 64);
+  ck(cudaMemsetAsync(d_r, 0, 3 * bt.size() * sizeof(int), c.stream), "memset r");
+  auto Vp = [&](int i) { return (cd*)F.Vp_buf.p + F.Vp_off[i]; };
+  // With a symmetric Z the column fill-ins are the transposed row fill-ins and
+  // the column Gram equals the row Gram: only the row side is formed, and the
+  // admissible-row norm is halved to match (the decisions are unchanged).
+  auto snorm = [&](int i) { return c.H.symmetric ? 0.5 * F.snorm2[i] : F.snorm2[i]; };
   bool anyfill = false;
   for (auto& f : info) anyfill |= f.fill;
+  std::vector<int> r(bt.size(), 0), sweeps;
   if (anyfill) {
-    GemmBatch gM, gT, gG, gY;
-    std::vector<EigTask> eig;
-    std::vector<SelTask> sel;
+    GemmBatch gM, gT, gG;
+    std::vector<PcholTask> pc;
     int maxp = 0;
     for (size_t q = 0; q < info.size(); ++q) {
       Info& f = info[q];
@@ -267,49 +288,120 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
         char* A = FB(id) + (size_t)lo * n * es;
         gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
       }
-      for (int id : f.colf) {
-        const int k = F.fill_pairs[id].first, lo = lo_of(k);
-        char* A = FB(id) + (size_t)lo * es;
-        gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
-      }
+      if (!c.H.symmetric)
+        for (int id : f.colf) {
+          const int k = F.fill_pairs[id].first, lo = lo_of(k);
+          char* A = FB(id) + (size_t)lo * es;
+          gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
+        }
+      gM.hermitian();
       gM.close();
       gT.task(S + f.T1, n, n, f.p, 1.0, 0.0);
-      gT.pair(S + f.M, n, OP_N, S + f.Vp, n, OP_N, n);
+      gT.pair(S + f.M, n, OP_N, Vp(f.i), n, OP_N, n);
       gT.close();
       gG.task(S + f.G, f.p, f.p, f.p, 1.0, 0.0);
-      gG.pair(S + f.Vp, n, OP_H, S + f.T1, n, OP_N, n);
+      gG.pair(Vp(f.i), n, OP_H, S + f.T1, n, OP_N, n);
       gG.close();
-      eig.push_back(EigTask{S + f.G, S + f.U, (double*)(S + f.lam), f.p});
+      pc.push_back(PcholTask{S + f.G, S + f.M, S + f.L, S + f.T, d_r + q, f.p, n, snorm(f.i), eps * eps});
       maxp = std::max(maxp, f.p);
-      gY.task(S + f.Y, n, n, f.p, 1.0, 0.0);
-      gY.pair(S + f.Vp, n, OP_N, S + f.U, f.p, OP_N, f.p);
-      gY.close();
-      sel.push_back(SelTask{S + f.M, (double*)(S + f.lam), d_r + q, n, f.p, F.snorm2[f.i], eps * eps});
     }
     run_gemm(c, gM, prec, P64, P64, "gram");
     run_gemm(c, gT, P64, P64, P64, "gram*Vp");
     run_gemm(c, gG, P64, P64, P64, "Vp^H*gram*Vp");
     {
+      const int i0 = c.st.add(pc);
+      c.st.upload(c);
+      ck(pchol_wy(c.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, c.stream), "pivoted cholesky");
+      c.launches++;
+    }
+    std::vector<int> rp(bt.size(), 0);
+    ck(cudaMemcpyAsync(rp.data(), d_r, bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read r'");
+    ck(cudaStreamSynchronize(c.stream), "sync after pivoted cholesky");
+    c.st.begin();
+    for (size_t q = 0; q < info.size(); ++q)
+      if (info[q].fill) info[q].rp = std::min(std::max(rp[q], 0), info[q].p);
+    // Ritz step on span(Qx) and the complement rotation Yf = Vp Q, Q = I - Y T Y^H
+    GemmBatch g1, g2, g3, g4, g5;
+    CopyBatch cp;
+    std::vector<EigTask> eig;
+    std::vector<SelTask> sel;
+    int maxr = 0;
+    for (size_t q = 0; q < info.size(); ++q) {
+      Info& f = info[q];
+      if (!f.fill || f.rp == 0) continue;
+      const int n = f.n, p = f.p, rr = f.rp;
+      cd* Y = S + f.L;
+      g1.task(S + f.W, p, p, rr, 1.0, 0.0);  // W = Y T
+      g1.pair(Y, p, OP_N, S + f.T, rr, OP_N, rr);
+      g1.close();
+      g1.task(S + f.W1, n, n, rr, 1.0, 0.0);  // W1 = Vp Y
+      g1.pair(Vp(f.i), n, OP_N, Y, p, OP_N, p);
+      g1.close();
+      cp.add(nullptr, P64, p, 0, 0, S + f.Qx, P64, p, p, rr, 2);                  // Qx = E
+      cp.add(Vp(f.i), P64, n, n, p, S + f.Yf, P64, n, n, p, 0);                   // Yf = Vp
+      g2.task(S + f.Qx, p, p, rr, -1.0, 1.0);  // Qx = E - W Y(0:r',:)^H
+      g2.pair(S + f.W, p, OP_N, Y, p, OP_H, rr);
+      g2.close();
+      g2.task(S + f.W2, n, n, rr, 1.0, 0.0);  // W2 = W1 T
+      g2.pair(S + f.W1, n, OP_N, S + f.T, rr, OP_N, rr);
+      g2.close();
+      g3.task(S + f.Z1, p, p, rr, 1.0, 0.0);  // Z1 = G' Qx
+      g3.pair(S + f.G, p, OP_N, S + f.Qx, p, OP_N, p);
+      g3.close();
+      g3.task(S + f.Yf, n, n, p, -1.0, 1.0);  // Yf = Vp - W2 Y^H
+      g3.pair(S + f.W2, n, OP_N, Y, p, OP_H, rr);
+      g3.close();
+      g4.task(S + f.Gh, rr, rr, rr, 1.0, 0.0);  // Ritz matrix Qx^H G' Qx
+      g4.pair(S + f.Qx, p, OP_H, S + f.Z1, p, OP_N, p);
+      g4.close();
+      eig.push_back(EigTask{S + f.Gh, S + f.U, (double*)(S + f.lam), rr, d_r + 2 * bt.size() + q});
+      sel.push_back(SelTask{S + f.M, (double*)(S + f.lam), d_r + bt.size() + q, n, rr, snorm(f.i), eps * eps});
+      maxr = std::max(maxr, rr);
+      g5.task(S + f.Y1, n, n, rr, 1.0, 0.0);  // Y1 = Yf(:, 0:r') U
+      g5.pair(S + f.Yf, n, OP_N, S + f.U, rr, OP_N, rr);
+      g5.close();
+    }
+    run_gemm(c, g1, P64, P64, P64, "WY 1");
+    run_copy(c, cp, "WY presets");
+    run_gemm(c, g2, P64, P64, P64, "WY 2");
+    run_gemm(c, g3, P64, P64, P64, "WY 3");
+    run_gemm(c, g4, P64, P64, P64, "ritz matrix");
+    if (!eig.empty()) {
       const int i0 = c.st.add(eig);
       c.st.upload(c);
-      ck(jacobi_eig(c.st.ptr<EigTask>(i0), (int)eig.size(), maxp, (int*)c.statusbuf.p, c.stream), "jacobi");
+      if (maxr >= 48) {
+        // large Ritz problems: one 8-CTA cluster per eigenproblem
+        const int64_t per = jacobi_cluster_scratch(maxr);
+        double* js = (double*)dev_ensure(c, c.jac_buf, (size_t)per * eig.size() * sizeof(double));
+        ck(jacobi_eig_cluster(c.st.ptr<EigTask>(i0), (int)eig.size(), maxr, 8, js, (int*)c.statusbuf.p, c.stream),
+           "jacobi (cluster)");
+      } else {
+        ck(jacobi_eig(c.st.ptr<EigTask>(i0), (int)eig.size(), maxr, (int*)c.statusbuf.p, c.stream), "jacobi");
+      }
       c.launches++;
-    }
-    run_gemm(c, gY, P64, P64, P64, "Vp*U");
-    {
-      const int i0 = c.st.add(sel);
+      const int i1 = c.st.add(sel);
       c.st.upload(c);
-      ck(select_rank(c.st.ptr<SelTask>(i0), (int)sel.size(), c.stream), "select");
+      ck(select_rank(c.st.ptr<SelTask>(i1), (int)sel.size(), c.stream), "select");
       c.launches++;
     }
+    run_gemm(c, g5, P64, P64, P64, "ritz vectors");
+    ck(cudaMemcpyAsync(r.data(), d_r + bt.size(), bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
+       "read r");
+    sweeps.resize(bt.size());
+    ck(cudaMemcpyAsync(sweeps.data(), d_r + 2 * bt.size(), bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
+       "read sweeps");
   }
-  std::vector<int> r(bt.size(), 0);
-  ck(cudaMemcpyAsync(r.data(), d_r, bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read r");
   ck(cudaStreamSynchronize(c.stream), "sync after step 0");
   c.st.begin();  // stream idle: staging can be reused
   for (size_t q = 0; q < info.size(); ++q) {
     const Info& f = info[q];
-    const int rr = std::min(std::max(r[q], 0), f.p);
+    const int rr = (f.fill && f.rp > 0) ? std::min(std::max(r[q], 0), f.rp) : 0;
+    if (f.fill && f.rp > 0) {
+      F.st_ritz_max = std::max(F.st_ritz_max, f.rp);
+      F.st_ritz_sum += f.rp;
+      F.st_ritz_n++;
+      if (!sweeps.empty()) F.st_sweeps_max = std::max(F.st_sweeps_max, sweeps[q]);
+    }
     r[q] = rr;
     F.kt[f.i] = f.k0 + rr;
     F.m[f.i] = f.n - F.kt[f.i];
@@ -321,11 +413,16 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
     const Info& f = info[q];
     const int n = f.n, m = F.m[f.i], rr = r[q];
     char* Q = P.Q + F.Q_off[f.i] * es;
-    const cd* src = f.fill ? S + f.Y : S + f.Vp;
-    // Q~ = [Y(:, r:p), B, Y(:, 0:r)]
-    qc.add(src + (size_t)rr * n, P64, n, n, m, Q, prec, n, n, m);
+    if (f.fill && f.rp > 0) {
+      // Q~ = [Y1(:, r:r'), Yf(:, r':p), B, Y1(:, 0:r)]  (eqs. 18-19)
+      const int rp = f.rp;
+      qc.add(S + f.Y1 + (size_t)rr * n, P64, n, n, rp - rr, Q, prec, n, n, rp - rr);
+      qc.add(S + f.Yf + (size_t)rp * n, P64, n, n, f.p - rp, Q + (size_t)(rp - rr) * n * es, prec, n, n, f.p - rp);
+      if (rr > 0) qc.add(S + f.Y1, P64, n, n, rr, Q + (size_t)(m + f.k0) * n * es, prec, n, n, rr);
+    } else {
+      qc.add(Vp(f.i), P64, n, n, f.p, Q, prec, n, n, f.p);
+    }
     qc.add(P.B + F.B_off[f.i], P64, n, n, f.k0, Q + (size_t)m * n * es, prec, n, n, f.k0);
-    if (rr > 0) qc.add(src, P64, n, n, rr, Q + (size_t)(m + f.k0) * n * es, prec, n, n, rr);
   }
   run_copy(c, qc, "form Q");
 
@@ -471,6 +568,24 @@ std::vector<Pair> merge_level(Ctx& c, LevelF& F, LevelF& Pn) {
     ac.add(S.fill + (F.fill_off[q] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a], F.kt[a], F.kt[b],
            d, prec, ld, F.kt[a], F.kt[b], 1);
   }
+  // complement of the padded transfer: the stored complement of T (rows of
+  // child 1 and child 2 at their places) plus one unit column per padded row
+  for (int p = 0; p < Pn.nc; ++p) {
+    const int c1 = 2 * p, c2 = 2 * p + 1, kp = Pn.k0[p], np_ = Pn.n[p], pp = np_ - kp;
+    if (pp <= 0) continue;
+    cd* V = (cd*)Pn.Vp_buf.p + Pn.Vp_off[p];
+    as.add(nullptr, P64, np_, 0, 0, V, P64, np_, np_, pp);
+    const int q = F.k0[c1] + F.k0[c2] - kp, pad1 = F.kt[c1] - F.k0[c1], pad2 = F.kt[c2] - F.k0[c2];
+    const cd* Tp = (const cd*)c.dTp.p + c.Tp_off[l - 1][p];
+    const int ldT = F.k0[c1] + F.k0[c2];
+    if (q > 0) {
+      ac.add(Tp, P64, ldT, F.k0[c1], q, V, P64, np_, F.k0[c1], q, 0);
+      ac.add(Tp + F.k0[c1], P64, ldT, F.k0[c2], q, V + F.kt[c1], P64, np_, F.k0[c2], q, 0);
+    }
+    if (pad1 > 0) ac.add(nullptr, P64, 0, 0, 0, V + F.k0[c1] + (size_t)q * np_, P64, np_, pad1, pad1, 2);
+    if (pad2 > 0)
+      ac.add(nullptr, P64, 0, 0, 0, V + F.kt[c1] + F.k0[c2] + (size_t)(q + pad1) * np_, P64, np_, pad2, pad2, 2);
+  }
   // padded transfers (eq. 23): rows of child 1, then rows of child 2
   for (int p = 0; p < Pn.nc; ++p) {
     const int c1 = 2 * p, c2 = 2 * p + 1, kp = Pn.k0[p];
@@ -594,10 +709,14 @@ void factorize(Ctx& c, double eps, int prec) {
       cb.add((const cd*)c.dD.p + c.D_off[q], P64, n[a], n[a], n[b], (char*)F.near_buf.p + F.near_off[q] * es, prec,
              n[a], n[a], n[b]);
     }
-    for (int t = 0; t < (1 << L); ++t)
+    for (int t = 0; t < (1 << L); ++t) {
       if (F.k0[t] > 0)
         cb.add((const cd*)c.dV.p + c.V_off[t], P64, n[t], n[t], F.k0[t], (cd*)F.B_buf.p + F.B_off[t], P64, n[t], n[t],
                F.k0[t]);
+      if (n[t] > F.k0[t])
+        cb.add((const cd*)c.dVp.p + c.Vp_off[t], P64, n[t], n[t], n[t] - F.k0[t], (cd*)F.Vp_buf.p + F.Vp_off[t], P64,
+               n[t], n[t], n[t] - F.k0[t]);
+    }
     run_copy(c, cb, "leaf init");
   }
   for (int li = 0; li <= L - l0; ++li) {

@@ -33,10 +33,15 @@ __device__ __forceinline__ void store_val(E* p, R re, R im) {
 
 constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
 
+template <class R> struct CxOf;
+template <> struct CxOf<double> { using T = cd; };
+template <> struct CxOf<float> { using T = cf; };
+
 template <class EI, class R, class EO>
 __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
                                             const GemmPair* __restrict__ pairs,
-                                            const GemmTile* __restrict__ tiles) {
+                                            const GemmTile* __restrict__ tiles,
+                                            typename CxOf<R>::T* __restrict__ ws) {
   __shared__ R As_r[BK][BM], As_i[BK][BM];
   __shared__ R Bs_r[BK][BN], Bs_i[BK][BN];
   const GemmTile tl = tiles[blockIdx.x];
@@ -49,13 +54,22 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc_r[i][j] = acc_i[i][j] = (R)0;
 
+  // this tile's share of the concatenated K range of all pairs
+  const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
+  const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
+  int64_t koff = 0;
   for (int pi = tk.p0; pi < tk.p0 + tk.np; ++pi) {
     const GemmPair pr = pairs[pi];
+    const int64_t kb = koff;
+    koff += pr.K;
+    if (koff <= klo || kb >= khi) continue;
+    const int kbeg = (int)(klo > kb ? klo - kb : 0);
+    const int kend = (int)(khi - kb < pr.K ? khi - kb : pr.K);
     const EI* A = (const EI*)pr.A;
     const EI* B = (const EI*)pr.B;
     const bool at = (pr.opA == OP_T || pr.opA == OP_H);
     const bool bt = (pr.opB == OP_T || pr.opB == OP_H);
-    for (int k0 = 0; k0 < pr.K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
       // A tile: BM x BK of op(A)
 #pragma unroll
       for (int r = 0; r < (BM * BK) / NT; ++r) {
@@ -63,7 +77,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
         int i, k;
         if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
         R re = 0, im = 0;
-        if (m0 + i < tk.M && k0 + k < pr.K) load_op<EI, R>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
+        if (m0 + i < tk.M && k0 + k < kend) load_op<EI, R>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
         As_r[k][i] = re;
         As_i[k][i] = im;
       }
@@ -74,7 +88,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
         int k, j;
         if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
         R re = 0, im = 0;
-        if (n0 + j < tk.N && k0 + k < pr.K) load_op<EI, R>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
+        if (n0 + j < tk.N && k0 + k < kend) load_op<EI, R>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
         Bs_r[k][j] = re;
         Bs_i[k][j] = im;
       }
@@ -96,6 +110,25 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
       }
       __syncthreads();
     }
+  }
+  if (tk.nk > 1) {
+    // partial sums of this chunk, unscaled
+    typename CxOf<R>::T* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty + 16 * i;
+      if (m >= tk.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n >= tk.N) continue;
+        typename CxOf<R>::T v;
+        v.re = acc_r[i][j];
+        v.im = acc_i[i][j];
+        W[(int64_t)m + (int64_t)n * tk.M] = v;
+      }
+    }
+    return;
   }
   EO* C = (EO*)tk.C;
   const R al = (R)tk.alpha, be = (R)tk.beta;
@@ -119,24 +152,94 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
   }
 }
 
+template <class R, class EO>
+__global__ void k_gemm_reduce(const GemmTask* __restrict__ tasks, const typename CxOf<R>::T* __restrict__ ws) {
+  const GemmTask tk = tasks[blockIdx.y];
+  if (tk.nk <= 1) return;
+  const int64_t mn = (int64_t)tk.M * tk.N;
+  EO* C = (EO*)tk.C;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+    R sr = 0, si = 0;
+    for (int kc = 0; kc < tk.nk; ++kc) {
+      const typename CxOf<R>::T v = ws[tk.ws_off + kc * mn + e];
+      sr += v.re;
+      si += v.im;
+    }
+    const int m = (int)(e % tk.M), n = (int)(e / tk.M);
+    EO* p = C + (size_t)m + (size_t)n * tk.ldc;
+    R re = (R)tk.alpha * sr, im = (R)tk.alpha * si;
+    if (tk.beta != 0.0) {
+      const EO c = *p;
+      re = fma((R)tk.beta, (R)c.re, re);
+      im = fma((R)tk.beta, (R)c.im, im);
+    }
+    store_val<EO, R>(p, re, im);
+  }
+}
+
+template <class EO>
+__global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks) {
+  const GemmTask tk = tasks[blockIdx.y];
+  if (!tk.herm) return;
+  const int64_t mn = (int64_t)tk.M * tk.N;
+  EO* C = (EO*)tk.C;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % tk.M), j = (int)(e / tk.M);
+    if (i / BM > j / BN) {
+      EO v = C[(size_t)j + (size_t)i * tk.ldc];
+      v.im = -v.im;
+      C[(size_t)i + (size_t)j * tk.ldc] = v;
+    }
+  }
+}
+
 }  // namespace
 
 int gemm_tile_m(int) { return BM; }
 int gemm_tile_n(int) { return BN; }
 
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
-                 int pin, int pout, int pacc, cudaStream_t s) {
+                 int pin, int pout, int pacc, void* ws, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (pin == P64 && pacc == P64 && pout == P64)
-    k_gemm<cd, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+    k_gemm<cd, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pin == P32 && pacc == P32 && pout == P32)
-    k_gemm<cf, float, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+    k_gemm<cf, float, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
   else if (pin == P32 && pacc == P64 && pout == P64)
-    k_gemm<cf, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+    k_gemm<cf, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pin == P64 && pacc == P64 && pout == P32)
-    k_gemm<cd, double, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles);
+    k_gemm<cd, double, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn, int pout, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  int gx = (maxmn + 255) / 256;
+  if (gx > 64) gx = 64;
+  if (gx < 1) gx = 1;
+  for (int t0 = 0; t0 < ntasks; t0 += 65535) {
+    const dim3 grid(gx, ntasks - t0 < 65535 ? ntasks - t0 : 65535);
+    if (pout == P64) k_gemm_mirror<cd><<<grid, 256, 0, s>>>(d_tasks + t0);
+    else k_gemm_mirror<cf><<<grid, 256, 0, s>>>(d_tasks + t0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_reduce(const GemmTask* d_tasks, int ntasks, int maxmn, int pout, int pacc, const void* ws,
+                        cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  int gx = (maxmn + 255) / 256;
+  if (gx > 64) gx = 64;
+  if (gx < 1) gx = 1;
+  for (int t0 = 0; t0 < ntasks; t0 += 65535) {
+    const dim3 grid(gx, ntasks - t0 < 65535 ? ntasks - t0 : 65535);
+    if (pacc == P64 && pout == P64) k_gemm_reduce<double, cd><<<grid, 256, 0, s>>>(d_tasks + t0, (const cd*)ws);
+    else if (pacc == P64 && pout == P32) k_gemm_reduce<double, cf><<<grid, 256, 0, s>>>(d_tasks + t0, (const cd*)ws);
+    else if (pacc == P32 && pout == P32) k_gemm_reduce<float, cf><<<grid, 256, 0, s>>>(d_tasks + t0, (const cf*)ws);
+    else return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

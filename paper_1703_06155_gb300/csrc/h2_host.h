@@ -4,6 +4,7 @@
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <string>
 #include <unordered_map>
@@ -52,11 +53,24 @@ struct H2Host {
   std::vector<std::vector<std::vector<cplx>>> S;     // [l][adm idx] kt x ks
   std::vector<std::vector<cplx>> D;                  // [inad[L] idx]
   std::vector<double> dscale;                        // global order (size N)
+  bool symmetric = false;                            // Z^T = Z (h2_build; checked by h2_load)
 };
 
-// Host H^2 construction (proxy + interpolative decomposition), h2_build.
+// Far-field sample Grams of one level: G[t] = Z(rows[t], F) Z(rows[t], F)^H,
+// rows in tree positions, F the tree-order ranges (start, count) of t.
+using GramFn = std::function<void(int level, const std::vector<std::vector<int64_t>>& rows,
+                                  const std::vector<std::vector<int64_t>>& ranges,
+                                  std::vector<std::vector<cplx>>& G)>;
+
+// H^2 construction (exact far-field sample + interpolative decomposition),
+// h2_build.  `gram` computes the sample Grams (GPU kernel, or the host loop
+// of host_only contexts).
 std::string build_h2(const double* pts, int64_t N, double k, double h, const double* chi, int64_t chi_len,
-                     double eps, const h2_opts& o, H2Host& H);
+                     double eps, const h2_opts& o, H2Host& H, const GramFn& gram);
+std::vector<cplx> host_complement(const std::vector<cplx>& B, int n, int k);
+void host_gram(const double* pts_tree, const double* sq_tree, double k, double w,
+               const std::vector<std::vector<int64_t>>& rows, const std::vector<std::vector<int64_t>>& ranges,
+               std::vector<std::vector<cplx>>& G);
 
 // ------------------------------------------------------------------------
 // Device memory: grow-only buffers owned by the context.
@@ -130,11 +144,14 @@ struct LevelF {
   std::vector<size_t> fill_off;
   std::vector<char> fill_live;
   std::vector<char> fill_is_adm;
-  std::vector<size_t> B_off, Q_off, inv_off, piv_off;
+  std::vector<size_t> B_off, Q_off, inv_off, piv_off, Vp_off;
   std::vector<double> snorm2;
-  DevBuf near_buf, fill_buf, B_buf, Q_buf, inv_buf, piv_buf, Ub_buf;
+  DevBuf near_buf, fill_buf, B_buf, Q_buf, inv_buf, piv_buf, Ub_buf, Vp_buf;
   std::vector<size_t> Ub_off;                  // per (cluster, nbr) for eq. 35
   std::vector<int> nbr_first;                  // first (cluster, nbr) index
+  // Step-0 statistics: Ritz subspace sizes and Jacobi sweeps
+  int st_ritz_max = 0, st_ritz_n = 0, st_sweeps_max = 0;
+  long st_ritz_sum = 0;
   // solve-time vector layout
   std::vector<int64_t> voff;                   // cluster offsets in level vector
   int64_t vlen = 0;
@@ -163,8 +180,9 @@ struct Ctx {
   std::string err;
   size_t dev_bytes = 0, dev_peak = 0;
   // device copy of the H^2 (FP64)
-  DevBuf dV, dT, dS, dD, dperm, dscale;
-  std::vector<size_t> V_off;                        // per leaf
+  DevBuf dV, dT, dS, dD, dperm, dscale, dVp, dTp;
+  std::vector<size_t> V_off, Vp_off;                // per leaf
+  std::vector<std::vector<size_t>> Tp_off;          // complements of T
   std::vector<std::vector<size_t>> T_off, S_off;    // [l][c] / [l][adm idx]
   std::vector<size_t> D_off;                        // per inad[L] pair
   std::vector<std::unordered_map<int64_t, int>> adm_id;  // [l] pair -> idx
@@ -175,7 +193,7 @@ struct Ctx {
   std::vector<LevelF> lev;  // lev[0] = leaf level L, ..., last = l0
   RootF root;
   // scratch
-  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf;
+  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf;
   Stager st;
   Stats stats;
   int64_t launches = 0;

@@ -28,8 +28,13 @@ struct GemmTask {
   int ldc, M, N;
   int p0, np;       // pairs [p0, p0+np)
   double alpha, beta;
+  int nk;           // split-K chunks (1: direct)
+  int64_t ws_off;   // split-K workspace offset (accumulator complex elements)
+  int ksz;          // split-K chunk length in the concatenated K of the pairs
+  int herm;         // 1: C is Hermitian, only tiles tm <= tn are computed and
+                    // gemm_mirror fills the rest
 };
-struct GemmTile { int task, tm, tn; };
+struct GemmTile { int task, tm, tn, kc; };
 
 // ---- in-place apply of a small square matrix to a panel -------------------
 //  left : X[r_lo:p, 0:w] = op(A)[r_lo:p, 0:p] * X[0:p, 0:w]
@@ -53,7 +58,7 @@ struct CopyTask {
   int lds, ldd, rows, cols;
   int srows, scols;        // source extent; entries outside it read as zero
   int src_prec, dst_prec;  // Prec of each side (complex64 or complex128)
-  int mode;                // 0 assign, 1 accumulate
+  int mode;                // 0 assign, 1 accumulate, 2 identity (src unused)
   int transpose;           // 1: dst = src^T (src is cols x rows)
   double alpha;
 };
@@ -75,6 +80,7 @@ struct EigTask {
   cd* U;
   double* lam;
   int p;
+  int* sweeps;  // may be NULL: number of sweeps used
 };
 
 // ---- partial-pivoting LU of one m x m block + explicit triangular inverses
@@ -95,6 +101,18 @@ struct SelTask {
   double snorm2, eps2;
 };
 
+// ---- Step 0 subspace: pivoted Cholesky of G' down to thr/(10p), Householder
+//  QR of the pivoted columns; Q = I - Y T Y^H, first r' columns Qx.
+struct PcholTask {
+  cd* G;          // p x p Gram in complement coordinates (ld p), preserved
+  const cd* M;    // n x n fill-in Gram (trace -> nu^2), may be NULL
+  cd* L;          // p x p scratch; on exit Y (p x r', unit lower trapezoidal)
+  cd* T;          // r' x r' upper triangular (ld r') -- sized p x p by caller
+  int* rout;      // r'
+  int p, n;
+  double snorm2, eps2;
+};
+
 // ---- blocked LU of the final block: one tall panel with partial pivoting --
 //  A[row0:row0+nrows, col0:col0+kb] factorized in place, ipiv[j] = absolute
 //  row swapped with row0+j, Linv = (unit lower L11)^{-1}, Uinv = U11^{-1}.
@@ -106,12 +124,30 @@ struct PanelTask {
   int lda, row0, col0, nrows, kb;
 };
 
+// ---- far-field sample Gram of the H^2 construction ------------------------
+//  G = Z(rows, F) Z(rows, F)^H over the tree-order column ranges F; only the
+//  tiles with tm <= tn (upper triangle) are written.
+struct KGramTask {
+  const int64_t* rows;    // nr tree positions
+  const int64_t* ranges;  // nranges (start, count) pairs of tree positions
+  cd* G;                  // nr x nr (ld nr)
+  int nr, nranges;
+};
+struct KGramTile { int task, tm, tn; };
+
 // ---- launches (all on `s`, return cudaGetLastError()) ---------------------
 // Element precision of A, B (inputs) and C (output), and the precision the
 // products are accumulated in.
+// split-K: tasks with nk > 1 write partial tiles to `ws` (accumulator
+// precision), then gemm_reduce sums them in a fixed order into C.
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
-                 int pacc, cudaStream_t s);
+                 int pacc, void* ws, cudaStream_t s);
+cudaError_t gemm_reduce(const GemmTask* d_tasks, int ntasks, int maxmn,
+                        int pout, int pacc, const void* ws, cudaStream_t s);
+// C[i, j] = conj(C[j, i]) for the entries of tiles below the diagonal
+cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn,
+                        int pout, cudaStream_t s);
 int gemm_tile_m(int pacc);
 int gemm_tile_n(int pacc);
 
@@ -127,15 +163,26 @@ cudaError_t householder_complement(const HhTask* d_tasks, int ntasks,
                                    cudaStream_t s);
 cudaError_t jacobi_eig(const EigTask* d_tasks, int ntasks, int maxp,
                        int* d_status, cudaStream_t s);
+// the same decomposition, one thread-block cluster of `csize` CTAs per task
+int64_t jacobi_cluster_scratch(int maxp);  // doubles per task
+cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
+                               int csize, double* d_scratch, int* d_status,
+                               cudaStream_t s);
 cudaError_t lu_small(const LuTask* d_tasks, int ntasks, int prec,
                      int* d_status, cudaStream_t s);
 cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
+cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, cudaStream_t s);
 cudaError_t lu_panel(const PanelTask* d_task, int prec, int* d_status,
                      cudaStream_t s);
 // apply the row interchanges ipiv[0:kb] (rows row0+j <-> ipiv[j]) to the
 // columns [c0, c1) of A (ld lda), in order (forward) or reversed
 cudaError_t swap_rows(void* A, int lda, const int* ipiv, int row0, int kb,
                       int c0, int c1, int prec, int reverse, cudaStream_t s);
+
+// pts / sq in tree order; w = s k^2 h^3 / (4 pi)
+cudaError_t kernel_gram(const KGramTask* d_tasks, const KGramTile* d_tiles,
+                        int ntiles, const double* d_pts, const double* d_sq,
+                        double k, double w, cudaStream_t s);
 
 // A[i, i] = v for i < n (other entries untouched)
 cudaError_t set_diag(void* A, int lda, int n, int prec, double v, cudaStream_t s);
