@@ -171,6 +171,30 @@ h2_status h2_matvec(h2_ctx* ctx, const void* x, void* y, int nrhs,
                     unsigned flags, void* stream);
 
 /*
+ * h2_matvec_noalloc - the product of h2_matvec (y = A x, or y = A^H x with
+ * H2_ADJOINT) for callers that must not allocate device memory during the
+ * call: for example a host thread in a real-time loop, or code whose device
+ * memory is fully reserved up front, which can only call into a context set
+ * up earlier.  The paper has no counterpart; this is a runtime variant of
+ * h2_matvec.
+ *   x, y      DEVICE, N x nrhs complex128, column-major, global order; must
+ *             not alias (host buffers are not accepted)
+ *   flags     0 or H2_ADJOINT
+ * All temporaries (permuted vectors, level coefficients, task descriptors)
+ * live in one static device array of 32 MiB that every GPU which loads the
+ * library holds until the process exits.  Sizes whose temporaries exceed it
+ * (about 2 N nrhs + 2 (sum of ranks) nrhs complex128 plus the task lists)
+ * are rejected with H2_EINVAL and a message.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array, which keeps the last
+ * call's contents (every entry a call reads it writes first), so calls that
+ * overlap on the GPU (other streams, other threads) race: serialize them.
+ */
+h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* x, void* y, int nrhs,
+                            unsigned flags, void* stream);
+
+/*
  * h2_export - copy the H^2 representation out in the h2_load layout (HOST
  * arrays, caller-allocated).  Call h2_export_sizes first: it returns the
  * element counts (complex entries for V, T, S, D; pairs for adm / near).

@@ -23,7 +23,8 @@ H2_ETIMEOUT, H2_ECUDA, H2_EINTERNAL, H2_ESTATE = -5, -6, -7, -8
 H2_FP64, H2_MIXED = 0, 1
 H2_ADJOINT, H2_REFINE, H2_USE_INVERSE, H2_HOST = 1, 2, 4, 8
 SYMBOLS = ("h2_default_opts", "h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec",
-           "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error", "h2_status_string", "h2_destroy")
+           "h2_matvec_noalloc", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error", "h2_status_string",
+           "h2_destroy")
 
 
 class h2_opts(ctypes.Structure):
@@ -61,6 +62,7 @@ def lib():
     L.h2_invert.argtypes = [P]
     L.h2_solve.argtypes = [P, P, P, I, ctypes.c_uint, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.h2_matvec.argtypes = [P, P, P, I, ctypes.c_uint, P]
+    L.h2_matvec_noalloc.argtypes = [P, P, P, I, ctypes.c_uint, P]
     L.h2_export_sizes.argtypes = [P] + [ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I)] + \
         [ctypes.POINTER(I64)] * 6
     L.h2_export.argtypes = [P] * 12
@@ -71,8 +73,8 @@ def lib():
     L.h2_status_string.restype = ctypes.c_char_p
     L.h2_destroy.argtypes = [P]
     L.h2_destroy.restype = None
-    for name in ("h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec", "h2_export_sizes",
-                 "h2_export", "h2_stats"):
+    for name in ("h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec", "h2_matvec_noalloc",
+                 "h2_export_sizes", "h2_export", "h2_stats"):
         getattr(L, name).restype = I
     _lib = L
     return L

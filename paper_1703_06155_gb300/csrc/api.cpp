@@ -20,6 +20,11 @@ struct h2_ctx {
   DevBuf bpts, bsq, bflat, bG;  // construction scratch
 };
 
+namespace h2 {
+Ctx* ctx_core(h2_ctx* x) { return &x->c; }
+const double* ctx_invscale(h2_ctx* x) { return (const double*)x->invscale.p; }
+}  // namespace h2
+
 namespace {
 
 thread_local std::string g_err;

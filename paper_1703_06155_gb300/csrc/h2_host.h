@@ -199,6 +199,10 @@ struct Ctx {
   int64_t launches = 0;
 };
 
+// accessors of the ABI context object (defined with it in api.cpp)
+Ctx* ctx_core(h2_ctx* x);
+const double* ctx_invscale(h2_ctx* x);
+
 void upload_h2(Ctx& c);
 void factorize(Ctx& c, double eps, int prec);
 void invert(Ctx& c);
