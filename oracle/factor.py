@@ -35,13 +35,19 @@ Readings of the paper (each listed in the design doc):
      the complement), so eqs. (7)-(8) hold to round-off.
   R5 partial pivoting inside the m_i x m_i block (largest |z|, lowest row).
   R6 clusters of one colour of the near-field graph are processed as one
-     batch (the 'colored' order); 'natural' is the paper's left-to-right sweep.
+     batch (the 'colored' order): Steps 0-1 of every cluster of the batch read
+     the state at the start of the batch, Step 2 transforms all block rows of
+     the batch and then all block columns, Step 3 forms all partial LUs and
+     panels and then all Schur updates.  Clusters of one colour are never near
+     neighbours, so this equals a sequential sweep up to the order in which
+     fill-ins of non-neighbours are transformed.  'natural' (one cluster per
+     batch) is the paper's left-to-right sweep.
 """
 import numpy as np
 import scipy.linalg as sla
 
 from . import dense
-from .tree import elimination_order
+from .tree import elimination_batches
 
 
 class ClusterFactor:
@@ -94,7 +100,8 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128):
         near_set = set(part.inad[l])
         adm_set = set(part.adm[l])
         nbrs = part.near_lists(l)
-        order = elimination_order(nbrs, ordering)
+        batches = elimination_batches(nbrs, ordering)
+        order = [i for bt in batches for i in bt]
         nc = 2 ** l
         k0 = np.array([B[c].shape[1] for c in range(nc)], dtype=np.int64)
         # sum of ||S||_F^2 over admissible blocks of row and column c (R2)
@@ -119,86 +126,99 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128):
         def act(c):
             return slice(int(m[c]), int(n[c])) if done[c] else slice(0, int(n[c]))
 
-        for i in order:
-            ni = int(n[i])
-            Bi = B[i]
-            ki = Bi.shape[1]
-            # ---- Step 0: update the cluster basis from stored fill-ins ----
-            # The complement of the incoming basis, from a Householder QR of
-            # B_i, gives G_i of eq. (16)/(25) in complement coordinates:
-            # G_i = Vp (Vp^H M Vp) Vp^H with M = sum F F^H (+ column side, R1),
-            # because I - B B^H = Vp Vp^H.  Its eigenvectors Vp U are then
-            # orthogonal to B_i by construction.
-            if ki == 0:
-                Vp = np.eye(ni, dtype=np.complex128)
-            else:
-                Qf, _ = np.linalg.qr(Bi, mode="complete")
-                Vp = Qf[:, ki:]
-            rows = [(k, fill[(i, k)]) for k in fill_rows[i]]
-            cols = [(k, fill[(k, i)]) for k in fill_cols[i]]
-            Vadd = np.zeros((ni, 0), dtype=np.complex128)
-            Vrest = Vp
-            if (rows or cols) and ni > ki:
-                M = np.zeros((ni, ni), dtype=np.complex128)
-                for k, Fm in rows:
-                    Fa = Fm[:, act(k)]
-                    M += Fa @ Fa.conj().T                       # eq. (16) inner sum
-                for k, Fm in cols:
-                    Fa = Fm[act(k), :]
-                    M += Fa.T @ Fa.conj()                       # column side (R1)
-                Gc = Vp.conj().T @ M @ Vp                       # eq. (16)/(25)
-                Gc = 0.5 * (Gc + Gc.conj().T)
-                w, U = np.linalg.eigh(Gc)                       # eq. (17)/(26)
-                nu2 = snorm2[i] + float(np.real(np.trace(M)))
-                thr = eps * eps * nu2
-                r = int(np.sum(w > thr))
-                if r:
-                    Vadd = Vp @ U[:, ::-1][:, :r]               # descending eigenvalues
-                    Vrest = Vp @ U[:, ::-1][:, r:]
-                    stats["rank_growth"] += r
-            Bi = np.hstack([Bi, Vadd])                          # eq. (18)/(27)
-            k = Bi.shape[1]
-            kt[i] = k
-            mi = ni - k
-            # ---- Step 1: complement, Q~_i = [V~^perp, V~] (eq. 19, R4) ----
-            Q = np.hstack([Vrest, Bi])
-            B[i] = Bi
-            # ---- Step 2: Z_cur <- Q_i^H Z_cur conj(Q_i) (eq. 5, Alg. 3) ----
-            Qh, Qb = Q.conj().T, Q.conj()
-            for j in nbrs[i]:
-                if j == i:
-                    near[(i, i)] = _round(Qh @ near[(i, i)] @ Qb, bulk)
+        for bt in batches:
+            # ---- Steps 0 and 1 for every cluster of the batch; they read the
+            # state at the start of the batch (R6) ----
+            step01 = {}
+            for i in bt:
+                ni = int(n[i])
+                Bi = B[i]
+                ki = Bi.shape[1]
+                # Step 0: the complement of the incoming basis, from a
+                # Householder QR of B_i, gives G_i of eq. (16)/(25) in
+                # complement coordinates: G_i = Vp (Vp^H M Vp) Vp^H with
+                # M = sum F F^H (+ column side, R1), because I - B B^H = Vp Vp^H.
+                # Its eigenvectors Vp U are orthogonal to B_i by construction.
+                if ki == 0:
+                    Vp = np.eye(ni, dtype=np.complex128)
                 else:
-                    cj = act(j)
-                    X = near[(i, j)]
-                    X[:, cj] = _round(Qh @ X[:, cj], bulk)
-                    X = near[(j, i)]
-                    X[cj, :] = _round(X[cj, :] @ Qb, bulk)
-            for kk in fill_rows[i]:
-                X = fill[(i, kk)]
-                ck = act(kk)
-                X[:, ck] = _round(Qh @ X[:, ck], bulk)
-            for kk in fill_cols[i]:
-                X = fill[(kk, i)]
-                ck = act(kk)
-                X[ck, :] = _round(X[ck, :] @ Qb, bulk)
-            # ---- Step 3: partial LU of the first m_i unknowns (Alg. 4) ----
-            cf = ClusterFactor()
-            cf.n, cf.kt, cf.m, cf.Q = ni, k, mi, Q
-            cf.Up, cf.Lp = {}, {}
-            cf.LU, cf.piv = None, None
-            if mi > 0:
-                LU, piv = dense.lu(near[(i, i)][:mi, :mi])     # eq. (11)
-                LU = _round(LU, bulk)
-                cf.LU, cf.piv = LU, piv
-                ps = {}
+                    Qf, _ = np.linalg.qr(Bi, mode="complete")
+                    Vp = Qf[:, ki:]
+                rows = [(k, fill[(i, k)]) for k in fill_rows[i]]
+                cols = [(k, fill[(k, i)]) for k in fill_cols[i]]
+                Vadd = np.zeros((ni, 0), dtype=np.complex128)
+                Vrest = Vp
+                if (rows or cols) and ni > ki:
+                    M = np.zeros((ni, ni), dtype=np.complex128)
+                    for k, Fm in rows:
+                        Fa = Fm[:, act(k)]
+                        M += Fa @ Fa.conj().T                   # eq. (16) inner sum
+                    for k, Fm in cols:
+                        Fa = Fm[act(k), :]
+                        M += Fa.T @ Fa.conj()                   # column side (R1)
+                    Gc = Vp.conj().T @ M @ Vp                   # eq. (16)/(25)
+                    Gc = 0.5 * (Gc + Gc.conj().T)
+                    w, U = np.linalg.eigh(Gc)                   # eq. (17)/(26)
+                    nu2 = snorm2[i] + float(np.real(np.trace(M)))
+                    thr = eps * eps * nu2
+                    r = int(np.sum(w > thr))
+                    if r:
+                        Vadd = Vp @ U[:, ::-1][:, :r]           # descending eigenvalues
+                        Vrest = Vp @ U[:, ::-1][:, r:]
+                        stats["rank_growth"] += r
+                Bn = np.hstack([Bi, Vadd])                      # eq. (18)/(27)
+                # Step 1: complement, Q~_i = [V~^perp, V~] (eq. 19, R4)
+                step01[i] = (Bn, np.hstack([Vrest, Bn]))
+            for i in bt:
+                B[i] = step01[i][0]
+                kt[i] = B[i].shape[1]
+            # ---- Step 2: Z_cur <- Q_i^H Z_cur conj(Q_i) (eq. 5, Alg. 3):
+            # block rows of the batch first, then block columns ----
+            for i in bt:
+                Qh = step01[i][1].conj().T
                 for j in nbrs[i]:
-                    cs = slice(mi, ni) if j == i else act(j)
-                    Uj = _round(_linv_p(LU, piv, near[(i, j)][:mi, cs]), bulk)   # Alg. 4 l.2
-                    Lj = _round(_x_uinv(near[(j, i)][cs, :mi], LU), bulk)       # Alg. 4 l.3
-                    cf.Up[j] = (Uj, cs)
-                    cf.Lp[j] = (Lj, cs)
-                    ps[j] = cs
+                    X = near[(i, j)]
+                    cj = slice(0, int(n[i])) if j == i else act(j)
+                    X[:, cj] = _round(Qh @ X[:, cj], bulk)
+                for kk in fill_rows[i]:
+                    X = fill[(i, kk)]
+                    ck = act(kk)
+                    X[:, ck] = _round(Qh @ X[:, ck], bulk)
+            for i in bt:
+                Qb = step01[i][1].conj()
+                for j in nbrs[i]:
+                    X = near[(j, i)]
+                    cj = slice(0, int(n[i])) if j == i else act(j)
+                    X[cj, :] = _round(X[cj, :] @ Qb, bulk)
+                for kk in fill_cols[i]:
+                    X = fill[(kk, i)]
+                    ck = act(kk)
+                    X[ck, :] = _round(X[ck, :] @ Qb, bulk)
+            # ---- Step 3: partial LU and panels of the batch, then the Schur
+            # updates (Alg. 4) ----
+            cfs = {}
+            for i in bt:
+                ni = int(n[i])
+                mi = ni - int(kt[i])
+                cf = ClusterFactor()
+                cf.n, cf.kt, cf.m, cf.Q = ni, int(kt[i]), mi, step01[i][1]
+                cf.Up, cf.Lp = {}, {}
+                cf.LU, cf.piv = None, None
+                if mi > 0:
+                    LU, piv = dense.lu(near[(i, i)][:mi, :mi])  # eq. (11)
+                    LU = _round(LU, bulk)
+                    cf.LU, cf.piv = LU, piv
+                    for j in nbrs[i]:
+                        cs = slice(mi, ni) if j == i else act(j)
+                        Uj = _round(_linv_p(LU, piv, near[(i, j)][:mi, cs]), bulk)   # Alg. 4 l.2
+                        Lj = _round(_x_uinv(near[(j, i)][cs, :mi], LU), bulk)       # Alg. 4 l.3
+                        cf.Up[j] = (Uj, cs)
+                        cf.Lp[j] = (Lj, cs)
+                cfs[i] = cf
+            for i in bt:
+                cf = cfs[i]
+                if cf.m == 0:
+                    continue
                 for j in nbrs[i]:                               # Alg. 4 l.4, eq. (12)
                     Lj, rs = cf.Lp[j]
                     for kk in nbrs[i]:
@@ -215,9 +235,10 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128):
                                 if (j, kk) not in adm_set:
                                     stats["pushed_blocks"] += 1
                             fill[(j, kk)][rs, cs] -= upd
-            m[i] = mi
-            done[i] = True
-            lev.cl[i] = cf
+            for i in bt:
+                m[i] = cfs[i].m
+                done[i] = True
+                lev.cl[i] = cfs[i]
         lev.kt = kt.copy()
         stats["kt_max"] = int(kt.max()) if nc else 0
         stats["n_max"] = int(n.max()) if nc else 0

@@ -115,6 +115,17 @@ def greedy_colouring(nbrs):
     return col
 
 
+def elimination_batches(nbrs, ordering):
+    """Clusters grouped into elimination batches: 'natural' = one cluster per
+    batch in index order (the left-to-right sweep of Sec. III); 'colored' =
+    the colour classes of the near-field graph in increasing colour."""
+    n = len(nbrs)
+    if ordering == "natural":
+        return [[i] for i in range(n)]
+    col = greedy_colouring(nbrs)
+    return [[i for i in range(n) if col[i] == c] for c in range(max(col) + 1 if n else 0)]
+
+
 def elimination_order(nbrs, ordering):
     """'natural': left-to-right sweep of Sec. III (i = 1..2^l);
     'colored': colour classes in increasing colour, each in increasing index."""
