@@ -103,6 +103,35 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def fp_peaks(clocks):
+    """Peak FP64 / FP32 (non-tensor) rates of the GB300 from unit counts and
+    the SM clock: 152 SMs, 2 FP64 FMA and 128 FP32 FMA per SM per clock."""
+    f = (clocks or {}).get("sm_max_mhz") or 2070.0
+    return {"fp64": 152 * 2 * 2 * f * 1e6 / 1e12, "fp32": 152 * 128 * 2 * f * 1e6 / 1e12, "mhz": f}
+
+
+def roofline(st, clocks):
+    """Roofline entry for the kernel class with the most device time among the
+    classes with an algorithmic flop count (per-launch CUDA events of the last
+    timed step, library profiling mode)."""
+    kern = st.get("kernels", {})
+    cands = [(k, v) for k, v in kern.items() if v.get("flops", 0) > 0 and v["ms"] > 0]
+    if not cands:
+        return None
+    k, v = max(cands, key=lambda kv: kv[1]["ms"])
+    pk = fp_peaks(clocks)
+    # Step-0 Grams and the Ritz / WY products accumulate in FP64; the bulk
+    # (Schur, transforms, panels) runs in complex64 on the FP32 pipe
+    fp64 = any(t in k for t in ("gram", "Vp", "WY", "ritz", "matvec", "root")) or st.get("prec") == "fp64"
+    peak = pk["fp64"] if fp64 else pk["fp32"]
+    achieved = v["flops"] / (v["ms"] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "launches": v["launches"],
+            "avg_launch_ms": v["ms"] / v["launches"],
+            "peak_source": "derived: 152 SM x %s FMA/clk x 2 flops x %.0f MHz (%s)" % (
+                "2 FP64" if fp64 else "128 FP32", pk["mhz"], "FP64 pipe" if fp64 else "FP32 pipe")}
+
+
 # --------------------------------------------------------------- oracle ---
 
 def oracle_sample(args, repeat=1):
@@ -174,7 +203,7 @@ def run_ours(args):
     pts = inputs.grid_points(args.grid, H)
     N = len(pts)
     t0 = time.perf_counter()
-    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream)
+    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream, profile=1)
     t_build = time.perf_counter() - t0
     b_host = inputs.rhs_gaussian(N, args.nrhs, args.seed + rank)  # independent instance per rank
     b = torch.from_numpy(b_host).to("cuda")
@@ -216,6 +245,7 @@ def run_ours(args):
         ms = float(t.item())
     st = A.stats()
     solve_info = dict(A.last_solve)
+    roof = roofline(st, cs.summary())
     # residual of the result against the H^2 matrix (FP64 matvec)
     r = A.matvec(x) - b
     res = float(torch.linalg.norm(r) / torch.linalg.norm(b))
@@ -253,6 +283,9 @@ def run_ours(args):
         "e2e": {"value": world * N / (e_ms / 1e3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
         "clocks": cs.summary(),
+        "roofline": roof,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
+                    sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:12]},
     }
     if args.json_extra:
         line["stats"] = st

@@ -71,6 +71,10 @@ typedef struct {
   int host_only;         /* 1: h2_build keeps the representation on the host
                             only (no GPU needed); such a context allows
                             h2_export, h2_stats and h2_destroy only         */
+  int profile;           /* 1: bracket every kernel launch with CUDA events
+                            on the call's stream and report per-kernel-class
+                            launches, device time and algorithmic flops in
+                            h2_stats ("kernels"); 0 (default): off          */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */

@@ -161,6 +161,7 @@ void h2_default_opts(h2_opts* o) {
   o->proxy_radius = 3.0;
   o->arena_cap_bytes = 0;
   o->host_only = 0;
+  o->profile = 0;
 }
 
 const char* h2_status_string(int s) {
@@ -622,6 +623,7 @@ h2_status h2_solve(h2_ctx* ctx, const void* b, void* xo, int nrhs, unsigned flag
     }
     if (flags & H2_HOST) ck(cudaMemcpyAsync(xo, dx, bytes, cudaMemcpyDeviceToHost, c.stream), "x D2H");
     ck(cudaStreamSynchronize(c.stream), "solve sync");
+    prof_resolve(c);
     c.stats.launches_solve = c.launches - l0;
     c.stats.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
@@ -655,6 +657,7 @@ h2_status h2_matvec(h2_ctx* ctx, const void* xi, void* y, int nrhs, unsigned fla
     apply_A(ctx, dx, dy, nrhs, flags & H2_ADJOINT);
     if (flags & H2_HOST) ck(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, c.stream), "y D2H");
     ck(cudaStreamSynchronize(c.stream), "matvec sync");
+    prof_resolve(c);
   });
 }
 
@@ -698,7 +701,16 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
       << ",\"ritz_max\":" << F.st_ritz_max << ",\"ritz_mean\":" << (F.st_ritz_n ? (double)F.st_ritz_sum / F.st_ritz_n : 0.0)
       << ",\"jacobi_sweeps_max\":" << F.st_sweeps_max << "}";
   }
-  o << "]}";
+  o << "],\"kernels\":{";
+  {
+    bool first = true;
+    for (const auto& [tag, a] : c.prof) {
+      o << (first ? "" : ",") << "\"" << tag << "\":{\"launches\":" << a.launches << ",\"ms\":" << a.ms
+        << ",\"flops\":" << a.flops << "}";
+      first = false;
+    }
+  }
+  o << "}}";
   const std::string s = o.str();
   const size_t n = std::min(cap - 1, s.size());
   std::memcpy(json, s.data(), n);

@@ -35,8 +35,13 @@ struct GemmBatch {
   // Tile list; tasks whose K is long compared with the number of output tiles
   // are split along K (deterministic two-pass sum) so that a launch keeps the
   // SMs busy.  Returns the split-K workspace size in accumulator elements.
+  double alg_flops = 0;  // 8 M N K per pair; Hermitian outputs: upper triangle only
   int64_t plan(int target_ctas = 4 * 152) {
     tl.clear();
+    alg_flops = 0;
+    for (auto& g : t)
+      for (int q = g.p0; q < g.p0 + g.np; ++q)
+        alg_flops += g.herm ? 4.0 * g.M * (double)(g.M + 1) * p[q].K : 8.0 * g.M * (double)g.N * p[q].K;
     const int bm = h2k::gemm_tile_m(0), bn = h2k::gemm_tile_n(0);
     auto ntile = [&](const h2k::GemmTask& g) {
       const int64_t a = (g.M + bm - 1) / bm, b = (g.N + bn - 1) / bn;

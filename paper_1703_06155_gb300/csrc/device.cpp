@@ -15,6 +15,48 @@ void DevBuf::release() {
 
 [[noreturn]] void fail(h2_status st, const std::string& msg) { throw Err{st, msg}; }
 
+static cudaEvent_t prof_event(Ctx& c) {
+  if (!c.prof_pool.empty()) {
+    cudaEvent_t e = c.prof_pool.back();
+    c.prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  ck(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+ProfScope::ProfScope(Ctx& c_, const std::string& tag, double flops) : c(c_), on(c_.opts.profile != 0) {
+  if (!on) return;
+  ProfRec r{tag, prof_event(c), prof_event(c), flops};
+  ck(cudaEventRecord(r.a, c.stream), "cudaEventRecord");
+  idx = c.prof_open.size();
+  c.prof_open.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (on) cudaEventRecord(c.prof_open[idx].b, c.stream);
+}
+
+void prof_resolve(Ctx& c) {
+  for (ProfRec& r : c.prof_open) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ProfAgg& a = c.prof[r.tag];
+      a.launches++;
+      a.ms += ms;
+      a.flops += r.flops;
+    } else {
+      cudaGetLastError();
+    }
+    c.prof_pool.push_back(r.a);
+    c.prof_pool.push_back(r.b);
+  }
+  c.prof_open.clear();
+}
+
+void prof_reset(Ctx& c) { c.prof.clear(); }
+
 void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(H2_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }

@@ -44,6 +44,7 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
   c.st.upload(c);
+  ProfScope ps(c, std::string("gemm:") + what, b.alg_flops);
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
           wsp, c.stream),
      what);
@@ -72,6 +73,7 @@ void run_apply(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
     for (int t0 = 0; t0 < b.t[i].w; t0 += tw) tiles.push_back(ApplyTile{(int)i, t0});
   const int i0 = c.st.add(b.t), i1 = c.st.add(tiles);
   c.st.upload(c);
+  ProfScope ps(c, std::string(left ? "apply_left:" : "apply_right:") + what, b.flops);
   if (left)
     ck(apply_left(c.st.ptr<ApplyTask>(i0), c.st.ptr<ApplyTile>(i1), (int)tiles.size(), prec, b.maxp, tw, c.stream),
        what);
@@ -85,6 +87,7 @@ void run_copy(Ctx& c, CopyBatch& b, const char* what) {
   if (b.empty()) return;
   const int i0 = c.st.add(b.t);
   c.st.upload(c);
+  ProfScope ps(c, std::string("copy:") + what, 0.0);
   ck(copy2d(c.st.ptr<CopyTask>(i0), (int)b.t.size(), c.stream), what);
   c.launches++;
 }
@@ -311,6 +314,7 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
     {
       const int i0 = c.st.add(pc);
       c.st.upload(c);
+      ProfScope ps(c, "pchol_wy", 0.0);
       ck(pchol_wy(c.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, c.stream), "pivoted cholesky");
       c.launches++;
     }
@@ -369,6 +373,7 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
     if (!eig.empty()) {
       const int i0 = c.st.add(eig);
       c.st.upload(c);
+      ProfScope ps(c, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0);
       if (maxr >= 48) {
         // large Ritz problems: one 8-CTA cluster per eigenproblem
         const int64_t per = jacobi_cluster_scratch(maxr);
@@ -392,6 +397,7 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
        "read sweeps");
   }
   ck(cudaStreamSynchronize(c.stream), "sync after step 0");
+  prof_resolve(c);
   c.st.begin();  // stream idle: staging can be reused
   for (size_t q = 0; q < info.size(); ++q) {
     const Info& f = info[q];
@@ -470,6 +476,7 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
   if (!lu.empty()) {
     const int i0 = c.st.add(lu);
     c.st.upload(c);
+    ProfScope ps(c, "lu", 0.0);
     ck(lu_small(c.st.ptr<LuTask>(i0), (int)lu.size(), prec, (int*)c.statusbuf.p, c.stream), "lu");
     c.launches++;
   }
@@ -647,7 +654,10 @@ void root_factor(Ctx& c, LevelF& F) {
                                         n, k0, k0, n - k0, kb}};
     const int i0 = c.st.add(pt);
     c.st.upload(c);
-    ck(lu_panel(c.st.ptr<PanelTask>(i0), prec, (int*)c.statusbuf.p, c.stream), "root panel");
+    {
+      ProfScope ps(c, "root_panel", 8.0 * (n - k0) * (double)kb * kb / 2);
+      ck(lu_panel(c.st.ptr<PanelTask>(i0), prec, (int*)c.statusbuf.p, c.stream), "root panel");
+    }
     ck(swap_rows(Rm, n, ipiv + k0, k0, kb, 0, k0, prec, 0, c.stream), "root swaps left");
     ck(swap_rows(Rm, n, ipiv + k0, k0, kb, k0 + kb, n, prec, 0, c.stream), "root swaps right");
     c.launches += 3;
@@ -672,6 +682,7 @@ void check_status(Ctx& c) {
   int st = 0;
   ck(cudaMemcpyAsync(&st, c.statusbuf.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read status");
   ck(cudaStreamSynchronize(c.stream), "status sync");
+  prof_resolve(c);
   if (st & 1) fail(H2_ESINGULAR, "zero pivot in a partial LU or in the final LU");
   if (st & 2) fail(H2_EINTERNAL, "Jacobi eigen-decomposition did not converge");
 }
@@ -685,6 +696,7 @@ void factorize(Ctx& c, double eps, int prec) {
   c.prec = prec;
   c.eps_fill = eps;
   c.stats.flops_factor = 0;
+  prof_reset(c);
   const int64_t launches0 = c.launches;
   H2Host& H = c.H;
   const int L = H.L, l0 = H.l0;

@@ -173,6 +173,18 @@ struct Stats {
   std::vector<std::string> level_json;
 };
 
+// Optional per-launch timing (h2_opts.profile): CUDA events on the launch
+// stream around each kernel, resolved after the call's final synchronize.
+struct ProfRec {
+  std::string tag;
+  cudaEvent_t a, b;
+  double flops;
+};
+struct ProfAgg {
+  int64_t launches = 0;
+  double ms = 0, flops = 0;
+};
+
 struct Ctx {
   H2Host H;
   cudaStream_t stream = nullptr;
@@ -197,7 +209,21 @@ struct Ctx {
   Stager st;
   Stats stats;
   int64_t launches = 0;
+  std::vector<ProfRec> prof_open;
+  std::vector<cudaEvent_t> prof_pool;
+  std::unordered_map<std::string, ProfAgg> prof;  // per kernel class, since the last reset
 };
+
+// RAII bracket of one kernel launch (no-op unless opts.profile)
+struct ProfScope {
+  Ctx& c;
+  bool on;
+  size_t idx = 0;
+  ProfScope(Ctx& c_, const std::string& tag, double flops);
+  ~ProfScope();
+};
+void prof_resolve(Ctx& c);  // after a stream synchronize: fold events into c.prof
+void prof_reset(Ctx& c);
 
 // accessors of the ABI context object (defined with it in api.cpp)
 Ctx* ctx_core(h2_ctx* x);
