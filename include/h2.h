@@ -199,6 +199,30 @@ h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* x, void* y, int nrhs,
                             unsigned flags, void* stream);
 
 /*
+ * h2_grad_chi - per-cell derivative of a real objective L through the solution
+ * map x = A(chi)^{-1} b of the volume-integral system A = I + s K D_chi (the
+ * matrix the paper's solver factors, with chi the per-cell contrast of the
+ * column scaling).  The paper has no counterpart: this is the adjoint
+ * (reverse-mode) derivative of its solve.  With g = dL/dx in the
+ * conjugate-Wirtinger convention (dL = Re sum conj(g) dx) and mu = A^{-H} g
+ * from h2_solve(..., H2_ADJOINT, ...) on the same factors,
+ *   grad[i] (=|+=) alpha / chi_i * sum_c Re( x[i,c] * conj(mu[i,c] - g[i,c]) )
+ * (dA/dchi_i = s K e_i e_i^T and A^H mu = g).  chi_i is the context's contrast
+ * (dscale_i^2 of h2_load; the chi of h2_build).
+ *   x, mu, g  DEVICE, N x nrhs complex128, column-major, global order; g may
+ *             be NULL (taken as 0: the form 2 Re(x conj(lambda)) / chi of an
+ *             objective whose chi-dependence outside the solve has been
+ *             folded into lambda, alpha = 2)
+ *   grad      DEVICE, N doubles, global order, caller-allocated
+ *   flags     0, or H2_GRAD_ACCUMULATE to add into grad
+ * Runs asynchronously on `stream` (one kernel, no synchronisation).
+ */
+#define H2_GRAD_ACCUMULATE 1u
+h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
+                      const void* g, int nrhs, double alpha, double* grad,
+                      unsigned flags, void* stream);
+
+/*
  * h2_export - copy the H^2 representation out in the h2_load layout (HOST
  * arrays, caller-allocated).  Call h2_export_sizes first: it returns the
  * element counts (complex entries for V, T, S, D; pairs for adm / near).

@@ -19,4 +19,6 @@ Modules
   dense   - own dense LU with partial pivoting, solve, inverse (brute force)
   factor  - Algorithms 1-4 (factorization), eq. 35 (inverse), Alg. 5-6 (solve),
             adjoint solve, iterative refinement
+  adjoint - dense derivative of the solve in the per-cell contrast (general
+            and reduced forms, probe objective, finite differences)
 """

@@ -34,6 +34,20 @@ def lu_solve(LU, piv, b):
     return y
 
 
+def lu_solve_adjoint(LU, piv, c):
+    """Solve A^H y = c from lu(A): A^H = U^H L^H P, so U^H z = c (forward),
+    L^H w = z (backward, unit diagonal), y = P^T w."""
+    z = np.asarray(c, dtype=np.complex128).copy()
+    n = LU.shape[0]
+    for i in range(n):
+        z[i] = (z[i] - np.conj(LU[:i, i]) @ z[:i]) / np.conj(LU[i, i])
+    for i in range(n - 1, -1, -1):
+        z[i] -= np.conj(LU[i + 1:, i]) @ z[i + 1:]
+    y = np.empty_like(z)
+    y[piv] = z
+    return y
+
+
 def solve(A, b):
     LU, piv = lu(A)
     return lu_solve(LU, piv, b)

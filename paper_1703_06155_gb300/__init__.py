@@ -22,9 +22,10 @@ H2_OK, H2_EINVAL, H2_ENOMEM, H2_ESINGULAR, H2_ENOCONV = 0, -1, -2, -3, -4
 H2_ETIMEOUT, H2_ECUDA, H2_EINTERNAL, H2_ESTATE = -5, -6, -7, -8
 H2_FP64, H2_MIXED = 0, 1
 H2_ADJOINT, H2_REFINE, H2_USE_INVERSE, H2_HOST = 1, 2, 4, 8
+H2_GRAD_ACCUMULATE = 1
 SYMBOLS = ("h2_default_opts", "h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec",
-           "h2_matvec_noalloc", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error", "h2_status_string",
-           "h2_destroy")
+           "h2_matvec_noalloc", "h2_grad_chi", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
+           "h2_status_string", "h2_destroy")
 
 
 class h2_opts(ctypes.Structure):
@@ -63,6 +64,7 @@ def lib():
     L.h2_solve.argtypes = [P, P, P, I, ctypes.c_uint, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.h2_matvec.argtypes = [P, P, P, I, ctypes.c_uint, P]
     L.h2_matvec_noalloc.argtypes = [P, P, P, I, ctypes.c_uint, P]
+    L.h2_grad_chi.argtypes = [P, P, P, P, I, D, P, ctypes.c_uint, P]
     L.h2_export_sizes.argtypes = [P] + [ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I)] + \
         [ctypes.POINTER(I64)] * 6
     L.h2_export.argtypes = [P] * 12
@@ -74,7 +76,7 @@ def lib():
     L.h2_destroy.argtypes = [P]
     L.h2_destroy.restype = None
     for name in ("h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec", "h2_matvec_noalloc",
-                 "h2_export_sizes", "h2_export", "h2_stats"):
+                 "h2_grad_chi", "h2_export_sizes", "h2_export", "h2_stats"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -115,9 +117,11 @@ def default_opts(**kw):
 class H2:
     """An H^2 matrix on the GPU with its factorization (one libh2 context)."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, chi=None):
         self._h = handle
         self.N = self._sizes()[0]
+        # the contrast the context was set up with (host float64, length N)
+        self.chi = None if chi is None else np.broadcast_to(np.asarray(chi, np.float64), (self.N,)).copy()
 
     # ---------------------------------------------------------------- setup
     @classmethod
@@ -131,7 +135,7 @@ class H2:
                             _stream(stream), ctypes.byref(out))
         if st != H2_OK:
             raise H2Error(st, "h2_build: " + lib().h2_last_error(None).decode())
-        return cls(out)
+        return cls(out, chi=c)
 
     @classmethod
     def load(cls, rep, stream=None, **opts):
@@ -153,7 +157,9 @@ class H2:
         del keep
         if st != H2_OK:
             raise H2Error(st, "h2_load: " + lib().h2_last_error(None).decode())
-        return cls(out)
+        ds = r.get("dscale")
+        # h2_load takes dscale = sqrt(chi); without it the columns are unscaled (chi = 1)
+        return cls(out, chi=1.0 if ds is None else np.asarray(ds, np.float64) ** 2)
 
     def _check(self, st, what):
         if st != H2_OK:
@@ -231,6 +237,29 @@ class H2:
             self._check(lib().h2_matvec(self._h, px, py, nrhs, flags | extra, _stream(stream)), "h2_matvec")
 
         return self._vec_call(x, None, fn)
+
+    def grad_chi(self, x, mu, g=None, alpha=1.0, out=None, accumulate=False, stream=None):
+        """grad[i] = alpha / chi_i * sum_c Re(x[i,c] conj(mu[i,c] - g[i,c])) on the device (h2_grad_chi).
+
+        x, mu, g: torch CUDA complex128 of shape (N,) or (N, nrhs); g may be None.
+        Returns (or fills) a float64 CUDA tensor of shape (N,)."""
+        import torch
+
+        def cm(a):
+            if a is None:
+                return None
+            if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.complex128):
+                raise TypeError("h2_grad_chi takes CUDA complex128 tensors")
+            return (a.reshape(1, -1) if a.ndim == 1 else a.T).contiguous()
+
+        xc, mc, gc = cm(x), cm(mu), cm(g)
+        if mc.shape != xc.shape or (gc is not None and gc.shape != xc.shape) or xc.shape[1] != self.N:
+            raise ValueError("x, mu, g must all be (N,) or (N, nrhs)")
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device=xc.device)
+        self._check(lib().h2_grad_chi(self._h, _ptr(xc), _ptr(mc), _ptr(gc), xc.shape[0], float(alpha), _ptr(out),
+                                      H2_GRAD_ACCUMULATE if accumulate else 0, _stream(stream)), "h2_grad_chi")
+        return out
 
     def stats(self):
         buf = ctypes.create_string_buffer(1 << 20)

@@ -661,6 +661,23 @@ h2_status h2_matvec(h2_ctx* ctx, const void* xi, void* y, int nrhs, unsigned fla
   });
 }
 
+h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu, const void* g, int nrhs, double alpha,
+                      double* grad, unsigned flags, void* stream) {
+  if (!ctx) return H2_EINVAL;
+  if (host_only(ctx)) return H2_ESTATE;
+  if (!x || !mu || !grad || nrhs <= 0 || (flags & ~H2_GRAD_ACCUMULATE)) {
+    ctx->c.err = "h2_grad_chi: bad argument (device x, mu, grad; nrhs > 0; flags 0 or H2_GRAD_ACCUMULATE)";
+    return H2_EINVAL;
+  }
+  return guard(ctx, [&]() {
+    Ctx& c = ctx->c;
+    ck(grad_chi((const cd*)x, (const cd*)mu, (const cd*)g, (const double*)c.dscale.p, c.H.tree.N, nrhs, alpha, grad,
+                (flags & H2_GRAD_ACCUMULATE) ? 1 : 0, (cudaStream_t)stream),
+       "grad_chi");
+    c.launches++;
+  });
+}
+
 h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
   if (!ctx || !json || cap == 0) return H2_EINVAL;
   const Ctx& c = ctx->c;

@@ -36,13 +36,17 @@ struct GemmBatch {
   // are split along K (deterministic two-pass sum) so that a launch keeps the
   // SMs busy.  Returns the split-K workspace size in accumulator elements.
   double alg_flops = 0;  // 8 M N K per pair; Hermitian outputs: upper triangle only
+  int skinny = 0;        // all outputs have N <= 16: 64 x 16 tiles
   int64_t plan(int target_ctas = 4 * 152) {
     tl.clear();
     alg_flops = 0;
+    skinny = 1;
+    for (auto& g : t)
+      if (g.N > 16 || g.herm) skinny = 0;
     for (auto& g : t)
       for (int q = g.p0; q < g.p0 + g.np; ++q)
         alg_flops += g.herm ? 4.0 * g.M * (double)(g.M + 1) * p[q].K : 8.0 * g.M * (double)g.N * p[q].K;
-    const int bm = h2k::gemm_tile_m(0), bn = h2k::gemm_tile_n(0);
+    const int bm = h2k::gemm_tile_m(skinny), bn = h2k::gemm_tile_n(skinny);
     auto ntile = [&](const h2k::GemmTask& g) {
       const int64_t a = (g.M + bm - 1) / bm, b = (g.N + bn - 1) / bn;
       return g.herm ? a * (a + 1) / 2 : a * b;

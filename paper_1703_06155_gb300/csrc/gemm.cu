@@ -31,28 +31,31 @@ __device__ __forceinline__ void store_val(E* p, R re, R im) {
   *p = v;
 }
 
-constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
+constexpr int BM = 64, BK = 8, NT = 256;
 
 template <class R> struct CxOf;
 template <> struct CxOf<double> { using T = cd; };
 template <> struct CxOf<float> { using T = cf; };
 
-template <class EI, class R, class EO>
+// BN = 64 (4 x 4 complex micro-tile per thread) or BN = 16 (4 x 1, for the
+// skinny products of the solve and the matvec, N = number of right-hand sides)
+template <class EI, class R, class EO, int BN>
 __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
                                             const GemmPair* __restrict__ pairs,
                                             const GemmTile* __restrict__ tiles,
                                             typename CxOf<R>::T* __restrict__ ws) {
+  constexpr int TN = BN / 16;
   __shared__ R As_r[BK][BM], As_i[BK][BM];
   __shared__ R Bs_r[BK][BN], Bs_i[BK][BN];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmTask tk = tasks[tl.task];
   const int m0 = tl.tm * BM, n0 = tl.tn * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  R acc_r[4][4], acc_i[4][4];
+  R acc_r[4][TN], acc_i[4][TN];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc_r[i][j] = acc_i[i][j] = (R)0;
+    for (int j = 0; j < TN; ++j) acc_r[i][j] = acc_i[i][j] = (R)0;
 
   // this tile's share of the concatenated K range of all pairs
   const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
@@ -83,8 +86,9 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
       }
       // B tile: BK x BN of op(B)
 #pragma unroll
-      for (int r = 0; r < (BK * BN) / NT; ++r) {
+      for (int r = 0; r < (BK * BN + NT - 1) / NT; ++r) {
         const int l = tid + r * NT;
+        if (l >= BK * BN) break;
         int k, j;
         if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
         R re = 0, im = 0;
@@ -95,15 +99,15 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < BK; ++k) {
-        R ar[4], ai[4], br[4], bi[4];
+        R ar[4], ai[4], br[TN], bi[TN];
 #pragma unroll
         for (int i = 0; i < 4; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
+        for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < TN; ++j) {
             acc_r[i][j] = fma(ar[i], br[j], fma(-ai[i], bi[j], acc_r[i][j]));
             acc_i[i][j] = fma(ar[i], bi[j], fma(ai[i], br[j], acc_i[i][j]));
           }
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
       const int m = m0 + ty + 16 * i;
       if (m >= tk.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         const int n = n0 + tx + 16 * j;
         if (n >= tk.N) continue;
         typename CxOf<R>::T v;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
     const int m = m0 + ty + 16 * i;
     if (m >= tk.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= tk.N) continue;
       EO* p = C + (size_t)m + (size_t)n * tk.ldc;
@@ -185,7 +189,7 @@ __global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks) {
   EO* C = (EO*)tk.C;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % tk.M), j = (int)(e / tk.M);
-    if (i / BM > j / BN) {
+    if (i / BM > j / BM) {
       EO v = C[(size_t)j + (size_t)i * tk.ldc];
       v.im = -v.im;
       C[(size_t)i + (size_t)j * tk.ldc] = v;
@@ -196,22 +200,29 @@ __global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks) {
 }  // namespace
 
 int gemm_tile_m(int) { return BM; }
-int gemm_tile_n(int) { return BN; }
+int gemm_tile_n(int skinny) { return skinny ? 16 : 64; }
 
-cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
-                 int pin, int pout, int pacc, void* ws, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
+template <int BN>
+static cudaError_t gemm_bn(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
+                           int pin, int pout, int pacc, void* ws, cudaStream_t s) {
   if (pin == P64 && pacc == P64 && pout == P64)
-    k_gemm<cd, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+    k_gemm<cd, double, cd, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pin == P32 && pacc == P32 && pout == P32)
-    k_gemm<cf, float, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
+    k_gemm<cf, float, cf, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
   else if (pin == P32 && pacc == P64 && pout == P64)
-    k_gemm<cf, double, cd><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+    k_gemm<cf, double, cd, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pin == P64 && pacc == P64 && pout == P32)
-    k_gemm<cd, double, cf><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+    k_gemm<cd, double, cf, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles, int pin,
+                 int pout, int pacc, void* ws, cudaStream_t s, int skinny) {
+  if (ntiles <= 0) return cudaSuccess;
+  return skinny ? gemm_bn<16>(d_tasks, d_pairs, d_tiles, ntiles, pin, pout, pacc, ws, s)
+                : gemm_bn<64>(d_tasks, d_pairs, d_tiles, ntiles, pin, pout, pacc, ws, s);
 }
 
 cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn, int pout, cudaStream_t s) {

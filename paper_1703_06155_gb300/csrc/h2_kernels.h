@@ -140,16 +140,17 @@ struct KGramTile { int task, tm, tn; };
 // products are accumulated in.
 // split-K: tasks with nk > 1 write partial tiles to `ws` (accumulator
 // precision), then gemm_reduce sums them in a fixed order into C.
+// skinny = 1: 64 x 16 output tiles (every task has N <= 16), else 64 x 64
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
-                 int pacc, void* ws, cudaStream_t s);
+                 int pacc, void* ws, cudaStream_t s, int skinny = 0);
 cudaError_t gemm_reduce(const GemmTask* d_tasks, int ntasks, int maxmn,
                         int pout, int pacc, const void* ws, cudaStream_t s);
 // C[i, j] = conj(C[j, i]) for the entries of tiles below the diagonal
 cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn,
                         int pout, cudaStream_t s);
-int gemm_tile_m(int pacc);
-int gemm_tile_n(int pacc);
+int gemm_tile_m(int skinny);
+int gemm_tile_n(int skinny);
 
 cudaError_t apply_left(const ApplyTask* d_tasks, const ApplyTile* d_tiles,
                        int ntiles, int prec, int maxp, int tw, cudaStream_t s);
@@ -199,6 +200,11 @@ cudaError_t col_norms2(const cd* x, int64_t N, int nrhs, double* d_out,
 // y = a - b   (complex128, N x nrhs contiguous)
 cudaError_t axpby(const cd* a, const cd* b, cd* y, int64_t n, double alpha,
                   double beta, cudaStream_t s);
+// grad[i] (=|+=) alpha / sqchi[i]^2 * sum_c Re(x[i,c] conj(mu[i,c] - g[i,c]))
+// (g may be null); all in the caller's (global) order
+cudaError_t grad_chi(const cd* x, const cd* mu, const cd* g, const double* sqchi,
+                     int64_t N, int nrhs, double alpha, double* grad,
+                     int accumulate, cudaStream_t s);
 // convert complex128 <-> complex64 (contiguous)
 cudaError_t convert(const void* in, int in_prec, void* out, int out_prec,
                     int64_t n, cudaStream_t s);

@@ -288,3 +288,91 @@ def test_planted_mistakes_are_caught(monkeypatch):
         test_self_term_quadrature()
     monkeypatch.undo()
     assert err_exact() < 1e-11
+
+
+# ------------------------------------------- derivative in the contrast ----
+
+
+def test_adjoint_lu_solve_against_lapack():
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40))
+    c = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    LU, piv = dense.lu(A)
+    y = dense.lu_solve_adjoint(LU, piv, c)
+    assert np.linalg.norm(y - np.linalg.solve(A.conj().T, c)) <= 1e-12 * np.linalg.norm(y)
+
+
+def test_grad_one_unknown_closed_form():
+    # N = 1: A = 1 + s kappa chi, x = b / A, L = |x|^2 (g = 2 x):
+    # dL/dchi = -2 |b|^2 Re(conj(A) s kappa) / |A|^4
+    from oracle import adjoint
+    kappa = kernel.self_term(K, H)
+    for s in (1.0, -1.0):
+        for chi in (0.5, 1.75, 3.0):
+            b = 0.3 - 1.1j
+            A = 1.0 + s * kappa * chi
+            x = b / A
+            g = 2.0 * x
+            mu = g / np.conj(A)
+            got = adjoint.grad_reduced(np.array([chi]), np.array([x]), np.array([mu]), np.array([g]))[0]
+            ref = -2.0 * abs(b) ** 2 * np.real(np.conj(A) * s * kappa) / abs(A) ** 4
+            assert abs(got - ref) <= 1e-12 * abs(ref)
+
+
+def _grad_problem(n=4, seed=4):
+    from oracle import adjoint
+    pts = inputs.grid_points(n, H)
+    N = len(pts)
+    chi = inputs.chi_random_cells(N, seed)
+    b = inputs.rhs_plane_wave(pts, K)
+    radius = 2.0 * (math.sqrt(3.0) / 2.0) * n * H
+    probes = inputs.fibonacci_sphere(64, pts.mean(axis=0), radius)
+    G = adjoint.probe_matrix(probes, pts, K, H)
+    return pts, chi, b, G
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_probe_gradient_forms_match_finite_differences(sign):
+    # reduced 2 Re(x conj(lambda)) / chi == general 2 Re(x conj(w - s K^H lambda))
+    # == central differences of dense solves (step 1e-6, error ~1e-10 relative)
+    from oracle import adjoint
+    pts, chi, b, G = _grad_problem()
+    A = kernel.dense_A(pts, chi, K, H, sign)
+    Kd = adjoint.dense_K(pts, K, H)
+    _, _, red, gen = adjoint.probe_gradient(A, Kd, G, chi, b, sign)
+    cells = [0, 7, 21, 63]
+    fd = adjoint.probe_fd(pts, chi, K, H, b, G, cells, 1e-6, sign)
+    scale = np.max(np.abs(red))
+    assert np.max(np.abs(red - gen)) <= 1e-12 * scale
+    assert np.max(np.abs(red[cells] - fd)) <= 1e-7 * scale
+
+
+def test_solve_gradient_with_incoming_g_matches_finite_differences():
+    # the solve-only derivative used by the autograd node: L = sum |W x|^2 for a
+    # fixed complex W (no chi outside the solve), g = 2 W^H W x
+    from oracle import adjoint
+    pts, chi, b, G = _grad_problem()
+    A = kernel.dense_A(pts, chi, K, H)
+    Kd = adjoint.dense_K(pts, K, H)
+    x = dense.solve(A, b)
+    g = 2.0 * (G.conj().T @ (G @ x))
+    mu = dense.solve(A.conj().T, g)
+    red = adjoint.grad_reduced(chi, x, mu, g)
+    gen = adjoint.grad_general(Kd, 1.0, x, mu)
+    cells = [3, 30, 60]
+    fd = []
+    for i in cells:
+        v = []
+        for d in (1e-6, -1e-6):
+            c = chi.copy()
+            c[i] += d
+            xi = dense.solve(kernel.dense_A(pts, c, K, H), b)
+            v.append(np.sum(np.abs(G @ xi) ** 2))
+        fd.append((v[0] - v[1]) / 2e-6)
+    scale = np.max(np.abs(red))
+    assert np.max(np.abs(red - gen)) <= 1e-12 * scale
+    assert np.max(np.abs(red[cells] - np.array(fd))) <= 1e-7 * scale
+    # planted mistake: dropping g (using the probe form without the direct
+    # term) is visibly wrong
+    bad = adjoint.grad_reduced(chi, x, mu)
+    assert np.max(np.abs(bad[cells] - np.array(fd))) > 1e-3 * scale
