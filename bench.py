@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-levels", action="store_true", help="kernel classes kept apart per tree level")
+    p.add_argument("--apply-path", type=int, default=0, choices=[0, 1, 2],
+                   help="Step 2 / panel applications: 0 auto, 1 in-place kernel, 2 GEMM + copy")
     p.add_argument("--json-extra", action="store_true", help="print per-level stats")
     p.add_argument("--profile-step", action="store_true",
                    help="build, then exactly one factorize + refined solve (for profiler captures)")
@@ -203,7 +206,8 @@ def run_ours(args):
     pts = inputs.grid_points(args.grid, H)
     N = len(pts)
     t0 = time.perf_counter()
-    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream, profile=1)
+    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream, profile=2 if args.profile_levels else 1,
+                 apply_path=args.apply_path)
     t_build = time.perf_counter() - t0
     b_host = inputs.rhs_gaussian(N, args.nrhs, args.seed + rank)  # independent instance per rank
     b = torch.from_numpy(b_host).to("cuda")
@@ -285,7 +289,7 @@ def run_ours(args):
         "clocks": cs.summary(),
         "roofline": roof,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
-                    sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:12]},
+                    sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:40 if args.profile_levels else 12]},
     }
     if args.json_extra:
         line["stats"] = st

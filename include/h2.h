@@ -74,7 +74,12 @@ typedef struct {
   int profile;           /* 1: bracket every kernel launch with CUDA events
                             on the call's stream and report per-kernel-class
                             launches, device time and algorithmic flops in
-                            h2_stats ("kernels"); 0 (default): off          */
+                            h2_stats ("kernels"); 2: the same, kept apart
+                            per tree level ("tag@l"); 0 (default): off      */
+  int apply_path;        /* Step 2 and panel applications (Alg. 3, Alg. 4):
+                            0 (default) automatic (currently 2), 1 in-place
+                            kernel (one CTA per column / row strip), 2
+                            batched GEMM into a workspace, then copied back */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */

@@ -111,6 +111,12 @@ struct CopyBatch {
 
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what);
 void run_apply(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what);
+// the same application by the batched GEMM: op(A) X (left) or X op(A)
+// (right) into a workspace, the output split over many CTAs, then copied back
+void run_apply_gemm(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what);
+inline void run_apply_narrow(Ctx& c, ApplyBatch& b, int prec, const char* what) {
+  run_apply_gemm(c, b, true, prec, what);
+}
 void run_copy(Ctx& c, CopyBatch& b, const char* what);
 
 }  // namespace h2

@@ -5,8 +5,8 @@
 //                          an orthonormal cluster basis by Householder QR
 //  jacobi_eig              Step 0 (eqs. 17, 26): eigen-decomposition of the
 //                          fill-in Gram in complement coordinates (FP64)
-//  lu_small                Step 3 (eq. 11): partial-pivoting LU of the
-//                          leading m x m block, with explicit L^{-1}P, U^{-1}
+//
+// (The partial LU of Step 3 is in lu.cu.)
 //
 // Reductions use warp shuffles and a shared-memory stage.  The Jacobi sweep
 // loop is bounded (kMaxSweeps); a matrix that does not converge within it
@@ -313,132 +313,6 @@ __global__ void __launch_bounds__(NT) k_jacobi(const EigTask* __restrict__ tasks
 // ----------------------------------------------------------------------------
 // Partial-pivoting LU of an m x m block (in place, ld lda), pivot = largest
 // |z| in the column, ties -> lowest row; then L^{-1} P and U^{-1}.
-template <class E>
-__global__ void __launch_bounds__(NT) k_lu(const LuTask* __restrict__ tasks, int* status) {
-  using R = typename RealOf<E>::T;
-  __shared__ R redv[NT];
-  __shared__ int redi[NT];
-  extern __shared__ int perm[];
-  const LuTask t = tasks[blockIdx.x];
-  const int m = t.m, ld = t.lda;
-  E* A = (E*)t.A;
-  for (int i = threadIdx.x; i < m; i += NT) perm[i] = i;
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    R best = -1;
-    int bi = m;
-    for (int i = j + threadIdx.x; i < m; i += NT) {
-      const E v = A[i + (size_t)j * ld];
-      const R a = (R)v.re * (R)v.re + (R)v.im * (R)v.im;
-      if (a > best || (a == best && i < bi)) { best = a; bi = i; }
-    }
-    redv[threadIdx.x] = best;
-    redi[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        const R o = redv[threadIdx.x + s];
-        const int oi = redi[threadIdx.x + s];
-        if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
-          redv[threadIdx.x] = o;
-          redi[threadIdx.x] = oi;
-        }
-      }
-      __syncthreads();
-    }
-    const int pr = redi[0];
-    const R pv = redv[0];
-    __syncthreads();
-    if (!(pv > (R)0)) {
-      if (threadIdx.x == 0 && status) atomicMax(status, 1);
-      return;
-    }
-    if (pr != j) {
-      for (int c = threadIdx.x; c < m; c += NT) {
-        const E a = A[j + (size_t)c * ld];
-        A[j + (size_t)c * ld] = A[pr + (size_t)c * ld];
-        A[pr + (size_t)c * ld] = a;
-      }
-      if (threadIdx.x == 0) { const int x = perm[j]; perm[j] = perm[pr]; perm[pr] = x; }
-    }
-    __syncthreads();
-    const E d = A[j + (size_t)j * ld];
-    const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
-    const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
-    for (int i = j + 1 + threadIdx.x; i < m; i += NT) {
-      E v = A[i + (size_t)j * ld];
-      const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
-      v.re = vr;
-      v.im = vi;
-      A[i + (size_t)j * ld] = v;
-    }
-    __syncthreads();
-    const int rem = m - j - 1;
-    for (int idx = threadIdx.x; idx < rem * rem; idx += NT) {
-      const int i = j + 1 + idx % rem, c = j + 1 + idx / rem;
-      const E l = A[i + (size_t)j * ld], u = A[j + (size_t)c * ld];
-      E v = A[i + (size_t)c * ld];
-      v.re = (R)v.re - ((R)l.re * (R)u.re - (R)l.im * (R)u.im);
-      v.im = (R)v.im - ((R)l.re * (R)u.im + (R)l.im * (R)u.re);
-      A[i + (size_t)c * ld] = v;
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < m; i += NT) t.piv[i] = perm[i];
-  // L^{-1} P: X = P (row r of P is e_{perm[r]}^T), then forward elimination
-  E* X = (E*)t.Linv;
-  for (int idx = threadIdx.x; idx < m * m; idx += NT) {
-    const int r = idx % m, c = idx / m;
-    E v;
-    v.re = (perm[r] == c) ? 1 : 0;
-    v.im = 0;
-    X[idx] = v;
-  }
-  __syncthreads();
-  for (int tt = 0; tt < m - 1; ++tt) {
-    const int rem = m - tt - 1;
-    for (int idx = threadIdx.x; idx < rem * m; idx += NT) {
-      const int i = tt + 1 + idx % rem, c = idx / rem;
-      const E l = A[i + (size_t)tt * ld], x = X[tt + (size_t)c * m];
-      E v = X[i + (size_t)c * m];
-      v.re = (R)v.re - ((R)l.re * (R)x.re - (R)l.im * (R)x.im);
-      v.im = (R)v.im - ((R)l.re * (R)x.im + (R)l.im * (R)x.re);
-      X[i + (size_t)c * m] = v;
-    }
-    __syncthreads();
-  }
-  // U^{-1}: back substitution on the identity
-  E* Y = (E*)t.Uinv;
-  for (int idx = threadIdx.x; idx < m * m; idx += NT) {
-    E v;
-    v.re = (idx % m == idx / m) ? 1 : 0;
-    v.im = 0;
-    Y[idx] = v;
-  }
-  __syncthreads();
-  for (int tt = m - 1; tt >= 0; --tt) {
-    const E d = A[tt + (size_t)tt * ld];
-    const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
-    const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
-    for (int c = threadIdx.x; c < m; c += NT) {
-      E v = Y[tt + (size_t)c * m];
-      const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
-      v.re = vr;
-      v.im = vi;
-      Y[tt + (size_t)c * m] = v;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < tt * m; idx += NT) {
-      const int i = idx % tt, c = idx / tt;
-      const E u = A[i + (size_t)tt * ld], y = Y[tt + (size_t)c * m];
-      E v = Y[i + (size_t)c * m];
-      v.re = (R)v.re - ((R)u.re * (R)y.re - (R)u.im * (R)y.im);
-      v.im = (R)v.im - ((R)u.re * (R)y.im + (R)u.im * (R)y.re);
-      Y[i + (size_t)c * m] = v;
-    }
-    __syncthreads();
-  }
-}
 
 // ----------------------------------------------------------------------------
 template <class ES, class ED>
@@ -577,19 +451,6 @@ cudaError_t jacobi_eig(const EigTask* d, int n, int maxp, int* st, cudaStream_t 
   size_t sm = (size_t)np * (4 * sizeof(double) + 2 * sizeof(int));
   if (sm < (size_t)maxp * sizeof(int) + 64) sm = (size_t)maxp * sizeof(int) + 64;
   k_jacobi<<<n, NT, sm, s>>>(d, st);
-  return cudaGetLastError();
-}
-
-cudaError_t lu_small(const LuTask* d, int n, int prec, int* st, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const size_t sm = 4096 * sizeof(int);
-  if (prec == P64) {
-    cudaFuncSetAttribute(k_lu<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_lu<cd><<<n, NT, sm, s>>>(d, st);
-  } else {
-    cudaFuncSetAttribute(k_lu<cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_lu<cf><<<n, NT, sm, s>>>(d, st);
-  }
   return cudaGetLastError();
 }
 

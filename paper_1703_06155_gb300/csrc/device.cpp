@@ -28,7 +28,7 @@ static cudaEvent_t prof_event(Ctx& c) {
 
 ProfScope::ProfScope(Ctx& c_, const std::string& tag, double flops) : c(c_), on(c_.opts.profile != 0) {
   if (!on) return;
-  ProfRec r{tag, prof_event(c), prof_event(c), flops};
+  ProfRec r{c.opts.profile == 2 ? tag + c.prof_suffix : tag, prof_event(c), prof_event(c), flops};
   ck(cudaEventRecord(r.a, c.stream), "cudaEventRecord");
   idx = c.prof_open.size();
   c.prof_open.push_back(r);

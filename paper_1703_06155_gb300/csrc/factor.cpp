@@ -83,6 +83,42 @@ void run_apply(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
   c.launches++;
 }
 
+void run_apply_gemm(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
+  if (b.empty()) return;
+  const size_t es = esz(prec);
+  std::vector<size_t> off;
+  size_t tot = 0;
+  for (const ApplyTask& t : b.t) {
+    off.push_back(tot);
+    tot += ((size_t)(t.p - t.lo) * t.w + 31) / 32 * 32;
+  }
+  char* W = (char*)dev_ensure(c, c.applybuf, tot * es);
+  GemmBatch g;
+  CopyBatch cb;
+  for (size_t i = 0; i < b.t.size(); ++i) {
+    const ApplyTask& t = b.t[i];
+    const int out = t.p - t.lo;
+    const bool tr = t.opA == OP_T || t.opA == OP_H;
+    if (left) {
+      // W (out x w) = op(A)[lo:p, 0:p] X[0:p, :]
+      const char* A = (const char*)t.A + (tr ? (size_t)t.lo * t.lda : (size_t)t.lo) * es;
+      g.task(W + off[i] * es, out, out, t.w, 1.0, 0.0);
+      g.pair(A, t.lda, t.opA, t.X, t.ldx, OP_N, t.p);
+      g.close();
+      cb.add(W + off[i] * es, prec, out, out, t.w, (char*)t.X + (size_t)t.lo * es, prec, t.ldx, out, t.w);
+    } else {
+      // W (w x out) = X[:, 0:p] op(A)[0:p, lo:p]
+      const char* A = (const char*)t.A + (tr ? (size_t)t.lo : (size_t)t.lo * t.lda) * es;
+      g.task(W + off[i] * es, t.w, t.w, out, 1.0, 0.0);
+      g.pair(t.X, t.ldx, OP_N, A, t.lda, t.opA, t.p);
+      g.close();
+      cb.add(W + off[i] * es, prec, t.w, t.w, out, (char*)t.X + (size_t)t.lo * t.ldx * es, prec, t.ldx, t.w, out);
+    }
+  }
+  run_gemm(c, g, prec, prec, prec, what);
+  run_copy(c, cb, what);
+}
+
 void run_copy(Ctx& c, CopyBatch& b, const char* what) {
   if (b.empty()) return;
   const int i0 = c.st.add(b.t);
@@ -93,6 +129,12 @@ void run_copy(Ctx& c, CopyBatch& b, const char* what) {
 }
 
 namespace {
+
+// Step 2 / panel applications: in-place kernel or GEMM + copy (h2_opts.apply_path)
+void run_apply_auto(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
+  if (c.opts.apply_path == 1) run_apply(c, b, left, prec, what);
+  else run_apply_gemm(c, b, left, prec, what);
+}
 
 void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std::vector<Pair>& carried) {
   const H2Host& H = c.H;
@@ -460,8 +502,8 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
       }
     }
   }
-  run_apply(c, L2, true, prec, "step2 rows");
-  run_apply(c, R2, false, prec, "step2 cols");
+  run_apply_auto(c, L2, true, prec, "step2 rows");
+  run_apply_auto(c, R2, false, prec, "step2 cols");
   c.stats.flops_factor += L2.flops + R2.flops;
 
   // Step 3: LU + explicit inverses, panels, Schur
@@ -477,7 +519,9 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
     const int i0 = c.st.add(lu);
     c.st.upload(c);
     ProfScope ps(c, "lu", 0.0);
-    ck(lu_small(c.st.ptr<LuTask>(i0), (int)lu.size(), prec, (int*)c.statusbuf.p, c.stream), "lu");
+    int maxm = 0;
+    for (const LuTask& q : lu) maxm = std::max(maxm, q.m);
+    ck(lu_blocked(c.st.ptr<LuTask>(i0), (int)lu.size(), maxm, prec, (int*)c.statusbuf.p, c.stream), "lu");
     c.launches++;
   }
   ApplyBatch PL, PR;
@@ -492,8 +536,8 @@ void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<ch
       PR.add(Uinv, m, OP_N, NB(j, i) + (size_t)lo * es, F.n[j], m, F.n[j] - lo, 0);
     }
   }
-  run_apply(c, PL, true, prec, "U panels");
-  run_apply(c, PR, false, prec, "L panels");
+  run_apply_auto(c, PL, true, prec, "U panels");
+  run_apply_auto(c, PR, false, prec, "L panels");
   c.stats.flops_factor += PL.flops + PR.flops;
 
   std::map<int64_t, std::vector<int>> tg;
@@ -733,12 +777,14 @@ void factorize(Ctx& c, double eps, int prec) {
   }
   for (int li = 0; li <= L - l0; ++li) {
     LevelF& F = c.lev[li];
+    c.prof_suffix = "@" + std::to_string(F.l);
     std::vector<char> done(F.nc, 0);
     for (const auto& bt : F.batches) process_batch(c, F, bt, done, eps);
     if (F.l > l0) merge_level(c, F, c.lev[li + 1]);
     else root_factor(c, F);
     check_status(c);
   }
+  c.prof_suffix.clear();
   c.factored = true;
   c.stats.launches_factor = c.launches - launches0;
   c.stats.t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -205,13 +205,14 @@ struct Ctx {
   std::vector<LevelF> lev;  // lev[0] = leaf level L, ..., last = l0
   RootF root;
   // scratch
-  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf;
+  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf, applybuf;
   Stager st;
   Stats stats;
   int64_t launches = 0;
   std::vector<ProfRec> prof_open;
   std::vector<cudaEvent_t> prof_pool;
   std::unordered_map<std::string, ProfAgg> prof;  // per kernel class, since the last reset
+  std::string prof_suffix;                        // profile == 2: "@<level>" appended to tags
 };
 
 // RAII bracket of one kernel launch (no-op unless opts.profile)

@@ -169,8 +169,10 @@ int64_t jacobi_cluster_scratch(int maxp);  // doubles per task
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
                                int csize, double* d_scratch, int* d_status,
                                cudaStream_t s);
-cudaError_t lu_small(const LuTask* d_tasks, int ntasks, int prec,
-                     int* d_status, cudaStream_t s);
+// Step 3 partial LU with pivoting + explicit L^{-1} P and U^{-1}; one CTA per
+// task, maxm = the largest m of the tasks (<= 4096)
+cudaError_t lu_blocked(const LuTask* d_tasks, int ntasks, int maxm, int prec,
+                       int* d_status, cudaStream_t s);
 cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
 cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, cudaStream_t s);
 cudaError_t lu_panel(const PanelTask* d_task, int prec, int* d_status,

@@ -187,8 +187,8 @@ void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {
           a1.add(Q(F, i), F.n[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
           if (F.m[i] > 0) a2.add(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
         }
-        run_apply(c, a1, true, prec, "fwd Q^H");
-        run_apply(c, a2, true, prec, "fwd L^-1");
+        run_apply_narrow(c, a1, prec, "fwd Q^H");
+        run_apply_narrow(c, a2, prec, "fwd L^-1");
         std::map<int, std::vector<int>> tg;
         for (int i : bt)
           if (F.m[i] > 0)
@@ -253,13 +253,13 @@ void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {
         }
         if (!use_inverse) {
           run_gemm(c, g, prec, prec, prec, "bwd update");
-          run_apply(c, a1, true, prec, "bwd U^-1");
+          run_apply_narrow(c, a1, prec, "bwd U^-1");
         } else {
-          run_apply(c, a1, true, prec, "inv U^-1");
+          run_apply_narrow(c, a1, prec, "inv U^-1");
           run_gemm(c, g, prec, prec, prec, "inv update");
         }
         for (int i : bt) a2.add(Q(F, i), F.n[i], OP_C, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
-        run_apply(c, a2, true, prec, "bwd conj Q");
+        run_apply_narrow(c, a2, prec, "bwd conj Q");
       }
       if (li > 0) merge_vec(c, c.lev[li - 1], F, vec[li - 1], v, nrhs, false);
     }
@@ -274,8 +274,8 @@ void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {
           a1.add(Q(F, i), F.n[i], OP_T, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
           if (F.m[i] > 0) a2.add(Uinv(F, i), F.m[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
         }
-        run_apply(c, a1, true, prec, "adj Q^T");
-        run_apply(c, a2, true, prec, "adj U^-H");
+        run_apply_narrow(c, a1, prec, "adj Q^T");
+        run_apply_narrow(c, a2, prec, "adj U^-H");
         std::map<int, std::vector<int>> tg;
         for (int i : bt)
           if (F.m[i] > 0)
@@ -316,8 +316,8 @@ void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {
           a2.add(Q(F, i), F.n[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
         }
         run_gemm(c, g, prec, prec, prec, "adj L^H update");
-        run_apply(c, a1, true, prec, "adj L^-H");
-        run_apply(c, a2, true, prec, "adj Q");
+        run_apply_narrow(c, a1, prec, "adj L^-H");
+        run_apply_narrow(c, a2, prec, "adj Q");
       }
       if (li > 0) merge_vec(c, c.lev[li - 1], F, vec[li - 1], v, nrhs, false);
     }

@@ -66,10 +66,10 @@ def test_matvec_parity(dev, n):
     assert rel(ya, ya_ref) < 1e-13
 
 
-@pytest.mark.parametrize("ordering", ["colored", "natural"])
-def test_exact_block_lu(dev, ordering):
+@pytest.mark.parametrize("ordering,apply_path", [("colored", 1), ("natural", 1), ("colored", 2)])
+def test_exact_block_lu(dev, ordering, apply_path):
     H = h2_problem(12, 64, 1e-6)
-    A = gpu_ctx(H, ordering=ordering)
+    A = gpu_ctx(H, ordering=ordering, apply_path=apply_path)
     A.factorize(0.0, "fp64")
     Zd = h2_dense(12, 64, 1e-6)
     b = inputs.rhs_gaussian(H.tree.N, 2, 11)
@@ -81,11 +81,11 @@ def test_exact_block_lu(dev, ordering):
     assert rel(xa, xae) < 1e-10
 
 
-@pytest.mark.parametrize("n,eps", [(12, 1e-6), (16, 1e-6), (12, 1e-4)])
-def test_fp64_parity(dev, n, eps):
+@pytest.mark.parametrize("n,eps,apply_path", [(12, 1e-6, 0), (16, 1e-6, 0), (12, 1e-4, 0), (16, 1e-6, 2)])
+def test_fp64_parity(dev, n, eps, apply_path):
     H = h2_problem(n, 64, eps)
     Fz = factorization(n, 64, eps, eps, "colored")
-    A = gpu_ctx(H)
+    A = gpu_ctx(H, apply_path=apply_path)
     A.factorize(eps, "fp64")
     b = inputs.rhs_gaussian(H.tree.N, 1, 0)[:, 0]
     x_orc = oracle_solve(Fz, b)
