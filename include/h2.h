@@ -204,6 +204,43 @@ h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* x, void* y, int nrhs,
                             unsigned flags, void* stream);
 
 /*
+ * h2_factorize_batch - h2_factorize (Algorithm 1) of `count` independent
+ * instances at once.  The paper factorizes one matrix; this runs the same
+ * per-level work of several matrices in the same launches: for each
+ * level-from-leaf index d (d = 0 at every instance's leaves) and each colour
+ * class b, Steps 0-3 of all instances that have that level and class form
+ * one batch (one launch per kernel), the merges of level d share launches,
+ * and the final blocks are factorized together.  Instances of different
+ * depth join as their levels come up.  Results equal those of h2_factorize
+ * of each instance up to the summation order of the batched products.
+ *   ctxs      count distinct contexts (not host_only), each built or loaded
+ *   eps_fill  prec: as h2_factorize, the same for all instances
+ * Runs on ctxs[0]'s stream; the host waits for it.  On error every
+ * instance's factorization is invalid and ctxs[0] holds the message.
+ */
+h2_status h2_factorize_batch(h2_ctx* const* ctxs, int count, double eps_fill,
+                             int prec);
+
+/*
+ * h2_solve_batch - h2_solve of `count` factorized instances with one
+ * right-hand-side block each (all nrhs wide): the forward / backward sweeps
+ * (Algorithms 5-6), the final blocks and, with H2_REFINE, the FP64 H^2
+ * matvecs of the refinement run as one launch per stage for all instances.
+ *   b[q], x[q]  DEVICE, N_q x nrhs complex128, column-major, global order of
+ *               instance q; x[q] may alias b[q]
+ *   flags       H2_ADJOINT, H2_REFINE, H2_USE_INVERSE (no H2_HOST)
+ *   tol         H2_REFINE: stop when every instance's residual (max over
+ *               its columns of ||b - A x|| / ||b||) is <= tol
+ *   iters,resid out (may be NULL): refinement steps, largest final residual
+ * H2_ENOCONV if refinement stops above tol.  Runs on `stream`; the host
+ * waits for it.  Messages go to ctxs[0].
+ */
+h2_status h2_solve_batch(h2_ctx* const* ctxs, int count, const void* const* b,
+                         void* const* x, int nrhs, unsigned flags, double tol,
+                         int max_iter, int* iters, double* resid,
+                         void* stream);
+
+/*
  * h2_grad_chi - per-cell derivative of a real objective L through the solution
  * map x = A(chi)^{-1} b of the volume-integral system A = I + s K D_chi (the
  * matrix the paper's solver factors, with chi the per-cell contrast of the

@@ -24,7 +24,7 @@ H2_FP64, H2_MIXED = 0, 1
 H2_ADJOINT, H2_REFINE, H2_USE_INVERSE, H2_HOST = 1, 2, 4, 8
 H2_GRAD_ACCUMULATE = 1
 SYMBOLS = ("h2_default_opts", "h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec",
-           "h2_matvec_noalloc", "h2_grad_chi", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
+           "h2_matvec_noalloc", "h2_factorize_batch", "h2_solve_batch", "h2_grad_chi", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
            "h2_status_string", "h2_destroy")
 
 
@@ -65,6 +65,8 @@ def lib():
     L.h2_matvec.argtypes = [P, P, P, I, ctypes.c_uint, P]
     L.h2_matvec_noalloc.argtypes = [P, P, P, I, ctypes.c_uint, P]
     L.h2_grad_chi.argtypes = [P, P, P, P, I, D, P, ctypes.c_uint, P]
+    L.h2_factorize_batch.argtypes = [P, I, D, I]
+    L.h2_solve_batch.argtypes = [P, I, P, P, I, ctypes.c_uint, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.h2_export_sizes.argtypes = [P] + [ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I)] + \
         [ctypes.POINTER(I64)] * 6
     L.h2_export.argtypes = [P] * 12
@@ -76,7 +78,7 @@ def lib():
     L.h2_destroy.argtypes = [P]
     L.h2_destroy.restype = None
     for name in ("h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec", "h2_matvec_noalloc",
-                 "h2_grad_chi", "h2_export_sizes", "h2_export", "h2_stats"):
+                 "h2_grad_chi", "h2_factorize_batch", "h2_solve_batch", "h2_export_sizes", "h2_export", "h2_stats"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -276,3 +278,45 @@ class H2:
             self.close()
         except Exception:
             pass
+
+
+def _handles(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c._h.value if hasattr(c._h, "value") else c._h for c in ctxs])
+    return arr
+
+
+def factorize_batch(ctxs, eps_fill, precision="fp64"):
+    """h2_factorize_batch: factorize several H2 contexts in shared launches."""
+    prec = {"fp64": H2_FP64, "mixed": H2_MIXED}[precision]
+    st = lib().h2_factorize_batch(_handles(ctxs), len(ctxs), float(eps_fill), prec)
+    if st != H2_OK:
+        raise H2Error(st, "h2_factorize_batch: " + lib().h2_last_error(ctxs[0]._h).decode())
+
+
+def solve_batch(ctxs, bs, adjoint=False, refine=False, tol=1e-6, max_iter=20, use_inverse=False, stream=None,
+                allow_noconv=False):
+    """h2_solve_batch: x_q = A_q^{-1} b_q for CUDA complex128 tensors b_q of
+    shape (N_q, nrhs) (same nrhs for all).  Returns (xs, info)."""
+    import torch
+    if len(bs) != len(ctxs):
+        raise ValueError("one right-hand side per context")
+    nrhs = bs[0].shape[1] if bs[0].ndim == 2 else 1
+    bc, xc = [], []
+    for b in bs:
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.complex128):
+            raise TypeError("h2_solve_batch takes CUDA complex128 tensors")
+        if (b.shape[1] if b.ndim == 2 else 1) != nrhs:
+            raise ValueError("all right-hand sides must have the same number of columns")
+        t = (b.reshape(1, -1) if b.ndim == 1 else b.T).contiguous()
+        bc.append(t)
+        xc.append(torch.empty_like(t))
+    flags = (H2_ADJOINT if adjoint else 0) | (H2_REFINE if refine else 0) | (H2_USE_INVERSE if use_inverse else 0)
+    it, res = ctypes.c_int(), ctypes.c_double()
+    barr = (ctypes.c_void_p * len(bc))(*[t.data_ptr() for t in bc])
+    xarr = (ctypes.c_void_p * len(xc))(*[t.data_ptr() for t in xc])
+    st = lib().h2_solve_batch(_handles(ctxs), len(ctxs), barr, xarr, nrhs, flags, float(tol), int(max_iter),
+                              ctypes.byref(it), ctypes.byref(res), _stream(stream))
+    if not (st == H2_OK or (allow_noconv and st == H2_ENOCONV)):
+        raise H2Error(st, "h2_solve_batch: " + lib().h2_last_error(ctxs[0]._h).decode())
+    xs = [(x.reshape(-1) if b.ndim == 1 else x.T) for x, b in zip(xc, bs)]
+    return xs, dict(iters=it.value, resid=res.value, status=st)

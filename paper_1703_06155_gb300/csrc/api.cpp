@@ -93,6 +93,84 @@ std::vector<double> col_norms(h2_ctx* x, const cd* v, int nrhs) {
   return h;
 }
 
+// ---- groups of independent instances (h2_*_batch) ----------------------
+
+std::vector<Ctx*> cores(const std::vector<h2_ctx*>& xs) {
+  std::vector<Ctx*> cs;
+  for (h2_ctx* x : xs) cs.push_back(&x->c);
+  return cs;
+}
+
+// outs[q] = A_q^{-1} ins[q] for every instance, one launch per stage
+void apply_Ainv_group(const std::vector<h2_ctx*>& xs, const std::vector<const cd*>& ins,
+                      const std::vector<cd*>& outs, int nrhs, bool adj, bool inv) {
+  Ctx& lc = xs[0]->c;
+  std::vector<void*> ts;
+  for (size_t q = 0; q < xs.size(); ++q) {
+    Ctx& c = xs[q]->c;
+    const int64_t N = c.H.tree.N;
+    void* t = dev_ensure(c, xs[q]->tA, (size_t)N * nrhs * esz(c.prec));
+    ck(permute_scale(ins[q], t, (const int64_t*)c.dperm.p,
+                     adj ? (const double*)xs[q]->invscale.p : (const double*)c.dscale.p, N, nrhs, P64, c.prec, 0, 0,
+                     lc.stream),
+       "permute in");
+    ts.push_back(t);
+  }
+  solve_tree_group(cores(xs), ts, nrhs, adj, inv);
+  for (size_t q = 0; q < xs.size(); ++q) {
+    Ctx& c = xs[q]->c;
+    ck(permute_scale(ts[q], outs[q], (const int64_t*)c.dperm.p,
+                     adj ? (const double*)c.dscale.p : (const double*)xs[q]->invscale.p, c.H.tree.N, nrhs, c.prec,
+                     P64, 1, 0, lc.stream),
+       "permute out");
+  }
+}
+
+// outs[q] = A_q ins[q] (FP64 H^2 matvec) for every instance
+void apply_A_group(const std::vector<h2_ctx*>& xs, const std::vector<const cd*>& ins, const std::vector<cd*>& outs,
+                   int nrhs, bool adj) {
+  Ctx& lc = xs[0]->c;
+  std::vector<const cd*> t1s;
+  std::vector<cd*> t2s;
+  for (size_t q = 0; q < xs.size(); ++q) {
+    Ctx& c = xs[q]->c;
+    const int64_t N = c.H.tree.N;
+    cd* t1 = (cd*)dev_ensure(c, xs[q]->tB, (size_t)N * nrhs * sizeof(cd));
+    cd* t2 = (cd*)dev_ensure(c, xs[q]->tC, (size_t)N * nrhs * sizeof(cd));
+    ck(permute_scale(ins[q], t1, (const int64_t*)c.dperm.p,
+                     adj ? (const double*)xs[q]->invscale.p : (const double*)c.dscale.p, N, nrhs, P64, P64, 0, 0,
+                     lc.stream),
+       "perm");
+    t1s.push_back(t1);
+    t2s.push_back(t2);
+  }
+  matvec_tree_group(cores(xs), t1s, t2s, nrhs, adj);
+  for (size_t q = 0; q < xs.size(); ++q) {
+    Ctx& c = xs[q]->c;
+    ck(permute_scale(t2s[q], outs[q], (const int64_t*)c.dperm.p,
+                     adj ? (const double*)c.dscale.p : (const double*)xs[q]->invscale.p, c.H.tree.N, nrhs, P64, P64, 1,
+                     0, lc.stream),
+       "perm");
+  }
+}
+
+// per-instance max over columns of ||v|| (one synchronize for the group)
+std::vector<std::vector<double>> col_norms_group(const std::vector<h2_ctx*>& xs, const std::vector<const cd*>& vs,
+                                                 int nrhs) {
+  Ctx& lc = xs[0]->c;
+  std::vector<std::vector<double>> h(xs.size(), std::vector<double>(nrhs));
+  for (size_t q = 0; q < xs.size(); ++q) {
+    Ctx& c = xs[q]->c;
+    double* d = (double*)dev_ensure(c, c.normbuf, (size_t)nrhs * sizeof(double) + 64);
+    ck(col_norms2(vs[q], c.H.tree.N, nrhs, d, lc.stream), "norms");
+    ck(cudaMemcpyAsync(h[q].data(), d, nrhs * sizeof(double), cudaMemcpyDeviceToHost, lc.stream), "norms D2H");
+  }
+  ck(cudaStreamSynchronize(lc.stream), "norms sync");
+  for (auto& v : h)
+    for (auto& v2 : v) v2 = std::sqrt(v2);
+  return h;
+}
+
 // Far-field sample Grams of one level on the GPU (kgram.cu).
 void gpu_gram(h2_ctx* x, double k, double w, const std::vector<std::vector<int64_t>>& rows,
               const std::vector<std::vector<int64_t>>& ranges, std::vector<std::vector<cplx>>& G) {
@@ -630,6 +708,118 @@ h2_status h2_solve(h2_ctx* ctx, const void* b, void* xo, int nrhs, unsigned flag
   });
   if (st == H2_OK && conv != H2_OK) {
     ctx->c.err = "refinement stopped above the tolerance";
+    return conv;
+  }
+  return st;
+}
+
+// Validates a group argument: count > 0, distinct GPU contexts.
+static bool group_ok(h2_ctx* const* ctxs, int count, std::vector<h2_ctx*>& xs) {
+  if (!ctxs || count <= 0) return false;
+  std::set<h2_ctx*> seen;
+  for (int q = 0; q < count; ++q) {
+    if (!ctxs[q] || ctxs[q]->c.opts.host_only || !seen.insert(ctxs[q]).second) return false;
+    xs.push_back(ctxs[q]);
+  }
+  return true;
+}
+
+h2_status h2_factorize_batch(h2_ctx* const* ctxs, int count, double eps_fill, int prec) {
+  std::vector<h2_ctx*> xs;
+  if (!group_ok(ctxs, count, xs)) return H2_EINVAL;
+  if (!(eps_fill >= 0) || (prec != H2_FP64 && prec != H2_MIXED)) {
+    xs[0]->c.err = "h2_factorize_batch: bad argument";
+    return H2_EINVAL;
+  }
+  std::vector<cudaStream_t> own;
+  for (h2_ctx* x : xs) own.push_back(x->c.stream);
+  const h2_status st = guard(xs[0], [&]() {
+    try {
+      factorize_group(cores(xs), eps_fill, prec == H2_FP64 ? P64 : P32);
+    } catch (...) {
+      for (h2_ctx* x : xs) x->c.factored = false;
+      throw;
+    }
+  });
+  for (size_t q = 0; q < xs.size(); ++q) {
+    xs[q]->c.stream = own[q];
+    if (st != H2_OK && q > 0) xs[q]->c.err = "h2_factorize_batch failed: " + xs[0]->c.err;
+  }
+  return st;
+}
+
+h2_status h2_solve_batch(h2_ctx* const* ctxs, int count, const void* const* b, void* const* xo, int nrhs,
+                         unsigned flags, double tol, int max_iter, int* iters, double* resid, void* stream) {
+  std::vector<h2_ctx*> xs;
+  if (!group_ok(ctxs, count, xs) || !b || !xo || nrhs <= 0 || (flags & ~7u)) return H2_EINVAL;
+  for (int q = 0; q < count; ++q)
+    if (!b[q] || !xo[q]) return H2_EINVAL;
+  if (iters) *iters = 0;
+  if (resid) *resid = -1;
+  h2_status conv = H2_OK;
+  const h2_status st = guard(xs[0], [&]() {
+    const bool adj = flags & H2_ADJOINT, inv = flags & H2_USE_INVERSE;
+    if (inv && adj) fail(H2_EINVAL, "H2_USE_INVERSE with H2_ADJOINT");
+    for (h2_ctx* x : xs) {
+      if (!x->c.factored) fail(H2_ESTATE, "h2_solve_batch before factorization");
+      if (inv && !x->c.inverted) fail(H2_ESTATE, "H2_USE_INVERSE before h2_invert");
+      x->c.stream = (cudaStream_t)stream;
+    }
+    Ctx& lc = xs[0]->c;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = lc.launches;
+    ck(cudaStreamSynchronize(lc.stream), "sync");
+    for (h2_ctx* x : xs) x->c.st.begin();
+    std::vector<const cd*> db;
+    std::vector<cd*> dx;
+    for (int q = 0; q < count; ++q) {
+      db.push_back((const cd*)b[q]);
+      dx.push_back((cd*)xo[q]);
+    }
+    if (!(flags & H2_REFINE)) {
+      apply_Ainv_group(xs, db, dx, nrhs, adj, inv);
+    } else {
+      std::vector<cd*> r;
+      for (int q = 0; q < count; ++q) {
+        Ctx& c = xs[q]->c;
+        const size_t bytes = (size_t)c.H.tree.N * nrhs * sizeof(cd);
+        r.push_back((cd*)dev_ensure(c, xs[q]->tR, bytes));
+        if (dx[q] == db[q]) {  // x aliases b: keep a copy of b for the residual
+          cd* bc = (cd*)dev_ensure(c, xs[q]->hb, bytes);
+          ck(cudaMemcpyAsync(bc, db[q], bytes, cudaMemcpyDeviceToDevice, lc.stream), "copy b");
+          db[q] = bc;
+        }
+      }
+      apply_Ainv_group(xs, db, dx, nrhs, adj, inv);
+      const auto nb = col_norms_group(xs, db, nrhs);
+      int it = 0;
+      double rel = 0;
+      std::vector<const cd*> cx(dx.begin(), dx.end()), cr(r.begin(), r.end());
+      for (;;) {
+        apply_A_group(xs, cx, r, nrhs, adj);
+        for (int q = 0; q < count; ++q)
+          ck(axpby(db[q], r[q], r[q], xs[q]->c.H.tree.N * (int64_t)nrhs, 1.0, -1.0, lc.stream), "residual");
+        const auto nr = col_norms_group(xs, cr, nrhs);
+        rel = 0;
+        for (int q = 0; q < count; ++q)
+          for (int k = 0; k < nrhs; ++k) rel = std::max(rel, nb[q][k] > 0 ? nr[q][k] / nb[q][k] : nr[q][k]);
+        if (rel <= tol || it >= max_iter) break;
+        apply_Ainv_group(xs, cr, r, nrhs, adj, inv);
+        for (int q = 0; q < count; ++q)
+          ck(axpby(dx[q], r[q], dx[q], xs[q]->c.H.tree.N * (int64_t)nrhs, 1.0, 1.0, lc.stream), "update");
+        ++it;
+      }
+      if (iters) *iters = it;
+      if (resid) *resid = rel;
+      if (rel > tol) conv = H2_ENOCONV;
+    }
+    ck(cudaStreamSynchronize(lc.stream), "solve sync");
+    prof_resolve(lc);
+    lc.stats.launches_solve = lc.launches - l0;
+    lc.stats.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  });
+  if (st == H2_OK && conv != H2_OK) {
+    xs[0]->c.err = "refinement stopped above the tolerance";
     return conv;
   }
   return st;

@@ -255,325 +255,393 @@ Ptrs ptrs(Ctx& c, LevelF& F) {
               (int*)F.piv_buf.p, esz(c.prec)};
 }
 
-void process_batch(Ctx& c, LevelF& F, const std::vector<int>& bt, std::vector<char>& done, double eps) {
-  const int prec = c.prec;
-  Ptrs P = ptrs(c, F);
-  const size_t es = P.es;
-  auto NB = [&](int j, int k) -> char* { return P.near + F.near_off.at(F.near_id.at(pkey(j, k))) * es; };
-  auto FB = [&](int id) -> char* { return P.fill + F.fill_off[id] * es; };
-  auto lo_of = [&](int j) { return done[j] ? F.m[j] : 0; };
-  std::set<int> inb(bt.begin(), bt.end());
+// One elimination batch of one instance; a group of instances processes its
+// jobs of the same level-from-leaf index and colour together.
+struct Job {
+  Ctx* c;
+  LevelF* F;
+  const std::vector<int>* bt;
+  std::vector<char>* done;
+};
+
+// Step-0 data of one cluster (scratch offsets in its instance's scratch)
+struct Info {
+  int i, n, k0, p, rp = 0;
+  bool fill;
+  size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1;
+  std::vector<int> rowf, colf;
+};
+
+// All launches go to the stream and staging buffers of `lc`; every job's
+// instance shares that stream.
+void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
+  const int prec = lc.prec;
+  const size_t es = esz(prec);
+  const size_t nj = jobs.size();
+  std::vector<Ptrs> P(nj);
+  std::vector<std::vector<Info>> info(nj);
+  std::vector<cd*> S(nj);
+  std::vector<int*> d_r(nj);
+  auto NB = [&](size_t q, int j, int k) -> char* {
+    const LevelF& F = *jobs[q].F;
+    return P[q].near + F.near_off.at(F.near_id.at(pkey(j, k))) * es;
+  };
+  auto FB = [&](size_t q, int id) -> char* { return P[q].fill + jobs[q].F->fill_off[id] * es; };
+  auto lo_of = [&](size_t q, int j) { return (*jobs[q].done)[j] ? jobs[q].F->m[j] : 0; };
+  auto Vp = [&](size_t q, int i) { return (cd*)jobs[q].F->Vp_buf.p + jobs[q].F->Vp_off[i]; };
+  // With a symmetric Z the column fill-ins are the transposed row fill-ins and
+  // the column Gram equals the row Gram: only the row side is formed, and the
+  // admissible-row norm is halved to match (the decisions are unchanged).
+  auto snorm = [&](size_t q, int i) {
+    return jobs[q].c->H.symmetric ? 0.5 * jobs[q].F->snorm2[i] : jobs[q].F->snorm2[i];
+  };
 
   // ------------------------------ Phase A (FP64) ---------------------------
   // Vp: complement of the incoming basis (stored with the level); G' = Vp^H M
   // Vp is the Gram of eq. (16) in complement coordinates.
-  struct Info {
-    int i, n, k0, p, rp = 0;
-    bool fill;
-    size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1;
-    std::vector<int> rowf, colf;
-  };
-  std::vector<Info> info;
-  size_t sc = 0;  // scratch in cd units
-  for (int i : bt) {
-    Info f{};
-    f.i = i;
-    f.n = F.n[i];
-    f.k0 = F.k0[i];
-    f.p = f.n - f.k0;
-    for (size_t q = 0; q < F.fill_pairs.size(); ++q) {
-      if (!F.fill_live[q]) continue;
-      if (F.fill_pairs[q].first == i) f.rowf.push_back((int)q);
-      if (F.fill_pairs[q].second == i) f.colf.push_back((int)q);
-    }
-    f.fill = (!f.rowf.empty() || !f.colf.empty()) && f.p > 0;
-    if (f.fill) {
-      const size_t n = f.n, p = f.p;
-      auto take = [&](size_t cnt) { const size_t o = sc; sc += cnt; return o; };
-      f.M = take(n * n);
-      f.T1 = take(n * p);
-      f.G = take(p * p);
-      f.L = take(p * p);
-      f.T = take(p * p);
-      f.W = take(p * p);
-      f.Qx = take(p * p);
-      f.Z1 = take(p * p);
-      f.Gh = take(p * p);
-      f.U = take(p * p);
-      f.lam = take(p / 2 + 1);
-      f.W1 = take(n * p);
-      f.W2 = take(n * p);
-      f.Yf = take(n * p);
-      f.Y1 = take(n * p);
-    }
-    info.push_back(f);
-  }
-  cd* S = (cd*)dev_ensure(c, c.scratch, (sc + 1) * sizeof(cd));
-  int* d_r = (int*)dev_ensure(c, c.normbuf, 3 * bt.size() * sizeof(int) + 64);
-  ck(cudaMemsetAsync(d_r, 0, 3 * bt.size() * sizeof(int), c.stream), "memset r");
-  auto Vp = [&](int i) { return (cd*)F.Vp_buf.p + F.Vp_off[i]; };
-  // With a symmetric Z the column fill-ins are the transposed row fill-ins and
-  // the column Gram equals the row Gram: only the row side is formed, and the
-  // admissible-row norm is halved to match (the decisions are unchanged).
-  auto snorm = [&](int i) { return c.H.symmetric ? 0.5 * F.snorm2[i] : F.snorm2[i]; };
   bool anyfill = false;
-  for (auto& f : info) anyfill |= f.fill;
-  std::vector<int> r(bt.size(), 0), sweeps;
+  for (size_t q = 0; q < nj; ++q) {
+    Ctx& c = *jobs[q].c;
+    LevelF& F = *jobs[q].F;
+    P[q] = ptrs(c, F);
+    size_t sc = 0;  // scratch in cd units
+    for (int i : *jobs[q].bt) {
+      Info f{};
+      f.i = i;
+      f.n = F.n[i];
+      f.k0 = F.k0[i];
+      f.p = f.n - f.k0;
+      for (size_t id = 0; id < F.fill_pairs.size(); ++id) {
+        if (!F.fill_live[id]) continue;
+        if (F.fill_pairs[id].first == i) f.rowf.push_back((int)id);
+        if (F.fill_pairs[id].second == i) f.colf.push_back((int)id);
+      }
+      f.fill = (!f.rowf.empty() || !f.colf.empty()) && f.p > 0;
+      if (f.fill) {
+        const size_t n = f.n, p = f.p;
+        auto take = [&](size_t cnt) { const size_t o = sc; sc += cnt; return o; };
+        f.M = take(n * n);
+        f.T1 = take(n * p);
+        f.G = take(p * p);
+        f.L = take(p * p);
+        f.T = take(p * p);
+        f.W = take(p * p);
+        f.Qx = take(p * p);
+        f.Z1 = take(p * p);
+        f.Gh = take(p * p);
+        f.U = take(p * p);
+        f.lam = take(p / 2 + 1);
+        f.W1 = take(n * p);
+        f.W2 = take(n * p);
+        f.Yf = take(n * p);
+        f.Y1 = take(n * p);
+        anyfill = true;
+      }
+      info[q].push_back(f);
+    }
+    S[q] = (cd*)dev_ensure(c, c.scratch, (sc + 1) * sizeof(cd));
+    const size_t nb = jobs[q].bt->size();
+    d_r[q] = (int*)dev_ensure(c, c.normbuf, 3 * nb * sizeof(int) + 64);
+    ck(cudaMemsetAsync(d_r[q], 0, 3 * nb * sizeof(int), lc.stream), "memset r");
+  }
+  std::vector<std::vector<int>> r(nj), sweeps(nj);
+  for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
   if (anyfill) {
     GemmBatch gM, gT, gG;
     std::vector<PcholTask> pc;
     int maxp = 0;
-    for (size_t q = 0; q < info.size(); ++q) {
-      Info& f = info[q];
-      if (!f.fill) continue;
-      const int n = f.n;
-      gM.task(S + f.M, n, n, n, 1.0, 0.0);
-      for (int id : f.rowf) {
-        const int k = F.fill_pairs[id].second, lo = lo_of(k);
-        char* A = FB(id) + (size_t)lo * n * es;
-        gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
-      }
-      if (!c.H.symmetric)
-        for (int id : f.colf) {
-          const int k = F.fill_pairs[id].first, lo = lo_of(k);
-          char* A = FB(id) + (size_t)lo * es;
-          gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
+    for (size_t q = 0; q < nj; ++q) {
+      const bool sym = jobs[q].c->H.symmetric;
+      const LevelF& F = *jobs[q].F;
+      for (size_t u = 0; u < info[q].size(); ++u) {
+        Info& f = info[q][u];
+        if (!f.fill) continue;
+        const int n = f.n;
+        cd* Sq = S[q];
+        gM.task(Sq + f.M, n, n, n, 1.0, 0.0);
+        for (int id : f.rowf) {
+          const int k = F.fill_pairs[id].second, lo = lo_of(q, k);
+          char* A = FB(q, id) + (size_t)lo * n * es;
+          gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
         }
-      gM.hermitian();
-      gM.close();
-      gT.task(S + f.T1, n, n, f.p, 1.0, 0.0);
-      gT.pair(S + f.M, n, OP_N, Vp(f.i), n, OP_N, n);
-      gT.close();
-      gG.task(S + f.G, f.p, f.p, f.p, 1.0, 0.0);
-      gG.pair(Vp(f.i), n, OP_H, S + f.T1, n, OP_N, n);
-      gG.close();
-      pc.push_back(PcholTask{S + f.G, S + f.M, S + f.L, S + f.T, d_r + q, f.p, n, snorm(f.i), eps * eps});
-      maxp = std::max(maxp, f.p);
+        if (!sym)
+          for (int id : f.colf) {
+            const int k = F.fill_pairs[id].first, lo = lo_of(q, k);
+            char* A = FB(q, id) + (size_t)lo * es;
+            gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
+          }
+        gM.hermitian();
+        gM.close();
+        gT.task(Sq + f.T1, n, n, f.p, 1.0, 0.0);
+        gT.pair(Sq + f.M, n, OP_N, Vp(q, f.i), n, OP_N, n);
+        gT.close();
+        gG.task(Sq + f.G, f.p, f.p, f.p, 1.0, 0.0);
+        gG.pair(Vp(q, f.i), n, OP_H, Sq + f.T1, n, OP_N, n);
+        gG.close();
+        pc.push_back(PcholTask{Sq + f.G, Sq + f.M, Sq + f.L, Sq + f.T, d_r[q] + u, f.p, n, snorm(q, f.i), eps * eps});
+        maxp = std::max(maxp, f.p);
+      }
     }
-    run_gemm(c, gM, prec, P64, P64, "gram");
-    run_gemm(c, gT, P64, P64, P64, "gram*Vp");
-    run_gemm(c, gG, P64, P64, P64, "Vp^H*gram*Vp");
+    run_gemm(lc, gM, prec, P64, P64, "gram");
+    run_gemm(lc, gT, P64, P64, P64, "gram*Vp");
+    run_gemm(lc, gG, P64, P64, P64, "Vp^H*gram*Vp");
     {
-      const int i0 = c.st.add(pc);
-      c.st.upload(c);
-      ProfScope ps(c, "pchol_wy", 0.0);
-      ck(pchol_wy(c.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, c.stream), "pivoted cholesky");
-      c.launches++;
+      const int i0 = lc.st.add(pc);
+      lc.st.upload(lc);
+      ProfScope ps(lc, "pchol_wy", 0.0);
+      ck(pchol_wy(lc.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, lc.stream), "pivoted cholesky");
+      lc.launches++;
     }
-    std::vector<int> rp(bt.size(), 0);
-    ck(cudaMemcpyAsync(rp.data(), d_r, bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read r'");
-    ck(cudaStreamSynchronize(c.stream), "sync after pivoted cholesky");
-    c.st.begin();
-    for (size_t q = 0; q < info.size(); ++q)
-      if (info[q].fill) info[q].rp = std::min(std::max(rp[q], 0), info[q].p);
+    std::vector<std::vector<int>> rp(nj);
+    for (size_t q = 0; q < nj; ++q) {
+      rp[q].assign(jobs[q].bt->size(), 0);
+      ck(cudaMemcpyAsync(rp[q].data(), d_r[q], rp[q].size() * sizeof(int), cudaMemcpyDeviceToHost, lc.stream),
+         "read r'");
+    }
+    ck(cudaStreamSynchronize(lc.stream), "sync after pivoted cholesky");
+    lc.st.begin();
+    for (size_t q = 0; q < nj; ++q)
+      for (size_t u = 0; u < info[q].size(); ++u)
+        if (info[q][u].fill) info[q][u].rp = std::min(std::max(rp[q][u], 0), info[q][u].p);
     // Ritz step on span(Qx) and the complement rotation Yf = Vp Q, Q = I - Y T Y^H
     GemmBatch g1, g2, g3, g4, g5;
     CopyBatch cp;
     std::vector<EigTask> eig;
     std::vector<SelTask> sel;
     int maxr = 0;
-    for (size_t q = 0; q < info.size(); ++q) {
-      Info& f = info[q];
-      if (!f.fill || f.rp == 0) continue;
-      const int n = f.n, p = f.p, rr = f.rp;
-      cd* Y = S + f.L;
-      g1.task(S + f.W, p, p, rr, 1.0, 0.0);  // W = Y T
-      g1.pair(Y, p, OP_N, S + f.T, rr, OP_N, rr);
-      g1.close();
-      g1.task(S + f.W1, n, n, rr, 1.0, 0.0);  // W1 = Vp Y
-      g1.pair(Vp(f.i), n, OP_N, Y, p, OP_N, p);
-      g1.close();
-      cp.add(nullptr, P64, p, 0, 0, S + f.Qx, P64, p, p, rr, 2);                  // Qx = E
-      cp.add(Vp(f.i), P64, n, n, p, S + f.Yf, P64, n, n, p, 0);                   // Yf = Vp
-      g2.task(S + f.Qx, p, p, rr, -1.0, 1.0);  // Qx = E - W Y(0:r',:)^H
-      g2.pair(S + f.W, p, OP_N, Y, p, OP_H, rr);
-      g2.close();
-      g2.task(S + f.W2, n, n, rr, 1.0, 0.0);  // W2 = W1 T
-      g2.pair(S + f.W1, n, OP_N, S + f.T, rr, OP_N, rr);
-      g2.close();
-      g3.task(S + f.Z1, p, p, rr, 1.0, 0.0);  // Z1 = G' Qx
-      g3.pair(S + f.G, p, OP_N, S + f.Qx, p, OP_N, p);
-      g3.close();
-      g3.task(S + f.Yf, n, n, p, -1.0, 1.0);  // Yf = Vp - W2 Y^H
-      g3.pair(S + f.W2, n, OP_N, Y, p, OP_H, rr);
-      g3.close();
-      g4.task(S + f.Gh, rr, rr, rr, 1.0, 0.0);  // Ritz matrix Qx^H G' Qx
-      g4.pair(S + f.Qx, p, OP_H, S + f.Z1, p, OP_N, p);
-      g4.close();
-      eig.push_back(EigTask{S + f.Gh, S + f.U, (double*)(S + f.lam), rr, d_r + 2 * bt.size() + q});
-      sel.push_back(SelTask{S + f.M, (double*)(S + f.lam), d_r + bt.size() + q, n, rr, snorm(f.i), eps * eps});
-      maxr = std::max(maxr, rr);
-      g5.task(S + f.Y1, n, n, rr, 1.0, 0.0);  // Y1 = Yf(:, 0:r') U
-      g5.pair(S + f.Yf, n, OP_N, S + f.U, rr, OP_N, rr);
-      g5.close();
+    for (size_t q = 0; q < nj; ++q) {
+      const size_t nb = jobs[q].bt->size();
+      cd* Sq = S[q];
+      for (size_t u = 0; u < info[q].size(); ++u) {
+        Info& f = info[q][u];
+        if (!f.fill || f.rp == 0) continue;
+        const int n = f.n, p = f.p, rr = f.rp;
+        cd* Y = Sq + f.L;
+        g1.task(Sq + f.W, p, p, rr, 1.0, 0.0);  // W = Y T
+        g1.pair(Y, p, OP_N, Sq + f.T, rr, OP_N, rr);
+        g1.close();
+        g1.task(Sq + f.W1, n, n, rr, 1.0, 0.0);  // W1 = Vp Y
+        g1.pair(Vp(q, f.i), n, OP_N, Y, p, OP_N, p);
+        g1.close();
+        cp.add(nullptr, P64, p, 0, 0, Sq + f.Qx, P64, p, p, rr, 2);        // Qx = E
+        cp.add(Vp(q, f.i), P64, n, n, p, Sq + f.Yf, P64, n, n, p, 0);      // Yf = Vp
+        g2.task(Sq + f.Qx, p, p, rr, -1.0, 1.0);  // Qx = E - W Y(0:r',:)^H
+        g2.pair(Sq + f.W, p, OP_N, Y, p, OP_H, rr);
+        g2.close();
+        g2.task(Sq + f.W2, n, n, rr, 1.0, 0.0);  // W2 = W1 T
+        g2.pair(Sq + f.W1, n, OP_N, Sq + f.T, rr, OP_N, rr);
+        g2.close();
+        g3.task(Sq + f.Z1, p, p, rr, 1.0, 0.0);  // Z1 = G' Qx
+        g3.pair(Sq + f.G, p, OP_N, Sq + f.Qx, p, OP_N, p);
+        g3.close();
+        g3.task(Sq + f.Yf, n, n, p, -1.0, 1.0);  // Yf = Vp - W2 Y^H
+        g3.pair(Sq + f.W2, n, OP_N, Y, p, OP_H, rr);
+        g3.close();
+        g4.task(Sq + f.Gh, rr, rr, rr, 1.0, 0.0);  // Ritz matrix Qx^H G' Qx
+        g4.pair(Sq + f.Qx, p, OP_H, Sq + f.Z1, p, OP_N, p);
+        g4.close();
+        eig.push_back(EigTask{Sq + f.Gh, Sq + f.U, (double*)(Sq + f.lam), rr, d_r[q] + 2 * nb + u});
+        sel.push_back(SelTask{Sq + f.M, (double*)(Sq + f.lam), d_r[q] + nb + u, n, rr, snorm(q, f.i), eps * eps});
+        maxr = std::max(maxr, rr);
+        g5.task(Sq + f.Y1, n, n, rr, 1.0, 0.0);  // Y1 = Yf(:, 0:r') U
+        g5.pair(Sq + f.Yf, n, OP_N, Sq + f.U, rr, OP_N, rr);
+        g5.close();
+      }
     }
-    run_gemm(c, g1, P64, P64, P64, "WY 1");
-    run_copy(c, cp, "WY presets");
-    run_gemm(c, g2, P64, P64, P64, "WY 2");
-    run_gemm(c, g3, P64, P64, P64, "WY 3");
-    run_gemm(c, g4, P64, P64, P64, "ritz matrix");
+    run_gemm(lc, g1, P64, P64, P64, "WY 1");
+    run_copy(lc, cp, "WY presets");
+    run_gemm(lc, g2, P64, P64, P64, "WY 2");
+    run_gemm(lc, g3, P64, P64, P64, "WY 3");
+    run_gemm(lc, g4, P64, P64, P64, "ritz matrix");
     if (!eig.empty()) {
-      const int i0 = c.st.add(eig);
-      c.st.upload(c);
-      ProfScope ps(c, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0);
+      const int i0 = lc.st.add(eig);
+      lc.st.upload(lc);
+      ProfScope ps(lc, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0);
       if (maxr >= 48) {
         // large Ritz problems: one 8-CTA cluster per eigenproblem
         const int64_t per = jacobi_cluster_scratch(maxr);
-        double* js = (double*)dev_ensure(c, c.jac_buf, (size_t)per * eig.size() * sizeof(double));
-        ck(jacobi_eig_cluster(c.st.ptr<EigTask>(i0), (int)eig.size(), maxr, 8, js, (int*)c.statusbuf.p, c.stream),
+        double* js = (double*)dev_ensure(lc, lc.jac_buf, (size_t)per * eig.size() * sizeof(double));
+        ck(jacobi_eig_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, 8, js, (int*)lc.statusbuf.p, lc.stream),
            "jacobi (cluster)");
       } else {
-        ck(jacobi_eig(c.st.ptr<EigTask>(i0), (int)eig.size(), maxr, (int*)c.statusbuf.p, c.stream), "jacobi");
+        ck(jacobi_eig(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, (int*)lc.statusbuf.p, lc.stream), "jacobi");
       }
-      c.launches++;
-      const int i1 = c.st.add(sel);
-      c.st.upload(c);
-      ck(select_rank(c.st.ptr<SelTask>(i1), (int)sel.size(), c.stream), "select");
-      c.launches++;
+      lc.launches++;
+      const int i1 = lc.st.add(sel);
+      lc.st.upload(lc);
+      ck(select_rank(lc.st.ptr<SelTask>(i1), (int)sel.size(), lc.stream), "select");
+      lc.launches++;
     }
-    run_gemm(c, g5, P64, P64, P64, "ritz vectors");
-    ck(cudaMemcpyAsync(r.data(), d_r + bt.size(), bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
-       "read r");
-    sweeps.resize(bt.size());
-    ck(cudaMemcpyAsync(sweeps.data(), d_r + 2 * bt.size(), bt.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
-       "read sweeps");
+    run_gemm(lc, g5, P64, P64, P64, "ritz vectors");
+    for (size_t q = 0; q < nj; ++q) {
+      const size_t nb = jobs[q].bt->size();
+      sweeps[q].assign(nb, 0);
+      ck(cudaMemcpyAsync(r[q].data(), d_r[q] + nb, nb * sizeof(int), cudaMemcpyDeviceToHost, lc.stream), "read r");
+      ck(cudaMemcpyAsync(sweeps[q].data(), d_r[q] + 2 * nb, nb * sizeof(int), cudaMemcpyDeviceToHost, lc.stream),
+         "read sweeps");
+    }
   }
-  ck(cudaStreamSynchronize(c.stream), "sync after step 0");
-  prof_resolve(c);
-  c.st.begin();  // stream idle: staging can be reused
-  for (size_t q = 0; q < info.size(); ++q) {
-    const Info& f = info[q];
-    const int rr = (f.fill && f.rp > 0) ? std::min(std::max(r[q], 0), f.rp) : 0;
-    if (f.fill && f.rp > 0) {
-      F.st_ritz_max = std::max(F.st_ritz_max, f.rp);
-      F.st_ritz_sum += f.rp;
-      F.st_ritz_n++;
-      if (!sweeps.empty()) F.st_sweeps_max = std::max(F.st_sweeps_max, sweeps[q]);
+  ck(cudaStreamSynchronize(lc.stream), "sync after step 0");
+  prof_resolve(lc);
+  lc.st.begin();  // stream idle: staging can be reused
+  for (size_t q = 0; q < nj; ++q) {
+    LevelF& F = *jobs[q].F;
+    for (size_t u = 0; u < info[q].size(); ++u) {
+      const Info& f = info[q][u];
+      const int rr = (f.fill && f.rp > 0) ? std::min(std::max(r[q][u], 0), f.rp) : 0;
+      if (f.fill && f.rp > 0) {
+        F.st_ritz_max = std::max(F.st_ritz_max, f.rp);
+        F.st_ritz_sum += f.rp;
+        F.st_ritz_n++;
+        if (!sweeps[q].empty()) F.st_sweeps_max = std::max(F.st_sweeps_max, sweeps[q][u]);
+      }
+      r[q][u] = rr;
+      F.kt[f.i] = f.k0 + rr;
+      F.m[f.i] = f.n - F.kt[f.i];
     }
-    r[q] = rr;
-    F.kt[f.i] = f.k0 + rr;
-    F.m[f.i] = f.n - F.kt[f.i];
   }
 
   // ------------------------------ Phase B (bulk) ---------------------------
   CopyBatch qc;
-  for (size_t q = 0; q < info.size(); ++q) {
-    const Info& f = info[q];
-    const int n = f.n, m = F.m[f.i], rr = r[q];
-    char* Q = P.Q + F.Q_off[f.i] * es;
-    if (f.fill && f.rp > 0) {
-      // Q~ = [Y1(:, r:r'), Yf(:, r':p), B, Y1(:, 0:r)]  (eqs. 18-19)
-      const int rp = f.rp;
-      qc.add(S + f.Y1 + (size_t)rr * n, P64, n, n, rp - rr, Q, prec, n, n, rp - rr);
-      qc.add(S + f.Yf + (size_t)rp * n, P64, n, n, f.p - rp, Q + (size_t)(rp - rr) * n * es, prec, n, n, f.p - rp);
-      if (rr > 0) qc.add(S + f.Y1, P64, n, n, rr, Q + (size_t)(m + f.k0) * n * es, prec, n, n, rr);
-    } else {
-      qc.add(Vp(f.i), P64, n, n, f.p, Q, prec, n, n, f.p);
+  for (size_t q = 0; q < nj; ++q) {
+    const LevelF& F = *jobs[q].F;
+    cd* Sq = S[q];
+    for (size_t u = 0; u < info[q].size(); ++u) {
+      const Info& f = info[q][u];
+      const int n = f.n, m = F.m[f.i], rr = r[q][u];
+      char* Q = P[q].Q + F.Q_off[f.i] * es;
+      if (f.fill && f.rp > 0) {
+        // Q~ = [Y1(:, r:r'), Yf(:, r':p), B, Y1(:, 0:r)]  (eqs. 18-19)
+        const int rp = f.rp;
+        qc.add(Sq + f.Y1 + (size_t)rr * n, P64, n, n, rp - rr, Q, prec, n, n, rp - rr);
+        qc.add(Sq + f.Yf + (size_t)rp * n, P64, n, n, f.p - rp, Q + (size_t)(rp - rr) * n * es, prec, n, n, f.p - rp);
+        if (rr > 0) qc.add(Sq + f.Y1, P64, n, n, rr, Q + (size_t)(m + f.k0) * n * es, prec, n, n, rr);
+      } else {
+        qc.add(Vp(q, f.i), P64, n, n, f.p, Q, prec, n, n, f.p);
+      }
+      qc.add(P[q].B + F.B_off[f.i], P64, n, n, f.k0, Q + (size_t)m * n * es, prec, n, n, f.k0);
     }
-    qc.add(P.B + F.B_off[f.i], P64, n, n, f.k0, Q + (size_t)m * n * es, prec, n, n, f.k0);
   }
-  run_copy(c, qc, "form Q");
+  run_copy(lc, qc, "form Q");
 
   // Step 2: rows (left, Q^H) then columns (right, conj Q)
   ApplyBatch L2, R2;
-  for (int i : bt) {
-    const int n = F.n[i], m = F.m[i];
-    const char* Q = P.Q + F.Q_off[i] * es;
-    for (int j : F.nbrs[i]) {
-      if (j == i) {
-        L2.add(Q, n, OP_H, NB(i, i), n, n, n, 0);
-        R2.add(Q, n, OP_C, NB(i, i), n, n, n, 0);
-      } else {
-        const int lo = lo_of(j);
-        L2.add(Q, n, OP_H, NB(i, j) + (size_t)lo * n * es, n, n, F.n[j] - lo, 0);
-        R2.add(Q, n, OP_C, NB(j, i) + (size_t)lo * es, F.n[j], n, F.n[j] - lo, 0);
+  for (size_t q = 0; q < nj; ++q) {
+    const LevelF& F = *jobs[q].F;
+    for (int i : *jobs[q].bt) {
+      const int n = F.n[i], m = F.m[i];
+      const char* Q = P[q].Q + F.Q_off[i] * es;
+      for (int j : F.nbrs[i]) {
+        if (j == i) {
+          L2.add(Q, n, OP_H, NB(q, i, i), n, n, n, 0);
+          R2.add(Q, n, OP_C, NB(q, i, i), n, n, n, 0);
+        } else {
+          const int lo = lo_of(q, j);
+          L2.add(Q, n, OP_H, NB(q, i, j) + (size_t)lo * n * es, n, n, F.n[j] - lo, 0);
+          R2.add(Q, n, OP_C, NB(q, j, i) + (size_t)lo * es, F.n[j], n, F.n[j] - lo, 0);
+        }
       }
-    }
-    for (size_t id = 0; id < F.fill_pairs.size(); ++id) {
-      if (!F.fill_live[id]) continue;
-      const auto [a, b] = F.fill_pairs[id];
-      if (a == i) {
-        const int lo = lo_of(b);
-        L2.add(Q, n, OP_H, FB((int)id) + (size_t)lo * n * es, n, n, F.n[b] - lo, m);
-      }
-      if (b == i) {
-        const int lo = lo_of(a);
-        R2.add(Q, n, OP_C, FB((int)id) + (size_t)lo * es, F.n[a], n, F.n[a] - lo, m);
+      for (size_t id = 0; id < F.fill_pairs.size(); ++id) {
+        if (!F.fill_live[id]) continue;
+        const auto [a, b] = F.fill_pairs[id];
+        if (a == i) {
+          const int lo = lo_of(q, b);
+          L2.add(Q, n, OP_H, FB(q, (int)id) + (size_t)lo * n * es, n, n, F.n[b] - lo, m);
+        }
+        if (b == i) {
+          const int lo = lo_of(q, a);
+          R2.add(Q, n, OP_C, FB(q, (int)id) + (size_t)lo * es, F.n[a], n, F.n[a] - lo, m);
+        }
       }
     }
   }
-  run_apply_auto(c, L2, true, prec, "step2 rows");
-  run_apply_auto(c, R2, false, prec, "step2 cols");
-  c.stats.flops_factor += L2.flops + R2.flops;
+  run_apply_auto(lc, L2, true, prec, "step2 rows");
+  run_apply_auto(lc, R2, false, prec, "step2 cols");
+  const double f2 = (L2.flops + R2.flops) / (double)nj;
 
   // Step 3: LU + explicit inverses, panels, Schur
   std::vector<LuTask> lu;
-  for (int i : bt) {
-    const int n = F.n[i], m = F.m[i];
-    if (m <= 0) continue;
-    char* inv = P.inv + F.inv_off[i] * es;
-    lu.push_back(LuTask{NB(i, i), inv, inv + (size_t)n * n * es, P.piv + F.piv_off[i], n, m});
-    c.stats.flops_factor += 8.0 / 3.0 * m * (double)m * m + 8.0 / 3.0 * m * (double)m * m;
+  for (size_t q = 0; q < nj; ++q) {
+    const LevelF& F = *jobs[q].F;
+    for (int i : *jobs[q].bt) {
+      const int n = F.n[i], m = F.m[i];
+      if (m <= 0) continue;
+      char* inv = P[q].inv + F.inv_off[i] * es;
+      lu.push_back(LuTask{NB(q, i, i), inv, inv + (size_t)n * n * es, P[q].piv + F.piv_off[i], n, m});
+      jobs[q].c->stats.flops_factor += 8.0 / 3.0 * m * (double)m * m + 8.0 / 3.0 * m * (double)m * m;
+    }
   }
   if (!lu.empty()) {
-    const int i0 = c.st.add(lu);
-    c.st.upload(c);
-    ProfScope ps(c, "lu", 0.0);
+    const int i0 = lc.st.add(lu);
+    lc.st.upload(lc);
+    ProfScope ps(lc, "lu", 0.0);
     int maxm = 0;
-    for (const LuTask& q : lu) maxm = std::max(maxm, q.m);
-    ck(lu_blocked(c.st.ptr<LuTask>(i0), (int)lu.size(), maxm, prec, (int*)c.statusbuf.p, c.stream), "lu");
-    c.launches++;
+    for (const LuTask& t : lu) maxm = std::max(maxm, t.m);
+    ck(lu_blocked(lc.st.ptr<LuTask>(i0), (int)lu.size(), maxm, prec, (int*)lc.statusbuf.p, lc.stream), "lu");
+    lc.launches++;
   }
   ApplyBatch PL, PR;
-  for (int i : bt) {
-    const int n = F.n[i], m = F.m[i];
-    if (m <= 0) continue;
-    const char* Linv = P.inv + F.inv_off[i] * es;
-    const char* Uinv = Linv + (size_t)n * n * es;
-    for (int j : F.nbrs[i]) {
-      const int lo = (j == i) ? m : lo_of(j);
-      PL.add(Linv, m, OP_N, NB(i, j) + (size_t)lo * n * es, n, m, F.n[j] - lo, 0);
-      PR.add(Uinv, m, OP_N, NB(j, i) + (size_t)lo * es, F.n[j], m, F.n[j] - lo, 0);
+  for (size_t q = 0; q < nj; ++q) {
+    const LevelF& F = *jobs[q].F;
+    for (int i : *jobs[q].bt) {
+      const int n = F.n[i], m = F.m[i];
+      if (m <= 0) continue;
+      const char* Linv = P[q].inv + F.inv_off[i] * es;
+      const char* Uinv = Linv + (size_t)n * n * es;
+      for (int j : F.nbrs[i]) {
+        const int lo = (j == i) ? m : lo_of(q, j);
+        PL.add(Linv, m, OP_N, NB(q, i, j) + (size_t)lo * n * es, n, m, F.n[j] - lo, 0);
+        PR.add(Uinv, m, OP_N, NB(q, j, i) + (size_t)lo * es, F.n[j], m, F.n[j] - lo, 0);
+      }
     }
   }
-  run_apply_auto(c, PL, true, prec, "U panels");
-  run_apply_auto(c, PR, false, prec, "L panels");
-  c.stats.flops_factor += PL.flops + PR.flops;
+  run_apply_auto(lc, PL, true, prec, "U panels");
+  run_apply_auto(lc, PR, false, prec, "L panels");
+  const double f3 = (PL.flops + PR.flops) / (double)nj;
 
-  std::map<int64_t, std::vector<int>> tg;
-  for (int i : bt) {
-    if (F.m[i] <= 0) continue;
-    for (int j : F.nbrs[i])
-      for (int k : F.nbrs[i]) tg[pkey(j, k)].push_back(i);
-  }
   GemmBatch gs;
-  for (auto& [key, cl] : tg) {
-    const int j = (int)(key >> 32), k = (int)(uint32_t)key;
-    const int rlo = inb.count(j) ? F.m[j] : lo_of(j);
-    const int clo = inb.count(k) ? F.m[k] : lo_of(k);
-    const int nj = F.n[j], nk = F.n[k];
-    char* C;
-    auto it = F.near_id.find(key);
-    if (it != F.near_id.end()) {
-      C = P.near + F.near_off[it->second] * es;
-    } else {
-      const int id = F.fill_id.at(key);
-      C = FB(id);
-      F.fill_live[id] = 1;
+  for (size_t q = 0; q < nj; ++q) {
+    LevelF& F = *jobs[q].F;
+    const std::vector<int>& bt = *jobs[q].bt;
+    std::set<int> inb(bt.begin(), bt.end());
+    std::map<int64_t, std::vector<int>> tg;
+    for (int i : bt) {
+      if (F.m[i] <= 0) continue;
+      for (int j : F.nbrs[i])
+        for (int k : F.nbrs[i]) tg[pkey(j, k)].push_back(i);
     }
-    gs.task(C + ((size_t)rlo + (size_t)clo * nj) * es, nj, nj - rlo, nk - clo, -1.0, 1.0);
-    for (int i : cl) {
-      const int ni = F.n[i], mi = F.m[i];
-      gs.pair(NB(j, i) + (size_t)rlo * es, nj, OP_N, NB(i, k) + (size_t)clo * ni * es, ni, OP_N, mi);
+    const double fl0 = gs.flops;
+    for (auto& [key, cl] : tg) {
+      const int j = (int)(key >> 32), k = (int)(uint32_t)key;
+      const int rlo = inb.count(j) ? F.m[j] : lo_of(q, j);
+      const int clo = inb.count(k) ? F.m[k] : lo_of(q, k);
+      const int nj_ = F.n[j], nk = F.n[k];
+      char* C;
+      auto it = F.near_id.find(key);
+      if (it != F.near_id.end()) {
+        C = P[q].near + F.near_off[it->second] * es;
+      } else {
+        const int id = F.fill_id.at(key);
+        C = FB(q, id);
+        F.fill_live[id] = 1;
+      }
+      gs.task(C + ((size_t)rlo + (size_t)clo * nj_) * es, nj_, nj_ - rlo, nk - clo, -1.0, 1.0);
+      for (int i : cl) {
+        const int ni = F.n[i], mi = F.m[i];
+        gs.pair(NB(q, j, i) + (size_t)rlo * es, nj_, OP_N, NB(q, i, k) + (size_t)clo * ni * es, ni, OP_N, mi);
+      }
+      gs.close();
     }
-    gs.close();
+    jobs[q].c->stats.flops_factor += gs.flops - fl0 + f2 + f3;
   }
-  run_gemm(c, gs, prec, prec, prec, "schur");
-  c.stats.flops_factor += gs.flops;
-  for (int i : bt) done[i] = 1;
+  run_gemm(lc, gs, prec, prec, prec, "schur");
+  for (size_t q = 0; q < nj; ++q)
+    for (int i : *jobs[q].bt) (*jobs[q].done)[i] = 1;
 }
 
-std::vector<Pair> merge_level(Ctx& c, LevelF& F, LevelF& Pn) {
+// Sets up the parent level and appends its merge copies to `as` / `ac` (the
+// caller launches them, for all instances of a group at once).
+void merge_level(Ctx& c, LevelF& F, LevelF& Pn, CopyBatch& as, CopyBatch& ac) {
   const int l = F.l;
   const size_t es = esz(c.prec);
   const int prec = c.prec;
@@ -587,7 +655,6 @@ std::vector<Pair> merge_level(Ctx& c, LevelF& F, LevelF& Pn) {
   Ptrs S = ptrs(c, F), D = ptrs(c, Pn);
   auto NBs = [&](int a, int b) { return S.near + F.near_off.at(F.near_id.at(pkey(a, b))) * es; };
   auto ro = [&](int a) { return (a & 1) ? F.kt[a - 1] : 0; };
-  CopyBatch as, ac;
   for (size_t q = 0; q < Pn.near_pairs.size(); ++q) {
     const auto [p, r] = Pn.near_pairs[q];
     char* dst = D.near + Pn.near_off[q] * es;
@@ -647,78 +714,101 @@ std::vector<Pair> merge_level(Ctx& c, LevelF& F, LevelF& Pn) {
     as.add(T, P64, ldT, F.k0[c1], kp, Bp, P64, Pn.n[p], F.kt[c1], kp);
     as.add(T + F.k0[c1], P64, ldT, F.k0[c2], kp, Bp + F.kt[c1], P64, Pn.n[p], F.kt[c2], kp);
   }
-  run_copy(c, as, "merge");
-  run_copy(c, ac, "merge fill");
-  return {};
 }
 
-void root_factor(Ctx& c, LevelF& F) {
-  const int prec = c.prec;
+// Blocked right-looking LU with partial pivoting of the final block of every
+// instance (Algorithm 1, last line); panel step pi of all instances runs in
+// the same launches.
+void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
+  const int prec = lc.prec;
   const size_t es = esz(prec);
-  const int l = F.l;
-  RootF& R = c.root;
-  R.kt = F.kt;
-  std::vector<int> off(F.nc + 1, 0);
-  for (int a = 0; a < F.nc; ++a) off[a + 1] = off[a] + F.kt[a];
-  const int n = off[F.nc];
-  R.n = n;
-  if (n == 0) return;
-  char* Rm = (char*)dev_ensure(c, R.R, (size_t)n * n * es);
-  Ptrs S = ptrs(c, F);
   CopyBatch as, ac;
-  for (int a = 0; a < F.nc; ++a)
-    for (int b = 0; b < F.nc; ++b) {
-      char* d = Rm + ((size_t)off[a] + (size_t)off[b] * n) * es;
-      const int64_t key = pkey(a, b);
-      if (F.near_id.count(key)) {
-        as.add(S.near + (F.near_off[F.near_id.at(key)] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a],
-               F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b]);
-      } else {
-        auto ai = c.adm_id[l].find(key);
-        if (ai == c.adm_id[l].end()) fail(H2_EINTERNAL, "final block: pair neither near nor admissible");
-        as.add((char*)c.dS.p + c.S_off[l][ai->second] * sizeof(cd), P64, F.k0[a], F.k0[a], F.k0[b], d, prec, n,
-               F.kt[a], F.kt[b]);
-        auto it = F.fill_id.find(key);
-        if (it != F.fill_id.end() && F.fill_live[it->second])
-          ac.add(S.fill + (F.fill_off[it->second] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a],
-                 F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b], 1);
+  int npan_max = 0;
+  for (Ctx* cp : cs) {
+    Ctx& c = *cp;
+    LevelF& F = c.lev.back();
+    const int l = F.l;
+    RootF& R = c.root;
+    R.kt = F.kt;
+    std::vector<int> off(F.nc + 1, 0);
+    for (int a = 0; a < F.nc; ++a) off[a + 1] = off[a] + F.kt[a];
+    const int n = off[F.nc];
+    R.n = n;
+    if (n == 0) continue;
+    char* Rm = (char*)dev_ensure(c, R.R, (size_t)n * n * es);
+    Ptrs S = ptrs(c, F);
+    for (int a = 0; a < F.nc; ++a)
+      for (int b = 0; b < F.nc; ++b) {
+        char* d = Rm + ((size_t)off[a] + (size_t)off[b] * n) * es;
+        const int64_t key = pkey(a, b);
+        if (F.near_id.count(key)) {
+          as.add(S.near + (F.near_off[F.near_id.at(key)] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec,
+                 F.n[a], F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b]);
+        } else {
+          auto ai = c.adm_id[l].find(key);
+          if (ai == c.adm_id[l].end()) fail(H2_EINTERNAL, "final block: pair neither near nor admissible");
+          as.add((char*)c.dS.p + c.S_off[l][ai->second] * sizeof(cd), P64, F.k0[a], F.k0[a], F.k0[b], d, prec, n,
+                 F.kt[a], F.kt[b]);
+          auto it = F.fill_id.find(key);
+          if (it != F.fill_id.end() && F.fill_live[it->second])
+            ac.add(S.fill + (F.fill_off[it->second] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a],
+                   F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b], 1);
+        }
+      }
+    const int nb = R.nb;
+    const int npan = (n + nb - 1) / nb;
+    dev_ensure(c, R.piv, (size_t)n * sizeof(int));
+    dev_ensure(c, R.Linv, (size_t)npan * nb * nb * es);
+    dev_ensure(c, R.Uinv, (size_t)npan * nb * nb * es);
+    npan_max = std::max(npan_max, npan);
+  }
+  run_copy(lc, as, "root assemble");
+  run_copy(lc, ac, "root assemble fill");
+  for (int pi = 0; pi < npan_max; ++pi) {
+    std::vector<PanelTask> pt;
+    std::vector<SwapTask> sw;
+    ApplyBatch ab;
+    GemmBatch g;
+    double fl = 0;
+    for (Ctx* cp : cs) {
+      Ctx& c = *cp;
+      RootF& R = c.root;
+      const int n = R.n, nb = R.nb;
+      if (pi * nb >= n) continue;
+      char* Rm = (char*)R.R.p;
+      char* Li = (char*)R.Linv.p;
+      char* Ui = (char*)R.Uinv.p;
+      int* ipiv = (int*)R.piv.p;
+      const int k0 = pi * nb, kb = std::min(nb, n - k0);
+      pt.push_back(PanelTask{Rm, Li + (size_t)pi * nb * nb * es, Ui + (size_t)pi * nb * nb * es, ipiv + k0, n, k0, k0,
+                             n - k0, kb});
+      sw.push_back(SwapTask{Rm, ipiv + k0, n, k0, kb, 0, k0, 0});
+      sw.push_back(SwapTask{Rm, ipiv + k0, n, k0, kb, k0 + kb, n, 0});
+      c.stats.flops_factor += 8.0 * (n - k0) * (double)kb * kb / 2;
+      fl += 8.0 * (n - k0) * (double)kb * kb / 2;
+      const int rest = n - k0 - kb;
+      if (rest > 0) {
+        const double f0 = g.flops, a0 = ab.flops;
+        ab.add(Li + (size_t)pi * nb * nb * es, kb, OP_N, Rm + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n, kb, rest, 0);
+        g.task(Rm + ((size_t)(k0 + kb) + (size_t)(k0 + kb) * n) * es, n, rest, rest, -1.0, 1.0);
+        g.pair(Rm + ((size_t)(k0 + kb) + (size_t)k0 * n) * es, n, OP_N, Rm + ((size_t)k0 + (size_t)(k0 + kb) * n) * es,
+               n, OP_N, kb);
+        g.close();
+        c.stats.flops_factor += g.flops - f0 + ab.flops - a0;
       }
     }
-  run_copy(c, as, "root assemble");
-  run_copy(c, ac, "root assemble fill");
-  // blocked right-looking LU with partial pivoting
-  const int nb = R.nb;
-  const int npan = (n + nb - 1) / nb;
-  int* ipiv = (int*)dev_ensure(c, R.piv, (size_t)n * sizeof(int));
-  char* Li = (char*)dev_ensure(c, R.Linv, (size_t)npan * nb * nb * es);
-  char* Ui = (char*)dev_ensure(c, R.Uinv, (size_t)npan * nb * nb * es);
-  for (int pi = 0; pi < npan; ++pi) {
-    const int k0 = pi * nb, kb = std::min(nb, n - k0);
-    std::vector<PanelTask> pt{PanelTask{Rm, Li + (size_t)pi * nb * nb * es, Ui + (size_t)pi * nb * nb * es, ipiv + k0,
-                                        n, k0, k0, n - k0, kb}};
-    const int i0 = c.st.add(pt);
-    c.st.upload(c);
     {
-      ProfScope ps(c, "root_panel", 8.0 * (n - k0) * (double)kb * kb / 2);
-      ck(lu_panel(c.st.ptr<PanelTask>(i0), prec, (int*)c.statusbuf.p, c.stream), "root panel");
+      const int i0 = lc.st.add(pt), i1 = lc.st.add(sw);
+      lc.st.upload(lc);
+      {
+        ProfScope ps(lc, "root_panel", fl);
+        ck(lu_panel(lc.st.ptr<PanelTask>(i0), (int)pt.size(), prec, (int*)lc.statusbuf.p, lc.stream), "root panel");
+      }
+      ck(swap_rows_batch(lc.st.ptr<SwapTask>(i1), (int)sw.size(), prec, lc.stream), "root swaps");
+      lc.launches += 2;
     }
-    ck(swap_rows(Rm, n, ipiv + k0, k0, kb, 0, k0, prec, 0, c.stream), "root swaps left");
-    ck(swap_rows(Rm, n, ipiv + k0, k0, kb, k0 + kb, n, prec, 0, c.stream), "root swaps right");
-    c.launches += 3;
-    c.stats.flops_factor += 8.0 * (n - k0) * (double)kb * kb / 2;
-    const int rest = n - k0 - kb;
-    if (rest > 0) {
-      ApplyBatch ab;
-      ab.add(Li + (size_t)pi * nb * nb * es, kb, OP_N, Rm + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n, kb, rest, 0);
-      run_apply(c, ab, true, prec, "root trsm");
-      GemmBatch g;
-      g.task(Rm + ((size_t)(k0 + kb) + (size_t)(k0 + kb) * n) * es, n, rest, rest, -1.0, 1.0);
-      g.pair(Rm + ((size_t)(k0 + kb) + (size_t)k0 * n) * es, n, OP_N, Rm + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n,
-             OP_N, kb);
-      g.close();
-      run_gemm(c, g, prec, prec, prec, "root update");
-      c.stats.flops_factor += ab.flops + g.flops;
-    }
+    run_apply(lc, ab, true, prec, "root trsm");
+    run_gemm(lc, g, prec, prec, prec, "root update");
   }
 }
 
@@ -733,61 +823,101 @@ void check_status(Ctx& c) {
 
 }  // namespace
 
-void factorize(Ctx& c, double eps, int prec) {
+// Algorithm 1 for a group of independent instances: level-from-leaf index
+// d and colour b of every instance run in the same launches (instances of
+// different depth join as their levels come up).  All launches go to the
+// first instance's stream; the others' streams are set to it for the call.
+void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
   const auto t0 = std::chrono::steady_clock::now();
-  c.factored = false;
-  c.inverted = false;
-  c.prec = prec;
-  c.eps_fill = eps;
-  c.stats.flops_factor = 0;
-  prof_reset(c);
-  const int64_t launches0 = c.launches;
-  H2Host& H = c.H;
-  const int L = H.L, l0 = H.l0;
-  dev_ensure(c, c.statusbuf, 64);
-  ck(cudaMemsetAsync(c.statusbuf.p, 0, 64, c.stream), "status memset");
-  ck(cudaStreamSynchronize(c.stream), "sync");
-  c.st.begin();
-  if ((int)c.lev.size() != L - l0 + 1) {
-    c.lev.clear();
-    c.lev.resize(L - l0 + 1);
+  Ctx& lc = *cs[0];
+  for (Ctx* c : cs) {
+    c->stream = lc.stream;
+    c->factored = false;
+    c->inverted = false;
+    c->prec = prec;
+    c->eps_fill = eps;
+    c->stats.flops_factor = 0;
+    prof_reset(*c);
   }
-  // leaf level: dense near blocks and leaf bases
+  const int64_t launches0 = lc.launches;
+  dev_ensure(lc, lc.statusbuf, 64);
+  ck(cudaMemsetAsync(lc.statusbuf.p, 0, 64, lc.stream), "status memset");
+  ck(cudaStreamSynchronize(lc.stream), "sync");
+  lc.st.begin();
+  int depth = 0;  // levels L .. l0 of the deepest instance
   {
-    std::vector<int> n(1 << L);
-    for (int t = 0; t < (1 << L); ++t) n[t] = (int)H.tree.size[L][t];
-    setup_level(c, c.lev[0], L, n, {});
-    LevelF& F = c.lev[0];
-    const size_t es = esz(prec);
     CopyBatch cb;
-    for (size_t q = 0; q < F.near_pairs.size(); ++q) {
-      const auto [a, b] = F.near_pairs[q];
-      cb.add((const cd*)c.dD.p + c.D_off[q], P64, n[a], n[a], n[b], (char*)F.near_buf.p + F.near_off[q] * es, prec,
-             n[a], n[a], n[b]);
+    for (Ctx* cp : cs) {
+      Ctx& c = *cp;
+      H2Host& H = c.H;
+      const int L = H.L, l0 = H.l0;
+      depth = std::max(depth, L - l0 + 1);
+      if ((int)c.lev.size() != L - l0 + 1) {
+        c.lev.clear();
+        c.lev.resize(L - l0 + 1);
+      }
+      // leaf level: dense near blocks and leaf bases
+      std::vector<int> n(1 << L);
+      for (int t = 0; t < (1 << L); ++t) n[t] = (int)H.tree.size[L][t];
+      setup_level(c, c.lev[0], L, n, {});
+      LevelF& F = c.lev[0];
+      const size_t es = esz(prec);
+      for (size_t q = 0; q < F.near_pairs.size(); ++q) {
+        const auto [a, b] = F.near_pairs[q];
+        cb.add((const cd*)c.dD.p + c.D_off[q], P64, n[a], n[a], n[b], (char*)F.near_buf.p + F.near_off[q] * es, prec,
+               n[a], n[a], n[b]);
+      }
+      for (int t = 0; t < (1 << L); ++t) {
+        if (F.k0[t] > 0)
+          cb.add((const cd*)c.dV.p + c.V_off[t], P64, n[t], n[t], F.k0[t], (cd*)F.B_buf.p + F.B_off[t], P64, n[t],
+                 n[t], F.k0[t]);
+        if (n[t] > F.k0[t])
+          cb.add((const cd*)c.dVp.p + c.Vp_off[t], P64, n[t], n[t], n[t] - F.k0[t], (cd*)F.Vp_buf.p + F.Vp_off[t], P64,
+                 n[t], n[t], n[t] - F.k0[t]);
+      }
     }
-    for (int t = 0; t < (1 << L); ++t) {
-      if (F.k0[t] > 0)
-        cb.add((const cd*)c.dV.p + c.V_off[t], P64, n[t], n[t], F.k0[t], (cd*)F.B_buf.p + F.B_off[t], P64, n[t], n[t],
-               F.k0[t]);
-      if (n[t] > F.k0[t])
-        cb.add((const cd*)c.dVp.p + c.Vp_off[t], P64, n[t], n[t], n[t] - F.k0[t], (cd*)F.Vp_buf.p + F.Vp_off[t], P64,
-               n[t], n[t], n[t] - F.k0[t]);
+    run_copy(lc, cb, "leaf init");
+  }
+  for (int d = 0; d < depth; ++d) {
+    std::vector<Ctx*> act;
+    for (Ctx* c : cs)
+      if (d < (int)c->lev.size()) act.push_back(c);
+    lc.prof_suffix = "@d" + std::to_string(d);
+    if (cs.size() == 1) lc.prof_suffix = "@" + std::to_string(cs[0]->lev[d].l);
+    std::vector<std::vector<char>> done(act.size());
+    size_t nbat = 0;
+    for (size_t q = 0; q < act.size(); ++q) {
+      done[q].assign(act[q]->lev[d].nc, 0);
+      nbat = std::max(nbat, act[q]->lev[d].batches.size());
     }
-    run_copy(c, cb, "leaf init");
+    for (size_t b = 0; b < nbat; ++b) {
+      std::vector<Job> jobs;
+      for (size_t q = 0; q < act.size(); ++q) {
+        LevelF& F = act[q]->lev[d];
+        if (b < F.batches.size()) jobs.push_back(Job{act[q], &F, &F.batches[b], &done[q]});
+      }
+      process_batches(lc, jobs, eps);
+    }
+    CopyBatch as, ac;
+    std::vector<Ctx*> roots;
+    for (Ctx* c : act) {
+      if (d + 1 < (int)c->lev.size()) merge_level(*c, c->lev[d], c->lev[d + 1], as, ac);
+      else roots.push_back(c);
+    }
+    run_copy(lc, as, "merge");
+    run_copy(lc, ac, "merge fill");
+    if (!roots.empty()) root_factor_group(lc, roots);
+    check_status(lc);
   }
-  for (int li = 0; li <= L - l0; ++li) {
-    LevelF& F = c.lev[li];
-    c.prof_suffix = "@" + std::to_string(F.l);
-    std::vector<char> done(F.nc, 0);
-    for (const auto& bt : F.batches) process_batch(c, F, bt, done, eps);
-    if (F.l > l0) merge_level(c, F, c.lev[li + 1]);
-    else root_factor(c, F);
-    check_status(c);
+  lc.prof_suffix.clear();
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (Ctx* c : cs) {
+    c->factored = true;
+    c->stats.t_factor_ms = ms;
   }
-  c.prof_suffix.clear();
-  c.factored = true;
-  c.stats.launches_factor = c.launches - launches0;
-  c.stats.t_factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  lc.stats.launches_factor = lc.launches - launches0;
 }
+
+void factorize(Ctx& c, double eps, int prec) { factorize_group({&c}, eps, prec); }
 
 }  // namespace h2

@@ -232,6 +232,12 @@ const double* ctx_invscale(h2_ctx* x);
 
 void upload_h2(Ctx& c);
 void factorize(Ctx& c, double eps, int prec);
+// Several independent instances in lockstep (launches on cs[0]'s stream)
+void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec);
+void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs, int nrhs, bool adjoint,
+                      bool use_inverse);
+void matvec_tree_group(const std::vector<Ctx*>& cs, const std::vector<const h2k::cd*>& xs,
+                       const std::vector<h2k::cd*>& ys, int nrhs, bool adjoint);
 void invert(Ctx& c);
 // x (tree order, bulk precision vector of length N*nrhs) <- Z^{-1} x in place
 void solve_tree(Ctx& c, void* x, int nrhs, bool adjoint, bool use_inverse);

@@ -175,8 +175,16 @@ cudaError_t lu_blocked(const LuTask* d_tasks, int ntasks, int maxm, int prec,
                        int* d_status, cudaStream_t s);
 cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
 cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, cudaStream_t s);
-cudaError_t lu_panel(const PanelTask* d_task, int prec, int* d_status,
+// one CTA per task
+cudaError_t lu_panel(const PanelTask* d_tasks, int ntasks, int prec, int* d_status,
                      cudaStream_t s);
+// the row interchanges of several panels, each on its own column range
+struct SwapTask {
+  void* A;
+  const int* ipiv;
+  int lda, row0, kb, c0, c1, reverse;
+};
+cudaError_t swap_rows_batch(const SwapTask* d_tasks, int ntasks, int prec, cudaStream_t s);
 // apply the row interchanges ipiv[0:kb] (rows row0+j <-> ipiv[j]) to the
 // columns [c0, c1) of A (ld lda), in order (forward) or reversed
 cudaError_t swap_rows(void* A, int lda, const int* ipiv, int row0, int kb,

@@ -15,113 +15,163 @@
 namespace h2 {
 using namespace h2k;
 
-void matvec_tree(Ctx& c, const cd* x, cd* y, int nrhs, bool adj) {
-  const H2Host& H = c.H;
-  const int L = H.L, l0 = H.l0;
-  const int64_t N = H.tree.N;
-  std::vector<std::vector<size_t>> koff(L + 1);
-  std::vector<size_t> K(L + 1, 0), base(L + 1, 0);
-  size_t tot = 0;
-  for (int l = l0; l <= L; ++l) {
-    koff[l].assign(size_t(1) << l, 0);
-    for (int t = 0; t < (1 << l); ++t) {
-      koff[l][t] = K[l];
-      K[l] += H.rank[l][t];
-    }
-    base[l] = tot;
-    tot += K[l] * nrhs;
-  }
-  cd* buf = (cd*)dev_ensure(c, c.scratch2, (2 * tot + 1) * sizeof(cd));
-  auto xh = [&](int l, int t) { return buf + base[l] + koff[l][t]; };
-  auto yh = [&](int l, int t) { return buf + tot + base[l] + koff[l][t]; };
-  const cd* Vd = (const cd*)c.dV.p;
-  const cd* Td = (const cd*)c.dT.p;
-  const cd* Sd = (const cd*)c.dS.p;
-  const cd* Dd = (const cd*)c.dD.p;
-  const int opUp = adj ? OP_H : OP_T, opDown = adj ? OP_C : OP_N;
-  // upward pass
-  {
-    GemmBatch g;
-    for (int t = 0; t < (1 << L); ++t) {
-      const int kt = H.rank[L][t], nt = (int)H.tree.size[L][t];
-      if (kt == 0) continue;
-      g.task(xh(L, t), (int)K[L], kt, nrhs, 1.0, 0.0);
-      g.pair(Vd + c.V_off[t], nt, opUp, x + H.tree.start[L][t], (int)N, OP_N, nt);
-      g.close();
-    }
-    run_gemm(c, g, P64, P64, P64, "matvec up leaf");
-  }
-  for (int l = L - 1; l >= l0; --l) {
-    GemmBatch g;
-    for (int t = 0; t < (1 << l); ++t) {
-      const int kt = H.rank[l][t];
-      const int k1 = H.rank[l + 1][2 * t], k2 = H.rank[l + 1][2 * t + 1];
-      if (kt == 0) continue;
-      g.task(xh(l, t), (int)K[l], kt, nrhs, 1.0, 0.0);
-      g.pair(Td + c.T_off[l][t], k1 + k2, opUp, xh(l + 1, 2 * t), (int)K[l + 1], OP_N, k1 + k2);
-      g.close();
-    }
-    run_gemm(c, g, P64, P64, P64, "matvec up");
-  }
-  // couplings
-  {
-    GemmBatch g;
+// The product for a group of instances: each stage (and each level-from-leaf
+// index of the upward / downward passes) is one launch over all instances.
+// xs[q], ys[q]: instance q's vectors in tree order (FP64, N x nrhs).
+void matvec_tree_group(const std::vector<Ctx*>& cs, const std::vector<const cd*>& xs, const std::vector<cd*>& ys,
+                       int nrhs, bool adj) {
+  Ctx& lc = *cs[0];
+  const size_t nq = cs.size();
+  struct Lay {
+    std::vector<std::vector<size_t>> koff;
+    std::vector<size_t> K, base;
+    cd* buf;
+    size_t tot;
+  };
+  std::vector<Lay> ly(nq);
+  int depth = 0;
+  for (size_t q = 0; q < nq; ++q) {
+    Ctx& c = *cs[q];
+    const H2Host& H = c.H;
+    const int L = H.L, l0 = H.l0;
+    depth = std::max(depth, L - l0);
+    Lay& y = ly[q];
+    y.koff.assign(L + 1, {});
+    y.K.assign(L + 1, 0);
+    y.base.assign(L + 1, 0);
+    y.tot = 0;
     for (int l = l0; l <= L; ++l) {
-      std::vector<std::vector<int>> by(size_t(1) << l);
-      for (size_t q = 0; q < H.part.adm[l].size(); ++q) {
-        const auto [t, s] = H.part.adm[l][q];
-        by[adj ? s : t].push_back((int)q);
+      y.koff[l].assign(size_t(1) << l, 0);
+      for (int t = 0; t < (1 << l); ++t) {
+        y.koff[l][t] = y.K[l];
+        y.K[l] += H.rank[l][t];
       }
-      for (int u = 0; u < (1 << l); ++u) {
-        const int ku = H.rank[l][u];
-        if (ku == 0) continue;
-        g.task(yh(l, u), (int)K[l], ku, nrhs, 1.0, 0.0);
-        for (int q : by[u]) {
-          const auto [t, s] = H.part.adm[l][q];
-          if (!adj) g.pair(Sd + c.S_off[l][q], H.rank[l][t], OP_N, xh(l, s), (int)K[l], OP_N, H.rank[l][s]);
-          else g.pair(Sd + c.S_off[l][q], H.rank[l][t], OP_H, xh(l, t), (int)K[l], OP_N, H.rank[l][t]);
+      y.base[l] = y.tot;
+      y.tot += y.K[l] * nrhs;
+    }
+    y.buf = (cd*)dev_ensure(c, c.scratch2, (2 * y.tot + 1) * sizeof(cd));
+  }
+  auto xh = [&](size_t q, int l, int t) { return ly[q].buf + ly[q].base[l] + ly[q].koff[l][t]; };
+  auto yh = [&](size_t q, int l, int t) { return ly[q].buf + ly[q].tot + ly[q].base[l] + ly[q].koff[l][t]; };
+  const int opUp = adj ? OP_H : OP_T, opDown = adj ? OP_C : OP_N;
+  // upward pass: leaves, then level L - d for d = 1, 2, ...
+  {
+    GemmBatch g;
+    for (size_t q = 0; q < nq; ++q) {
+      Ctx& c = *cs[q];
+      const H2Host& H = c.H;
+      const int L = H.L;
+      for (int t = 0; t < (1 << L); ++t) {
+        const int kt = H.rank[L][t], nt = (int)H.tree.size[L][t];
+        if (kt == 0) continue;
+        g.task(xh(q, L, t), (int)ly[q].K[L], kt, nrhs, 1.0, 0.0);
+        g.pair((const cd*)c.dV.p + c.V_off[t], nt, opUp, xs[q] + H.tree.start[L][t], (int)H.tree.N, OP_N, nt);
+        g.close();
+      }
+    }
+    run_gemm(lc, g, P64, P64, P64, "matvec up leaf");
+  }
+  for (int d = 1; d <= depth; ++d) {
+    GemmBatch g;
+    for (size_t q = 0; q < nq; ++q) {
+      Ctx& c = *cs[q];
+      const H2Host& H = c.H;
+      const int l = H.L - d;
+      if (l < H.l0) continue;
+      for (int t = 0; t < (1 << l); ++t) {
+        const int kt = H.rank[l][t];
+        const int k1 = H.rank[l + 1][2 * t], k2 = H.rank[l + 1][2 * t + 1];
+        if (kt == 0) continue;
+        g.task(xh(q, l, t), (int)ly[q].K[l], kt, nrhs, 1.0, 0.0);
+        g.pair((const cd*)c.dT.p + c.T_off[l][t], k1 + k2, opUp, xh(q, l + 1, 2 * t), (int)ly[q].K[l + 1], OP_N,
+               k1 + k2);
+        g.close();
+      }
+    }
+    run_gemm(lc, g, P64, P64, P64, "matvec up");
+  }
+  // couplings of every level
+  {
+    GemmBatch g;
+    for (size_t q = 0; q < nq; ++q) {
+      Ctx& c = *cs[q];
+      const H2Host& H = c.H;
+      const cd* Sd = (const cd*)c.dS.p;
+      for (int l = H.l0; l <= H.L; ++l) {
+        std::vector<std::vector<int>> by(size_t(1) << l);
+        for (size_t u = 0; u < H.part.adm[l].size(); ++u) {
+          const auto [t, s2] = H.part.adm[l][u];
+          by[adj ? s2 : t].push_back((int)u);
+        }
+        for (int v = 0; v < (1 << l); ++v) {
+          const int kv = H.rank[l][v];
+          if (kv == 0) continue;
+          g.task(yh(q, l, v), (int)ly[q].K[l], kv, nrhs, 1.0, 0.0);
+          for (int u : by[v]) {
+            const auto [t, s2] = H.part.adm[l][u];
+            if (!adj)
+              g.pair(Sd + c.S_off[l][u], H.rank[l][t], OP_N, xh(q, l, s2), (int)ly[q].K[l], OP_N, H.rank[l][s2]);
+            else
+              g.pair(Sd + c.S_off[l][u], H.rank[l][t], OP_H, xh(q, l, t), (int)ly[q].K[l], OP_N, H.rank[l][t]);
+          }
+          g.close();
+        }
+      }
+    }
+    run_gemm(lc, g, P64, P64, P64, "matvec couple");
+  }
+  // downward pass: level L - d for d = depth .. 1
+  for (int d = depth; d >= 1; --d) {
+    GemmBatch g;
+    for (size_t q = 0; q < nq; ++q) {
+      Ctx& c = *cs[q];
+      const H2Host& H = c.H;
+      const int l = H.L - d;
+      if (l < H.l0) continue;
+      for (int t = 0; t < (1 << l); ++t) {
+        const int kt = H.rank[l][t];
+        const int k1 = H.rank[l + 1][2 * t], k2 = H.rank[l + 1][2 * t + 1];
+        if (kt == 0 || k1 + k2 == 0) continue;
+        g.task(yh(q, l + 1, 2 * t), (int)ly[q].K[l + 1], k1 + k2, nrhs, 1.0, 1.0);
+        g.pair((const cd*)c.dT.p + c.T_off[l][t], k1 + k2, opDown, yh(q, l, t), (int)ly[q].K[l], OP_N, kt);
+        g.close();
+      }
+    }
+    run_gemm(lc, g, P64, P64, P64, "matvec down");
+  }
+  // leaves: basis part and dense near field
+  {
+    GemmBatch g;
+    for (size_t q = 0; q < nq; ++q) {
+      Ctx& c = *cs[q];
+      const H2Host& H = c.H;
+      const int L = H.L;
+      const int64_t N = H.tree.N;
+      const cd* Vd = (const cd*)c.dV.p;
+      const cd* Dd = (const cd*)c.dD.p;
+      std::vector<std::vector<int>> by(size_t(1) << L);
+      for (size_t u = 0; u < H.part.inad[L].size(); ++u) {
+        const auto [t, s2] = H.part.inad[L][u];
+        by[adj ? s2 : t].push_back((int)u);
+      }
+      for (int v = 0; v < (1 << L); ++v) {
+        const int nv = (int)H.tree.size[L][v], kv = H.rank[L][v];
+        g.task(ys[q] + H.tree.start[L][v], (int)N, nv, nrhs, 1.0, 0.0);
+        if (kv > 0) g.pair(Vd + c.V_off[v], nv, opDown, yh(q, L, v), (int)ly[q].K[L], OP_N, kv);
+        for (int u : by[v]) {
+          const auto [t, s2] = H.part.inad[L][u];
+          const int nt = (int)H.tree.size[L][t], ns = (int)H.tree.size[L][s2];
+          if (!adj) g.pair(Dd + c.D_off[u], nt, OP_N, xs[q] + H.tree.start[L][s2], (int)N, OP_N, ns);
+          else g.pair(Dd + c.D_off[u], nt, OP_H, xs[q] + H.tree.start[L][t], (int)N, OP_N, nt);
         }
         g.close();
       }
     }
-    run_gemm(c, g, P64, P64, P64, "matvec couple");
-  }
-  // downward pass
-  for (int l = l0; l < L; ++l) {
-    GemmBatch g;
-    for (int t = 0; t < (1 << l); ++t) {
-      const int kt = H.rank[l][t];
-      const int k1 = H.rank[l + 1][2 * t], k2 = H.rank[l + 1][2 * t + 1];
-      if (kt == 0 || k1 + k2 == 0) continue;
-      g.task(yh(l + 1, 2 * t), (int)K[l + 1], k1 + k2, nrhs, 1.0, 1.0);
-      g.pair(Td + c.T_off[l][t], k1 + k2, opDown, yh(l, t), (int)K[l], OP_N, kt);
-      g.close();
-    }
-    run_gemm(c, g, P64, P64, P64, "matvec down");
-  }
-  // leaves: basis part and dense near field
-  {
-    std::vector<std::vector<int>> by(size_t(1) << L);
-    for (size_t q = 0; q < H.part.inad[L].size(); ++q) {
-      const auto [t, s] = H.part.inad[L][q];
-      by[adj ? s : t].push_back((int)q);
-    }
-    GemmBatch g;
-    for (int u = 0; u < (1 << L); ++u) {
-      const int nu = (int)H.tree.size[L][u], ku = H.rank[L][u];
-      g.task(y + H.tree.start[L][u], (int)N, nu, nrhs, 1.0, 0.0);
-      if (ku > 0) g.pair(Vd + c.V_off[u], nu, opDown, yh(L, u), (int)K[L], OP_N, ku);
-      for (int q : by[u]) {
-        const auto [t, s] = H.part.inad[L][q];
-        const int nt = (int)H.tree.size[L][t], ns = (int)H.tree.size[L][s];
-        if (!adj) g.pair(Dd + c.D_off[q], nt, OP_N, x + H.tree.start[L][s], (int)N, OP_N, ns);
-        else g.pair(Dd + c.D_off[q], nt, OP_H, x + H.tree.start[L][t], (int)N, OP_N, nt);
-      }
-      g.close();
-    }
-    run_gemm(c, g, P64, P64, P64, "matvec leaf");
+    run_gemm(lc, g, P64, P64, P64, "matvec leaf");
   }
 }
+
+void matvec_tree(Ctx& c, const cd* x, cd* y, int nrhs, bool adj) { matvec_tree_group({&c}, {x}, {y}, nrhs, adj); }
 
 // Explicit factor-form inverse (eq. 35): the diagonal inverses L^{-1}P and
 // U^{-1} exist already; add -U^{-1} U_ik for every U panel and the inverse of

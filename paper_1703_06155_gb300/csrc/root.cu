@@ -40,11 +40,11 @@ __global__ void __launch_bounds__(NT) k_select(const SelTask* __restrict__ tasks
 }
 
 template <class E>
-__global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ task, int* status) {
+__global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ tasks, int* status) {
   using R = typename RealOf<E>::T;
   __shared__ R redv[NT];
   __shared__ int redi[NT];
-  const PanelTask t = *task;
+  const PanelTask t = tasks[blockIdx.x];
   E* A = (E*)t.A;
   const int ld = t.lda, kb = t.kb;
   auto at = [&](int r, int c) -> E& { return A[(size_t)(t.row0 + r) + (size_t)(t.col0 + c) * ld]; };
@@ -176,7 +176,32 @@ __global__ void k_swap_rows(E* A, int lda, const int* ipiv, int row0, int kb, in
   }
 }
 
+template <class E>
+__global__ void k_swap_rows_batch(const SwapTask* __restrict__ tasks) {
+  const SwapTask t = tasks[blockIdx.y];
+  E* A = (E*)t.A;
+  for (int c = t.c0 + blockIdx.x * blockDim.x + threadIdx.x; c < t.c1; c += gridDim.x * blockDim.x) {
+    for (int q = 0; q < t.kb; ++q) {
+      const int j = t.reverse ? t.kb - 1 - q : q;
+      const int r1 = t.row0 + j, r2 = t.ipiv[j];
+      if (r1 != r2) {
+        const E a = A[(size_t)r1 + (size_t)c * t.lda];
+        A[(size_t)r1 + (size_t)c * t.lda] = A[(size_t)r2 + (size_t)c * t.lda];
+        A[(size_t)r2 + (size_t)c * t.lda] = a;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t swap_rows_batch(const SwapTask* d, int n, int prec, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 g(8, n);
+  if (prec == P64) k_swap_rows_batch<cd><<<g, 128, 0, s>>>(d);
+  else k_swap_rows_batch<cf><<<g, 128, 0, s>>>(d);
+  return cudaGetLastError();
+}
 
 cudaError_t select_rank(const SelTask* d, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
@@ -184,9 +209,10 @@ cudaError_t select_rank(const SelTask* d, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t lu_panel(const PanelTask* d, int prec, int* st, cudaStream_t s) {
-  if (prec == P64) k_lu_panel<cd><<<1, NT, 0, s>>>(d, st);
-  else k_lu_panel<cf><<<1, NT, 0, s>>>(d, st);
+cudaError_t lu_panel(const PanelTask* d, int n, int prec, int* st, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (prec == P64) k_lu_panel<cd><<<n, NT, 0, s>>>(d, st);
+  else k_lu_panel<cf><<<n, NT, 0, s>>>(d, st);
   return cudaGetLastError();
 }
 

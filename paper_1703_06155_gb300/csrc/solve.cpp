@@ -34,294 +34,401 @@ char* NBp(Ctx& c, const LevelF& F, int j, int k) {
   return (char*)F.near_buf.p + F.near_off.at(F.near_id.at(pkey(j, k))) * esz(c.prec);
 }
 
-void merge_vec(Ctx& c, const LevelF& F, const LevelF& Pn, Vec v, Vec vp, int nrhs, bool up) {
-  const int prec = c.prec;
+// x_c <- R_c^{-1} x_c (or R_c^{-H} x_c) with the blocked LU of the final block
+// of every instance c; panel step pi of all instances shares the launches.
+void root_solve_group(Ctx& lc, const std::vector<Ctx*>& cs, const std::vector<char*>& xs,
+                      const std::vector<int>& lds, int nrhs, bool adjoint) {
+  const int prec = lc.prec;
   const size_t es = esz(prec);
-  CopyBatch cb;
-  for (int p = 0; p < Pn.nc; ++p)
-    for (int a = 2 * p; a <= 2 * p + 1; ++a) {
-      const int o = (a & 1) ? F.kt[a - 1] : 0;
-      char* child = v.p + (size_t)(F.voff[a] + F.m[a]) * es;
-      char* par = vp.p + (size_t)(Pn.voff[p] + o) * es;
-      if (up) cb.add(child, prec, (int)v.ld, F.kt[a], nrhs, par, prec, (int)vp.ld, F.kt[a], nrhs);
-      else cb.add(par, prec, (int)vp.ld, F.kt[a], nrhs, child, prec, (int)v.ld, F.kt[a], nrhs);
-    }
-  run_copy(c, cb, up ? "vec merge" : "vec scatter");
-}
-
-void root_vec(Ctx& c, const LevelF& F, Vec v, Vec vr, int nrhs, bool up) {
-  const int prec = c.prec;
-  const size_t es = esz(prec);
-  CopyBatch cb;
-  int off = 0;
-  for (int a = 0; a < F.nc; ++a) {
-    char* lv = v.p + (size_t)(F.voff[a] + F.m[a]) * es;
-    char* rv = vr.p + (size_t)off * es;
-    if (up) cb.add(lv, prec, (int)v.ld, F.kt[a], nrhs, rv, prec, (int)vr.ld, F.kt[a], nrhs);
-    else cb.add(rv, prec, (int)vr.ld, F.kt[a], nrhs, lv, prec, (int)v.ld, F.kt[a], nrhs);
-    off += F.kt[a];
-  }
-  run_copy(c, cb, up ? "root gather" : "root scatter");
-}
-
-// x <- R^{-1} x (or R^{-H} x) with the blocked LU of the final block
-void root_solve(Ctx& c, char* x, int ld, int nrhs, bool adjoint) {
-  RootF& R = c.root;
-  const int n = R.n, nb = R.nb, prec = c.prec;
-  if (n == 0) return;
-  const size_t es = esz(prec);
-  char* Rm = (char*)R.R.p;
-  char* Li = (char*)R.Linv.p;
-  char* Ui = (char*)R.Uinv.p;
-  const int npan = (n + nb - 1) / nb;
-  auto panel = [&](int pi, int& k0, int& kb) { k0 = pi * nb; kb = std::min(nb, n - k0); };
+  int npan_max = 0;
+  for (Ctx* c : cs)
+    if (c->root.n > 0) npan_max = std::max(npan_max, (c->root.n + c->root.nb - 1) / c->root.nb);
+  if (npan_max == 0) return;
+  auto swaps = [&](int reverse) {
+    std::vector<SwapTask> sw;
+    for (size_t q = 0; q < cs.size(); ++q)
+      if (cs[q]->root.n > 0)
+        sw.push_back(SwapTask{xs[q], (const int*)cs[q]->root.piv.p, lds[q], 0, cs[q]->root.n, 0, nrhs, reverse});
+    const int i0 = lc.st.add(sw);
+    lc.st.upload(lc);
+    ck(swap_rows_batch(lc.st.ptr<SwapTask>(i0), (int)sw.size(), prec, lc.stream), "root swaps");
+    lc.launches++;
+  };
+  // step(pi, kind) adds instance q's work of panel pi to the batches
+  auto panel = [&](size_t q, int pi, int& k0, int& kb) {
+    const RootF& R = cs[q]->root;
+    k0 = pi * R.nb;
+    kb = std::min(R.nb, R.n - k0);
+    return k0 < R.n;
+  };
+  auto rm = [&](size_t q) { return (char*)cs[q]->root.R.p; };
+  auto li = [&](size_t q, int pi) { return (char*)cs[q]->root.Linv.p + (size_t)pi * cs[q]->root.nb * cs[q]->root.nb * es; };
+  auto ui = [&](size_t q, int pi) { return (char*)cs[q]->root.Uinv.p + (size_t)pi * cs[q]->root.nb * cs[q]->root.nb * es; };
   if (!adjoint) {
-    ck(swap_rows(x, ld, (const int*)R.piv.p, 0, n, 0, nrhs, prec, 0, c.stream), "root swaps");
-    c.launches++;
-    for (int pi = 0; pi < npan; ++pi) {
-      int k0, kb;
-      panel(pi, k0, kb);
+    swaps(0);
+    for (int pi = 0; pi < npan_max; ++pi) {
       ApplyBatch ab;
-      ab.add(Li + (size_t)pi * nb * nb * es, kb, OP_N, x + (size_t)k0 * es, ld, kb, nrhs, 0);
-      run_apply(c, ab, true, prec, "root fwd");
-      const int rest = n - k0 - kb;
-      if (rest > 0) {
-        GemmBatch g;
-        g.task(x + (size_t)(k0 + kb) * es, ld, rest, nrhs, -1.0, 1.0);
-        g.pair(Rm + ((size_t)(k0 + kb) + (size_t)k0 * n) * es, n, OP_N, x + (size_t)k0 * es, ld, OP_N, kb);
-        g.close();
-        run_gemm(c, g, prec, prec, prec, "root fwd update");
+      GemmBatch g;
+      for (size_t q = 0; q < cs.size(); ++q) {
+        int k0, kb;
+        if (!panel(q, pi, k0, kb)) continue;
+        const int n = cs[q]->root.n, ld = lds[q];
+        char* x = xs[q];
+        ab.add(li(q, pi), kb, OP_N, x + (size_t)k0 * es, ld, kb, nrhs, 0);
+        const int rest = n - k0 - kb;
+        if (rest > 0) {
+          g.task(x + (size_t)(k0 + kb) * es, ld, rest, nrhs, -1.0, 1.0);
+          g.pair(rm(q) + ((size_t)(k0 + kb) + (size_t)k0 * n) * es, n, OP_N, x + (size_t)k0 * es, ld, OP_N, kb);
+          g.close();
+        }
       }
+      run_apply(lc, ab, true, prec, "root fwd");
+      run_gemm(lc, g, prec, prec, prec, "root fwd update");
     }
-    for (int pi = npan - 1; pi >= 0; --pi) {
-      int k0, kb;
-      panel(pi, k0, kb);
-      const int rest = n - k0 - kb;
-      if (rest > 0) {
-        GemmBatch g;
-        g.task(x + (size_t)k0 * es, ld, kb, nrhs, -1.0, 1.0);
-        g.pair(Rm + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n, OP_N, x + (size_t)(k0 + kb) * es, ld, OP_N, rest);
-        g.close();
-        run_gemm(c, g, prec, prec, prec, "root bwd update");
-      }
+    for (int pi = npan_max - 1; pi >= 0; --pi) {
       ApplyBatch ab;
-      ab.add(Ui + (size_t)pi * nb * nb * es, kb, OP_N, x + (size_t)k0 * es, ld, kb, nrhs, 0);
-      run_apply(c, ab, true, prec, "root bwd");
+      GemmBatch g;
+      for (size_t q = 0; q < cs.size(); ++q) {
+        int k0, kb;
+        if (!panel(q, pi, k0, kb)) continue;
+        const int n = cs[q]->root.n, ld = lds[q];
+        char* x = xs[q];
+        const int rest = n - k0 - kb;
+        if (rest > 0) {
+          g.task(x + (size_t)k0 * es, ld, kb, nrhs, -1.0, 1.0);
+          g.pair(rm(q) + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n, OP_N, x + (size_t)(k0 + kb) * es, ld, OP_N,
+                 rest);
+          g.close();
+        }
+        ab.add(ui(q, pi), kb, OP_N, x + (size_t)k0 * es, ld, kb, nrhs, 0);
+      }
+      run_gemm(lc, g, prec, prec, prec, "root bwd update");
+      run_apply(lc, ab, true, prec, "root bwd");
     }
   } else {
     // R = P^T L U  ->  R^{-H} = P^T L^{-H} U^{-H}
-    for (int pi = 0; pi < npan; ++pi) {
-      int k0, kb;
-      panel(pi, k0, kb);
+    for (int pi = 0; pi < npan_max; ++pi) {
       ApplyBatch ab;
-      ab.add(Ui + (size_t)pi * nb * nb * es, kb, OP_H, x + (size_t)k0 * es, ld, kb, nrhs, 0);
-      run_apply(c, ab, true, prec, "root adj U");
-      const int rest = n - k0 - kb;
-      if (rest > 0) {
-        GemmBatch g;
-        g.task(x + (size_t)(k0 + kb) * es, ld, rest, nrhs, -1.0, 1.0);
-        g.pair(Rm + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n, OP_H, x + (size_t)k0 * es, ld, OP_N, kb);
-        g.close();
-        run_gemm(c, g, prec, prec, prec, "root adj U update");
+      GemmBatch g;
+      for (size_t q = 0; q < cs.size(); ++q) {
+        int k0, kb;
+        if (!panel(q, pi, k0, kb)) continue;
+        const int n = cs[q]->root.n, ld = lds[q];
+        char* x = xs[q];
+        ab.add(ui(q, pi), kb, OP_H, x + (size_t)k0 * es, ld, kb, nrhs, 0);
+        const int rest = n - k0 - kb;
+        if (rest > 0) {
+          g.task(x + (size_t)(k0 + kb) * es, ld, rest, nrhs, -1.0, 1.0);
+          g.pair(rm(q) + ((size_t)k0 + (size_t)(k0 + kb) * n) * es, n, OP_H, x + (size_t)k0 * es, ld, OP_N, kb);
+          g.close();
+        }
       }
+      run_apply(lc, ab, true, prec, "root adj U");
+      run_gemm(lc, g, prec, prec, prec, "root adj U update");
     }
-    for (int pi = npan - 1; pi >= 0; --pi) {
-      int k0, kb;
-      panel(pi, k0, kb);
-      const int rest = n - k0 - kb;
-      if (rest > 0) {
-        GemmBatch g;
-        g.task(x + (size_t)k0 * es, ld, kb, nrhs, -1.0, 1.0);
-        g.pair(Rm + ((size_t)(k0 + kb) + (size_t)k0 * n) * es, n, OP_H, x + (size_t)(k0 + kb) * es, ld, OP_N, rest);
-        g.close();
-        run_gemm(c, g, prec, prec, prec, "root adj L update");
-      }
+    for (int pi = npan_max - 1; pi >= 0; --pi) {
       ApplyBatch ab;
-      ab.add(Li + (size_t)pi * nb * nb * es, kb, OP_H, x + (size_t)k0 * es, ld, kb, nrhs, 0);
-      run_apply(c, ab, true, prec, "root adj L");
+      GemmBatch g;
+      for (size_t q = 0; q < cs.size(); ++q) {
+        int k0, kb;
+        if (!panel(q, pi, k0, kb)) continue;
+        const int n = cs[q]->root.n, ld = lds[q];
+        char* x = xs[q];
+        const int rest = n - k0 - kb;
+        if (rest > 0) {
+          g.task(x + (size_t)k0 * es, ld, kb, nrhs, -1.0, 1.0);
+          g.pair(rm(q) + ((size_t)(k0 + kb) + (size_t)k0 * n) * es, n, OP_H, x + (size_t)(k0 + kb) * es, ld, OP_N,
+                 rest);
+          g.close();
+        }
+        ab.add(li(q, pi), kb, OP_H, x + (size_t)k0 * es, ld, kb, nrhs, 0);
+      }
+      run_gemm(lc, g, prec, prec, prec, "root adj L update");
+      run_apply(lc, ab, true, prec, "root adj L");
     }
-    ck(swap_rows(x, ld, (const int*)R.piv.p, 0, n, 0, nrhs, prec, 1, c.stream), "root swaps");
-    c.launches++;
+    swaps(1);
   }
 }
 
 }  // namespace
 
-void root_solve_public(Ctx& c, char* x, int ld, int nrhs, bool adjoint) { root_solve(c, x, ld, nrhs, adjoint); }
+void root_solve_public(Ctx& c, char* x, int ld, int nrhs, bool adjoint) {
+  root_solve_group(c, {&c}, {x}, {ld}, nrhs, adjoint);
+}
 
-void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {
-  if (!c.factored) fail(H2_ESTATE, "solve before factorize");
-  const int prec = c.prec;
+// One instance's level vectors for a solve
+struct SolveVecs {
+  std::vector<Vec> vec;  // vec[0] = x itself (tree order, ld N)
+  Vec vr;                // final-block vector
+};
+
+// Forward (Algorithm 5) / backward (Algorithm 6) substitution, or the adjoint
+// traversal, for a group of instances: level-from-leaf index d and colour b
+// of every instance share the launches.  xs[q]: instance q's vector in tree
+// order (bulk precision, N x nrhs).
+void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs, int nrhs, bool adjoint,
+                      bool use_inverse) {
+  Ctx& lc = *cs[0];
+  const int prec = lc.prec;
   const size_t es = esz(prec);
-  const int nlev = (int)c.lev.size();
-  // level vectors: level 0 is x itself (tree order, ld N)
-  std::vector<Vec> vec(nlev);
-  size_t tot = 0;
-  std::vector<size_t> off(nlev, 0);
-  for (int li = 1; li < nlev; ++li) {
-    off[li] = tot;
-    tot += (size_t)c.lev[li].vlen * nrhs;
+  const size_t nq = cs.size();
+  std::vector<SolveVecs> sv(nq);
+  int depth = 0;
+  for (size_t q = 0; q < nq; ++q) {
+    Ctx& c = *cs[q];
+    if (!c.factored) fail(H2_ESTATE, "solve before factorize");
+    if (c.prec != prec) fail(H2_EINVAL, "instances factorized in different precisions");
+    const int nlev = (int)c.lev.size();
+    depth = std::max(depth, nlev);
+    std::vector<size_t> off(nlev, 0);
+    size_t tot = 0;
+    for (int li = 1; li < nlev; ++li) {
+      off[li] = tot;
+      tot += (size_t)c.lev[li].vlen * nrhs;
+    }
+    const size_t roff = tot;
+    tot += (size_t)c.root.n * nrhs;
+    char* buf = (char*)dev_ensure(c, c.vecbuf, (tot + 1) * es);
+    sv[q].vec.resize(nlev);
+    sv[q].vec[0] = Vec{(char*)xs[q], c.H.tree.N};
+    for (int li = 1; li < nlev; ++li) sv[q].vec[li] = Vec{buf + off[li] * es, c.lev[li].vlen};
+    sv[q].vr = Vec{buf + roff * es, c.root.n};
   }
-  const size_t roff = tot;
-  tot += (size_t)c.root.n * nrhs;
-  char* buf = (char*)dev_ensure(c, c.vecbuf, (tot + 1) * es);
-  vec[0] = Vec{(char*)xv, c.H.tree.N};
-  for (int li = 1; li < nlev; ++li) vec[li] = Vec{buf + off[li] * es, c.lev[li].vlen};
-  Vec vr{buf + roff * es, c.root.n};
-
+  auto has = [&](size_t q, int d) { return d < (int)cs[q]->lev.size(); };
+  auto top = [&](size_t q) { return (int)cs[q]->lev.size() - 1; };
   auto Q = [&](const LevelF& F, int i) { return (char*)F.Q_buf.p + F.Q_off[i] * es; };
   auto Linv = [&](const LevelF& F, int i) { return (char*)F.inv_buf.p + F.inv_off[i] * es; };
   auto Uinv = [&](const LevelF& F, int i) {
     return (char*)F.inv_buf.p + (F.inv_off[i] + (size_t)F.n[i] * F.n[i]) * es;
   };
   auto seg = [&](const Vec& v, const LevelF& F, int i, int r0) { return v.p + (size_t)(F.voff[i] + r0) * es; };
+  auto nbat = [&](int d) {
+    size_t nb = 0;
+    for (size_t q = 0; q < nq; ++q)
+      if (has(q, d)) nb = std::max(nb, cs[q]->lev[d].batches.size());
+    return (int)nb;
+  };
+  // children -> parent (up) or parent -> children (down) between level d and d+1
+  auto merge = [&](int d, bool up) {
+    CopyBatch cb;
+    for (size_t q = 0; q < nq; ++q) {
+      if (!has(q, d + 1)) continue;
+      const LevelF& F = cs[q]->lev[d];
+      const LevelF& Pn = cs[q]->lev[d + 1];
+      const Vec v = sv[q].vec[d], vp = sv[q].vec[d + 1];
+      for (int p = 0; p < Pn.nc; ++p)
+        for (int a = 2 * p; a <= 2 * p + 1; ++a) {
+          const int o = (a & 1) ? F.kt[a - 1] : 0;
+          char* child = v.p + (size_t)(F.voff[a] + F.m[a]) * es;
+          char* par = vp.p + (size_t)(Pn.voff[p] + o) * es;
+          if (up) cb.add(child, prec, (int)v.ld, F.kt[a], nrhs, par, prec, (int)vp.ld, F.kt[a], nrhs);
+          else cb.add(par, prec, (int)vp.ld, F.kt[a], nrhs, child, prec, (int)v.ld, F.kt[a], nrhs);
+        }
+    }
+    run_copy(lc, cb, up ? "vec merge" : "vec scatter");
+  };
+  // kept parts of the top level <-> final-block vector
+  auto rootvec = [&](bool up) {
+    CopyBatch cb;
+    for (size_t q = 0; q < nq; ++q) {
+      const LevelF& F = cs[q]->lev.back();
+      const Vec v = sv[q].vec[top(q)], vr = sv[q].vr;
+      int off = 0;
+      for (int a = 0; a < F.nc; ++a) {
+        char* lv = v.p + (size_t)(F.voff[a] + F.m[a]) * es;
+        char* rv = vr.p + (size_t)off * es;
+        if (up) cb.add(lv, prec, (int)v.ld, F.kt[a], nrhs, rv, prec, (int)vr.ld, F.kt[a], nrhs);
+        else cb.add(rv, prec, (int)vr.ld, F.kt[a], nrhs, lv, prec, (int)v.ld, F.kt[a], nrhs);
+        off += F.kt[a];
+      }
+    }
+    run_copy(lc, cb, up ? "root gather" : "root scatter");
+  };
+  auto root = [&](bool adj) {
+    std::vector<char*> rx;
+    std::vector<int> rld;
+    for (size_t q = 0; q < nq; ++q) {
+      rx.push_back(sv[q].vr.p);
+      rld.push_back((int)sv[q].vr.ld);
+    }
+    if (use_inverse && !adj) {
+      GemmBatch g;
+      CopyBatch cb;
+      for (size_t q = 0; q < nq; ++q) {
+        Ctx& c = *cs[q];
+        if (c.root.n == 0) continue;
+        char* tmp = (char*)dev_ensure(c, c.vecbuf2, (size_t)c.root.n * nrhs * es);
+        g.task(tmp, c.root.n, c.root.n, nrhs, 1.0, 0.0);
+        g.pair(c.root.Rinv.p, c.root.n, OP_N, rx[q], rld[q], OP_N, c.root.n);
+        g.close();
+        cb.add(tmp, prec, c.root.n, c.root.n, nrhs, rx[q], prec, rld[q], c.root.n, nrhs);
+      }
+      run_gemm(lc, g, prec, prec, prec, "root inverse apply");
+      run_copy(lc, cb, "root inverse copy");
+    } else {
+      root_solve_group(lc, cs, rx, rld, nrhs, adj);
+    }
+  };
 
   if (!adjoint) {
     // ---------------- forward: L y = b (Algorithm 5) ----------------
-    for (int li = 0; li < nlev; ++li) {
-      LevelF& F = c.lev[li];
-      Vec v = vec[li];
-      for (const auto& bt : F.batches) {
+    for (int d = 0; d < depth; ++d) {
+      for (int b = 0; b < nbat(d); ++b) {
         ApplyBatch a1, a2;
-        for (int i : bt) {
-          a1.add(Q(F, i), F.n[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
-          if (F.m[i] > 0) a2.add(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
-        }
-        run_apply_narrow(c, a1, prec, "fwd Q^H");
-        run_apply_narrow(c, a2, prec, "fwd L^-1");
-        std::map<int, std::vector<int>> tg;
-        for (int i : bt)
-          if (F.m[i] > 0)
-            for (int j : F.nbrs[i]) tg[j].push_back(i);
         GemmBatch g;
-        for (auto& [j, cl] : tg) {
-          const int rlo = lo_at(F, j, cl[0]);
-          g.task(seg(v, F, j, rlo), (int)v.ld, F.n[j] - rlo, nrhs, -1.0, 1.0);
-          for (int i : cl) g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_N, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
-          g.close();
-        }
-        run_gemm(c, g, prec, prec, prec, "fwd update");
-      }
-      if (li + 1 < nlev) merge_vec(c, F, c.lev[li + 1], v, vec[li + 1], nrhs, true);
-    }
-    root_vec(c, c.lev[nlev - 1], vec[nlev - 1], vr, nrhs, true);
-    if (use_inverse && c.root.n > 0) {
-      char* tmp = (char*)dev_ensure(c, c.vecbuf2, (size_t)c.root.n * nrhs * es);
-      GemmBatch g;
-      g.task(tmp, c.root.n, c.root.n, nrhs, 1.0, 0.0);
-      g.pair(c.root.Rinv.p, c.root.n, OP_N, vr.p, (int)vr.ld, OP_N, c.root.n);
-      g.close();
-      run_gemm(c, g, prec, prec, prec, "root inverse apply");
-      CopyBatch cb;
-      cb.add(tmp, prec, c.root.n, c.root.n, nrhs, vr.p, prec, (int)vr.ld, c.root.n, nrhs);
-      run_copy(c, cb, "root inverse copy");
-    } else {
-      root_solve(c, vr.p, (int)vr.ld, nrhs, false);
-    }
-    root_vec(c, c.lev[nlev - 1], vec[nlev - 1], vr, nrhs, false);
-    // ---------------- backward: U x = y (Algorithm 6) ----------------
-    for (int li = nlev - 1; li >= 0; --li) {
-      LevelF& F = c.lev[li];
-      Vec v = vec[li];
-      for (int b = (int)F.batches.size() - 1; b >= 0; --b) {
-        const auto& bt = F.batches[b];
-        GemmBatch g;
-        ApplyBatch a1, a2;
-        for (int i : bt) {
-          const int mi = F.m[i];
-          if (mi <= 0) continue;
-          if (!use_inverse) {
-            g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, -1.0, 1.0);
-            for (int k : F.nbrs[i]) {
-              const int clo = lo_at(F, k, i);
-              g.pair(NBp(c, F, i, k) + (size_t)clo * F.n[i] * es, F.n[i], OP_N, seg(v, F, k, clo), (int)v.ld, OP_N,
-                     F.n[k] - clo);
-            }
-            g.close();
-          } else {
-            // eq. (35): x_i' = U^{-1} x_i' + sum_k (-U^{-1} U_ik) x_k
-            g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, 1.0, 1.0);
-            for (size_t q = 0; q < F.nbrs[i].size(); ++q) {
-              const int k = F.nbrs[i][q];
-              const int clo = lo_at(F, k, i);
-              g.pair((char*)F.Ub_buf.p + F.Ub_off[F.nbr_first[i] + q] * es, mi, OP_N, seg(v, F, k, clo), (int)v.ld,
-                     OP_N, F.n[k] - clo);
-            }
+        for (size_t q = 0; q < nq; ++q) {
+          if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
+          Ctx& c = *cs[q];
+          const LevelF& F = c.lev[d];
+          const Vec v = sv[q].vec[d];
+          const auto& bt = F.batches[b];
+          for (int i : bt) {
+            a1.add(Q(F, i), F.n[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
+            if (F.m[i] > 0) a2.add(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
+          }
+          std::map<int, std::vector<int>> tg;
+          for (int i : bt)
+            if (F.m[i] > 0)
+              for (int j : F.nbrs[i]) tg[j].push_back(i);
+          for (auto& [j, cl] : tg) {
+            const int rlo = lo_at(F, j, cl[0]);
+            g.task(seg(v, F, j, rlo), (int)v.ld, F.n[j] - rlo, nrhs, -1.0, 1.0);
+            for (int i : cl)
+              g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_N, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
             g.close();
           }
-          a1.add(Uinv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+        }
+        run_apply_narrow(lc, a1, prec, "fwd Q^H");
+        run_apply_narrow(lc, a2, prec, "fwd L^-1");
+        run_gemm(lc, g, prec, prec, prec, "fwd update");
+      }
+      merge(d, true);
+    }
+    rootvec(true);
+    root(false);
+    rootvec(false);
+    // ---------------- backward: U x = y (Algorithm 6) ----------------
+    for (int d = depth - 1; d >= 0; --d) {
+      for (int b = nbat(d) - 1; b >= 0; --b) {
+        GemmBatch g;
+        ApplyBatch a1, a2;
+        for (size_t q = 0; q < nq; ++q) {
+          if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
+          Ctx& c = *cs[q];
+          const LevelF& F = c.lev[d];
+          const Vec v = sv[q].vec[d];
+          const auto& bt = F.batches[b];
+          for (int i : bt) {
+            const int mi = F.m[i];
+            if (mi <= 0) continue;
+            if (!use_inverse) {
+              g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, -1.0, 1.0);
+              for (int k : F.nbrs[i]) {
+                const int clo = lo_at(F, k, i);
+                g.pair(NBp(c, F, i, k) + (size_t)clo * F.n[i] * es, F.n[i], OP_N, seg(v, F, k, clo), (int)v.ld, OP_N,
+                       F.n[k] - clo);
+              }
+              g.close();
+            } else {
+              // eq. (35): x_i' = U^{-1} x_i' + sum_k (-U^{-1} U_ik) x_k
+              g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, 1.0, 1.0);
+              for (size_t u = 0; u < F.nbrs[i].size(); ++u) {
+                const int k = F.nbrs[i][u];
+                const int clo = lo_at(F, k, i);
+                g.pair((char*)F.Ub_buf.p + F.Ub_off[F.nbr_first[i] + u] * es, mi, OP_N, seg(v, F, k, clo),
+                       (int)v.ld, OP_N, F.n[k] - clo);
+              }
+              g.close();
+            }
+            a1.add(Uinv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+          }
+          for (int i : bt) a2.add(Q(F, i), F.n[i], OP_C, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
         }
         if (!use_inverse) {
-          run_gemm(c, g, prec, prec, prec, "bwd update");
-          run_apply_narrow(c, a1, prec, "bwd U^-1");
+          run_gemm(lc, g, prec, prec, prec, "bwd update");
+          run_apply_narrow(lc, a1, prec, "bwd U^-1");
         } else {
-          run_apply_narrow(c, a1, prec, "inv U^-1");
-          run_gemm(c, g, prec, prec, prec, "inv update");
+          run_apply_narrow(lc, a1, prec, "inv U^-1");
+          run_gemm(lc, g, prec, prec, prec, "inv update");
         }
-        for (int i : bt) a2.add(Q(F, i), F.n[i], OP_C, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
-        run_apply_narrow(c, a2, prec, "bwd conj Q");
+        run_apply_narrow(lc, a2, prec, "bwd conj Q");
       }
-      if (li > 0) merge_vec(c, c.lev[li - 1], F, vec[li - 1], v, nrhs, false);
+      if (d > 0) merge(d - 1, false);
     }
   } else {
     // ------------- adjoint: Z^{-H} = (U^{-1}-part)^H then (L^{-1}-part)^H -------------
-    for (int li = 0; li < nlev; ++li) {
-      LevelF& F = c.lev[li];
-      Vec v = vec[li];
-      for (const auto& bt : F.batches) {
+    for (int d = 0; d < depth; ++d) {
+      for (int b = 0; b < nbat(d); ++b) {
         ApplyBatch a1, a2;
-        for (int i : bt) {
-          a1.add(Q(F, i), F.n[i], OP_T, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
-          if (F.m[i] > 0) a2.add(Uinv(F, i), F.m[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
-        }
-        run_apply_narrow(c, a1, prec, "adj Q^T");
-        run_apply_narrow(c, a2, prec, "adj U^-H");
-        std::map<int, std::vector<int>> tg;
-        for (int i : bt)
-          if (F.m[i] > 0)
-            for (int k : F.nbrs[i]) tg[k].push_back(i);
         GemmBatch g;
-        for (auto& [k, cl] : tg) {
-          const int clo = lo_at(F, k, cl[0]);
-          g.task(seg(v, F, k, clo), (int)v.ld, F.n[k] - clo, nrhs, -1.0, 1.0);
-          for (int i : cl)
-            g.pair(NBp(c, F, i, k) + (size_t)clo * F.n[i] * es, F.n[i], OP_H, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
-          g.close();
-        }
-        run_gemm(c, g, prec, prec, prec, "adj U^H update");
-      }
-      if (li + 1 < nlev) merge_vec(c, F, c.lev[li + 1], v, vec[li + 1], nrhs, true);
-    }
-    root_vec(c, c.lev[nlev - 1], vec[nlev - 1], vr, nrhs, true);
-    root_solve(c, vr.p, (int)vr.ld, nrhs, true);
-    root_vec(c, c.lev[nlev - 1], vec[nlev - 1], vr, nrhs, false);
-    for (int li = nlev - 1; li >= 0; --li) {
-      LevelF& F = c.lev[li];
-      Vec v = vec[li];
-      for (int b = (int)F.batches.size() - 1; b >= 0; --b) {
-        const auto& bt = F.batches[b];
-        GemmBatch g;
-        ApplyBatch a1, a2;
-        for (int i : bt) {
-          const int mi = F.m[i];
-          if (mi > 0) {
-            g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, -1.0, 1.0);
-            for (int j : F.nbrs[i]) {
-              const int rlo = lo_at(F, j, i);
-              g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_H, seg(v, F, j, rlo), (int)v.ld, OP_N, F.n[j] - rlo);
-            }
-            g.close();
-            a1.add(Linv(F, i), mi, OP_H, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+        for (size_t q = 0; q < nq; ++q) {
+          if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
+          Ctx& c = *cs[q];
+          const LevelF& F = c.lev[d];
+          const Vec v = sv[q].vec[d];
+          const auto& bt = F.batches[b];
+          for (int i : bt) {
+            a1.add(Q(F, i), F.n[i], OP_T, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
+            if (F.m[i] > 0) a2.add(Uinv(F, i), F.m[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
           }
-          a2.add(Q(F, i), F.n[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
+          std::map<int, std::vector<int>> tg;
+          for (int i : bt)
+            if (F.m[i] > 0)
+              for (int k : F.nbrs[i]) tg[k].push_back(i);
+          for (auto& [k, cl] : tg) {
+            const int clo = lo_at(F, k, cl[0]);
+            g.task(seg(v, F, k, clo), (int)v.ld, F.n[k] - clo, nrhs, -1.0, 1.0);
+            for (int i : cl)
+              g.pair(NBp(c, F, i, k) + (size_t)clo * F.n[i] * es, F.n[i], OP_H, seg(v, F, i, 0), (int)v.ld, OP_N,
+                     F.m[i]);
+            g.close();
+          }
         }
-        run_gemm(c, g, prec, prec, prec, "adj L^H update");
-        run_apply_narrow(c, a1, prec, "adj L^-H");
-        run_apply_narrow(c, a2, prec, "adj Q");
+        run_apply_narrow(lc, a1, prec, "adj Q^T");
+        run_apply_narrow(lc, a2, prec, "adj U^-H");
+        run_gemm(lc, g, prec, prec, prec, "adj U^H update");
       }
-      if (li > 0) merge_vec(c, c.lev[li - 1], F, vec[li - 1], v, nrhs, false);
+      merge(d, true);
+    }
+    rootvec(true);
+    root(true);
+    rootvec(false);
+    for (int d = depth - 1; d >= 0; --d) {
+      for (int b = nbat(d) - 1; b >= 0; --b) {
+        GemmBatch g;
+        ApplyBatch a1, a2;
+        for (size_t q = 0; q < nq; ++q) {
+          if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
+          Ctx& c = *cs[q];
+          const LevelF& F = c.lev[d];
+          const Vec v = sv[q].vec[d];
+          const auto& bt = F.batches[b];
+          for (int i : bt) {
+            const int mi = F.m[i];
+            if (mi > 0) {
+              g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, -1.0, 1.0);
+              for (int j : F.nbrs[i]) {
+                const int rlo = lo_at(F, j, i);
+                g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_H, seg(v, F, j, rlo), (int)v.ld, OP_N,
+                       F.n[j] - rlo);
+              }
+              g.close();
+              a1.add(Linv(F, i), mi, OP_H, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+            }
+            a2.add(Q(F, i), F.n[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
+          }
+        }
+        run_gemm(lc, g, prec, prec, prec, "adj L^H update");
+        run_apply_narrow(lc, a1, prec, "adj L^-H");
+        run_apply_narrow(lc, a2, prec, "adj Q");
+      }
+      if (d > 0) merge(d - 1, false);
     }
   }
+}
+
+void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {
+  solve_tree_group({&c}, {xv}, nrhs, adjoint, use_inverse);
 }
 
 }  // namespace h2

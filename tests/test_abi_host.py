@@ -133,3 +133,18 @@ def test_bad_arguments_are_rejected(libh2):
     assert libh2.h2_factorize(None, 1e-6, 0) == -1
     assert libh2.h2_load(0, 0, 0, None, None, None, None, None, None, None, None, 0, None, None, None, None, None,
                          ctypes.byref(out)) == -1
+
+
+def test_batch_calls_reject_bad_groups(libh2):
+    # no GPU needed: the group checks run before any device work
+    from paper_1703_06155_gb300 import H2
+    pts = inputs.grid_points(4, H)
+    a = H2.build(pts, K, H, 3.0, 1e-6, host_only=1)
+    arr = (ctypes.c_void_p * 2)(a._h.value, a._h.value)
+    assert libh2.h2_factorize_batch(None, 1, 1e-6, 0) == -1
+    assert libh2.h2_factorize_batch(arr, 0, 1e-6, 0) == -1
+    assert libh2.h2_factorize_batch(arr, 2, 1e-6, 0) == -1      # the same context twice
+    assert libh2.h2_factorize_batch(arr, 1, 1e-6, 0) == -1      # host_only context
+    one = (ctypes.c_void_p * 1)(None)
+    assert libh2.h2_solve_batch(arr, 1, one, one, 1, 0, 1e-6, 1, None, None, None) == -1
+    a.close()
