@@ -378,7 +378,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         gG.task(Sq + f.G, f.p, f.p, f.p, 1.0, 0.0);
         gG.pair(Vp(q, f.i), n, OP_H, Sq + f.T1, n, OP_N, n);
         gG.close();
-        pc.push_back(PcholTask{Sq + f.G, Sq + f.M, Sq + f.L, Sq + f.T, d_r[q] + u, f.p, n, snorm(q, f.i), eps * eps});
+        pc.push_back(
+            PcholTask{Sq + f.G, Sq + f.M, Sq + f.L, Sq + f.T, d_r[q] + u, f.p, n, snorm(q, f.i), eps * eps, Sq + f.W});
         maxp = std::max(maxp, f.p);
       }
     }
@@ -458,10 +459,13 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       lc.st.upload(lc);
       ProfScope ps(lc, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0);
       if (maxr >= 48) {
-        // large Ritz problems: one 8-CTA cluster per eigenproblem
+        // large Ritz problems: one cluster of CTAs per eigenproblem (16 when
+        // few problems share the launch, so that more SMs work on each)
         const int64_t per = jacobi_cluster_scratch(maxr);
         double* js = (double*)dev_ensure(lc, lc.jac_buf, (size_t)per * eig.size() * sizeof(double));
-        ck(jacobi_eig_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, 8, js, (int*)lc.statusbuf.p, lc.stream),
+        const int csize = eig.size() * 16 <= 152 ? 16 : 8;
+        ck(jacobi_eig_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, csize, js, (int*)lc.statusbuf.p,
+                              lc.stream),
            "jacobi (cluster)");
       } else {
         ck(jacobi_eig(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, (int*)lc.statusbuf.p, lc.stream), "jacobi");

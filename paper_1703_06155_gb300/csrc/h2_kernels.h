@@ -111,6 +111,7 @@ struct PcholTask {
   int* rout;      // r'
   int p, n;
   double snorm2, eps2;
+  cd* W;          // p x p scratch (Y^H Y)
 };
 
 // ---- blocked LU of the final block: one tall panel with partial pivoting --

@@ -199,7 +199,25 @@ cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int
   const int64_t per = jacobi_cluster_scratch(maxp);
   cudaError_t e = cudaMemsetAsync(d_scratch, 0, (size_t)per * ntasks * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  if (csize > 8) cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (csize > 8) {
+    cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    // fall back to the portable size if the device cannot co-schedule csize CTAs
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(csize, 1, 1);
+    q.blockDim = dim3(NT, 1, 1);
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = csize;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi_cl, &q) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      csize = 8;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ntasks * csize, 1, 1);
   cfg.blockDim = dim3(NT, 1, 1);

@@ -12,19 +12,43 @@
 //      basis of span(L).
 // The caller then forms the Ritz matrix Qx^H G' Qx (r' x r'), diagonalizes it
 // (Jacobi), keeps the Ritz pairs above thr, and applies Q to the complement
-// basis with GEMMs.  Reductions use warp shuffles; one CTA per cluster.
+// basis with GEMMs.
+//
+// FP64 runs at 2 FMA per clock per SM on this GPU, so one problem is spread
+// over a thread-block cluster of C CTAs (C = 1 .. 16, chosen per launch):
+//   * pivoted Cholesky: rows are split in contiguous blocks over the CTAs;
+//     per pivot step each CTA forms its rows of the new column (left-looking,
+//     the k-sum split over several threads per row), updates its diagonal
+//     residuals and publishes its local pivot candidate and remaining trace;
+//     after one cluster barrier every CTA reduces the candidates read through
+//     distributed shared memory, so all take the same decisions;
+//   * Householder QR: columns are dealt round-robin; per column one cluster
+//     barrier (the owner of column j+1 applies reflector j to it first, then
+//     forms reflector j+1 before the barrier);
+//   * compact WY: W = Y^H Y by column owners, then the rows of T
+//     (T(i,j) = -tau_j sum_k T(i,k) W(k,j)) are independent and split over
+//     the CTAs.
+// Barriers are hardware cluster barriers; every loop is bounded by p.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "h2_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace h2k {
 namespace {
 
 constexpr int NT = 256;
+constexpr int PMAX = 1024;
 
 __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+// CTA-wide sum (all threads call; result to all)
 __device__ double bsum(double v, double* red) {
   v = wsum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -43,103 +67,148 @@ __device__ double bsum(double v, double* red) {
   return t;
 }
 
-__global__ void __launch_bounds__(NT) k_pchol_wy(const PcholTask* __restrict__ tasks) {
-  __shared__ double red[32];
-  __shared__ double bv[NT];
-  __shared__ int bi[NT];
-  __shared__ double tau_r[1024], tau_i[1024], tmp_r[1024], tmp_i[1024];
-  extern __shared__ unsigned char sm_raw[];
-  double* d = reinterpret_cast<double*>(sm_raw);  // p diagonal residuals
-  int* piv = reinterpret_cast<int*>(d + tasks[blockIdx.x].p + 1);
-  const PcholTask t = tasks[blockIdx.x];
+// better candidate: larger value, ties -> lower row
+__device__ __forceinline__ bool better(double v, int i, double bv, int bi) { return v > bv || (v == bv && i < bi); }
+
+__global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict__ tasks) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const PcholTask t = tasks[blockIdx.x / C];
   const int p = t.p;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = NT / 32;
+  __shared__ double red[32];
+  __shared__ double dl[PMAX];            // diagonal residuals of the own rows
+  __shared__ unsigned char used[PMAX];   // own rows already pivoted
+  __shared__ cd prow[PMAX];              // pivot row L[pc, 0:j]
+  __shared__ double cand_v[2], cand_t[2];
+  __shared__ int cand_i[2];
+  __shared__ double wv[NT / 32];
+  __shared__ int wi[NT / 32];
   cd* G = t.G;
-  cd* L = t.L;  // p x p scratch (ld p); becomes Y
-  // nu^2 = snorm2 + trace(M)
+  cd* L = t.L;  // p x p (ld p); becomes Y
+  // own rows: a contiguous block
+  const int rb = (p + C - 1) / C;
+  const int r0 = min(p, rank * rb), r1 = min(p, r0 + rb), nr = r1 - r0;
+  // nu^2 = snorm2 + trace(M) (every CTA computes it)
   double tr = 0;
   if (t.M)
-    for (int i = threadIdx.x; i < t.n; i += NT) tr += t.M[i + (size_t)i * t.n].re;
+    for (int i = tid; i < t.n; i += NT) tr += t.M[i + (size_t)i * t.n].re;
   tr = bsum(tr, red);
   const double thr = t.eps2 * (t.snorm2 + tr);
   const double tau = thr / 10.0;  // bound on the trace of the remainder
-  for (int i = threadIdx.x; i < p; i += NT) {
-    d[i] = G[i + (size_t)i * p].re;
-    piv[i] = i;
+  const int rmax = p < PMAX ? p : PMAX;
+  for (int i = tid; i < nr; i += NT) {
+    dl[i] = G[(r0 + i) + (size_t)(r0 + i) * p].re;
+    used[i] = 0;
   }
-  for (int idx = threadIdx.x; idx < p * p; idx += NT) {
-    cd z;
-    z.re = 0;
-    z.im = 0;
-    L[idx] = z;
+  for (int idx = tid; idx < nr * rmax; idx += NT) {
+    const int i = r0 + idx % nr, k = idx / nr;
+    L[i + (size_t)k * p].re = 0;
+    L[i + (size_t)k * p].im = 0;
   }
   __syncthreads();
-  int r = 0;
-  const int rmax = p < 1024 ? p : 1024;
-  for (int j = 0; j < rmax; ++j) {
-    // pivot: largest remaining diagonal (ties -> lowest position)
-    double best = -1;
-    int bq = p;
-    double trs = 0;
-    for (int q = j + threadIdx.x; q < p; q += NT) {
-      const double v = d[piv[q]];
-      trs += v > 0 ? v : 0;
-      if (v > best || (v == best && q < bq)) { best = v; bq = q; }
+  // threads per row for the left-looking k-sums
+  int tpr = 1;
+  while (tpr < 32 && tpr * 2 * max(nr, 1) <= NT) tpr *= 2;
+
+  // local candidate + remaining trace -> slot s
+  auto publish = [&](int s) {
+    double bv = -1, ts = 0;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < nr; i += NT) {
+      if (used[i]) continue;
+      const double v = dl[i];
+      ts += v > 0 ? v : 0;
+      if (better(v, r0 + i, bv, bi)) { bv = v; bi = r0 + i; }
     }
-    trs = bsum(trs, red);
-    bv[threadIdx.x] = best;
-    bi[threadIdx.x] = bq;
+    // block argmax (warp shuffles, then warp 0)
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { wv[warp] = bv; wi[warp] = bi; }
+    ts = bsum(ts, red);  // contains __syncthreads
+    if (tid < 32) {
+      bv = lane < nw ? wv[lane] : -1.0;
+      bi = lane < nw ? wi[lane] : 0x7fffffff;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      }
+      if (tid == 0) { cand_v[s] = bv; cand_i[s] = bi; cand_t[s] = ts; }
+    }
+  };
+  // reduce the C published candidates of slot s (all CTAs get the same)
+  auto gather = [&](int s, double& dv, int& pc, double& trs) {
+    dv = -1;
+    pc = 0x7fffffff;
+    trs = 0;
+    for (int q = 0; q < C; ++q) {
+      const double v = *cl.map_shared_rank(&cand_v[s], q);
+      const int i = *cl.map_shared_rank(&cand_i[s], q);
+      trs += *cl.map_shared_rank(&cand_t[s], q);
+      if (better(v, i, dv, pc)) { dv = v; pc = i; }
+    }
+  };
+
+  // ---------------------------------------------------- pivoted Cholesky
+  publish(0);
+  __threadfence();
+  cl.sync();
+  int r = 0;
+  for (int j = 0; j < rmax; ++j) {
+    double dv, trs;
+    int pc;
+    gather(j & 1, dv, pc, trs);
+    if (!(trs > tau) || !(dv > 0.0)) break;
+    const double sd = sqrt(dv);
+    // pivot row entries L[pc, 0:j] (written by its owner in earlier steps)
+    for (int k = tid; k < j; k += NT) prow[k] = L[pc + (size_t)k * p];
     __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        const double o = bv[threadIdx.x + s];
-        const int oi = bi[threadIdx.x + s];
-        if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-          bv[threadIdx.x] = o;
-          bi[threadIdx.x] = oi;
+    // column j for the own rows not yet pivoted (the pivot row gives sd)
+    const int rows_per_pass = NT / tpr;
+    for (int base = 0; base < nr; base += rows_per_pass) {
+      const int li = base + tid / tpr, sub = tid % tpr;
+      const bool act = li < nr && !used[li];
+      const int i = r0 + li;
+      double vr = 0, vi = 0;
+      if (act)
+        for (int k = sub; k < j; k += tpr) {
+          const cd a = L[i + (size_t)k * p], b = prow[k];  // a * conj(b)
+          vr += a.re * b.re + a.im * b.im;
+          vi += a.im * b.re - a.re * b.im;
+        }
+      for (int o = tpr / 2; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (act && sub == 0) {
+        cd z;
+        z.re = (G[i + (size_t)pc * p].re - vr) / sd;
+        z.im = (G[i + (size_t)pc * p].im - vi) / sd;
+        L[i + (size_t)j * p] = z;
+        if (i == pc) {
+          used[li] = 1;
+        } else {
+          dl[li] -= z.re * z.re + z.im * z.im;
         }
       }
-      __syncthreads();
-    }
-    const double dv = bv[0];
-    const int qb = bi[0];
-    __syncthreads();
-    if (!(trs > tau) || !(dv > 0.0)) break;
-    if (threadIdx.x == 0) {
-      const int x = piv[j];
-      piv[j] = piv[qb];
-      piv[qb] = x;
     }
     __syncthreads();
-    const int pc = piv[j];
-    const double sd = sqrt(dv);
-    // column j of L for the rows not yet pivoted (original row indexing)
-    for (int q = j + threadIdx.x; q < p; q += NT) {
-      const int i = piv[q];
-      double vr = G[i + (size_t)pc * p].re, vi = G[i + (size_t)pc * p].im;
-      for (int k = 0; k < j; ++k) {
-        const cd a = L[i + (size_t)k * p], b = L[pc + (size_t)k * p];  // a * conj(b)
-        vr -= a.re * b.re + a.im * b.im;
-        vi -= a.im * b.re - a.re * b.im;
-      }
-      cd z;
-      z.re = vr / sd;
-      z.im = vi / sd;
-      L[i + (size_t)j * p] = z;
-    }
-    __syncthreads();
-    for (int q = j + 1 + threadIdx.x; q < p; q += NT) {
-      const int i = piv[q];
-      const cd z = L[i + (size_t)j * p];
-      d[i] -= z.re * z.re + z.im * z.im;
-    }
-    __syncthreads();
+    publish((j + 1) & 1);
+    __threadfence();
+    cl.sync();
     r = j + 1;
   }
-  // Householder QR of L(:, 0:r) in place (zlarfg convention, v_0 = 1)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT / 32;
-  for (int j = 0; j < r; ++j) {
+
+  // ---------------------------------------- Householder QR of L(:, 0:r)
+  cd* T = t.T;  // r x r (ld r): tau_j on the diagonal while the QR runs
+  auto reflector = [&](int j) {
     double s = 0;
-    for (int i = j + 1 + threadIdx.x; i < p; i += NT) {
+    for (int i = j + 1 + tid; i < p; i += NT) {
       const cd v = L[i + (size_t)j * p];
       s += v.re * v.re + v.im * v.im;
     }
@@ -153,7 +222,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy(const PcholTask* __restrict__ t
       ti_ = -al.im / beta;
       const double dr = al.re - beta, di = al.im, dd = dr * dr + di * di;
       const double scr = dr / dd, sci = -di / dd;
-      for (int i = j + 1 + threadIdx.x; i < p; i += NT) {
+      for (int i = j + 1 + tid; i < p; i += NT) {
         cd v = L[i + (size_t)j * p];
         const double vr = v.re * scr - v.im * sci, vi = v.re * sci + v.im * scr;
         v.re = vr;
@@ -161,93 +230,142 @@ __global__ void __launch_bounds__(NT) k_pchol_wy(const PcholTask* __restrict__ t
         L[i + (size_t)j * p] = v;
       }
     }
-    if (threadIdx.x == 0) { tau_r[j] = tr_; tau_i[j] = ti_; }
-    __syncthreads();
-    if (!(tr_ == 0.0 && ti_ == 0.0))
-      for (int c = j + 1 + warp; c < r; c += nw) {
-        double dr = 0, di = 0;
-        for (int i = j + lane; i < p; i += 32) {
-          const cd w = L[i + (size_t)c * p];
-          cd v;
-          if (i == j) { v.re = 1; v.im = 0; } else v = L[i + (size_t)j * p];
-          dr += v.re * w.re + v.im * w.im;
-          di += v.re * w.im - v.im * w.re;
-        }
-        dr = wsum(dr);
-        di = wsum(di);
-        const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
-        for (int i = j + lane; i < p; i += 32) {
-          cd v;
-          if (i == j) { v.re = 1; v.im = 0; } else v = L[i + (size_t)j * p];
-          cd w = L[i + (size_t)c * p];
-          w.re -= v.re * fr - v.im * fi;
-          w.im -= v.re * fi + v.im * fr;
-          L[i + (size_t)c * p] = w;
-        }
-      }
-    __syncthreads();
+    if (tid == 0) {
+      T[j + (size_t)j * r].re = tr_;
+      T[j + (size_t)j * r].im = ti_;
+    }
+  };
+  // apply H_j^H to column c (one warp)
+  auto apply_col = [&](int j, int c, double tr_, double ti_) {
+    double dr = 0, di = 0;
+    for (int i = j + lane; i < p; i += 32) {
+      const cd w = L[i + (size_t)c * p];
+      cd v;
+      if (i == j) { v.re = 1; v.im = 0; } else v = L[i + (size_t)j * p];
+      dr += v.re * w.re + v.im * w.im;
+      di += v.re * w.im - v.im * w.re;
+    }
+    dr = wsum(dr);
+    di = wsum(di);
+    const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
+    for (int i = j + lane; i < p; i += 32) {
+      cd v;
+      if (i == j) { v.re = 1; v.im = 0; } else v = L[i + (size_t)j * p];
+      cd w = L[i + (size_t)c * p];
+      w.re -= v.re * fr - v.im * fi;
+      w.im -= v.re * fi + v.im * fr;
+      L[i + (size_t)c * p] = w;
+    }
+  };
+  if (r > 0) {
+    if (rank == 0) reflector(0);
+    __threadfence();
+    cl.sync();
   }
-  // Y: unit lower trapezoidal reflectors (upper part zeroed, v_0 = 1)
-  for (int idx = threadIdx.x; idx < p * r; idx += NT) {
-    const int i = idx % p, j = idx / p;
-    if (i < j) { L[idx].re = 0; L[idx].im = 0; }
-    else if (i == j) { L[idx].re = 1; L[idx].im = 0; }
-  }
-  __syncthreads();
-  // compact WY: T upper triangular, T_jj = tau_j,
-  // T(0:j, j) = -tau_j T(0:j, 0:j) (Y(:, 0:j)^H Y(:, j))
-  cd* T = t.T;  // r x r (ld r)
-  for (int idx = threadIdx.x; idx < r * r; idx += NT) {
-    cd z;
-    z.re = 0;
-    z.im = 0;
-    T[idx] = z;
-  }
-  __syncthreads();
   for (int j = 0; j < r; ++j) {
-    // w = Y(:, 0:j)^H Y(:, j)   (stored temporarily in T(0:j, j))
-    for (int k = warp; k < j; k += nw) {
+    const double tr_ = T[j + (size_t)j * r].re, ti_ = T[j + (size_t)j * r].im;
+    if (!(tr_ == 0.0 && ti_ == 0.0)) {
+      // own columns c > j, c = rank (mod C)
+      int first = j + 1 + ((rank - (j + 1)) % C + C) % C;
+      for (int c = first + warp * C; c < r; c += nw * C) apply_col(j, c, tr_, ti_);
+    }
+    __syncthreads();
+    if (j + 1 < r && (j + 1) % C == rank) reflector(j + 1);
+    __threadfence();
+    cl.sync();
+  }
+  // Y: unit lower trapezoidal reflectors (upper part zeroed, v_0 = 1), own columns
+  for (int c = rank; c < r; c += C)
+    for (int i = tid; i <= c && i < p; i += NT) {
+      L[i + (size_t)c * p].re = (i == c) ? 1 : 0;
+      L[i + (size_t)c * p].im = 0;
+    }
+  __threadfence();
+  cl.sync();
+
+  // ------------------------------------------------------- compact WY T
+  // W(k, j) = Y(:, k)^H Y(:, j), k < j, into the scratch (ld r), by column owners
+  cd* W = t.W;
+  for (int c = rank; c < r; c += C)
+    for (int k = warp; k < c; k += nw) {
       double sr = 0, si = 0;
-      for (int i = lane; i < p; i += 32) {
-        const cd a = L[i + (size_t)k * p], b = L[i + (size_t)j * p];
+      for (int i = c + lane; i < p; i += 32) {  // Y(i, c) = 0 for i < c
+        const cd a = L[i + (size_t)k * p], b = L[i + (size_t)c * p];
         sr += a.re * b.re + a.im * b.im;
         si += a.re * b.im - a.im * b.re;
       }
       sr = wsum(sr);
       si = wsum(si);
-      if (lane == 0) { T[k + (size_t)j * r].re = sr; T[k + (size_t)j * r].im = si; }
+      if (lane == 0) { W[k + (size_t)c * r].re = sr; W[k + (size_t)c * r].im = si; }
     }
-    __syncthreads();
-    // T(0:j, j) = -tau_j T(0:j,0:j) w   (upper triangular matvec)
-    for (int i = threadIdx.x; i < j; i += NT) {
+  __threadfence();
+  cl.sync();
+  // rows of T: T(i, i) = tau_i, T(i, j) = -tau_j sum_{k=i}^{j-1} T(i, k) W(k, j);
+  // one warp per own row (rows i = rank mod C), strictly lower part zeroed
+  for (int i = rank + warp * C; i < r; i += nw * C) {
+    for (int k = lane; k < i; k += 32) {
+      T[i + (size_t)k * r].re = 0;
+      T[i + (size_t)k * r].im = 0;
+    }
+    for (int j = i + 1; j < r; ++j) {
       double sr = 0, si = 0;
-      for (int k = i; k < j; ++k) {
-        const cd a = T[i + (size_t)k * r], w = T[k + (size_t)j * r];
+      for (int k = i + lane; k < j; k += 32) {
+        const cd a = T[i + (size_t)k * r], w = W[k + (size_t)j * r];
         sr += a.re * w.re - a.im * w.im;
         si += a.re * w.im + a.im * w.re;
       }
-      tmp_r[i] = sr;
-      tmp_i[i] = si;
+      sr = wsum(sr);
+      si = wsum(si);
+      const double tr2 = T[j + (size_t)j * r].re, ti2 = T[j + (size_t)j * r].im;
+      if (lane == 0) {
+        T[i + (size_t)j * r].re = -(tr2 * sr - ti2 * si);
+        T[i + (size_t)j * r].im = -(tr2 * si + ti2 * sr);
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < j; i += NT) {
-      const double sr = tmp_r[i], si = tmp_i[i];
-      const double tr2 = tau_r[j], ti2 = tau_i[j];
-      T[i + (size_t)j * r].re = -(tr2 * sr - ti2 * si);
-      T[i + (size_t)j * r].im = -(tr2 * si + ti2 * sr);
-    }
-    if (threadIdx.x == 0) { T[j + (size_t)j * r].re = tau_r[j]; T[j + (size_t)j * r].im = tau_i[j]; }
-    __syncthreads();
   }
-  if (threadIdx.x == 0) *t.rout = r;
+  if (rank == 0 && tid == 0) *t.rout = r;
 }
 
 }  // namespace
 
 cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const size_t sm = (size_t)(maxp + 2) * sizeof(double) + (size_t)(maxp + 2) * sizeof(int);
-  k_pchol_wy<<<n, NT, sm, s>>>(d);
+  if (maxp > PMAX) return cudaErrorInvalidValue;
+  // CTAs per problem: spread few problems over the SMs, keep >= 16 rows each
+  int csize = std::max(1, std::min(16, std::min(152 / n, maxp / 16)));
+  if (csize > 8) {
+    cudaFuncSetAttribute(k_pchol_wy_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(csize, 1, 1);
+    q.blockDim = dim3(NT, 1, 1);
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = csize;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pchol_wy_cl, &q) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      csize = 8;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n * csize, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_pchol_wy_cl, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
