@@ -36,17 +36,41 @@ struct GemmBatch {
   // are split along K (deterministic two-pass sum) so that a launch keeps the
   // SMs busy.  Returns the split-K workspace size in accumulator elements.
   double alg_flops = 0;  // 8 M N K per pair; Hermitian outputs: upper triangle only
-  int skinny = 0;        // all outputs have N <= 16: 64 x 16 tiles
+  int shape = 0;         // output tile shape (h2k::gemm_tile_m / gemm_tile_n)
+  int pina = -1;         // precision of the A operands if it differs from B's
   int64_t plan(int target_ctas = 4 * 152) {
     tl.clear();
     alg_flops = 0;
-    skinny = 1;
-    for (auto& g : t)
-      if (g.N > 16 || g.herm) skinny = 0;
-    for (auto& g : t)
+    std::vector<int64_t> kt(t.size(), 0);
+    for (size_t ti = 0; ti < t.size(); ++ti)
+      for (int q = t[ti].p0; q < t[ti].p0 + t[ti].np; ++q) kt[ti] += p[q].K;
+    for (size_t ti = 0; ti < t.size(); ++ti) {
+      const auto& g = t[ti];
       for (int q = g.p0; q < g.p0 + g.np; ++q)
         alg_flops += g.herm ? 4.0 * g.M * (double)(g.M + 1) * p[q].K : 8.0 * g.M * (double)g.N * p[q].K;
-    const int bm = h2k::gemm_tile_m(skinny), bn = h2k::gemm_tile_n(skinny);
+    }
+    // tile shape: least padded work, small tiles charged for their lower
+    // arithmetic intensity; Hermitian outputs need square tiles
+    bool anyherm = false;
+    for (auto& g : t) anyherm |= g.herm != 0;
+    static const double penalty[4] = {1.0, 1.08, 1.15, 1.3};
+    double best = -1;
+    for (int sh = 0; sh < 4; ++sh) {
+      if (anyherm && (sh == 1 || sh == 3)) continue;
+      const int bm = h2k::gemm_tile_m(sh), bn = h2k::gemm_tile_n(sh);
+      double w = 0;
+      for (size_t ti = 0; ti < t.size(); ++ti) {
+        const auto& g = t[ti];
+        const double a = (g.M + bm - 1) / bm, b = (g.N + bn - 1) / bn;
+        w += (g.herm ? a * (a + 1) / 2 : a * b) * bm * (double)bn * (double)kt[ti];
+      }
+      w *= penalty[sh];
+      if (best < 0 || w < best) {
+        best = w;
+        shape = sh;
+      }
+    }
+    const int bm = h2k::gemm_tile_m(shape), bn = h2k::gemm_tile_n(shape);
     auto ntile = [&](const h2k::GemmTask& g) {
       const int64_t a = (g.M + bm - 1) / bm, b = (g.N + bn - 1) / bn;
       return g.herm ? a * (a + 1) / 2 : a * b;
@@ -56,8 +80,7 @@ struct GemmBatch {
     int64_t ws = 0;
     for (size_t ti = 0; ti < t.size(); ++ti) {
       h2k::GemmTask& g = t[ti];
-      int64_t K = 0;
-      for (int q = g.p0; q < g.p0 + g.np; ++q) K += p[q].K;
+      const int64_t K = kt[ti];
       int nk = 1;
       if (tiles0 < target_ctas && K >= 128) {
         nk = (int)std::min<int64_t>((target_ctas + tiles0 - 1) / tiles0, K / 64);

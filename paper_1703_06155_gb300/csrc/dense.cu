@@ -401,6 +401,32 @@ __global__ void k_col_norms2(const cd* x, int64_t N, double* out) {
   if (threadIdx.x == 0) out[c] = s;
 }
 
+// ||block||_F^2 of every block (one CTA per block), then per task the sum of
+// its blocks' partials in block order (deterministic)
+template <class E>
+__global__ void k_frob2_part(const FrobBlock* __restrict__ blocks, double* __restrict__ part) {
+  __shared__ double red[32];
+  const FrobBlock k = blocks[blockIdx.x];
+  const E* A = (const E*)k.A;
+  double s = 0;
+  for (int c = 0; c < k.cols; ++c)
+    for (int r = threadIdx.x; r < k.rows; r += NT) {
+      const E v = A[r + (int64_t)c * k.lda];
+      s += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+    }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_frob2_sum(const FrobTask* __restrict__ tasks, int ntasks, const double* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntasks) return;
+  const FrobTask t = tasks[i];
+  double s = 0;
+  for (int b = t.b0; b < t.b0 + t.nb; ++b) s += part[b];
+  *t.out = s;
+}
+
 __global__ void k_axpby(const cd* a, const cd* b, cd* y, int64_t n, double al, double be) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     cd v;
@@ -484,6 +510,17 @@ cudaError_t permute_scale(const void* in, void* out, const int64_t* perm, const 
 cudaError_t col_norms2(const cd* x, int64_t N, int nrhs, double* out, cudaStream_t s) {
   if (nrhs <= 0) return cudaSuccess;
   k_col_norms2<<<nrhs, NT, 0, s>>>(x, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t frob2(const FrobTask* d_tasks, int ntasks, const FrobBlock* d_blocks, int nblocks, double* d_part,
+                  int prec, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (nblocks > 0) {
+    if (prec == P64) k_frob2_part<cd><<<nblocks, NT, 0, s>>>(d_blocks, d_part);
+    else k_frob2_part<cf><<<nblocks, NT, 0, s>>>(d_blocks, d_part);
+  }
+  k_frob2_sum<<<(ntasks + 127) / 128, 128, 0, s>>>(d_tasks, ntasks, d_part);
   return cudaGetLastError();
 }
 

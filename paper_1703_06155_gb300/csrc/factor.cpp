@@ -46,7 +46,7 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   c.st.upload(c);
   ProfScope ps(c, std::string("gemm:") + what, b.alg_flops);
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
-          wsp, c.stream, b.skinny),
+          wsp, c.stream, b.shape, b.pina),
      what);
   c.launches++;
   if (ws > 0) {
@@ -60,7 +60,7 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   for (auto& g : b.t)
     if (g.herm) maxh = std::max(maxh, g.M * g.N);
   if (maxh > 0) {
-    ck(gemm_mirror(c.st.ptr<GemmTask>(i0), (int)b.t.size(), maxh, pout, c.stream), what);
+    ck(gemm_mirror(c.st.ptr<GemmTask>(i0), (int)b.t.size(), maxh, pout, h2k::gemm_tile_m(b.shape), c.stream), what);
     c.launches++;
   }
 }
@@ -268,7 +268,9 @@ struct Job {
 struct Info {
   int i, n, k0, p, rp = 0;
   bool fill;
-  size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1;
+  bool proj = false;  // Gram formed in complement coordinates: X = Vp^H F, G' = X X^H
+  int64_t wsum = 0;   // total fill-in width of the row (and column)
+  size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1, X, tr;
   std::vector<int> rowf, colf;
 };
 
@@ -320,8 +322,21 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       if (f.fill) {
         const size_t n = f.n, p = f.p;
         auto take = [&](size_t cnt) { const size_t o = sc; sc += cnt; return o; };
-        f.M = take(n * n);
-        f.T1 = take(n * p);
+        for (int id : f.rowf) f.wsum += F.n[F.fill_pairs[id].second] - lo_of(q, F.fill_pairs[id].second);
+        if (!c.H.symmetric)
+          for (int id : f.colf) f.wsum += F.n[F.fill_pairs[id].first] - lo_of(q, F.fill_pairs[id].first);
+        // FP64 work of the two ways to form G' = Vp^H M Vp (M = sum F F^H):
+        //   full:       M (4 n^2 W, Hermitian) + M Vp (8 n^2 p) + Vp^H (M Vp) (8 n p^2)
+        //   projected:  X = Vp^H F (8 p n W) + X X^H (4 p^2 W, Hermitian)
+        const double W = (double)f.wsum, dn = n, dp = p;
+        f.proj = (8 * dp * dn + 4 * dp * dp) * W < 4 * dn * dn * W + 8 * dn * dn * dp + 8 * dn * dp * dp;
+        f.tr = take(1);
+        if (f.proj) {
+          f.X = take(p * (size_t)f.wsum);
+        } else {
+          f.M = take(n * n);
+          f.T1 = take(n * p);
+        }
         f.G = take(p * p);
         f.L = take(p * p);
         f.T = take(p * p);
@@ -347,8 +362,10 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   std::vector<std::vector<int>> r(nj), sweeps(nj);
   for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
   if (anyfill) {
-    GemmBatch gM, gT, gG;
+    GemmBatch gM, gX, gT, gG;
     std::vector<PcholTask> pc;
+    std::vector<FrobTask> ft;
+    std::vector<FrobBlock> fb;
     int maxp = 0;
     for (size_t q = 0; q < nj; ++q) {
       const bool sym = jobs[q].c->H.symmetric;
@@ -356,34 +373,82 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       for (size_t u = 0; u < info[q].size(); ++u) {
         Info& f = info[q][u];
         if (!f.fill) continue;
-        const int n = f.n;
+        const int n = f.n, p = f.p;
         cd* Sq = S[q];
-        gM.task(Sq + f.M, n, n, n, 1.0, 0.0);
+        // trace(M) = sum of ||F||_F^2 over the row (and column) fill-ins
+        const int b0 = (int)fb.size();
         for (int id : f.rowf) {
           const int k = F.fill_pairs[id].second, lo = lo_of(q, k);
-          char* A = FB(q, id) + (size_t)lo * n * es;
-          gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
+          fb.push_back(FrobBlock{FB(q, id) + (size_t)lo * n * es, n, n, F.n[k] - lo});
         }
         if (!sym)
           for (int id : f.colf) {
             const int k = F.fill_pairs[id].first, lo = lo_of(q, k);
-            char* A = FB(q, id) + (size_t)lo * es;
-            gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
+            fb.push_back(FrobBlock{FB(q, id) + (size_t)lo * es, F.n[k], F.n[k] - lo, n});
           }
-        gM.hermitian();
-        gM.close();
-        gT.task(Sq + f.T1, n, n, f.p, 1.0, 0.0);
-        gT.pair(Sq + f.M, n, OP_N, Vp(q, f.i), n, OP_N, n);
-        gT.close();
-        gG.task(Sq + f.G, f.p, f.p, f.p, 1.0, 0.0);
-        gG.pair(Vp(q, f.i), n, OP_H, Sq + f.T1, n, OP_N, n);
-        gG.close();
-        pc.push_back(
-            PcholTask{Sq + f.G, Sq + f.M, Sq + f.L, Sq + f.T, d_r[q] + u, f.p, n, snorm(q, f.i), eps * eps, Sq + f.W});
-        maxp = std::max(maxp, f.p);
+        ft.push_back(FrobTask{b0, (int)fb.size() - b0, (double*)(Sq + f.tr)});
+        if (f.proj) {
+          // X = Vp^H [F_row ..., F_col^T ...]  (p x W), then G' = X X^H
+          int64_t off = 0;
+          for (int id : f.rowf) {
+            const int k = F.fill_pairs[id].second, lo = lo_of(q, k), w = F.n[k] - lo;
+            gX.task(Sq + f.X + (size_t)off * p, p, p, w, 1.0, 0.0);
+            gX.pair(Vp(q, f.i), n, OP_H, FB(q, id) + (size_t)lo * n * es, n, OP_N, n);
+            gX.close();
+            off += w;
+          }
+          if (!sym)
+            for (int id : f.colf) {
+              const int k = F.fill_pairs[id].first, lo = lo_of(q, k), w = F.n[k] - lo;
+              gX.task(Sq + f.X + (size_t)off * p, p, p, w, 1.0, 0.0);
+              gX.pair(Vp(q, f.i), n, OP_H, FB(q, id) + (size_t)lo * es, F.n[k], OP_T, n);
+              gX.close();
+              off += w;
+            }
+          gG.task(Sq + f.G, p, p, p, 1.0, 0.0);
+          gG.pair(Sq + f.X, p, OP_N, Sq + f.X, p, OP_H, (int)f.wsum);
+          gG.hermitian();
+          gG.close();
+        } else {
+          gM.task(Sq + f.M, n, n, n, 1.0, 0.0);
+          for (int id : f.rowf) {
+            const int k = F.fill_pairs[id].second, lo = lo_of(q, k);
+            char* A = FB(q, id) + (size_t)lo * n * es;
+            gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
+          }
+          if (!sym)
+            for (int id : f.colf) {
+              const int k = F.fill_pairs[id].first, lo = lo_of(q, k);
+              char* A = FB(q, id) + (size_t)lo * es;
+              gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
+            }
+          gM.hermitian();
+          gM.close();
+          gT.task(Sq + f.T1, n, n, p, 1.0, 0.0);
+          gT.pair(Sq + f.M, n, OP_N, Vp(q, f.i), n, OP_N, n);
+          gT.close();
+          gG.task(Sq + f.G, p, p, p, 1.0, 0.0);
+          gG.pair(Vp(q, f.i), n, OP_H, Sq + f.T1, n, OP_N, n);
+          gG.close();
+        }
+        pc.push_back(PcholTask{Sq + f.G, (const double*)(Sq + f.tr), Sq + f.L, Sq + f.T, d_r[q] + u, p, n,
+                               snorm(q, f.i), eps * eps, Sq + f.W});
+        maxp = std::max(maxp, p);
       }
     }
+    {
+      const int i0 = lc.st.add(ft), i1 = lc.st.add(fb);
+      lc.st.upload(lc);
+      ProfScope ps(lc, "trace", 0.0);
+      double* part = (double*)dev_ensure(lc, lc.frobbuf, (fb.size() + 1) * sizeof(double));
+      ck(frob2(lc.st.ptr<FrobTask>(i0), (int)ft.size(), lc.st.ptr<FrobBlock>(i1), (int)fb.size(), part, prec,
+               lc.stream),
+         "fill trace");
+      lc.launches += 2;
+    }
+    gX.pina = P64;
     run_gemm(lc, gM, prec, P64, P64, "gram");
+    run_gemm(lc, gX, prec, P64, P64, "Vp^H*F");
     run_gemm(lc, gT, P64, P64, P64, "gram*Vp");
     run_gemm(lc, gG, P64, P64, P64, "Vp^H*gram*Vp");
     {
@@ -442,7 +507,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         g4.pair(Sq + f.Qx, p, OP_H, Sq + f.Z1, p, OP_N, p);
         g4.close();
         eig.push_back(EigTask{Sq + f.Gh, Sq + f.U, (double*)(Sq + f.lam), rr, d_r[q] + 2 * nb + u});
-        sel.push_back(SelTask{Sq + f.M, (double*)(Sq + f.lam), d_r[q] + nb + u, n, rr, snorm(q, f.i), eps * eps});
+        sel.push_back(
+            SelTask{(const double*)(Sq + f.tr), (double*)(Sq + f.lam), d_r[q] + nb + u, n, rr, snorm(q, f.i), eps * eps});
         maxr = std::max(maxr, rr);
         g5.task(Sq + f.Y1, n, n, rr, 1.0, 0.0);  // Y1 = Yf(:, 0:r') U
         g5.pair(Sq + f.Yf, n, OP_N, Sq + f.U, rr, OP_N, rr);

@@ -31,29 +31,32 @@ __device__ __forceinline__ void store_val(E* p, R re, R im) {
   *p = v;
 }
 
-constexpr int BM = 64, BK = 8, NT = 256;
+constexpr int BK = 8, NT = 256;
 
 template <class R> struct CxOf;
 template <> struct CxOf<double> { using T = cd; };
 template <> struct CxOf<float> { using T = cf; };
 
-// BN = 64 (4 x 4 complex micro-tile per thread) or BN = 16 (4 x 1, for the
-// skinny products of the solve and the matvec, N = number of right-hand sides)
-template <class EI, class R, class EO, int BN>
+// Tile BM x BN with BM in {32, 64}, BN in {16, 32, 64}: each thread owns a
+// (BM / 16) x (BN / 16) complex micro-tile.  Narrow tiles serve the
+// right-hand-side products of the solve and the matvec and the small
+// complement-side Grams of Step 0, where 64 x 64 tiles would mostly compute
+// padding.
+template <class EA, class EB, class R, class EO, int BM, int BN>
 __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
                                             const GemmPair* __restrict__ pairs,
                                             const GemmTile* __restrict__ tiles,
                                             typename CxOf<R>::T* __restrict__ ws) {
-  constexpr int TN = BN / 16;
+  constexpr int TN = BN / 16, TMR = BM / 16;
   __shared__ R As_r[BK][BM], As_i[BK][BM];
   __shared__ R Bs_r[BK][BN], Bs_i[BK][BN];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmTask tk = tasks[tl.task];
   const int m0 = tl.tm * BM, n0 = tl.tn * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  R acc_r[4][TN], acc_i[4][TN];
+  R acc_r[TMR][TN], acc_i[TMR][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TMR; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc_r[i][j] = acc_i[i][j] = (R)0;
 
@@ -68,8 +71,8 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
     if (koff <= klo || kb >= khi) continue;
     const int kbeg = (int)(klo > kb ? klo - kb : 0);
     const int kend = (int)(khi - kb < pr.K ? khi - kb : pr.K);
-    const EI* A = (const EI*)pr.A;
-    const EI* B = (const EI*)pr.B;
+    const EA* A = (const EA*)pr.A;
+    const EB* B = (const EB*)pr.B;
     const bool at = (pr.opA == OP_T || pr.opA == OP_H);
     const bool bt = (pr.opB == OP_T || pr.opB == OP_H);
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
         int i, k;
         if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
         R re = 0, im = 0;
-        if (m0 + i < tk.M && k0 + k < kend) load_op<EI, R>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
+        if (m0 + i < tk.M && k0 + k < kend) load_op<EA, R>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
         As_r[k][i] = re;
         As_i[k][i] = im;
       }
@@ -92,20 +95,20 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
         int k, j;
         if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
         R re = 0, im = 0;
-        if (n0 + j < tk.N && k0 + k < kend) load_op<EI, R>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
+        if (n0 + j < tk.N && k0 + k < kend) load_op<EB, R>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
         Bs_r[k][j] = re;
         Bs_i[k][j] = im;
       }
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < BK; ++k) {
-        R ar[4], ai[4], br[TN], bi[TN];
+        R ar[TMR], ai[TMR], br[TN], bi[TN];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
+        for (int i = 0; i < TMR; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
 #pragma unroll
         for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TMR; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
             acc_r[i][j] = fma(ar[i], br[j], fma(-ai[i], bi[j], acc_r[i][j]));
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
     // partial sums of this chunk, unscaled
     typename CxOf<R>::T* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TMR; ++i) {
       const int m = m0 + ty + 16 * i;
       if (m >= tk.M) continue;
 #pragma unroll
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
   EO* C = (EO*)tk.C;
   const R al = (R)tk.alpha, be = (R)tk.beta;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TMR; ++i) {
     const int m = m0 + ty + 16 * i;
     if (m >= tk.M) continue;
 #pragma unroll
@@ -182,14 +185,14 @@ __global__ void k_gemm_reduce(const GemmTask* __restrict__ tasks, const typename
 }
 
 template <class EO>
-__global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks) {
+__global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks, int bm) {
   const GemmTask tk = tasks[blockIdx.y];
   if (!tk.herm) return;
   const int64_t mn = (int64_t)tk.M * tk.N;
   EO* C = (EO*)tk.C;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % tk.M), j = (int)(e / tk.M);
-    if (i / BM > j / BM) {
+    if (i / bm > j / bm) {
       EO v = C[(size_t)j + (size_t)i * tk.ldc];
       v.im = -v.im;
       C[(size_t)i + (size_t)j * tk.ldc] = v;
@@ -199,41 +202,50 @@ __global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks) {
 
 }  // namespace
 
-int gemm_tile_m(int) { return BM; }
-int gemm_tile_n(int skinny) { return skinny ? 16 : 64; }
+// tile shapes: 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16
+int gemm_tile_m(int shape) { return shape >= 2 ? 32 : 64; }
+int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : 16; }
 
-template <int BN>
-static cudaError_t gemm_bn(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
-                           int pin, int pout, int pacc, void* ws, cudaStream_t s) {
-  if (pin == P64 && pacc == P64 && pout == P64)
-    k_gemm<cd, double, cd, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
-  else if (pin == P32 && pacc == P32 && pout == P32)
-    k_gemm<cf, float, cf, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
-  else if (pin == P32 && pacc == P64 && pout == P64)
-    k_gemm<cf, double, cd, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
-  else if (pin == P64 && pacc == P64 && pout == P32)
-    k_gemm<cd, double, cf, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+template <int BM, int BN>
+static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
+                             int pina, int pin, int pout, int pacc, void* ws, cudaStream_t s) {
+  if (pina == P64 && pin == P64 && pacc == P64 && pout == P64)
+    k_gemm<cd, cd, double, cd, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+  else if (pina == P32 && pin == P32 && pacc == P32 && pout == P32)
+    k_gemm<cf, cf, float, cf, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
+  else if (pina == P32 && pin == P32 && pacc == P64 && pout == P64)
+    k_gemm<cf, cf, double, cd, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+  else if (pina == P64 && pin == P64 && pacc == P64 && pout == P32)
+    k_gemm<cd, cd, double, cf, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+  else if (pina == P64 && pin == P32 && pacc == P64 && pout == P64)
+    k_gemm<cd, cf, double, cd, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles, int pin,
-                 int pout, int pacc, void* ws, cudaStream_t s, int skinny) {
+                 int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina) {
   if (ntiles <= 0) return cudaSuccess;
-  return skinny ? gemm_bn<16>(d_tasks, d_pairs, d_tiles, ntiles, pin, pout, pacc, ws, s)
-                : gemm_bn<64>(d_tasks, d_pairs, d_tiles, ntiles, pin, pout, pacc, ws, s);
+  if (pina < 0) pina = pin;
+  switch (shape) {
+    case 0: return gemm_tile<64, 64>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
+    case 1: return gemm_tile<64, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
+    case 2: return gemm_tile<32, 32>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
+    case 3: return gemm_tile<32, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn, int pout, cudaStream_t s) {
+cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn, int pout, int bm, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
   int gx = (maxmn + 255) / 256;
   if (gx > 64) gx = 64;
   if (gx < 1) gx = 1;
   for (int t0 = 0; t0 < ntasks; t0 += 65535) {
     const dim3 grid(gx, ntasks - t0 < 65535 ? ntasks - t0 : 65535);
-    if (pout == P64) k_gemm_mirror<cd><<<grid, 256, 0, s>>>(d_tasks + t0);
-    else k_gemm_mirror<cf><<<grid, 256, 0, s>>>(d_tasks + t0);
+    if (pout == P64) k_gemm_mirror<cd><<<grid, 256, 0, s>>>(d_tasks + t0, bm);
+    else k_gemm_mirror<cf><<<grid, 256, 0, s>>>(d_tasks + t0, bm);
   }
   return cudaGetLastError();
 }

@@ -205,7 +205,7 @@ struct Ctx {
   std::vector<LevelF> lev;  // lev[0] = leaf level L, ..., last = l0
   RootF root;
   // scratch
-  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf, applybuf;
+  DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf, applybuf, frobbuf;
   Stager st;
   Stats stats;
   int64_t launches = 0;

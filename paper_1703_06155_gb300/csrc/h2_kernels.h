@@ -94,18 +94,28 @@ struct LuTask {
 
 // ---- Step 0 rank selection: r = #{lambda_j > eps^2 (snorm2 + trace(M))} ---
 struct SelTask {
-  const cd* M;        // n x n Gram (trace), may be NULL (trace 0)
+  const double* trM;  // trace of the fill-in Gram M (sum of ||F||_F^2)
   const double* lam;  // p eigenvalues, decreasing
   int* out;           // r
   int n, p;
   double snorm2, eps2;
 };
 
+// ---- sum of squared Frobenius norms of a list of blocks (trace of M) ------
+struct FrobBlock {
+  const void* A;
+  int lda, rows, cols;
+};
+struct FrobTask {
+  int b0, nb;   // blocks [b0, b0 + nb)
+  double* out;
+};
+
 // ---- Step 0 subspace: pivoted Cholesky of G' down to thr/(10p), Householder
 //  QR of the pivoted columns; Q = I - Y T Y^H, first r' columns Qx.
 struct PcholTask {
   cd* G;          // p x p Gram in complement coordinates (ld p), preserved
-  const cd* M;    // n x n fill-in Gram (trace -> nu^2), may be NULL
+  const double* trM;  // trace of the fill-in Gram M (-> nu^2)
   cd* L;          // p x p scratch; on exit Y (p x r', unit lower trapezoidal)
   cd* T;          // r' x r' upper triangular (ld r') -- sized p x p by caller
   int* rout;      // r'
@@ -141,17 +151,21 @@ struct KGramTile { int task, tm, tn; };
 // products are accumulated in.
 // split-K: tasks with nk > 1 write partial tiles to `ws` (accumulator
 // precision), then gemm_reduce sums them in a fixed order into C.
-// skinny = 1: 64 x 16 output tiles (every task has N <= 16), else 64 x 64
+// shape: output tile 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16
+// (gemm_tile_m / gemm_tile_n).  pina >= 0: precision of the A operands when
+// it differs from B's (pin); supported: A complex128 with B complex64, FP64
+// accumulation.
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
-                 int pacc, void* ws, cudaStream_t s, int skinny = 0);
+                 int pacc, void* ws, cudaStream_t s, int shape = 0,
+                 int pina = -1);
 cudaError_t gemm_reduce(const GemmTask* d_tasks, int ntasks, int maxmn,
                         int pout, int pacc, const void* ws, cudaStream_t s);
-// C[i, j] = conj(C[j, i]) for the entries of tiles below the diagonal
+// C[i, j] = conj(C[j, i]) for the entries of bm x bm tiles below the diagonal
 cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn,
-                        int pout, cudaStream_t s);
-int gemm_tile_m(int skinny);
-int gemm_tile_n(int skinny);
+                        int pout, int bm, cudaStream_t s);
+int gemm_tile_m(int shape);
+int gemm_tile_n(int shape);
 
 cudaError_t apply_left(const ApplyTask* d_tasks, const ApplyTile* d_tiles,
                        int ntiles, int prec, int maxp, int tw, cudaStream_t s);
@@ -211,6 +225,10 @@ cudaError_t col_norms2(const cd* x, int64_t N, int nrhs, double* d_out,
 // y = a - b   (complex128, N x nrhs contiguous)
 cudaError_t axpby(const cd* a, const cd* b, cd* y, int64_t n, double alpha,
                   double beta, cudaStream_t s);
+// FrobTask.out = sum of ||block||_F^2 (blocks complex128 or complex64);
+// d_part: nblocks doubles of scratch
+cudaError_t frob2(const FrobTask* d_tasks, int ntasks, const FrobBlock* d_blocks, int nblocks, double* d_part,
+                  int prec, cudaStream_t s);
 // grad[i] (=|+=) alpha / sqchi[i]^2 * sum_c Re(x[i,c] conj(mu[i,c] - g[i,c]))
 // (g may be null); all in the caller's (global) order
 cudaError_t grad_chi(const cd* x, const cd* mu, const cd* g, const double* sqchi,

@@ -224,7 +224,7 @@ extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout,
     const GemmBatch& g = stages[i];
     if (g.tl.empty()) continue;
     e = gemm((const GemmTask*)(dtask + offs[i].t), (const GemmPair*)(dtask + offs[i].p),
-             (const GemmTile*)(dtask + offs[i].tl), (int)g.tl.size(), P64, P64, P64, nullptr, s, g.skinny);
+             (const GemmTile*)(dtask + offs[i].tl), (int)g.tl.size(), P64, P64, P64, nullptr, s, g.shape);
     if (e != cudaSuccess) return fail_cuda(e, "gemm");
   }
   e = permute_scale(t2, yout, (const int64_t*)c.dperm.p, adj ? sc : isc, N, nrhs, P64, P64, 1, 0, s);

@@ -15,19 +15,9 @@ template <> struct RealOf<cf> { using T = float; };
 // of ||S||_F^2 over the admissible blocks of the cluster's row and column,
 // trace(M) the squared Frobenius norm of its fill-ins (eqs. 17 / 26).
 __global__ void __launch_bounds__(NT) k_select(const SelTask* __restrict__ tasks) {
-  __shared__ double red[NT];
   __shared__ int cnt[NT];
   const SelTask t = tasks[blockIdx.x];
-  double tr = 0;
-  if (t.M)
-    for (int i = threadIdx.x; i < t.n; i += NT) tr += t.M[i + (size_t)i * t.n].re;
-  red[threadIdx.x] = tr;
-  __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double thr = t.eps2 * (t.snorm2 + red[0]);
+  const double thr = t.eps2 * (t.snorm2 + *t.trM);
   int c = 0;
   for (int j = threadIdx.x; j < t.p; j += NT) c += t.lam[j] > thr;
   cnt[threadIdx.x] = c;

@@ -90,12 +90,8 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
   // own rows: a contiguous block
   const int rb = (p + C - 1) / C;
   const int r0 = min(p, rank * rb), r1 = min(p, r0 + rb), nr = r1 - r0;
-  // nu^2 = snorm2 + trace(M) (every CTA computes it)
-  double tr = 0;
-  if (t.M)
-    for (int i = tid; i < t.n; i += NT) tr += t.M[i + (size_t)i * t.n].re;
-  tr = bsum(tr, red);
-  const double thr = t.eps2 * (t.snorm2 + tr);
+  // nu^2 = snorm2 + trace(M)
+  const double thr = t.eps2 * (t.snorm2 + *t.trM);
   const double tau = thr / 10.0;  // bound on the trace of the remainder
   const int rmax = p < PMAX ? p : PMAX;
   for (int i = tid; i < nr; i += NT) {
