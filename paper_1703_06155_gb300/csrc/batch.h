@@ -38,7 +38,9 @@ struct GemmBatch {
   double alg_flops = 0;  // 8 M N K per pair; Hermitian outputs: upper triangle only
   int shape = 0;         // output tile shape (h2k::gemm_tile_m / gemm_tile_n)
   int pina = -1;         // precision of the A operands if it differs from B's
-  int64_t plan(int target_ctas = 4 * 152) {
+  // fp64: FP64-accumulating launch (the FP64 pipe bounds it, so padding is
+  // what costs); FP32 launches keep 64-wide tiles unless padding dominates
+  int64_t plan(int target_ctas = 4 * 152, bool fp64 = true) {
     tl.clear();
     alg_flops = 0;
     std::vector<int64_t> kt(t.size(), 0);
@@ -53,7 +55,8 @@ struct GemmBatch {
     // arithmetic intensity; Hermitian outputs need square tiles
     bool anyherm = false;
     for (auto& g : t) anyherm |= g.herm != 0;
-    static const double penalty[4] = {1.0, 1.08, 1.15, 1.3};
+    static const double pen64[4] = {1.0, 1.08, 1.15, 1.3}, pen32[4] = {1.0, 1.6, 2.2, 3.5};
+    const double* penalty = fp64 ? pen64 : pen32;
     double best = -1;
     for (int sh = 0; sh < 4; ++sh) {
       if (anyherm && (sh == 1 || sh == 3)) continue;

@@ -38,7 +38,7 @@ using namespace h2k;
 
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what) {
   if (b.empty()) return;
-  const int64_t ws = b.plan();
+  const int64_t ws = b.plan(4 * 152, pacc == P64);
   if (b.tl.empty()) return;
   void* wsp = nullptr;
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
