@@ -325,11 +325,16 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         for (int id : f.rowf) f.wsum += F.n[F.fill_pairs[id].second] - lo_of(q, F.fill_pairs[id].second);
         if (!c.H.symmetric)
           for (int id : f.colf) f.wsum += F.n[F.fill_pairs[id].first] - lo_of(q, F.fill_pairs[id].first);
-        // FP64 work of the two ways to form G' = Vp^H M Vp (M = sum F F^H):
+        // Two ways to form G' = Vp^H M Vp (M = sum F F^H), FP64 flops:
         //   full:       M (4 n^2 W, Hermitian) + M Vp (8 n^2 p) + Vp^H (M Vp) (8 n p^2)
         //   projected:  X = Vp^H F (8 p n W) + X X^H (4 p^2 W, Hermitian)
+        // With a complex64 bulk the fill-ins F carry FP32 rounding already, so
+        // X is formed on the FP32 pipe (its singular values move by ~u32 ||F||,
+        // the same order as that rounding) and only X X^H, the eigen-problem and
+        // the rank decision run in FP64.  The FP64 bulk takes the cheaper order.
         const double W = (double)f.wsum, dn = n, dp = p;
-        f.proj = (8 * dp * dn + 4 * dp * dp) * W < 4 * dn * dn * W + 8 * dn * dn * dp + 8 * dn * dp * dp;
+        f.proj = prec == P32 ||
+                 (8 * dp * dn + 4 * dp * dp) * W < 4 * dn * dn * W + 8 * dn * dn * dp + 8 * dn * dp * dp;
         f.tr = take(1);
         if (f.proj) {
           f.X = take(p * (size_t)f.wsum);
@@ -362,7 +367,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   std::vector<std::vector<int>> r(nj), sweeps(nj);
   for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
   if (anyfill) {
-    GemmBatch gM, gX, gT, gG;
+    GemmBatch gM, gX, gXX, gT, gG;
     std::vector<PcholTask> pc;
     std::vector<FrobTask> ft;
     std::vector<FrobBlock> fb;
@@ -388,11 +393,12 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           }
         ft.push_back(FrobTask{b0, (int)fb.size() - b0, (double*)(Sq + f.tr)});
         if (f.proj) {
-          // X = Vp^H [F_row ..., F_col^T ...]  (p x W), then G' = X X^H
+          // X = Vp^H [F_row ..., F_col^T ...]  (p x W, bulk precision), then G' = X X^H
           int64_t off = 0;
+          char* Xb = (char*)(Sq + f.X);
           for (int id : f.rowf) {
             const int k = F.fill_pairs[id].second, lo = lo_of(q, k), w = F.n[k] - lo;
-            gX.task(Sq + f.X + (size_t)off * p, p, p, w, 1.0, 0.0);
+            gX.task(Xb + (size_t)off * p * es, p, p, w, 1.0, 0.0);
             gX.pair(Vp(q, f.i), n, OP_H, FB(q, id) + (size_t)lo * n * es, n, OP_N, n);
             gX.close();
             off += w;
@@ -400,15 +406,22 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           if (!sym)
             for (int id : f.colf) {
               const int k = F.fill_pairs[id].first, lo = lo_of(q, k), w = F.n[k] - lo;
-              gX.task(Sq + f.X + (size_t)off * p, p, p, w, 1.0, 0.0);
+              gX.task(Xb + (size_t)off * p * es, p, p, w, 1.0, 0.0);
               gX.pair(Vp(q, f.i), n, OP_H, FB(q, id) + (size_t)lo * es, F.n[k], OP_T, n);
               gX.close();
               off += w;
             }
-          gG.task(Sq + f.G, p, p, p, 1.0, 0.0);
-          gG.pair(Sq + f.X, p, OP_N, Sq + f.X, p, OP_H, (int)f.wsum);
-          gG.hermitian();
-          gG.close();
+          if (prec == P32) {
+            gXX.task(Sq + f.G, p, p, p, 1.0, 0.0);
+            gXX.pair(Sq + f.X, p, OP_N, Sq + f.X, p, OP_H, (int)f.wsum);
+            gXX.hermitian();
+            gXX.close();
+          } else {
+            gG.task(Sq + f.G, p, p, p, 1.0, 0.0);
+            gG.pair(Sq + f.X, p, OP_N, Sq + f.X, p, OP_H, (int)f.wsum);
+            gG.hermitian();
+            gG.close();
+          }
         } else {
           gM.task(Sq + f.M, n, n, n, 1.0, 0.0);
           for (int id : f.rowf) {
@@ -448,7 +461,10 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     }
     gX.pina = P64;
     run_gemm(lc, gM, prec, P64, P64, "gram");
-    run_gemm(lc, gX, prec, P64, P64, "Vp^H*F");
+    // X = Vp^H F: complex128 result with the FP64 bulk, complex64 (FP32 pipe)
+    // with the complex64 bulk; then X X^H accumulates in FP64
+    run_gemm(lc, gX, prec, prec, prec, "Vp^H*F");
+    run_gemm(lc, gXX, P32, P64, P64, "X*X^H");
     run_gemm(lc, gT, P64, P64, P64, "gram*Vp");
     run_gemm(lc, gG, P64, P64, P64, "Vp^H*gram*Vp");
     {

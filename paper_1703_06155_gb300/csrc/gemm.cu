@@ -219,6 +219,8 @@ static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, c
     k_gemm<cd, cd, double, cf, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pina == P64 && pin == P32 && pacc == P64 && pout == P64)
     k_gemm<cd, cf, double, cd, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+  else if (pina == P64 && pin == P32 && pacc == P32 && pout == P32)
+    k_gemm<cd, cf, float, cf, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

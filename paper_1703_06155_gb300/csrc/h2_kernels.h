@@ -154,7 +154,7 @@ struct KGramTile { int task, tm, tn; };
 // shape: output tile 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16
 // (gemm_tile_m / gemm_tile_n).  pina >= 0: precision of the A operands when
 // it differs from B's (pin); supported: A complex128 with B complex64, FP64
-// accumulation.
+// accumulation into complex128 or FP32 accumulation into complex64.
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
                  int pacc, void* ws, cudaStream_t s, int shape = 0,
