@@ -877,7 +877,8 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
   o << "{\"N\":" << c.H.tree.N << ",\"L\":" << c.H.L << ",\"l0\":" << c.H.l0 << ",\"factored\":" << (c.factored ? 1 : 0)
     << ",\"prec\":\"" << (c.prec == P64 ? "fp64" : "mixed") << "\",\"eps_fill\":" << c.eps_fill
     << ",\"t_build_ms\":" << c.stats.t_build_ms << ",\"t_factor_ms\":" << c.stats.t_factor_ms
-    << ",\"t_solve_ms\":" << c.stats.t_solve_ms << ",\"flops_factor\":" << c.stats.flops_factor
+    << ",\"t_solve_ms\":" << c.stats.t_solve_ms << ",\"t_factor_sync_ms\":" << c.stats.t_sync_ms
+    << ",\"flops_factor\":" << c.stats.flops_factor
     << ",\"launches_factor\":" << c.stats.launches_factor << ",\"launches_solve\":" << c.stats.launches_solve
     << ",\"refine_iters\":" << c.stats.refine_iters << ",\"refine_resid\":" << c.stats.refine_resid
     << ",\"symmetric\":" << (c.H.symmetric ? 1 : 0) << ",\"dev_bytes\":" << c.dev_bytes << ",\"dev_peak\":" << c.dev_peak << ",\"root_n\":" << c.root.n

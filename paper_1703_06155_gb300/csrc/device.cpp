@@ -3,6 +3,8 @@
 
 #include <algorithm>
 
+#include <chrono>
+
 #include "h2_host.h"
 
 namespace h2 {
@@ -59,6 +61,12 @@ void prof_reset(Ctx& c) { c.prof.clear(); }
 
 void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(H2_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void sync_timed(Ctx& c, cudaStream_t s, const char* what) {
+  const auto t0 = std::chrono::steady_clock::now();
+  ck(cudaStreamSynchronize(s), what);
+  c.stats.t_sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {

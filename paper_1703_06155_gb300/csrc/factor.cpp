@@ -480,7 +480,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       ck(cudaMemcpyAsync(rp[q].data(), d_r[q], rp[q].size() * sizeof(int), cudaMemcpyDeviceToHost, lc.stream),
          "read r'");
     }
-    ck(cudaStreamSynchronize(lc.stream), "sync after pivoted cholesky");
+    sync_timed(lc, lc.stream, "sync after pivoted cholesky");
     lc.st.begin();
     for (size_t q = 0; q < nj; ++q)
       for (size_t u = 0; u < info[q].size(); ++u)
@@ -567,7 +567,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
          "read sweeps");
     }
   }
-  ck(cudaStreamSynchronize(lc.stream), "sync after step 0");
+  sync_timed(lc, lc.stream, "sync after step 0");
   prof_resolve(lc);
   lc.st.begin();  // stream idle: staging can be reused
   for (size_t q = 0; q < nj; ++q) {
@@ -901,7 +901,7 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
 void check_status(Ctx& c) {
   int st = 0;
   ck(cudaMemcpyAsync(&st, c.statusbuf.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read status");
-  ck(cudaStreamSynchronize(c.stream), "status sync");
+  sync_timed(c, c.stream, "status sync");
   prof_resolve(c);
   if (st & 1) fail(H2_ESINGULAR, "zero pivot in a partial LU or in the final LU");
   if (st & 2) fail(H2_EINTERNAL, "Jacobi eigen-decomposition did not converge");
@@ -923,6 +923,7 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
     c->prec = prec;
     c->eps_fill = eps;
     c->stats.flops_factor = 0;
+    c->stats.t_sync_ms = 0;
     prof_reset(*c);
   }
   const int64_t launches0 = lc.launches;

@@ -166,6 +166,7 @@ struct RootF {
 
 struct Stats {
   double t_factor_ms = 0, t_solve_ms = 0, t_build_ms = 0;
+  double t_sync_ms = 0;  // factorization: host time blocked in stream synchronizes
   double flops_factor = 0;
   int64_t launches_factor = 0, launches_solve = 0;
   int refine_iters = 0;
@@ -224,6 +225,8 @@ struct ProfScope {
   ~ProfScope();
 };
 void prof_resolve(Ctx& c);  // after a stream synchronize: fold events into c.prof
+// cudaStreamSynchronize with the blocked host time added to c.stats.t_sync_ms
+void sync_timed(Ctx& c, cudaStream_t s, const char* what);
 void prof_reset(Ctx& c);
 
 // accessors of the ABI context object (defined with it in api.cpp)
