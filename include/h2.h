@@ -138,7 +138,9 @@ h2_status h2_load(int64_t N, int L, int l0, const int64_t* perm,
 /*
  * h2_factorize - Algorithm 1 of the paper (Steps 0-3 per cluster, eqs.
  * 4-33; coupling / transfer update and merge per level; LU of the final
- * block), giving Z = LU in the product form of eq. (34).
+ * block), giving Z = LU in the product form of eq. (34).  The partial-LU
+ * diagonal blocks and the final block are also inverted explicitly (the
+ * solves apply those inverses, cf. eq. 35).
  *   eps_fill  truncation of the fill-in basis update, eqs. (17)/(26)
  *   prec      h2_prec
  * Replaces any earlier factorization of the context.  H2_ESINGULAR on a zero
@@ -147,9 +149,10 @@ h2_status h2_load(int64_t N, int L, int l0, const int64_t* perm,
 h2_status h2_factorize(h2_ctx* ctx, double eps_fill, int prec);
 
 /*
- * h2_invert - explicit factor-form inverse of eq. (35): inverts every
- * partial-LU diagonal block and the final block and pre-multiplies the U
- * panels, so that H2_USE_INVERSE solves use matrix-vector products only.
+ * h2_invert - explicit factor-form inverse of eq. (35): on top of the
+ * diagonal and final-block inverses formed by h2_factorize, pre-multiplies
+ * the U panels, so that H2_USE_INVERSE solves use matrix-vector products
+ * only.
  * Requires a factorization (H2_ESTATE otherwise).
  */
 h2_status h2_invert(h2_ctx* ctx);

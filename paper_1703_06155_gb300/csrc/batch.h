@@ -55,10 +55,10 @@ struct GemmBatch {
     // arithmetic intensity; Hermitian outputs need square tiles
     bool anyherm = false;
     for (auto& g : t) anyherm |= g.herm != 0;
-    static const double pen64[4] = {1.0, 1.08, 1.15, 1.3}, pen32[4] = {1.0, 1.6, 2.2, 3.5};
+    static const double pen64[5] = {1.0, 1.08, 1.15, 1.3, 1.3}, pen32[5] = {1.0, 1.6, 2.2, 3.5, 5.0};
     const double* penalty = fp64 ? pen64 : pen32;
     double best = -1;
-    for (int sh = 0; sh < 4; ++sh) {
+    for (int sh = 0; sh < 5; ++sh) {
       if (anyherm && (sh == 1 || sh == 3)) continue;
       const int bm = h2k::gemm_tile_m(sh), bn = h2k::gemm_tile_n(sh);
       double w = 0;

@@ -409,11 +409,11 @@ __global__ void k_frob2_part(const FrobBlock* __restrict__ blocks, double* __res
   const FrobBlock k = blocks[blockIdx.x];
   const E* A = (const E*)k.A;
   double s = 0;
-  for (int c = 0; c < k.cols; ++c)
-    for (int r = threadIdx.x; r < k.rows; r += NT) {
-      const E v = A[r + (int64_t)c * k.lda];
-      s += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
-    }
+  const int64_t tot = (int64_t)k.rows * k.cols;
+  for (int64_t e = threadIdx.x; e < tot; e += NT) {
+    const E v = A[(e % k.rows) + (e / k.rows) * (int64_t)k.lda];
+    s += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+  }
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }

@@ -59,6 +59,13 @@ void prof_resolve(Ctx& c) {
 
 void prof_reset(Ctx& c) { c.prof.clear(); }
 
+HostScope::~HostScope() {
+  if (c.opts.profile != 2) return;
+  ProfAgg& a = c.prof[std::string("host:") + tag + c.prof_suffix];
+  a.launches++;
+  a.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(H2_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }

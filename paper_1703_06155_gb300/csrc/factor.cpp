@@ -29,6 +29,7 @@
 #include <chrono>
 #include <cmath>
 #include <map>
+#include <memory>
 #include <set>
 
 #include "batch.h"
@@ -38,6 +39,7 @@ using namespace h2k;
 
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what) {
   if (b.empty()) return;
+  HostScope hs(c, "run_gemm");
   const int64_t ws = b.plan(4 * 152, pacc == P64);
   if (b.tl.empty()) return;
   void* wsp = nullptr;
@@ -121,6 +123,7 @@ void run_apply_gemm(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what
 
 void run_copy(Ctx& c, CopyBatch& b, const char* what) {
   if (b.empty()) return;
+  HostScope hs(c, "run_copy");
   const int i0 = c.st.add(b.t);
   c.st.upload(c);
   ProfScope ps(c, std::string("copy:") + what, 0.0);
@@ -202,6 +205,12 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.fill_is_adm.push_back(c.adm_id[l].count(pkey(a, b)) ? 1 : 0);
     tot += (size_t)n[a] * n[b];
   }
+  F.fill_row.assign(nc, {});
+  F.fill_col.assign(nc, {});
+  for (size_t q = 0; q < F.fill_pairs.size(); ++q) {
+    F.fill_row[F.fill_pairs[q].first].push_back((int)q);
+    F.fill_col[F.fill_pairs[q].second].push_back((int)q);
+  }
   dev_ensure(c, F.fill_buf, tot * es);
   if (tot) ck(cudaMemsetAsync(F.fill_buf.p, 0, tot * es, c.stream), "fill memset");
   // bases (FP64), Q (bulk), L^{-1}P and U^{-1} (bulk), pivots
@@ -231,13 +240,18 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   dev_ensure(c, F.piv_buf, tp * sizeof(int));
   dev_ensure(c, F.Vp_buf, tvp * sizeof(cd));
   // sum of ||S||_F^2 over the admissible blocks of each row and column
-  F.snorm2.assign(nc, 0.0);
-  for (size_t q = 0; q < H.part.adm[l].size(); ++q) {
-    double v = 0;
-    for (const cplx& z : H.S[l][q]) v += std::norm(z);
-    F.snorm2[H.part.adm[l][q].first] += v;
-    F.snorm2[H.part.adm[l][q].second] += v;
+  if ((int)c.snorm2_cache.size() <= l) c.snorm2_cache.resize(l + 1);
+  std::vector<double>& sn = c.snorm2_cache[l];
+  if ((int)sn.size() != nc) {
+    sn.assign(nc, 0.0);
+    for (size_t q = 0; q < H.part.adm[l].size(); ++q) {
+      double v = 0;
+      for (const cplx& z : H.S[l][q]) v += std::norm(z);
+      sn[H.part.adm[l][q].first] += v;
+      sn[H.part.adm[l][q].second] += v;
+    }
   }
+  F.snorm2 = sn;
 }
 
 struct Ptrs {
@@ -302,6 +316,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   // Vp: complement of the incoming basis (stored with the level); G' = Vp^H M
   // Vp is the Gram of eq. (16) in complement coordinates.
   bool anyfill = false;
+  auto hsA = std::make_unique<HostScope>(lc, "phaseA-plan");
   for (size_t q = 0; q < nj; ++q) {
     Ctx& c = *jobs[q].c;
     LevelF& F = *jobs[q].F;
@@ -313,11 +328,10 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       f.n = F.n[i];
       f.k0 = F.k0[i];
       f.p = f.n - f.k0;
-      for (size_t id = 0; id < F.fill_pairs.size(); ++id) {
-        if (!F.fill_live[id]) continue;
-        if (F.fill_pairs[id].first == i) f.rowf.push_back((int)id);
-        if (F.fill_pairs[id].second == i) f.colf.push_back((int)id);
-      }
+      for (int id : F.fill_row[i])
+        if (F.fill_live[id]) f.rowf.push_back(id);
+      for (int id : F.fill_col[i])
+        if (F.fill_live[id]) f.colf.push_back(id);
       f.fill = (!f.rowf.empty() || !f.colf.empty()) && f.p > 0;
       if (f.fill) {
         const size_t n = f.n, p = f.p;
@@ -366,6 +380,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   }
   std::vector<std::vector<int>> r(nj), sweeps(nj);
   for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
+  hsA.reset();
   if (anyfill) {
     GemmBatch gM, gX, gXX, gT, gG;
     std::vector<PcholTask> pc;
@@ -588,6 +603,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   }
 
   // ------------------------------ Phase B (bulk) ---------------------------
+  auto hsB = std::make_unique<HostScope>(lc, "phaseB-Q-step2-plan");
   CopyBatch qc;
   for (size_t q = 0; q < nj; ++q) {
     const LevelF& F = *jobs[q].F;
@@ -627,20 +643,19 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           R2.add(Q, n, OP_C, NB(q, j, i) + (size_t)lo * es, F.n[j], n, F.n[j] - lo, 0);
         }
       }
-      for (size_t id = 0; id < F.fill_pairs.size(); ++id) {
+      for (int id : F.fill_row[i]) {
         if (!F.fill_live[id]) continue;
-        const auto [a, b] = F.fill_pairs[id];
-        if (a == i) {
-          const int lo = lo_of(q, b);
-          L2.add(Q, n, OP_H, FB(q, (int)id) + (size_t)lo * n * es, n, n, F.n[b] - lo, m);
-        }
-        if (b == i) {
-          const int lo = lo_of(q, a);
-          R2.add(Q, n, OP_C, FB(q, (int)id) + (size_t)lo * es, F.n[a], n, F.n[a] - lo, m);
-        }
+        const int b = F.fill_pairs[id].second, lo = lo_of(q, b);
+        L2.add(Q, n, OP_H, FB(q, id) + (size_t)lo * n * es, n, n, F.n[b] - lo, m);
+      }
+      for (int id : F.fill_col[i]) {
+        if (!F.fill_live[id]) continue;
+        const int a = F.fill_pairs[id].first, lo = lo_of(q, a);
+        R2.add(Q, n, OP_C, FB(q, id) + (size_t)lo * es, F.n[a], n, F.n[a] - lo, m);
       }
     }
   }
+  hsB.reset();
   run_apply_auto(lc, L2, true, prec, "step2 rows");
   run_apply_auto(lc, R2, false, prec, "step2 cols");
   const double f2 = (L2.flops + R2.flops) / (double)nj;
@@ -686,6 +701,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   const double f3 = (PL.flops + PR.flops) / (double)nj;
 
   GemmBatch gs;
+  auto hsS = std::make_unique<HostScope>(lc, "schur-plan");
   for (size_t q = 0; q < nj; ++q) {
     LevelF& F = *jobs[q].F;
     const std::vector<int>& bt = *jobs[q].bt;
@@ -720,6 +736,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     }
     jobs[q].c->stats.flops_factor += gs.flops - fl0 + f2 + f3;
   }
+  hsS.reset();
   run_gemm(lc, gs, prec, prec, prec, "schur");
   for (size_t q = 0; q < nj; ++q)
     for (int i : *jobs[q].bt) (*jobs[q].done)[i] = 1;
@@ -898,6 +915,43 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
   }
 }
 
+// Explicit inverse of every instance's final block (R^{-1} = the blocked LU
+// solve applied to the identity), so that a solve's final-block step is one
+// GEMM (the paper's eq. 35 inverse of the last factor).
+void root_inverse_group(Ctx& lc, const std::vector<Ctx*>& cs) {
+  const int prec = lc.prec;
+  const size_t es = esz(prec);
+  std::vector<char*> xs;
+  std::vector<int> lds;
+  std::vector<Ctx*> act;
+  for (Ctx* c : cs) {
+    const int n = c->root.n;
+    if (n == 0) continue;
+    char* Ri = (char*)dev_ensure(*c, c->root.Rinv, (size_t)n * n * es);
+    ck(cudaMemsetAsync(Ri, 0, (size_t)n * n * es, lc.stream), "Rinv memset");
+    ck(set_diag(Ri, n, n, prec, 1.0, lc.stream), "Rinv identity");
+    lc.launches++;
+    xs.push_back(Ri);
+    lds.push_back(n);
+    act.push_back(c);
+  }
+  if (act.empty()) return;
+  // the RHS widths differ per instance: group by width
+  std::map<int, std::vector<size_t>> by;
+  for (size_t q = 0; q < act.size(); ++q) by[act[q]->root.n].push_back(q);
+  for (auto& [n, qs] : by) {
+    std::vector<Ctx*> c2;
+    std::vector<char*> x2;
+    std::vector<int> l2;
+    for (size_t q : qs) {
+      c2.push_back(act[q]);
+      x2.push_back(xs[q]);
+      l2.push_back(lds[q]);
+    }
+    root_solve_grouped(lc, c2, x2, l2, n, false);
+  }
+}
+
 void check_status(Ctx& c) {
   int st = 0;
   ck(cudaMemcpyAsync(&st, c.statusbuf.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read status");
@@ -987,13 +1041,18 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
     }
     CopyBatch as, ac;
     std::vector<Ctx*> roots;
+    auto hsM = std::make_unique<HostScope>(lc, "merge-setup");
     for (Ctx* c : act) {
       if (d + 1 < (int)c->lev.size()) merge_level(*c, c->lev[d], c->lev[d + 1], as, ac);
       else roots.push_back(c);
     }
+    hsM.reset();
     run_copy(lc, as, "merge");
     run_copy(lc, ac, "merge fill");
-    if (!roots.empty()) root_factor_group(lc, roots);
+    if (!roots.empty()) {
+      root_factor_group(lc, roots);
+      root_inverse_group(lc, roots);
+    }
     check_status(lc);
   }
   lc.prof_suffix.clear();

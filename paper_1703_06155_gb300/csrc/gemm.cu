@@ -37,7 +37,7 @@ template <class R> struct CxOf;
 template <> struct CxOf<double> { using T = cd; };
 template <> struct CxOf<float> { using T = cf; };
 
-// Tile BM x BN with BM in {32, 64}, BN in {16, 32, 64}: each thread owns a
+// Tile BM x BN with BM in {16, 32, 64}, BN in {16, 32, 64}: each thread owns a
 // (BM / 16) x (BN / 16) complex micro-tile.  Narrow tiles serve the
 // right-hand-side products of the solve and the matvec and the small
 // complement-side Grams of Step 0, where 64 x 64 tiles would mostly compute
@@ -78,8 +78,9 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
       // A tile: BM x BK of op(A)
 #pragma unroll
-      for (int r = 0; r < (BM * BK) / NT; ++r) {
+      for (int r = 0; r < (BM * BK + NT - 1) / NT; ++r) {
         const int l = tid + r * NT;
+        if (l >= BM * BK) break;
         int i, k;
         if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
         R re = 0, im = 0;
@@ -202,8 +203,8 @@ __global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks, int bm) {
 
 }  // namespace
 
-// tile shapes: 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16
-int gemm_tile_m(int shape) { return shape >= 2 ? 32 : 64; }
+// tile shapes: 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16, 4 = 16 x 16
+int gemm_tile_m(int shape) { return shape == 4 ? 16 : shape >= 2 ? 32 : 64; }
 int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : 16; }
 
 template <int BM, int BN>
@@ -235,6 +236,7 @@ cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTil
     case 1: return gemm_tile<64, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
     case 2: return gemm_tile<32, 32>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
     case 3: return gemm_tile<32, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
+    case 4: return gemm_tile<16, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,6 +1,7 @@
 // Host-side data structures of libh2: cluster tree, block partition, the H^2
 // representation (FP64, tree order) and the per-context device state.
 #pragma once
+#include <chrono>
 #include <complex>
 #include <cstdint>
 #include <cstring>
@@ -143,6 +144,7 @@ struct LevelF {
   std::unordered_map<int64_t, int> fill_id;
   std::vector<size_t> fill_off;
   std::vector<char> fill_live;
+  std::vector<std::vector<int>> fill_row, fill_col;  // fill pairs by row / column cluster
   std::vector<char> fill_is_adm;
   std::vector<size_t> B_off, Q_off, inv_off, piv_off, Vp_off;
   std::vector<double> snorm2;
@@ -214,6 +216,18 @@ struct Ctx {
   std::vector<cudaEvent_t> prof_pool;
   std::unordered_map<std::string, ProfAgg> prof;  // per kernel class, since the last reset
   std::string prof_suffix;                        // profile == 2: "@<level>" appended to tags
+  // sum of ||S||_F^2 over the admissible blocks of each cluster's row and
+  // column, per level (depends on the H^2 only; computed once)
+  std::vector<std::vector<double>> snorm2_cache;
+};
+
+// Host wall time of a planning phase, kept as class "host:<tag>" (profile == 2)
+struct HostScope {
+  Ctx& c;
+  const char* tag;
+  std::chrono::steady_clock::time_point t0;
+  HostScope(Ctx& c_, const char* tag_) : c(c_), tag(tag_), t0(std::chrono::steady_clock::now()) {}
+  ~HostScope();
 };
 
 // RAII bracket of one kernel launch (no-op unless opts.profile)
@@ -239,6 +253,9 @@ void factorize(Ctx& c, double eps, int prec);
 void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec);
 void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs, int nrhs, bool adjoint,
                       bool use_inverse);
+// blocked-LU solve with the final blocks of several instances (same nrhs)
+void root_solve_grouped(Ctx& lc, const std::vector<Ctx*>& cs, const std::vector<char*>& xs,
+                        const std::vector<int>& lds, int nrhs, bool adjoint);
 void matvec_tree_group(const std::vector<Ctx*>& cs, const std::vector<const h2k::cd*>& xs,
                        const std::vector<h2k::cd*>& ys, int nrhs, bool adjoint);
 void invert(Ctx& c);

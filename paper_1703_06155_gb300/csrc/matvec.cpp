@@ -174,9 +174,9 @@ void matvec_tree_group(const std::vector<Ctx*>& cs, const std::vector<const cd*>
 void matvec_tree(Ctx& c, const cd* x, cd* y, int nrhs, bool adj) { matvec_tree_group({&c}, {x}, {y}, nrhs, adj); }
 
 // Explicit factor-form inverse (eq. 35): the diagonal inverses L^{-1}P and
-// U^{-1} exist already; add -U^{-1} U_ik for every U panel and the inverse of
-// the final block, so the backward sweep is matrix-vector products only.
-void root_solve_public(Ctx& c, char* x, int ld, int nrhs, bool adjoint);
+// U^{-1} and the inverse of the final block exist after the factorization;
+// add -U^{-1} U_ik for every U panel, so the backward sweep is matrix-vector
+// products only.
 
 void invert(Ctx& c) {
   if (!c.factored) fail(H2_ESTATE, "invert before factorize");
@@ -208,13 +208,6 @@ void invert(Ctx& c) {
       }
     }
     run_gemm(c, g, prec, prec, prec, "inverse panels");
-  }
-  RootF& R = c.root;
-  if (R.n > 0) {
-    char* Ri = (char*)dev_ensure(c, R.Rinv, (size_t)R.n * R.n * es);
-    ck(cudaMemsetAsync(Ri, 0, (size_t)R.n * R.n * es, c.stream), "Rinv memset");
-    ck(set_diag(Ri, R.n, R.n, prec, 1.0, c.stream), "Rinv identity");
-    root_solve_public(c, Ri, R.n, R.n, false);
   }
   ck(cudaStreamSynchronize(c.stream), "invert sync");
   c.inverted = true;

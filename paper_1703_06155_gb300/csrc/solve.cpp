@@ -152,8 +152,9 @@ void root_solve_group(Ctx& lc, const std::vector<Ctx*>& cs, const std::vector<ch
 
 }  // namespace
 
-void root_solve_public(Ctx& c, char* x, int ld, int nrhs, bool adjoint) {
-  root_solve_group(c, {&c}, {x}, {ld}, nrhs, adjoint);
+void root_solve_grouped(Ctx& lc, const std::vector<Ctx*>& cs, const std::vector<char*>& xs,
+                        const std::vector<int>& lds, int nrhs, bool adjoint) {
+  root_solve_group(lc, cs, xs, lds, nrhs, adjoint);
 }
 
 // One instance's level vectors for a solve
@@ -244,30 +245,23 @@ void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs,
     }
     run_copy(lc, cb, up ? "root gather" : "root scatter");
   };
+  // final block: x_r <- R^{-1} x_r (R^{-H} for the adjoint) with the explicit
+  // inverse formed at factorization time: one GEMM for all instances
   auto root = [&](bool adj) {
-    std::vector<char*> rx;
-    std::vector<int> rld;
+    GemmBatch g;
+    CopyBatch cb;
     for (size_t q = 0; q < nq; ++q) {
-      rx.push_back(sv[q].vr.p);
-      rld.push_back((int)sv[q].vr.ld);
+      Ctx& c = *cs[q];
+      const int n = c.root.n;
+      if (n == 0) continue;
+      char* tmp = (char*)dev_ensure(c, c.vecbuf2, (size_t)n * nrhs * es);
+      g.task(tmp, n, n, nrhs, 1.0, 0.0);
+      g.pair(c.root.Rinv.p, n, adj ? OP_H : OP_N, sv[q].vr.p, (int)sv[q].vr.ld, OP_N, n);
+      g.close();
+      cb.add(tmp, prec, n, n, nrhs, sv[q].vr.p, prec, (int)sv[q].vr.ld, n, nrhs);
     }
-    if (use_inverse && !adj) {
-      GemmBatch g;
-      CopyBatch cb;
-      for (size_t q = 0; q < nq; ++q) {
-        Ctx& c = *cs[q];
-        if (c.root.n == 0) continue;
-        char* tmp = (char*)dev_ensure(c, c.vecbuf2, (size_t)c.root.n * nrhs * es);
-        g.task(tmp, c.root.n, c.root.n, nrhs, 1.0, 0.0);
-        g.pair(c.root.Rinv.p, c.root.n, OP_N, rx[q], rld[q], OP_N, c.root.n);
-        g.close();
-        cb.add(tmp, prec, c.root.n, c.root.n, nrhs, rx[q], prec, rld[q], c.root.n, nrhs);
-      }
-      run_gemm(lc, g, prec, prec, prec, "root inverse apply");
-      run_copy(lc, cb, "root inverse copy");
-    } else {
-      root_solve_group(lc, cs, rx, rld, nrhs, adj);
-    }
+    run_gemm(lc, g, prec, prec, prec, adj ? "root inverse^H apply" : "root inverse apply");
+    run_copy(lc, cb, "root inverse copy");
   };
 
   if (!adjoint) {
