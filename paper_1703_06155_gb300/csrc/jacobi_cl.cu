@@ -6,11 +6,12 @@
 // but each eigenproblem runs on one cluster of CTAs so that its FP64 work is
 // spread over several SMs.  Per round:
 //   1. each CTA computes the rotations of the pairs it owns (pair i is owned by
-//      CTA i mod C) and publishes them in global scratch;
-//   2. each CTA rotates the columns of A and U of its own pairs;
-//   3. each CTA applies all row rotations to the columns it owns (col mod C).
-// Phases are separated by __threadfence() + cluster barriers (hardware
-// barrier.cluster; no software spin).  A matrix whose sweeps do not converge
+//      CTA i mod C), publishes them in global scratch and rotates the columns
+//      of A and U of those pairs (no other CTA touches them in this phase);
+//   2. each CTA applies all row rotations to the columns it owns (col mod C).
+// Phases are separated by cluster barriers with release / acquire semantics
+// (hardware barrier.cluster; no software spin), which order the global-memory
+// traffic of the cluster's threads.  A matrix whose sweeps do not converge
 // within kMaxSweeps sets status bit 2 and returns its current state.
 #include <cooperative_groups.h>
 
@@ -23,6 +24,11 @@ namespace {
 
 constexpr int NT = 512;
 constexpr int kMaxSweeps = 60;
+
+// cluster-wide barrier: arrive with release, wait with acquire (cluster scope)
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ tasks, double* __restrict__ scratch,
                                                  int64_t scratch_per_task, int* status) {
@@ -78,14 +84,13 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
   fro = red[0];
   // off-diagonal entries at the rounding level of the matrix are not rotated
   const double gmin = fmax(1e-300, 4e-16 * sqrt(fro));
-  __threadfence();
-  cl.sync();
+  cluster_barrier();
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (fro == 0.0) break;
     for (int r = 0; r < pe - 1; ++r) {
-      // 1. rotations of own pairs
-      for (int i = rank * NT + threadIdx.x; i < np; i += C * NT) {
+      // 1a. rotations of own pairs (pair i is owned by CTA i mod C)
+      for (int i = rank + threadIdx.x * C; i < np; i += NT * C) {
         int a, b;
         if (i == 0) { a = pe - 1; b = r; } else { a = (r + i) % (pe - 1); b = (r - i + pe - 1) % (pe - 1); }
         if (a > b) { const int x = a; a = b; b = x; }
@@ -111,9 +116,8 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
         rer[i] = er;
         rei[i] = ei;
       }
-      __threadfence();
-      cl.sync();
-      // 2. columns of A and U of own pairs
+      __syncthreads();
+      // 1b. columns of A and U of own pairs (pair ii is owned by CTA ii mod C)
       for (int ii = rank; ii < np; ii += C) {
         const double s = rs[ii];
         if (s == 0.0) continue;
@@ -133,9 +137,8 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
           M[row + (size_t)b * p] = nb;
         }
       }
-      __threadfence();
-      cl.sync();
-      // 3. rows of A, columns owned by this CTA, all pairs
+      cluster_barrier();
+      // 2. rows of A, columns owned by this CTA, all pairs
       const int ncol = (p - rank + C - 1) / C;
       for (int idx = threadIdx.x; idx < np * ncol; idx += NT) {
         const int i = idx / ncol, col = rank + (idx % ncol) * C;
@@ -156,8 +159,7 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
         A[a + (size_t)col * p] = na;
         A[b + (size_t)col * p] = nb;
       }
-      __threadfence();
-      cl.sync();
+      cluster_barrier();
     }
     if (!flags[sweep]) break;
   }

@@ -28,7 +28,8 @@
 //   * compact WY: W = Y^H Y by column owners, then the rows of T
 //     (T(i,j) = -tau_j sum_k T(i,k) W(k,j)) are independent and split over
 //     the CTAs.
-// Barriers are hardware cluster barriers; every loop is bounded by p.
+// Barriers are hardware cluster barriers with release / acquire semantics;
+// every loop is bounded by p.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -42,6 +43,12 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int PMAX = 1024;
+
+// cluster-wide barrier: arrive with release, wait with acquire (cluster scope;
+// orders the global and distributed-shared-memory traffic of the cluster)
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -152,8 +159,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
 
   // ---------------------------------------------------- pivoted Cholesky
   publish(0);
-  __threadfence();
-  cl.sync();
+  cluster_barrier();
   int r = 0;
   for (int j = 0; j < rmax; ++j) {
     double dv, trs;
@@ -195,8 +201,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
     }
     __syncthreads();
     publish((j + 1) & 1);
-    __threadfence();
-    cl.sync();
+    cluster_barrier();
     r = j + 1;
   }
 
@@ -255,8 +260,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
   };
   if (r > 0) {
     if (rank == 0) reflector(0);
-    __threadfence();
-    cl.sync();
+    cluster_barrier();
   }
   for (int j = 0; j < r; ++j) {
     const double tr_ = T[j + (size_t)j * r].re, ti_ = T[j + (size_t)j * r].im;
@@ -267,8 +271,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
     }
     __syncthreads();
     if (j + 1 < r && (j + 1) % C == rank) reflector(j + 1);
-    __threadfence();
-    cl.sync();
+    cluster_barrier();
   }
   // Y: unit lower trapezoidal reflectors (upper part zeroed, v_0 = 1), own columns
   for (int c = rank; c < r; c += C)
@@ -276,8 +279,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
       L[i + (size_t)c * p].re = (i == c) ? 1 : 0;
       L[i + (size_t)c * p].im = 0;
     }
-  __threadfence();
-  cl.sync();
+  cluster_barrier();
 
   // ------------------------------------------------------- compact WY T
   // W(k, j) = Y(:, k)^H Y(:, j), k < j, into the scratch (ld r), by column owners
@@ -294,8 +296,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
       si = wsum(si);
       if (lane == 0) { W[k + (size_t)c * r].re = sr; W[k + (size_t)c * r].im = si; }
     }
-  __threadfence();
-  cl.sync();
+  cluster_barrier();
   // rows of T: T(i, i) = tau_i, T(i, j) = -tau_j sum_{k=i}^{j-1} T(i, k) W(k, j);
   // one warp per own row (rows i = rank mod C), strictly lower part zeroed
   for (int i = rank + warp * C; i < r; i += nw * C) {
