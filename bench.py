@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--workload", default="grid", choices=["grid", "batch"],
                    help="grid: one instance (default); batch: many independent instances in shared launches")
     p.add_argument("--instances", type=int, default=64, help="batch workload: number of instances")
+    p.add_argument("--solve-graph-check", action="store_true",
+                   help="also time repeated solves with CUDA-graph replay (builds a second context)")
     p.add_argument("--profile-levels", action="store_true", help="kernel classes kept apart per tree level")
     p.add_argument("--apply-path", type=int, default=0, choices=[0, 1, 2],
                    help="Step 2 / panel applications: 0 auto, 1 in-place kernel, 2 GEMM + copy")
@@ -339,6 +341,27 @@ def run_ours(args):
     A.solve(b, refine=True, tol=args.tol, max_iter=30)
     fp64_solve_ms = (time.perf_counter() - s0) * 1e3
     fp64_iters = A.last_solve["iters"]
+    # repeated solves with the same factors: plain launches vs CUDA-graph replay
+    # of the sweeps (h2_opts.solve_graph; not part of the metric)
+    A.factorize(args.eps, args.prec)
+    G = H2.build(pts, K, H, args.chi, args.eps, stream=stream, solve_graph=1) if args.solve_graph_check else None
+
+    def solves(ctx, n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            ctx.solve(b, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    solve_graph = None
+    if G is not None:
+        G.factorize(args.eps, args.prec)
+        solves(G, 2)  # sizing run + capture
+        solve_graph = {"ms_per_solve_plain": solves(A, 10), "ms_per_solve_graph": solves(G, 10)}
+        G.close()
     # e2e: same step through the public API with HOST buffers
     A.factorize(args.eps, args.prec)
     e0 = time.perf_counter()
@@ -366,6 +389,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
         "clocks": cs.summary(),
         "roofline": roof,
+        "solve_graph": solve_graph,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
                     sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:40 if args.profile_levels else 12]},
     }

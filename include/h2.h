@@ -80,6 +80,10 @@ typedef struct {
                             0 (default) automatic (currently 2), 1 in-place
                             kernel (one CTA per column / row strip), 2
                             batched GEMM into a workspace, then copied back */
+  int solve_graph;       /* 1: the forward / backward sweeps of repeated
+                            solves (same vectors, nrhs, direction, factors)
+                            are captured once into a CUDA graph and replayed;
+                            0 (default): launched one by one              */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */

@@ -32,7 +32,8 @@ class h2_opts(ctypes.Structure):
     _fields_ = [("leafsize", ctypes.c_int), ("eta", ctypes.c_double), ("sign", ctypes.c_double),
                 ("ordering", ctypes.c_int), ("proxy_min", ctypes.c_int), ("proxy_radius", ctypes.c_double),
                 ("arena_cap_bytes", ctypes.c_size_t),
-                ("host_only", ctypes.c_int), ("profile", ctypes.c_int), ("apply_path", ctypes.c_int)]
+                ("host_only", ctypes.c_int), ("profile", ctypes.c_int), ("apply_path", ctypes.c_int),
+                ("solve_graph", ctypes.c_int)]
 
 
 class H2Error(RuntimeError):

@@ -241,6 +241,7 @@ void h2_default_opts(h2_opts* o) {
   o->host_only = 0;
   o->profile = 0;
   o->apply_path = 0;
+  o->solve_graph = 0;
 }
 
 const char* h2_status_string(int s) {

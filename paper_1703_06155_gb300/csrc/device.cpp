@@ -28,7 +28,8 @@ static cudaEvent_t prof_event(Ctx& c) {
   return e;
 }
 
-ProfScope::ProfScope(Ctx& c_, const std::string& tag, double flops) : c(c_), on(c_.opts.profile != 0) {
+ProfScope::ProfScope(Ctx& c_, const std::string& tag, double flops)
+    : c(c_), on(c_.opts.profile != 0 && !c_.capturing) {
   if (!on) return;
   ProfRec r{c.opts.profile == 2 ? tag + c.prof_suffix : tag, prof_event(c), prof_event(c), flops};
   ck(cudaEventRecord(r.a, c.stream), "cudaEventRecord");
@@ -81,6 +82,7 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes) return b.p;
   const size_t old = b.bytes;
   const size_t want = std::max(bytes, old + old / 4);
+  if (c.capturing) fail(H2_EINTERNAL, "device allocation during graph capture");
   if (c.opts.arena_cap_bytes && c.dev_bytes - old + want > c.opts.arena_cap_bytes)
     fail(H2_ENOMEM, "device arena cap exceeded");
   // the old contents are not kept: grow-only scratch / per-factorization arenas
@@ -98,6 +100,7 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
   }
   b.p = p;
   b.bytes = want;
+  c.gen++;
   c.dev_bytes += want;
   c.dev_peak = std::max(c.dev_peak, c.dev_bytes);
   return p;
@@ -105,6 +108,10 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
 
 Stager::~Stager() {
   if (pinned) cudaFreeHost(pinned);
+}
+
+SolveGraph::~SolveGraph() {
+  if (exec) cudaGraphExecDestroy(exec);
 }
 
 void Stager::upload(Ctx& c) {

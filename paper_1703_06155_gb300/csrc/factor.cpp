@@ -972,6 +972,7 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
   Ctx& lc = *cs[0];
   for (Ctx* c : cs) {
     c->stream = lc.stream;
+    c->epoch++;
     c->factored = false;
     c->inverted = false;
     c->prec = prec;

@@ -117,6 +117,16 @@ struct Stager {
   std::vector<size_t> offs;
   ~Stager();
   void begin() { host.clear(); offs.clear(); uploaded = 0; }
+  void swap(Stager& o) {
+    host.swap(o.host);
+    std::swap(uploaded, o.uploaded);
+    std::swap(pinned, o.pinned);
+    std::swap(cap, o.cap);
+    DevBuf t = std::move(dev);
+    dev = std::move(o.dev);
+    o.dev = std::move(t);
+    offs.swap(o.offs);
+  }
   template <class T>
   int add(const std::vector<T>& v) {
     size_t o = (host.size() + 255) & ~(size_t)255;
@@ -205,6 +215,11 @@ struct Ctx {
   bool factored = false, inverted = false;
   int prec = 0;
   double eps_fill = 0;
+  // CUDA-graph replay of solves: a graph is valid while no device buffer of
+  // its instances was (re)allocated (gen) and none was refactorized (epoch)
+  uint64_t gen = 0, epoch = 0;
+  bool capturing = false;
+  std::vector<std::unique_ptr<struct SolveGraph>> graphs;
   std::vector<LevelF> lev;  // lev[0] = leaf level L, ..., last = l0
   RootF root;
   // scratch
@@ -219,6 +234,21 @@ struct Ctx {
   // sum of ||S||_F^2 over the admissible blocks of each cluster's row and
   // column, per level (depends on the H^2 only; computed once)
   std::vector<std::vector<double>> snorm2_cache;
+};
+
+// A captured forward / backward (or adjoint) sweep of a group of instances:
+// its task lists live in its own staging buffers, so replays need no host
+// planning.  Owned by the group's first context.
+struct SolveGraph {
+  std::vector<Ctx*> cs;
+  std::vector<void*> xs;
+  int nrhs = 0;
+  bool adjoint = false, inverse = false;
+  std::vector<uint64_t> gens, epochs;
+  Stager st;
+  cudaGraphExec_t exec = nullptr;
+  int64_t nlaunch = 0;  // kernels per replay
+  ~SolveGraph();
 };
 
 // Host wall time of a planning phase, kept as class "host:<tag>" (profile == 2)

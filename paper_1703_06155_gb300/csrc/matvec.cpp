@@ -180,6 +180,7 @@ void matvec_tree(Ctx& c, const cd* x, cd* y, int nrhs, bool adj) { matvec_tree_g
 
 void invert(Ctx& c) {
   if (!c.factored) fail(H2_ESTATE, "invert before factorize");
+  c.epoch++;
   const int prec = c.prec;
   const size_t es = esz(prec);
   for (LevelF& F : c.lev) {

@@ -167,8 +167,8 @@ struct SolveVecs {
 // traversal, for a group of instances: level-from-leaf index d and colour b
 // of every instance share the launches.  xs[q]: instance q's vector in tree
 // order (bulk precision, N x nrhs).
-void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs, int nrhs, bool adjoint,
-                      bool use_inverse) {
+static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<void*>& xs, int nrhs, bool adjoint,
+                              bool use_inverse) {
   Ctx& lc = *cs[0];
   const int prec = lc.prec;
   const size_t es = esz(prec);
@@ -419,6 +419,100 @@ void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs,
       if (d > 0) merge(d - 1, false);
     }
   }
+}
+
+// With h2_opts.solve_graph the sweeps of a given (instances, vectors, nrhs,
+// direction) are run normally once with the graph's own staging buffers,
+// captured into a CUDA graph on the second call and replayed afterwards; any
+// device (re)allocation or refactorization of an instance retires the graph.
+void solve_tree_group(const std::vector<Ctx*>& cs, const std::vector<void*>& xs, int nrhs, bool adjoint,
+                      bool use_inverse) {
+  Ctx& lc = *cs[0];
+  if (!lc.opts.solve_graph) {
+    solve_tree_sweeps(cs, xs, nrhs, adjoint, use_inverse);
+    return;
+  }
+  SolveGraph* g = nullptr;
+  for (auto& u : lc.graphs)
+    if (u->cs == cs && u->xs == xs && u->nrhs == nrhs && u->adjoint == adjoint && u->inverse == use_inverse) {
+      g = u.get();
+      break;
+    }
+  auto state = [&](std::vector<uint64_t>& gens, std::vector<uint64_t>& epochs) {
+    gens.clear();
+    epochs.clear();
+    for (Ctx* c : cs) {
+      gens.push_back(c->gen);
+      epochs.push_back(c->epoch);
+    }
+  };
+  std::vector<uint64_t> gens, epochs;
+  state(gens, epochs);
+  if (g && g->exec && g->gens == gens && g->epochs == epochs) {
+    ProfScope ps(lc, "solve graph", 0.0);
+    ck(cudaGraphLaunch(g->exec, lc.stream), "graph launch");
+    lc.launches += g->nlaunch;
+    return;
+  }
+  if (!g || g->gens != gens || g->epochs != epochs) {
+    // first call (or stale): run normally with the graph's staging buffers
+    if (!g) {
+      if (lc.graphs.size() >= 8) lc.graphs.erase(lc.graphs.begin());
+      lc.graphs.push_back(std::make_unique<SolveGraph>());
+      g = lc.graphs.back().get();
+      g->cs = cs;
+      g->xs = xs;
+      g->nrhs = nrhs;
+      g->adjoint = adjoint;
+      g->inverse = use_inverse;
+    }
+    if (g->exec) {
+      cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+    }
+    lc.st.swap(g->st);
+    try {
+      lc.st.begin();
+      solve_tree_sweeps(cs, xs, nrhs, adjoint, use_inverse);
+    } catch (...) {
+      lc.st.swap(g->st);
+      throw;
+    }
+    lc.st.swap(g->st);
+    state(g->gens, g->epochs);
+    return;
+  }
+  // second call with unchanged buffers: capture, instantiate, launch
+  lc.st.swap(g->st);
+  lc.st.begin();
+  const int64_t l0 = lc.launches;
+  for (Ctx* c : cs) c->capturing = true;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(lc.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    try {
+      solve_tree_sweeps(cs, xs, nrhs, adjoint, use_inverse);
+    } catch (...) {
+      ok = false;
+    }
+    ok = (cudaStreamEndCapture(lc.stream, &graph) == cudaSuccess) && ok;
+  }
+  for (Ctx* c : cs) c->capturing = false;
+  lc.st.swap(g->st);
+  if (ok && graph) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    // capture refused something: run the sweeps normally this time
+    cudaGetLastError();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+    g->epochs.clear();
+    lc.launches = l0;
+    solve_tree_sweeps(cs, xs, nrhs, adjoint, use_inverse);
+    return;
+  }
+  g->nlaunch = lc.launches - l0;
+  ck(cudaGraphLaunch(g->exec, lc.stream), "graph launch");
 }
 
 void solve_tree(Ctx& c, void* xv, int nrhs, bool adjoint, bool use_inverse) {

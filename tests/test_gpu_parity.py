@@ -159,3 +159,30 @@ def test_singular_pivot_reports_status(dev):
 def gpu_ctx_rep(rep):
     from paper_1703_06155_gb300 import H2
     return H2.load(rep)
+
+
+def test_solve_graph_replay(dev):
+    # h2_opts.solve_graph: 1st solve runs normally, 2nd is captured, later ones
+    # replay the CUDA graph; all must equal the plain launches bit for bit, and
+    # a refactorization must retire the graph
+    eps = 1e-6
+    H = h2_problem(12, 64, eps)
+    A0 = gpu_ctx(H)
+    A1 = gpu_ctx(H, solve_graph=1)
+    s = torch.cuda.Stream()
+    b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 3, 17)).to(dev)
+    for prec in ("mixed", "fp64"):
+        A0.factorize(eps, prec)
+        A1.factorize(eps, prec)
+        with torch.cuda.stream(s):
+            ref = A0.solve(b, stream=s)
+            refa = A0.solve(b, adjoint=True, stream=s)
+            for _ in range(4):
+                x = A1.solve(b, stream=s)
+                xa = A1.solve(b, adjoint=True, stream=s)
+                assert torch.equal(x, ref) and torch.equal(xa, refa)
+            xr = A1.solve(b, refine=True, tol=1e-12, max_iter=20, stream=s)
+        s.synchronize()
+        Zd = h2_dense(12, 64, eps)
+        xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
+        assert rel(xr.cpu().numpy(), xe) < 1e-10
