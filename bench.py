@@ -193,6 +193,24 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------- multi-rank ----
+
+def max_over_ranks(ms, dist, device):
+    """Step time of the whole job: the slowest rank's (replicas run
+    independent instances; there is no data-path collective)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, n_per_rank, ms):
+    """Unknowns per second of all ranks together (weak scaling)."""
+    return world * n_per_rank / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU ---
 
 def run_batch(args):
@@ -322,11 +340,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     st = A.stats()
     solve_info = dict(A.last_solve)
     roof = roofline(st, cs.summary())
@@ -369,7 +383,7 @@ def run_ours(args):
         A.factorize(args.eps, args.prec)
         xh = A.solve(b_host, refine=True, tol=args.tol, max_iter=30)
     e_ms = (time.perf_counter() - e0) * 1e3 / max(1, args.steps // 2)
-    value = world * N / (ms / 1e3)
+    value = whole_job_value(world, N, ms)
     line = {
         "metric": "H2 factorize+solve unknowns/s (rel. residual 1e-6)", "value": value, "unit": "unknowns/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
