@@ -84,6 +84,14 @@ typedef struct {
                             solves (same vectors, nrhs, direction, factors)
                             are captured once into a CUDA graph and replayed;
                             0 (default): launched one by one              */
+  int split_target;      /* batched GEMM: split the K range of long products
+                            until a launch has about this many CTAs
+                            (0 = default, 4 per SM)                         */
+  int cluster_max;       /* Step 0: most CTAs in the thread-block cluster of
+                            one subspace / eigen problem (1..16; 0 = 16)    */
+  int tile_policy;       /* batched GEMM tile shape: 0 (default) least padded
+                            work per launch; 1 64 x 64 (64 x 16 when every
+                            output has <= 16 columns)                      */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -270,6 +278,15 @@ h2_status h2_solve_batch(h2_ctx* const* ctxs, int count, const void* const* b,
 h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
                       const void* g, int nrhs, double alpha, double* grad,
                       unsigned flags, void* stream);
+
+/*
+ * h2_set_opts - change the run-time tunables of a context (apply_path,
+ * solve_graph, split_target, cluster_max, tile_policy, profile) without
+ * rebuilding it; the other fields of *opts are ignored.  They take effect at
+ * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
+ * counterpart in the paper: used by the autotuner.
+ */
+h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* opts);
 
 /*
  * h2_export - copy the H^2 representation out in the h2_load layout (HOST

@@ -24,7 +24,8 @@ H2_FP64, H2_MIXED = 0, 1
 H2_ADJOINT, H2_REFINE, H2_USE_INVERSE, H2_HOST = 1, 2, 4, 8
 H2_GRAD_ACCUMULATE = 1
 SYMBOLS = ("h2_default_opts", "h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec",
-           "h2_matvec_noalloc", "h2_factorize_batch", "h2_solve_batch", "h2_grad_chi", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
+           "h2_matvec_noalloc", "h2_factorize_batch", "h2_solve_batch", "h2_grad_chi", "h2_set_opts",
+           "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
            "h2_status_string", "h2_destroy")
 
 
@@ -33,7 +34,8 @@ class h2_opts(ctypes.Structure):
                 ("ordering", ctypes.c_int), ("proxy_min", ctypes.c_int), ("proxy_radius", ctypes.c_double),
                 ("arena_cap_bytes", ctypes.c_size_t),
                 ("host_only", ctypes.c_int), ("profile", ctypes.c_int), ("apply_path", ctypes.c_int),
-                ("solve_graph", ctypes.c_int)]
+                ("solve_graph", ctypes.c_int), ("split_target", ctypes.c_int), ("cluster_max", ctypes.c_int),
+                ("tile_policy", ctypes.c_int)]
 
 
 class H2Error(RuntimeError):
@@ -67,6 +69,7 @@ def lib():
     L.h2_matvec_noalloc.argtypes = [P, P, P, I, ctypes.c_uint, P]
     L.h2_grad_chi.argtypes = [P, P, P, P, I, D, P, ctypes.c_uint, P]
     L.h2_factorize_batch.argtypes = [P, I, D, I]
+    L.h2_set_opts.argtypes = [P, ctypes.POINTER(h2_opts)]
     L.h2_solve_batch.argtypes = [P, I, P, P, I, ctypes.c_uint, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.h2_export_sizes.argtypes = [P] + [ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I)] + \
         [ctypes.POINTER(I64)] * 6
@@ -79,7 +82,8 @@ def lib():
     L.h2_destroy.argtypes = [P]
     L.h2_destroy.restype = None
     for name in ("h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec", "h2_matvec_noalloc",
-                 "h2_grad_chi", "h2_factorize_batch", "h2_solve_batch", "h2_export_sizes", "h2_export", "h2_stats"):
+                 "h2_grad_chi", "h2_factorize_batch", "h2_solve_batch", "h2_set_opts", "h2_export_sizes", "h2_export",
+                 "h2_stats"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -263,6 +267,12 @@ class H2:
         self._check(lib().h2_grad_chi(self._h, _ptr(xc), _ptr(mc), _ptr(gc), xc.shape[0], float(alpha), _ptr(out),
                                       H2_GRAD_ACCUMULATE if accumulate else 0, _stream(stream)), "h2_grad_chi")
         return out
+
+    def set_opts(self, **kw):
+        """h2_set_opts: change run-time tunables (apply_path, solve_graph,
+        split_target, cluster_max, tile_policy, profile) of this context."""
+        o = default_opts(**kw)
+        self._check(lib().h2_set_opts(self._h, ctypes.byref(o)), "h2_set_opts")
 
     def stats(self):
         buf = ctypes.create_string_buffer(1 << 20)

@@ -1,0 +1,64 @@
+"""Autotuner of the run-time tunables of a context (h2_set_opts).
+
+For one workload (a built context and its right-hand sides) it times the
+step a user repeats -- factorization plus refined solve -- with CUDA events
+for candidate settings of
+
+  tile_policy   batched-GEMM tile shape rule (least padded work / 64-wide),
+  split_target  CTAs a GEMM launch is split-K'ed up to,
+  cluster_max   CTAs per Step-0 subspace / eigen problem,
+  apply_path    Step-2 and panel applications (GEMM + copy / in place),
+
+one parameter at a time from the defaults (coordinate descent), keeps the
+fastest setting of each and leaves it set on the context.  Every timing runs
+in the library; this module only chooses among them.
+"""
+import torch
+
+DEFAULT_SPACE = {
+    "tile_policy": [0, 1],
+    "split_target": [0, 304, 1216],
+    "cluster_max": [16, 8],
+    "apply_path": [2, 1],
+}
+
+
+def _time_step(ctx, b, eps, precision, tol, stream, repeats):
+    ctx.factorize(eps, precision)  # warm-up (arenas sized)
+    ctx.solve(b, refine=True, tol=tol, max_iter=30, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(repeats):
+        ctx.factorize(eps, precision)
+        ctx.solve(b, refine=True, tol=tol, max_iter=30, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / repeats
+
+
+def autotune(ctx, b, eps, precision="mixed", tol=1e-6, space=None, repeats=2, stream=None, profile=0):
+    """Returns (best settings, list of (settings, ms per step)); the best
+    settings are left applied to `ctx`."""
+    space = dict(DEFAULT_SPACE if space is None else space)
+    stream = stream or torch.cuda.current_stream()
+    best = {k: v[0] for k, v in space.items()}
+    log = []
+
+    def run(cfg):
+        ctx.set_opts(profile=profile, **cfg)
+        ms = _time_step(ctx, b, eps, precision, tol, stream, repeats)
+        log.append((dict(cfg), ms))
+        return ms
+
+    best_ms = run(best)
+    for key, values in space.items():
+        for v in values:
+            if v == best[key]:
+                continue
+            cfg = dict(best, **{key: v})
+            ms = run(cfg)
+            if ms < best_ms:
+                best_ms, best = ms, cfg
+    ctx.set_opts(profile=profile, **best)
+    return best, log

@@ -242,6 +242,24 @@ void h2_default_opts(h2_opts* o) {
   o->profile = 0;
   o->apply_path = 0;
   o->solve_graph = 0;
+  o->split_target = 0;
+  o->cluster_max = 0;
+  o->tile_policy = 0;
+}
+
+h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
+  if (!ctx || !o || o->apply_path < 0 || o->apply_path > 2 || o->split_target < 0 || o->cluster_max < 0 ||
+      o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2)
+    return H2_EINVAL;
+  h2_opts& c = ctx->c.opts;
+  c.apply_path = o->apply_path;
+  c.solve_graph = o->solve_graph;
+  c.split_target = o->split_target;
+  c.cluster_max = o->cluster_max;
+  c.tile_policy = o->tile_policy;
+  c.profile = o->profile;
+  ctx->c.graphs.clear();
+  return H2_OK;
 }
 
 const char* h2_status_string(int s) {

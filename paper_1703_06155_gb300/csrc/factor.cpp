@@ -40,7 +40,7 @@ using namespace h2k;
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what) {
   if (b.empty()) return;
   HostScope hs(c, "run_gemm");
-  const int64_t ws = b.plan(4 * 152, pacc == P64);
+  const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 4 * 152, pacc == P64, c.opts.tile_policy);
   if (b.tl.empty()) return;
   void* wsp = nullptr;
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
@@ -486,7 +486,9 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       const int i0 = lc.st.add(pc);
       lc.st.upload(lc);
       ProfScope ps(lc, "pchol_wy", 0.0);
-      ck(pchol_wy(lc.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, lc.stream), "pivoted cholesky");
+      ck(pchol_wy(lc.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, lc.opts.cluster_max > 0 ? lc.opts.cluster_max : 16,
+                  lc.stream),
+         "pivoted cholesky");
       lc.launches++;
     }
     std::vector<std::vector<int>> rp(nj);
@@ -560,7 +562,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         // few problems share the launch, so that more SMs work on each)
         const int64_t per = jacobi_cluster_scratch(maxr);
         double* js = (double*)dev_ensure(lc, lc.jac_buf, (size_t)per * eig.size() * sizeof(double));
-        const int csize = eig.size() * 16 <= 152 ? 16 : 8;
+        const int cmax = lc.opts.cluster_max > 0 ? lc.opts.cluster_max : 16;
+        const int csize = std::min(cmax, eig.size() * 16 <= 152 ? 16 : 8);
         ck(jacobi_eig_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, csize, js, (int*)lc.statusbuf.p,
                               lc.stream),
            "jacobi (cluster)");

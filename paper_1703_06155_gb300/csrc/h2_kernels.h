@@ -189,7 +189,8 @@ cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
 cudaError_t lu_blocked(const LuTask* d_tasks, int ntasks, int maxm, int prec,
                        int* d_status, cudaStream_t s);
 cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
-cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, cudaStream_t s);
+// one thread-block cluster of up to cmax (<= 16) CTAs per task
+cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, int cmax, cudaStream_t s);
 // one CTA per task
 cudaError_t lu_panel(const PanelTask* d_tasks, int ntasks, int prec, int* d_status,
                      cudaStream_t s);

@@ -326,11 +326,11 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
 
 }  // namespace
 
-cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, cudaStream_t s) {
+cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, int cmax, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (maxp > PMAX) return cudaErrorInvalidValue;
   // CTAs per problem: spread few problems over the SMs, keep >= 16 rows each
-  int csize = std::max(1, std::min(16, std::min(152 / n, maxp / 16)));
+  int csize = std::max(1, std::min(std::min(16, cmax), std::min(152 / n, maxp / 16)));
   if (csize > 8) {
     cudaFuncSetAttribute(k_pchol_wy_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t q = {};

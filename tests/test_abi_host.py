@@ -148,3 +148,15 @@ def test_batch_calls_reject_bad_groups(libh2):
     one = (ctypes.c_void_p * 1)(None)
     assert libh2.h2_solve_batch(arr, 1, one, one, 1, 0, 1e-6, 1, None, None, None) == -1
     a.close()
+
+
+def test_set_opts_validates(libh2):
+    from paper_1703_06155_gb300 import H2, H2Error, default_opts
+    pts = inputs.grid_points(4, H)
+    a = H2.build(pts, K, H, 3.0, 1e-6, host_only=1)
+    a.set_opts(apply_path=1, split_target=300, cluster_max=8, tile_policy=1)
+    for bad in (dict(apply_path=3), dict(cluster_max=17), dict(tile_policy=2), dict(split_target=-1)):
+        with pytest.raises(H2Error):
+            a.set_opts(**bad)
+    assert libh2.h2_set_opts(None, ctypes.byref(default_opts())) == -1
+    a.close()

@@ -186,3 +186,20 @@ def test_solve_graph_replay(dev):
         Zd = h2_dense(12, 64, eps)
         xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
         assert rel(xr.cpu().numpy(), xe) < 1e-10
+
+
+def test_autotune_keeps_results(dev):
+    # the tuner only picks among equivalent execution settings: the solution
+    # stays the exact-block-LU one at eps = 0 for every setting it leaves
+    from paper_1703_06155_gb300.autotune import autotune
+    H = h2_problem(12, 64, 1e-6)
+    A = gpu_ctx(H)
+    b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 2, 3)).to(dev)
+    best, log = autotune(A, b, 0.0, "fp64", tol=1e-12, repeats=1,
+                         space={"tile_policy": [0, 1], "cluster_max": [16, 4], "apply_path": [2, 1]})
+    assert set(best) == {"tile_policy", "cluster_max", "apply_path"} and len(log) >= 4
+    A.factorize(0.0, "fp64")
+    Zd = h2_dense(12, 64, 1e-6)
+    x = A.solve(b).cpu().numpy()
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
+    assert rel(x, xe) < 1e-10
