@@ -226,7 +226,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.Q_off.push_back(tq);
     tq += (size_t)n[i] * n[i];
     F.inv_off.push_back(ti);
-    ti += 2 * (size_t)n[i] * n[i];
+    ti += 3 * (size_t)n[i] * n[i];  // L^{-1}P, U^{-1}, scratch of the inversion
     F.piv_off.push_back(tp);
     tp += n[i];
     F.Vp_off.push_back(tvp);
@@ -671,7 +671,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       const int n = F.n[i], m = F.m[i];
       if (m <= 0) continue;
       char* inv = P[q].inv + F.inv_off[i] * es;
-      lu.push_back(LuTask{NB(q, i, i), inv, inv + (size_t)n * n * es, P[q].piv + F.piv_off[i], n, m});
+      lu.push_back(LuTask{NB(q, i, i), inv, inv + (size_t)n * n * es, P[q].piv + F.piv_off[i], n, m,
+                          inv + 2 * (size_t)n * n * es});
       jobs[q].c->stats.flops_factor += 8.0 / 3.0 * m * (double)m * m + 8.0 / 3.0 * m * (double)m * m;
     }
   }

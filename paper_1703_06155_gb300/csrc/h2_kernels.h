@@ -90,6 +90,7 @@ struct LuTask {
   void* Uinv;     // m x m out: U^{-1}   (ld m)
   int* piv;       // m out: piv[r] = original row now at r
   int lda, m;
+  void* scratch;  // m x m work space of the inversion
 };
 
 // ---- Step 0 rank selection: r = #{lambda_j > eps^2 (snorm2 + trace(M))} ---
@@ -184,8 +185,9 @@ int64_t jacobi_cluster_scratch(int maxp);  // doubles per task
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
                                int csize, double* d_scratch, int* d_status,
                                cudaStream_t s);
-// Step 3 partial LU with pivoting + explicit L^{-1} P and U^{-1}; one CTA per
-// task, maxm = the largest m of the tasks (<= 4096)
+// Step 3 partial LU with pivoting (one CTA per task), then explicit L^{-1} P
+// and U^{-1} (two CTAs per task, in a second launch); maxm = the largest m of
+// the tasks (<= 4096)
 cudaError_t lu_blocked(const LuTask* d_tasks, int ntasks, int maxm, int prec,
                        int* d_status, cudaStream_t s);
 cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);

@@ -11,8 +11,9 @@
 //     memory), and the trailing block is updated by a CTA-wide tiled GEMM
 //     (64 x 64 output tiles, 32-deep K slices staged in shared memory, 4 x 4
 //     complex micro-tiles);
-//   * L^{-1} and U^{-1} are formed block row by block row with the same GEMM
-//     (X[I, :I] = -L[I,I]^{-1} L[I, :I] X[:I, :I]) and L^{-1} P is L^{-1} with
+//   * in a second launch (two CTAs per task, concurrently) L^{-1} and U^{-1}
+//     are formed block row by block row with the same GEMM
+//     (X[I, :I] = -L[I,I]^{-1} L[I, :I] X[:I, :I]); L^{-1} P is L^{-1} with
 //     its columns permuted.
 // A zero pivot sets status bit 1 and the CTA returns.
 #include <algorithm>
@@ -288,43 +289,60 @@ __global__ void __launch_bounds__(NT) k_lu_blk(const LuTask* __restrict__ tasks,
     }
   }
   for (int i = tid; i < m; i += NT) t.piv[i] = perm[i];
+}
 
-  // ------------------------------------------------ L^{-1} (in Uinv) ------
-  // X[I, 0:I0] = -L[I,I]^{-1} L[I, 0:I0] X[0:I0, 0:I0]; X[I, I] = L[I,I]^{-1}
-  E* X = (E*)t.Uinv;
-  for (int I0 = 0; I0 < m; I0 += NBMAX) {
-    const int ib = min(NBMAX, m - I0);
-    if (I0 > 0) cta_gemm<E, R>(X + I0, m, A + I0, ld, X, m, ib, I0, I0, (R)-1, true, gs);
-    for (int idx = tid; idx < ib * ib; idx += NT) {
-      const int r = idx % ib, c = idx / ib;
-      Ls[r + c * NBMAX] = A[(size_t)(I0 + r) + (size_t)(I0 + c) * ld];
-    }
-    __syncthreads();
-    diag_inverse<E, R>(Ls, ib, Ds, false);
-    __syncthreads();
-    if (I0 > 0) cta_gemm<E, R>(X + I0, m, Ds, NBMAX, X + I0, m, ib, I0, ib, (R)1, true, gs);
-    for (int idx = tid; idx < ib * (m - I0); idx += NT) {
-      const int r = idx % ib, c = I0 + idx / ib;
-      E v;
-      if (c < I0 + ib) {
-        v = Ds[r + (c - I0) * NBMAX];
-      } else {
-        v.re = 0;
-        v.im = 0;
+// L^{-1} P (even CTA of the task's pair) or U^{-1} (odd CTA) from the packed
+// LU of k_lu_blk; both run at once.
+template <class E>
+__global__ void __launch_bounds__(NT) k_lu_inv(const LuTask* __restrict__ tasks) {
+  using R = typename RealOf<E>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  GemmSmem<R>& gs = *reinterpret_cast<GemmSmem<R>*>(smraw);
+  E* Ls = reinterpret_cast<E*>(smraw + sizeof(GemmSmem<R>));  // NBMAX x NBMAX, ld NBMAX
+  E* Ds = Ls + NBMAX * NBMAX;                                  // NBMAX x NBMAX, ld NBMAX
+  const LuTask t = tasks[blockIdx.x >> 1];
+  const bool lower = (blockIdx.x & 1) == 0;
+  const int m = t.m, ld = t.lda;
+  const int tid = threadIdx.x;
+  const E* A = (const E*)t.A;
+  if (lower) {
+    // ------------------------------------------------ L^{-1} (in scratch) --
+    // X[I, 0:I0] = -L[I,I]^{-1} L[I, 0:I0] X[0:I0, 0:I0]; X[I, I] = L[I,I]^{-1}
+    E* X = (E*)t.scratch;
+    for (int I0 = 0; I0 < m; I0 += NBMAX) {
+      const int ib = min(NBMAX, m - I0);
+      if (I0 > 0) cta_gemm<E, R>(X + I0, m, A + I0, ld, X, m, ib, I0, I0, (R)-1, true, gs);
+      for (int idx = tid; idx < ib * ib; idx += NT) {
+        const int r = idx % ib, c = idx / ib;
+        Ls[r + c * NBMAX] = A[(size_t)(I0 + r) + (size_t)(I0 + c) * ld];
       }
-      X[(size_t)(I0 + r) + (size_t)c * m] = v;
+      __syncthreads();
+      diag_inverse<E, R>(Ls, ib, Ds, false);
+      __syncthreads();
+      if (I0 > 0) cta_gemm<E, R>(X + I0, m, Ds, NBMAX, X + I0, m, ib, I0, ib, (R)1, true, gs);
+      for (int idx = tid; idx < ib * (m - I0); idx += NT) {
+        const int r = idx % ib, c = I0 + idx / ib;
+        E v;
+        if (c < I0 + ib) {
+          v = Ds[r + (c - I0) * NBMAX];
+        } else {
+          v.re = 0;
+          v.im = 0;
+        }
+        X[(size_t)(I0 + r) + (size_t)c * m] = v;
+      }
+      __syncthreads();
+    }
+    // L^{-1} P: column r of L^{-1} is column piv[r] of the result
+    E* Lp = (E*)t.Linv;
+    for (int idx = tid; idx < m * m; idx += NT) {
+      const int i = idx % m, r = idx / m;
+      Lp[(size_t)i + (size_t)t.piv[r] * m] = X[idx];
     }
     __syncthreads();
+    return;
   }
-  // L^{-1} P: column r of L^{-1} is column perm[r] of the result
-  E* Lp = (E*)t.Linv;
-  for (int idx = tid; idx < m * m; idx += NT) {
-    const int i = idx % m, r = idx / m;
-    Lp[(size_t)i + (size_t)perm[r] * m] = X[idx];
-  }
-  __syncthreads();
-
-  // ------------------------------------------------------- U^{-1} --------
+  // ------------------------------------------------ U^{-1} (odd CTA) ------
   // Y[I, J0:m] = -U[I,I]^{-1} U[I, J0:m] Y[J0:m, J0:m]; Y[I, I] = U[I,I]^{-1}
   E* Y = (E*)t.Uinv;
   const int nblk = (m + NBMAX - 1) / NBMAX;
@@ -366,6 +384,12 @@ size_t lu_smem(int maxm, int nb) {
 }
 
 template <class E>
+size_t lu_inv_smem() {
+  using R = typename RealOf<E>::T;
+  return sizeof(GemmSmem<R>) + 2 * (size_t)NBMAX * NBMAX * sizeof(E) + 16;
+}
+
+template <class E>
 cudaError_t launch_lu(const LuTask* d, int n, int maxm, int* st, cudaStream_t s) {
   // panel width: as wide as the shared-memory budget allows (at most 32)
   constexpr size_t kPanelBytes = 104 * 1024;
@@ -375,6 +399,11 @@ cudaError_t launch_lu(const LuTask* d, int n, int maxm, int* st, cudaStream_t s)
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_lu_blk<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_lu_blk<E><<<n, NT, sm, s>>>(d, nb, maxm, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smi = lu_inv_smem<E>();
+  cudaFuncSetAttribute(k_lu_inv<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
+  k_lu_inv<E><<<2 * n, NT, smi, s>>>(d);
   return cudaGetLastError();
 }
 
