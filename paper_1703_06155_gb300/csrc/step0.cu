@@ -77,7 +77,7 @@ __device__ double bsum(double v, double* red) {
 // better candidate: larger value, ties -> lower row
 __device__ __forceinline__ bool better(double v, int i, double bv, int bi) { return v > bv || (v == bv && i < bi); }
 
-__global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict__ tasks, int lrow_smem) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -94,6 +94,10 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
   __shared__ int wi[NT / 32];
   cd* G = t.G;
   cd* L = t.L;  // p x p (ld p); becomes Y
+  // the own rows of L during the pivoted Cholesky: row-major in shared memory
+  // (ld = rmax) when they fit (lrow_smem), else in place in L
+  extern __shared__ __align__(16) unsigned char lsm[];
+  cd* Ls = reinterpret_cast<cd*>(lsm);
   // own rows: a contiguous block
   const int rb = (p + C - 1) / C;
   const int r0 = min(p, rank * rb), r1 = min(p, r0 + rb), nr = r1 - r0;
@@ -105,10 +109,13 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
     dl[i] = G[(r0 + i) + (size_t)(r0 + i) * p].re;
     used[i] = 0;
   }
+  // element (li, k) of the own rows
+  const size_t ls_r = lrow_smem ? (size_t)rmax : 1, ls_k = lrow_smem ? 1 : (size_t)p;
+  cd* Lo = lrow_smem ? Ls : L + r0;
   for (int idx = tid; idx < nr * rmax; idx += NT) {
-    const int i = r0 + idx % nr, k = idx / nr;
-    L[i + (size_t)k * p].re = 0;
-    L[i + (size_t)k * p].im = 0;
+    const int li = idx % nr, k = idx / nr;
+    Lo[li * ls_r + k * ls_k].re = 0;
+    Lo[li * ls_r + k * ls_k].im = 0;
   }
   __syncthreads();
   // threads per row for the left-looking k-sums
@@ -167,8 +174,15 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
     gather(j & 1, dv, pc, trs);
     if (!(trs > tau) || !(dv > 0.0)) break;
     const double sd = sqrt(dv);
-    // pivot row entries L[pc, 0:j] (written by its owner in earlier steps)
-    for (int k = tid; k < j; k += NT) prow[k] = L[pc + (size_t)k * p];
+    // pivot row entries L[pc, 0:j] (written by its owner in earlier steps;
+    // read from the owner's shared memory when the rows live there)
+    if (lrow_smem) {
+      const int owner = pc / rb, lpc = pc - owner * rb;
+      const cd* src = cl.map_shared_rank(Ls, owner) + (size_t)lpc * rmax;
+      for (int k = tid; k < j; k += NT) prow[k] = src[k];
+    } else {
+      for (int k = tid; k < j; k += NT) prow[k] = L[pc + (size_t)k * p];
+    }
     __syncthreads();
     // column j for the own rows not yet pivoted (the pivot row gives sd)
     const int rows_per_pass = NT / tpr;
@@ -179,7 +193,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
       double vr = 0, vi = 0;
       if (act)
         for (int k = sub; k < j; k += tpr) {
-          const cd a = L[i + (size_t)k * p], b = prow[k];  // a * conj(b)
+          const cd a = Lo[li * ls_r + k * ls_k], b = prow[k];  // a * conj(b)
           vr += a.re * b.re + a.im * b.im;
           vi += a.im * b.re - a.re * b.im;
         }
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
         cd z;
         z.re = (G[i + (size_t)pc * p].re - vr) / sd;
         z.im = (G[i + (size_t)pc * p].im - vi) / sd;
-        L[i + (size_t)j * p] = z;
+        Lo[li * ls_r + j * ls_k] = z;
         if (i == pc) {
           used[li] = 1;
         } else {
@@ -205,6 +219,14 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
     r = j + 1;
   }
 
+  if (lrow_smem) {
+    // own rows to the column-major L for the QR (columns 0:r)
+    for (int idx = tid; idx < nr * r; idx += NT) {
+      const int li = idx % nr, k = idx / nr;
+      L[(r0 + li) + (size_t)k * p] = Ls[li * (size_t)rmax + k];
+    }
+    cluster_barrier();
+  }
   // ---------------------------------------- Householder QR of L(:, 0:r)
   cd* T = t.T;  // r x r (ld r): tau_j on the diagonal while the QR runs
   auto reflector = [&](int j) {
@@ -349,10 +371,16 @@ cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, int cmax, cudaStream_t
       csize = 8;
     }
   }
+  // own rows of L in shared memory when they fit
+  const int rb = (maxp + csize - 1) / csize, rmax = maxp < PMAX ? maxp : PMAX;
+  const size_t lbytes = (size_t)rb * rmax * sizeof(cd);
+  const int lrow_smem = lbytes <= 180 * 1024 ? 1 : 0;
+  const size_t dyn = lrow_smem ? lbytes : 0;
+  if (dyn > 0) cudaFuncSetAttribute(k_pchol_wy_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n * csize, 1, 1);
   cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -361,7 +389,7 @@ cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, int cmax, cudaStream_t
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_pchol_wy_cl, d);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_pchol_wy_cl, d, lrow_smem);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
