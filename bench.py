@@ -134,10 +134,27 @@ def roofline(st, clocks):
     peak = pk["fp64"] if fp64 else pk["fp32"]
     achieved = v["flops"] / (v["ms"] * 1e-3) / 1e12
     return {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "launches": v["launches"],
+            "frac": achieved / peak, "traffic": measured_traffic(k), "launches": v["launches"],
             "avg_launch_ms": v["ms"] / v["launches"],
             "peak_source": "derived: 152 SM x %s FMA/clk x 2 flops x %.0f MHz (%s)" % (
                 "2 FP64" if fp64 else "128 FP32", pk["mhz"], "FP64 pipe" if fp64 else "FP32 pipe")}
+
+
+def measured_traffic(kernel_class):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken for this kernel class with the current GEMM
+    source (else None: the counters no longer describe the kernel)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, "paper_1703_06155_gb300", "csrc", "gemm.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if d.get("kernel_class") != kernel_class.split("@")[0] or d.get("gemm_cu_sha256") != sha:
+        return None
+    return d.get("dram_bytes_per_launch")
 
 
 # --------------------------------------------------------------- oracle ---
