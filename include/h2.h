@@ -92,6 +92,10 @@ typedef struct {
   int tile_policy;       /* batched GEMM tile shape: 0 (default) least padded
                             work per launch; 1 64 x 64 (64 x 16 when every
                             output has <= 16 columns)                      */
+  int tensor_cores;      /* 1 (default): complex64 64 x 64 GEMM tiles of the
+                            mixed bulk on the tensor cores (TF32 MMA with a
+                            hi / lo split of each operand, FP32 accuracy);
+                            0: FP32 FMA pipe                               */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -281,7 +285,8 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 
 /*
  * h2_set_opts - change the run-time tunables of a context (apply_path,
- * solve_graph, split_target, cluster_max, tile_policy, profile) without
+ * solve_graph, split_target, cluster_max, tile_policy, tensor_cores, profile)
+ * without
  * rebuilding it; the other fields of *opts are ignored.  They take effect at
  * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
  * counterpart in the paper: used by the autotuner.

@@ -245,6 +245,7 @@ void h2_default_opts(h2_opts* o) {
   o->split_target = 0;
   o->cluster_max = 0;
   o->tile_policy = 0;
+  o->tensor_cores = 1;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
@@ -257,6 +258,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   c.split_target = o->split_target;
   c.cluster_max = o->cluster_max;
   c.tile_policy = o->tile_policy;
+  c.tensor_cores = o->tensor_cores;
   c.profile = o->profile;
   ctx->c.graphs.clear();
   return H2_OK;

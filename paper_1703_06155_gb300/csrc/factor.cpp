@@ -48,7 +48,7 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   c.st.upload(c);
   ProfScope ps(c, std::string("gemm:") + what, b.alg_flops);
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
-          wsp, c.stream, b.shape, b.pina),
+          wsp, c.stream, b.shape, b.pina, c.opts.tensor_cores),
      what);
   c.launches++;
   if (ws > 0) {

@@ -160,6 +160,165 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
   }
 }
 
+// ---- complex64 tiles on the tensor cores (3xTF32) ----------------------
+//
+// The same 64 x 64 tile / task / pair / split-K scheme as k_gemm, with the
+// products on warp-level TF32 MMAs (m16n8k8, FP32 accumulation).  Each FP32
+// operand x is split into x_hi = tf32(x) and x_lo = tf32(x - x_hi), and
+// a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi (the a_lo b_lo term is below FP32
+// rounding), so the result keeps FP32 accuracy.  Complex products:
+// C_re += A_re B_re + (-A_im) B_im, C_im += A_re B_im + A_im B_re.
+// 8 warps in a 2 x 4 grid, each owning a 32 x 16 sub-tile (2 x 2 MMA tiles).
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// c += a b with the three-term split (small terms first)
+__device__ __forceinline__ void mma3(float* c, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
+                                     const uint32_t* bl) {
+  mma_tf32(c, al, bh);
+  mma_tf32(c, ah, bl);
+  mma_tf32(c, ah, bh);
+}
+
+__global__ void __launch_bounds__(NT) k_gemm_tc(const GemmTask* __restrict__ tasks,
+                                               const GemmPair* __restrict__ pairs,
+                                               const GemmTile* __restrict__ tiles, cf* __restrict__ ws) {
+  constexpr int BM = 64, BN = 64, LA = BM + 8, LB = BN + 8;  // padded rows: conflict-free fragments
+  __shared__ float As_r[BK][LA], As_i[BK][LA];
+  __shared__ float Bs_r[BK][LB], Bs_i[BK][LB];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask tk = tasks[tl.task];
+  const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, q = lane & 3;
+  float cr[2][2][4], ci[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cr[a][b][e] = ci[a][b][e] = 0.f;
+
+  const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
+  const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
+  int64_t koff = 0;
+  for (int pi = tk.p0; pi < tk.p0 + tk.np; ++pi) {
+    const GemmPair pr = pairs[pi];
+    const int64_t kb = koff;
+    koff += pr.K;
+    if (koff <= klo || kb >= khi) continue;
+    const int kbeg = (int)(klo > kb ? klo - kb : 0);
+    const int kend = (int)(khi - kb < pr.K ? khi - kb : pr.K);
+    const cf* A = (const cf*)pr.A;
+    const cf* B = (const cf*)pr.B;
+    const bool at = (pr.opA == OP_T || pr.opA == OP_H);
+    const bool bt = (pr.opB == OP_T || pr.opB == OP_H);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < (BM * BK) / NT; ++r) {
+        const int l = tid + r * NT;
+        int i, k;
+        if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
+        float re = 0, im = 0;
+        if (m0 + i < tk.M && k0 + k < kend) load_op<cf, float>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
+        As_r[k][i] = re;
+        As_i[k][i] = im;
+      }
+#pragma unroll
+      for (int r = 0; r < (BK * BN) / NT; ++r) {
+        const int l = tid + r * NT;
+        int k, j;
+        if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
+        float re = 0, im = 0;
+        if (n0 + j < tk.N && k0 + k < kend) load_op<cf, float>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
+        Bs_r[k][j] = re;
+        Bs_i[k][j] = im;
+      }
+      __syncthreads();
+      // B fragments (k x n = 8 x 8): b0 = B[q][g], b1 = B[q + 4][g]
+      uint32_t brh[2][2], brl[2][2], bih[2][2], bil[2][2];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int c = wn * 16 + nt * 8 + g;
+        split_tf32(Bs_r[q][c], brh[nt][0], brl[nt][0]);
+        split_tf32(Bs_r[q + 4][c], brh[nt][1], brl[nt][1]);
+        split_tf32(Bs_i[q][c], bih[nt][0], bil[nt][0]);
+        split_tf32(Bs_i[q + 4][c], bih[nt][1], bil[nt][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        // A fragments (m x k = 16 x 8): a0 = A[g][q], a1 = A[g + 8][q], a2 = A[g][q + 4], a3 = A[g + 8][q + 4]
+        const int rw = wm * 32 + mt * 16 + g;
+        uint32_t arh[4], arl[4], aih[4], ail[4], anh[4], anl[4];
+        split_tf32(As_r[q][rw], arh[0], arl[0]);
+        split_tf32(As_r[q][rw + 8], arh[1], arl[1]);
+        split_tf32(As_r[q + 4][rw], arh[2], arl[2]);
+        split_tf32(As_r[q + 4][rw + 8], arh[3], arl[3]);
+        split_tf32(As_i[q][rw], aih[0], ail[0]);
+        split_tf32(As_i[q][rw + 8], aih[1], ail[1]);
+        split_tf32(As_i[q + 4][rw], aih[2], ail[2]);
+        split_tf32(As_i[q + 4][rw + 8], aih[3], ail[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {  // -A_im: flip the sign bits
+          anh[e] = aih[e] ^ 0x80000000u;
+          anl[e] = ail[e] ^ 0x80000000u;
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          mma3(cr[mt][nt], arh, arl, brh[nt], brl[nt]);
+          mma3(cr[mt][nt], anh, anl, bih[nt], bil[nt]);
+          mma3(ci[mt][nt], arh, arl, bih[nt], bil[nt]);
+          mma3(ci[mt][nt], aih, ail, brh[nt], brl[nt]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // C fragment: c0 = (g, 2q), c1 = (g, 2q + 1), c2 = (g + 8, 2q), c3 = (g + 8, 2q + 1)
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = m0 + wm * 32 + mt * 16 + g + (e >> 1) * 8;
+        const int n = n0 + wn * 16 + nt * 8 + 2 * q + (e & 1);
+        if (m >= tk.M || n >= tk.N) continue;
+        if (tk.nk > 1) {
+          cf v;
+          v.re = cr[mt][nt][e];
+          v.im = ci[mt][nt][e];
+          ws[tk.ws_off + (int64_t)tl.kc * tk.M * tk.N + (int64_t)m + (int64_t)n * tk.M] = v;
+        } else {
+          cf* p = (cf*)tk.C + (size_t)m + (size_t)n * tk.ldc;
+          float re = (float)tk.alpha * cr[mt][nt][e], im = (float)tk.alpha * ci[mt][nt][e];
+          if (tk.beta != 0.0) {
+            const cf c = *p;
+            re = fmaf((float)tk.beta, c.re, re);
+            im = fmaf((float)tk.beta, c.im, im);
+          }
+          p->re = re;
+          p->im = im;
+        }
+      }
+}
+
 template <class R, class EO>
 __global__ void k_gemm_reduce(const GemmTask* __restrict__ tasks, const typename CxOf<R>::T* __restrict__ ws) {
   const GemmTask tk = tasks[blockIdx.y];
@@ -228,9 +387,13 @@ static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, c
 }
 
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles, int pin,
-                 int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina) {
+                 int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina, int tensor) {
   if (ntiles <= 0) return cudaSuccess;
   if (pina < 0) pina = pin;
+  if (tensor && shape == 0 && pina == P32 && pin == P32 && pacc == P32 && pout == P32) {
+    k_gemm_tc<<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
+    return cudaGetLastError();
+  }
   switch (shape) {
     case 0: return gemm_tile<64, 64>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
     case 1: return gemm_tile<64, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);

@@ -203,3 +203,23 @@ def test_autotune_keeps_results(dev):
     x = A.solve(b).cpu().numpy()
     xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
     assert rel(x, xe) < 1e-10
+
+
+def test_tensor_core_bulk_matches_fma_bulk(dev):
+    # the complex64 bulk on the tensor cores (3xTF32) and on the FP32 FMA pipe
+    # give FP32-close factorizations; both refine to the exact H^2 solution
+    eps = 1e-6
+    n = 16
+    H = h2_problem(n, 64, eps)
+    A1 = gpu_ctx(H, tensor_cores=1)
+    A0 = gpu_ctx(H, tensor_cores=0)
+    A1.factorize(eps, "mixed")
+    A0.factorize(eps, "mixed")
+    b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 2, 23)).to(dev)
+    x1, x0 = A1.solve(b).cpu().numpy(), A0.solve(b).cpu().numpy()
+    assert rel(x1, x0) < 1e-4
+    Zd = h2_dense(n, 64, eps)
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
+    assert rel(x1, xe) < 1e-4
+    xr = A1.solve(b, refine=True, tol=1e-12, max_iter=30).cpu().numpy()
+    assert rel(xr, xe) < 1e-10
