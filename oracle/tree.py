@@ -102,16 +102,29 @@ class Partition:
 
 
 def greedy_colouring(nbrs):
-    """Greedy colouring of the near-field graph: visit clusters in increasing
-    index and give each the smallest colour unused by its coloured neighbours.
-    Clusters of one colour are never near neighbours of each other."""
-    col = [-1] * len(nbrs)
-    for i in range(len(nbrs)):
-        used = {col[j] for j in nbrs[i] if j != i and col[j] >= 0}
+    """Colouring of the near-field graph by saturation degree (DSatur): repeatedly
+    take the uncoloured cluster with the most distinct colours among its
+    neighbours (ties: more neighbours, then the lowest index) and give it the
+    smallest colour unused by its neighbours.  Clusters of one colour are never
+    near neighbours of each other."""
+    n = len(nbrs)
+    adj = [set(j for j in nbrs[i] if j != i) for i in range(n)]
+    col = [-1] * n
+    sat = [set() for _ in range(n)]
+    for _ in range(n):
+        best, bi = None, -1
+        for i in range(n):
+            if col[i] >= 0:
+                continue
+            key = (len(sat[i]), len(adj[i]), -i)
+            if best is None or key > best:
+                best, bi = key, i
         c = 0
-        while c in used:
+        while c in sat[bi]:
             c += 1
-        col[i] = c
+        col[bi] = c
+        for j in adj[bi]:
+            sat[j].add(c)
     return col
 
 

@@ -166,7 +166,10 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   if (c.opts.ordering == H2_ORDER_NATURAL) {
     for (int i = 0; i < nc; ++i) F.batches.push_back({i});
   } else {
-    const std::vector<int> col = greedy_colours(F.nbrs);
+    // the colouring depends on the partition only: computed once per level
+    if ((int)c.colour_cache.size() <= l) c.colour_cache.resize(l + 1);
+    if ((int)c.colour_cache[l].size() != nc) c.colour_cache[l] = greedy_colours(F.nbrs);
+    const std::vector<int>& col = c.colour_cache[l];
     const int ncol = *std::max_element(col.begin(), col.end()) + 1;
     F.batches.assign(ncol, {});
     for (int i = 0; i < nc; ++i) F.batches[col[i]].push_back(i);

@@ -234,6 +234,7 @@ struct Ctx {
   // sum of ||S||_F^2 over the admissible blocks of each cluster's row and
   // column, per level (depends on the H^2 only; computed once)
   std::vector<std::vector<double>> snorm2_cache;
+  std::vector<std::vector<int>> colour_cache;  // near-field colouring per level
 };
 
 // A captured forward / backward (or adjoint) sweep of a group of instances:

@@ -120,16 +120,38 @@ std::vector<std::vector<int>> near_lists(const Partition& p, int l) {
 
 // Smallest colour not used by an already coloured near neighbour, visiting
 // clusters in increasing index; a colour class has no two near neighbours.
+// Colouring of the near-field graph by saturation degree: repeatedly colour
+// the uncoloured cluster with the most distinct neighbour colours (ties: more
+// neighbours, then the lowest index) with the smallest colour its neighbours
+// do not use.  Clusters of one colour are never near neighbours.
 std::vector<int> greedy_colours(const std::vector<std::vector<int>>& nbrs) {
-  std::vector<int> col(nbrs.size(), -1);
-  std::vector<char> used;
-  for (size_t i = 0; i < nbrs.size(); ++i) {
-    used.assign(nbrs.size() + 1, 0);
+  const int n = (int)nbrs.size();
+  std::vector<int> col(n, -1), deg(n, 0), nsat(n, 0);
+  std::vector<std::vector<char>> seen(n);  // seen[i][c]: colour c among i's neighbours
+  for (int i = 0; i < n; ++i)
     for (int j : nbrs[i])
-      if ((size_t)j != i && col[j] >= 0) used[col[j]] = 1;
+      if (j != i) ++deg[i];
+  std::vector<char> used;
+  for (int step = 0; step < n; ++step) {
+    int bi = -1;
+    for (int i = 0; i < n; ++i) {
+      if (col[i] >= 0) continue;
+      if (bi < 0 || nsat[i] > nsat[bi] || (nsat[i] == nsat[bi] && deg[i] > deg[bi])) bi = i;
+    }
+    used.assign(n + 1, 0);
+    for (int j : nbrs[bi])
+      if (j != bi && col[j] >= 0) used[col[j]] = 1;
     int c = 0;
     while (used[c]) ++c;
-    col[i] = c;
+    col[bi] = c;
+    for (int j : nbrs[bi]) {
+      if (j == bi || col[j] >= 0) continue;
+      if ((int)seen[j].size() <= c) seen[j].resize(c + 1, 0);
+      if (!seen[j][c]) {
+        seen[j][c] = 1;
+        ++nsat[j];
+      }
+    }
   }
   return col;
 }
