@@ -92,10 +92,11 @@ typedef struct {
   int tile_policy;       /* batched GEMM tile shape: 0 (default) least padded
                             work per launch; 1 64 x 64 (64 x 16 when every
                             output has <= 16 columns)                      */
-  int tensor_cores;      /* 1 (default): complex64 64 x 64 GEMM tiles of the
-                            mixed bulk on the tensor cores (TF32 MMA with a
-                            hi / lo split of each operand, FP32 accuracy);
-                            0: FP32 FMA pipe                               */
+  int tensor_cores;      /* complex64 64 x 64 GEMM tiles of the mixed bulk:
+                            2 (default): tcgen05 MMAs with the accumulator
+                            in tensor memory; 1: warp-level TF32 MMAs; both
+                            split each operand into TF32 hi + lo parts
+                            (FP32 accuracy); 0: FP32 FMA pipe             */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */

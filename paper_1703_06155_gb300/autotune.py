@@ -8,7 +8,8 @@ for candidate settings of
   split_target  CTAs a GEMM launch is split-K'ed up to,
   cluster_max   CTAs per Step-0 subspace / eigen problem,
   apply_path    Step-2 and panel applications (GEMM + copy / in place),
-  tensor_cores  complex64 tiles on the tensor cores (3xTF32) / FP32 FMAs,
+  tensor_cores  complex64 tiles on tcgen05 / warp-level tensor-core MMAs
+                (3xTF32) or on FP32 FMAs,
 
 one parameter at a time from the defaults (coordinate descent), keeps the
 fastest setting of each and leaves it set on the context.  Every timing runs
@@ -17,7 +18,7 @@ in the library; this module only chooses among them.
 import torch
 
 DEFAULT_SPACE = {
-    "tensor_cores": [1, 0],
+    "tensor_cores": [2, 1, 0],
     "tile_policy": [0, 1],
     "split_target": [0, 304, 1216],
     "cluster_max": [16, 8],

@@ -245,12 +245,13 @@ void h2_default_opts(h2_opts* o) {
   o->split_target = 0;
   o->cluster_max = 0;
   o->tile_policy = 0;
-  o->tensor_cores = 1;
+  o->tensor_cores = 2;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   if (!ctx || !o || o->apply_path < 0 || o->apply_path > 2 || o->split_target < 0 || o->cluster_max < 0 ||
-      o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2)
+      o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
+      o->tensor_cores < 0 || o->tensor_cores > 2)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -292,7 +293,7 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   h2_ctx* x = new h2_ctx();
   h2_default_opts(&x->c.opts);
   if (opts) x->c.opts = *opts;
-  if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0)) {
+  if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2) {
     delete x;
     g_err = "h2_build: bad options";
     return H2_EINVAL;
@@ -936,7 +937,9 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
     bool first = true;
     for (const auto& [tag, a] : c.prof) {
       o << (first ? "" : ",") << "\"" << tag << "\":{\"launches\":" << a.launches << ",\"ms\":" << a.ms
-        << ",\"flops\":" << a.flops << "}";
+        << ",\"flops\":" << a.flops;
+      if (a.pipe) o << ",\"pipe\":\"" << a.pipe << "\"";
+      o << "}";
       first = false;
     }
   }

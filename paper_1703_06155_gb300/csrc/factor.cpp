@@ -46,7 +46,10 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
   c.st.upload(c);
-  ProfScope ps(c, std::string("gemm:") + what, b.alg_flops);
+  const int pa = b.pina < 0 ? pin : b.pina;
+  const int tc = (b.shape == 0 && pa == P32 && pin == P32 && pacc == P32 && pout == P32) ? c.opts.tensor_cores : 0;
+  const char* pipe = pacc == P64 ? "fp64" : tc == 2 ? "tcgen05_tf32x3" : tc == 1 ? "mma_tf32x3" : "fp32";
+  ProfScope ps(c, std::string("gemm:") + what, b.alg_flops, pipe);
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
           wsp, c.stream, b.shape, b.pina, c.opts.tensor_cores),
      what);
@@ -75,7 +78,7 @@ void run_apply(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
     for (int t0 = 0; t0 < b.t[i].w; t0 += tw) tiles.push_back(ApplyTile{(int)i, t0});
   const int i0 = c.st.add(b.t), i1 = c.st.add(tiles);
   c.st.upload(c);
-  ProfScope ps(c, std::string(left ? "apply_left:" : "apply_right:") + what, b.flops);
+  ProfScope ps(c, std::string(left ? "apply_left:" : "apply_right:") + what, b.flops, prec == P64 ? "fp64" : "fp32");
   if (left)
     ck(apply_left(c.st.ptr<ApplyTask>(i0), c.st.ptr<ApplyTile>(i1), (int)tiles.size(), prec, b.maxp, tw, c.stream),
        what);
@@ -911,7 +914,7 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
       const int i0 = lc.st.add(pt), i1 = lc.st.add(sw);
       lc.st.upload(lc);
       {
-        ProfScope ps(lc, "root_panel", fl);
+        ProfScope ps(lc, "root_panel", fl, prec == P64 ? "fp64" : "fp32");
         ck(lu_panel(lc.st.ptr<PanelTask>(i0), (int)pt.size(), prec, (int*)lc.statusbuf.p, lc.stream), "root panel");
       }
       ck(swap_rows_batch(lc.st.ptr<SwapTask>(i1), (int)sw.size(), prec, lc.stream), "root swaps");
@@ -966,6 +969,8 @@ void check_status(Ctx& c) {
   prof_resolve(c);
   if (st & 1) fail(H2_ESINGULAR, "zero pivot in a partial LU or in the final LU");
   if (st & 2) fail(H2_EINTERNAL, "Jacobi eigen-decomposition did not converge");
+  if (c.opts.tensor_cores == 2 && h2k::gemm_umma_timeouts() != 0)
+    fail(H2_EINTERNAL, "a tensor-core GEMM tile gave up waiting for its MMAs");
 }
 
 }  // namespace

@@ -144,18 +144,25 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
   for (int i = 0; i < TMR; ++i) {
     const int m = m0 + ty + 16 * i;
     if (m >= tk.M) continue;
+    // a row's C values in flight together, then the updates
+    EO old[TN];
+    if (tk.beta != 0.0) {
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n < tk.N) old[j] = C[(size_t)m + (size_t)n * tk.ldc];
+      }
+    }
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= tk.N) continue;
-      EO* p = C + (size_t)m + (size_t)n * tk.ldc;
       R re = al * acc_r[i][j], im = al * acc_i[i][j];
       if (tk.beta != 0.0) {
-        const EO c = *p;
-        re = fma(be, (R)c.re, re);
-        im = fma(be, (R)c.im, im);
+        re = fma(be, (R)old[j].re, re);
+        im = fma(be, (R)old[j].im, im);
       }
-      store_val<EO, R>(p, re, im);
+      store_val<EO, R>(C + (size_t)m + (size_t)n * tk.ldc, re, im);
     }
   }
 }
@@ -291,8 +298,20 @@ __global__ void __launch_bounds__(NT) k_gemm_tc(const GemmTask* __restrict__ tas
     }
   }
   // C fragment: c0 = (g, 2q), c1 = (g, 2q + 1), c2 = (g + 8, 2q), c3 = (g + 8, 2q + 1)
+  const bool useold = tk.nk <= 1 && tk.beta != 0.0;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int mt = 0; mt < 2; ++mt) {
+    cf old[2][4];  // this row block's C values in flight together
+    if (useold) {
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int m = m0 + wm * 32 + mt * 16 + g + (e >> 1) * 8;
+          const int n = n0 + wn * 16 + nt * 8 + 2 * q + (e & 1);
+          if (m < tk.M && n < tk.N) old[nt][e] = ((const cf*)tk.C)[(size_t)m + (size_t)n * tk.ldc];
+        }
+    }
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -306,17 +325,347 @@ __global__ void __launch_bounds__(NT) k_gemm_tc(const GemmTask* __restrict__ tas
           v.im = ci[mt][nt][e];
           ws[tk.ws_off + (int64_t)tl.kc * tk.M * tk.N + (int64_t)m + (int64_t)n * tk.M] = v;
         } else {
-          cf* p = (cf*)tk.C + (size_t)m + (size_t)n * tk.ldc;
           float re = (float)tk.alpha * cr[mt][nt][e], im = (float)tk.alpha * ci[mt][nt][e];
-          if (tk.beta != 0.0) {
-            const cf c = *p;
-            re = fmaf((float)tk.beta, c.re, re);
-            im = fmaf((float)tk.beta, c.im, im);
+          if (useold) {
+            re = fmaf((float)tk.beta, old[nt][e].re, re);
+            im = fmaf((float)tk.beta, old[nt][e].im, im);
           }
-          p->re = re;
-          p->im = im;
+          cf v;
+          v.re = re;
+          v.im = im;
+          ((cf*)tk.C)[(size_t)m + (size_t)n * tk.ldc] = v;
         }
       }
+  }
+}
+
+// ---- complex64 tiles on the 5th-generation tensor cores (tcgen05, 3xTF32) --
+//
+// The same 64 x 64 tile / task / pair / split-K scheme again, with the
+// products issued asynchronously to the tensor cores and accumulated in tensor
+// memory (TMEM).  The complex tile is one real 128 x 64 product
+//   D = A' B'^T,  A' row m      = [Re A(m,k), -Im A(m,k)]_k
+//                 A' row 64 + m = [Im A(m,k),  Re A(m,k)]_k
+//                 B' row n      = [Re B(k,n),  Im B(k,n)]_k
+// so that TMEM lanes 0..63 end up holding Re C and lanes 64..127 Im C.  Every
+// operand is staged as hi = tf32(x) and lo = tf32(x - hi) planes and
+// D += A'lo B'hi + A'hi B'lo + A'hi B'hi (the lo*lo term is below FP32
+// rounding).  Shared-memory operands use the K-major, no-swizzle canonical
+// layout: core matrices of 8 rows x 16 bytes, 8-row groups 128 B apart (SBO),
+// K-adjacent core matrices LBO apart; LBO is padded by 16 B so that the
+// 16-byte staging stores of a warp spread over all banks.
+//
+// All 256 threads stage one chunk of BKC complex K into one of S stages
+// (global loads -> hi/lo split -> shared stores, the next chunk's loads issued
+// before the barrier); thread 0 then issues the chunk's MMAs and commits them
+// to the stage's mbarrier, which the stagers wait on before they refill it.
+// Every wait is bounded: a wait that runs out marks the tile (NaN output) and
+// counts in g_umma_timeouts, and the CTA still frees its TMEM.
+
+__device__ unsigned int g_umma_timeouts = 0;
+
+namespace umma {
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: start, LBO, SBO = 128 B, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t a, uint32_t lbo) {
+  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) | ((uint64_t)(128 >> 4) << 32) |
+         (1ull << 46);
+}
+// instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 K-major, M = 128, N = 64
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return r != 0;
+}
+// wait for the given phase of `bar`; gives up after ~2 s (or, unless
+// draining, at once when another thread of the CTA already gave up) and
+// reports it in *fail
+__device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity, volatile int* fail, bool drain = false) {
+  const long long t0 = clock64();
+  while (!try_wait(bar, parity)) {
+    if (!drain && *fail) return false;
+    if (clock64() - t0 > 4000000000ll) {
+      *fail = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ float tf(float x) { return __uint_as_float(to_tf32(x)); }
+
+template <int BKC, int S>
+struct Cfg {
+  static constexpr int KC = BKC / 2;  // 16-byte K groups (2 complex) per operand row
+  static constexpr int LBO_A = 16 * 128 + 16, LBO_B = 8 * 128 + 16;
+  static constexpr int PLANE_A = KC * LBO_A, PLANE_B = KC * LBO_B;
+  static constexpr int STAGE = 2 * PLANE_A + 2 * PLANE_B;  // A hi, A lo, B hi, B lo
+  static constexpr int DLD = 65;                           // epilogue staging row stride (floats)
+  static constexpr int BODY = S * STAGE > 128 * DLD * 4 ? S * STAGE : 128 * DLD * 4;
+  static constexpr int SMEM = BODY + 1024;                 // + alignment slack
+  static constexpr int NI = 64 * KC / NT;                  // A (and B) items per thread and chunk
+  static_assert(BKC % 4 == 0 && NI >= 1 && 64 * KC % NT == 0, "chunk shape");
+};
+
+// position in the concatenated K range of a tile's pairs
+struct Cursor {
+  int pi, k0, kend;
+  int64_t koff;
+};
+}  // namespace umma
+
+template <int BKC, int S>
+__global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict__ tasks,
+                                                 const GemmPair* __restrict__ pairs,
+                                                 const GemmTile* __restrict__ tiles, cf* __restrict__ ws) {
+  using C_ = umma::Cfg<BKC, S>;
+  constexpr int KC = C_::KC, NI = C_::NI;
+  extern __shared__ unsigned char smraw[];
+  __shared__ uint64_t bars[S];
+  __shared__ uint32_t tslot;
+  __shared__ int fail;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask tk = tasks[tl.task];
+  const int m0 = tl.tm * 64, n0 = tl.tn * 64;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
+  const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
+
+  // next chunk of BKC complex K (within one pair); false at the end
+  auto advance = [&](umma::Cursor& c) -> bool {
+    c.k0 += BKC;
+    while (c.k0 >= c.kend) {
+      if (++c.pi >= tk.p0 + tk.np) return false;
+      const int K = pairs[c.pi].K;
+      const int64_t kb = c.koff;
+      c.koff += K;
+      if (c.koff <= klo || kb >= khi) {
+        c.k0 = c.kend = 0;
+        continue;
+      }
+      c.k0 = (int)(klo > kb ? klo - kb : 0);
+      c.kend = (int)(khi - kb < K ? khi - kb : K);
+    }
+    return true;
+  };
+  // this thread's share of a chunk: NI A items and NI B items of 2 complex each
+  float4 ra[NI], rb[NI];
+  auto load = [&](float4 (&xa)[NI], float4 (&xb)[NI], const umma::Cursor& c) {
+    const GemmPair pr = pairs[c.pi];
+    const cf* A = (const cf*)pr.A;
+    const cf* B = (const cf*)pr.B;
+    const bool at = (pr.opA == OP_T || pr.opA == OP_H), bt = (pr.opB == OP_T || pr.opB == OP_H);
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int it = tid + r * NT;
+      const int m = at ? it / KC : (it & 63), kp = at ? it % KC : (it >> 6);
+      const int k = c.k0 + 2 * kp;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m0 + m < tk.M) {
+        if (k < c.kend) load_op<cf, float>(A, pr.lda, pr.opA, m0 + m, k, v.x, v.y);
+        if (k + 1 < c.kend) load_op<cf, float>(A, pr.lda, pr.opA, m0 + m, k + 1, v.z, v.w);
+      }
+      xa[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int it = tid + r * NT;
+      const int n = bt ? (it & 63) : it / KC, kp = bt ? (it >> 6) : it % KC;
+      const int k = c.k0 + 2 * kp;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (n0 + n < tk.N) {
+        if (k < c.kend) load_op<cf, float>(B, pr.ldb, pr.opB, k, n0 + n, v.x, v.y);
+        if (k + 1 < c.kend) load_op<cf, float>(B, pr.ldb, pr.opB, k + 1, n0 + n, v.z, v.w);
+      }
+      xb[r] = v;
+    }
+  };
+  // split the staged registers into the hi / lo planes of stage st
+  auto store = [&](unsigned char* st, const float4 (&xa)[NI], const float4 (&xb)[NI], const umma::Cursor& c) {
+    const GemmPair& pr = pairs[c.pi];
+    const bool at = (pr.opA == OP_T || pr.opA == OP_H), bt = (pr.opB == OP_T || pr.opB == OP_H);
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int it = tid + r * NT;
+      const int m = at ? it / KC : (it & 63), kp = at ? it % KC : (it >> 6);
+      const float4 v = xa[r];
+      const float4 h = make_float4(umma::tf(v.x), umma::tf(v.y), umma::tf(v.z), umma::tf(v.w));
+      const float4 l = make_float4(umma::tf(v.x - h.x), umma::tf(v.y - h.y), umma::tf(v.z - h.z), umma::tf(v.w - h.w));
+      const int o0 = kp * C_::LBO_A + (m >> 3) * 128 + (m & 7) * 16;
+      const int o1 = o0 + 8 * 128;  // row 64 + m
+      *(float4*)(st + o0) = make_float4(h.x, -h.y, h.z, -h.w);
+      *(float4*)(st + o1) = make_float4(h.y, h.x, h.w, h.z);
+      *(float4*)(st + C_::PLANE_A + o0) = make_float4(l.x, -l.y, l.z, -l.w);
+      *(float4*)(st + C_::PLANE_A + o1) = make_float4(l.y, l.x, l.w, l.z);
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) {
+      const int it = tid + r * NT;
+      const int n = bt ? (it & 63) : it / KC, kp = bt ? (it >> 6) : it % KC;
+      const float4 v = xb[r];
+      const float4 h = make_float4(umma::tf(v.x), umma::tf(v.y), umma::tf(v.z), umma::tf(v.w));
+      const float4 l = make_float4(umma::tf(v.x - h.x), umma::tf(v.y - h.y), umma::tf(v.z - h.z), umma::tf(v.w - h.w));
+      const int o = 2 * C_::PLANE_A + kp * C_::LBO_B + (n >> 3) * 128 + (n & 7) * 16;
+      *(float4*)(st + o) = h;
+      *(float4*)(st + C_::PLANE_B + o) = l;
+    }
+  };
+  // store alpha * (re, im) (+ beta C) or the unscaled split-K partial
+  auto emit = [&](int m, int n, float re, float im) {
+    if (tk.nk > 1) {
+      cf v;
+      v.re = re;
+      v.im = im;
+      ws[tk.ws_off + (int64_t)tl.kc * tk.M * tk.N + (int64_t)m + (int64_t)n * tk.M] = v;
+    } else {
+      cf* p = (cf*)tk.C + (size_t)m + (size_t)n * tk.ldc;
+      re *= (float)tk.alpha;
+      im *= (float)tk.alpha;
+      if (tk.beta != 0.0) {
+        const cf cv = *p;
+        re = fmaf((float)tk.beta, cv.re, re);
+        im = fmaf((float)tk.beta, cv.im, im);
+      }
+      p->re = re;
+      p->im = im;
+    }
+  };
+
+  umma::Cursor cur{tk.p0 - 1, 0, 0, 0};
+  if (!advance(cur)) {  // no K overlaps this tile: C = beta C (zero partial)
+    for (int e = tid; e < 64 * 64; e += NT) {
+      const int m = m0 + (e & 63), n = n0 + (e >> 6);
+      if (m < tk.M && n < tk.N) emit(m, n, 0.f, 0.f);
+    }
+    return;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::saddr(&tslot)),
+                 "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::saddr(&bars[s])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail = 0;
+  }
+  load(ra, rb, cur);
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t sbase = umma::saddr(sm);
+
+  int c = 0;
+  for (;;) {
+    const int s = c % S;
+    if (c >= S) umma::wait(umma::saddr(&bars[s]), (uint32_t)((c / S - 1) & 1), &fail);
+    store(sm + s * C_::STAGE, ra, rb, cur);
+    const bool more = advance(cur);
+    if (more) load(ra, rb, cur);  // next chunk's loads in flight across the barrier and the MMAs
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      umma::fence_after();
+      const uint32_t a = sbase + s * C_::STAGE, bb = a + 2 * C_::PLANE_A;
+#pragma unroll
+      for (int ks = 0; ks < BKC / 4; ++ks) {
+        const uint64_t ah = umma::sdesc(a + 2 * ks * C_::LBO_A, C_::LBO_A);
+        const uint64_t al = umma::sdesc(a + C_::PLANE_A + 2 * ks * C_::LBO_A, C_::LBO_A);
+        const uint64_t bh = umma::sdesc(bb + 2 * ks * C_::LBO_B, C_::LBO_B);
+        const uint64_t bl = umma::sdesc(bb + C_::PLANE_B + 2 * ks * C_::LBO_B, C_::LBO_B);
+        umma::mma(tmem, al, bh, (c > 0 || ks > 0) ? 1u : 0u);
+        umma::mma(tmem, ah, bl, 1u);
+        umma::mma(tmem, ah, bh, 1u);
+      }
+      umma::commit(umma::saddr(&bars[s]));
+    }
+    ++c;
+    if (!more) break;
+  }
+  // drain: the last commit of every stage (the last of all covers every MMA
+  // of the tile; waiting for each leaves no arrive in flight at exit)
+  for (int s = 0; s < S && s < c; ++s) {
+    const int ncommit = (c - 1 - s) / S + 1;
+    umma::wait(umma::saddr(&bars[s]), (uint32_t)((ncommit - 1) & 1), &fail, true);
+  }
+  umma::fence_after();
+  __syncthreads();
+  // C values of the beta term: all loads in flight together (rather than one
+  // load-store round trip per element), overlapping the TMEM read-out
+  constexpr int EPT = 64 * 64 / NT;
+  const bool useold = tk.nk <= 1 && tk.beta != 0.0;
+  cf cold[EPT];
+  if (useold) {
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * NT, m = m0 + (e & 63), n = n0 + (e >> 6);
+      if (m < tk.M && n < tk.N) cold[i] = ((const cf*)tk.C)[(size_t)m + (size_t)n * tk.ldc];
+    }
+  }
+  const bool ok = fail == 0;
+  float* Ds = (float*)sm;  // 128 x 64 accumulator, row stride DLD
+  if (ok) {
+    const int row = 32 * (warp & 3) + lane, cb = 32 * (warp >> 2);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      uint32_t v[8];
+      const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cb + 8 * h);
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                   : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Ds[row * C_::DLD + cb + 8 * h + j] = __uint_as_float(v[j]);
+    }
+  } else if (tid == 0) {
+    atomicAdd(&g_umma_timeouts, 1u);
+  }
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+  const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int e = tid + i * NT, mi = e & 63, nj = e >> 6;
+    const int m = m0 + mi, n = n0 + nj;
+    if (m >= tk.M || n >= tk.N) continue;
+    float re = ok ? Ds[mi * C_::DLD + nj] : nan, im = ok ? Ds[(64 + mi) * C_::DLD + nj] : nan;
+    if (tk.nk > 1) {
+      cf v;
+      v.re = re;
+      v.im = im;
+      ws[tk.ws_off + (int64_t)tl.kc * tk.M * tk.N + (int64_t)m + (int64_t)n * tk.M] = v;
+    } else {
+      re *= (float)tk.alpha;
+      im *= (float)tk.alpha;
+      if (useold) {
+        re = fmaf((float)tk.beta, cold[i].re, re);
+        im = fmaf((float)tk.beta, cold[i].im, im);
+      }
+      cf v;
+      v.re = re;
+      v.im = im;
+      ((cf*)tk.C)[(size_t)m + (size_t)n * tk.ldc] = v;
+    }
+  }
 }
 
 template <class R, class EO>
@@ -386,11 +735,39 @@ static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, c
   return cudaGetLastError();
 }
 
+#ifndef UMMA_BKC
+#define UMMA_BKC 8
+#endif
+#ifndef UMMA_S
+#define UMMA_S 2
+#endif
+
+template <int BKC, int S>
+static cudaError_t gemm_umma(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
+                             cf* ws, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_gemm_umma<BKC, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               umma::Cfg<BKC, S>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gemm_umma<BKC, S><<<ntiles, NT, umma::Cfg<BKC, S>::SMEM, s>>>(d_tasks, d_pairs, d_tiles, ws);
+  return cudaGetLastError();
+}
+
+unsigned int gemm_umma_timeouts() {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_umma_timeouts, sizeof(v)) != cudaSuccess) return ~0u;
+  return v;
+}
+
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles, int pin,
                  int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina, int tensor) {
   if (ntiles <= 0) return cudaSuccess;
   if (pina < 0) pina = pin;
   if (tensor && shape == 0 && pina == P32 && pin == P32 && pacc == P32 && pout == P32) {
+    if (tensor == 2) return gemm_umma<UMMA_BKC, UMMA_S>(d_tasks, d_pairs, d_tiles, ntiles, (cf*)ws, s);
     k_gemm_tc<<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
     return cudaGetLastError();
   }

@@ -192,10 +192,12 @@ struct ProfRec {
   std::string tag;
   cudaEvent_t a, b;
   double flops;
+  const char* pipe;  // arithmetic unit of the products (GEMMs), else null
 };
 struct ProfAgg {
   int64_t launches = 0;
   double ms = 0, flops = 0;
+  const char* pipe = nullptr;
 };
 
 struct Ctx {
@@ -266,7 +268,7 @@ struct ProfScope {
   Ctx& c;
   bool on;
   size_t idx = 0;
-  ProfScope(Ctx& c_, const std::string& tag, double flops);
+  ProfScope(Ctx& c_, const std::string& tag, double flops, const char* pipe = nullptr);
   ~ProfScope();
 };
 void prof_resolve(Ctx& c);  // after a stream synchronize: fold events into c.prof

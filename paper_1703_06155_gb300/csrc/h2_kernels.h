@@ -156,7 +156,8 @@ struct KGramTile { int task, tm, tn; };
 // (gemm_tile_m / gemm_tile_n).  pina >= 0: precision of the A operands when
 // it differs from B's (pin); supported: A complex128 with B complex64, FP64
 // accumulation into complex128 or FP32 accumulation into complex64.
-// tensor = 1: complex64 64 x 64 products on the tensor cores (3xTF32)
+// tensor = 1: complex64 64 x 64 products on warp-level TF32 MMAs (3xTF32);
+// tensor = 2: the same on tcgen05 MMAs with TMEM accumulators (3xTF32)
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
                  int pacc, void* ws, cudaStream_t s, int shape = 0,
@@ -167,6 +168,9 @@ cudaError_t gemm_reduce(const GemmTask* d_tasks, int ntasks, int maxmn,
 cudaError_t gemm_mirror(const GemmTask* d_tasks, int ntasks, int maxmn,
                         int pout, int bm, cudaStream_t s);
 int gemm_tile_m(int shape);
+// tiles of the tcgen05 path that gave up waiting for their MMAs (NaN output);
+// ~0u when the counter cannot be read
+unsigned int gemm_umma_timeouts();
 int gemm_tile_n(int shape);
 
 cudaError_t apply_left(const ApplyTask* d_tasks, const ApplyTile* d_tiles,

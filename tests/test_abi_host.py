@@ -155,7 +155,8 @@ def test_set_opts_validates(libh2):
     pts = inputs.grid_points(4, H)
     a = H2.build(pts, K, H, 3.0, 1e-6, host_only=1)
     a.set_opts(apply_path=1, split_target=300, cluster_max=8, tile_policy=1)
-    for bad in (dict(apply_path=3), dict(cluster_max=17), dict(tile_policy=2), dict(split_target=-1)):
+    for bad in (dict(apply_path=3), dict(cluster_max=17), dict(tile_policy=2), dict(split_target=-1),
+                dict(tensor_cores=3), dict(tensor_cores=-1)):
         with pytest.raises(H2Error):
             a.set_opts(**bad)
     assert libh2.h2_set_opts(None, ctypes.byref(default_opts())) == -1

@@ -207,13 +207,15 @@ def test_autotune_keeps_results(dev):
     assert rel(x, xe) < 1e-10
 
 
-def test_tensor_core_bulk_matches_fma_bulk(dev):
-    # the complex64 bulk on the tensor cores (3xTF32) and on the FP32 FMA pipe
+@pytest.mark.parametrize("tc", [1, 2])
+def test_tensor_core_bulk_matches_fma_bulk(dev, tc):
+    # the complex64 bulk on the tensor cores (3xTF32: warp-level MMAs, or
+    # tcgen05 MMAs accumulating in tensor memory) and on the FP32 FMA pipe
     # give FP32-close factorizations; both refine to the exact H^2 solution
     eps = 1e-6
     n = 16
     H = h2_problem(n, 64, eps)
-    A1 = gpu_ctx(H, tensor_cores=1)
+    A1 = gpu_ctx(H, tensor_cores=tc)
     A0 = gpu_ctx(H, tensor_cores=0)
     A1.factorize(eps, "mixed")
     A0.factorize(eps, "mixed")
