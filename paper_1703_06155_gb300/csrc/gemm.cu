@@ -423,10 +423,14 @@ struct Cfg {
   static_assert(BKC % 4 == 0 && NI >= 1 && 64 * KC % NT == 0, "chunk shape");
 };
 
-// position in the concatenated K range of a tile's pairs
+// position in the concatenated K range of a tile's pairs, with the current
+// pair's operands (read once, when the cursor enters the pair)
 struct Cursor {
   int pi, k0, kend;
   int64_t koff;
+  const cf* A;
+  const cf* B;
+  int lda, ldb, opA, opB;
 };
 }  // namespace umma
 
@@ -453,59 +457,71 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
     c.k0 += BKC;
     while (c.k0 >= c.kend) {
       if (++c.pi >= tk.p0 + tk.np) return false;
-      const int K = pairs[c.pi].K;
+      const GemmPair pr = pairs[c.pi];
       const int64_t kb = c.koff;
-      c.koff += K;
+      c.koff += pr.K;
       if (c.koff <= klo || kb >= khi) {
         c.k0 = c.kend = 0;
         continue;
       }
       c.k0 = (int)(klo > kb ? klo - kb : 0);
-      c.kend = (int)(khi - kb < K ? khi - kb : K);
+      c.kend = (int)(khi - kb < pr.K ? khi - kb : pr.K);
+      c.A = (const cf*)pr.A;
+      c.B = (const cf*)pr.B;
+      c.lda = pr.lda;
+      c.ldb = pr.ldb;
+      c.opA = pr.opA;
+      c.opB = pr.opB;
     }
     return true;
   };
-  // this thread's share of a chunk: NI A items and NI B items of 2 complex each
+  // this thread's share of a chunk: NI A items and NI B items of 2 complex
+  // each, as loaded (no operation on the values, so the loads stay in flight
+  // until the chunk is staged); out-of-range elements are read from a clamped
+  // in-range address and zeroed at staging (validity bits am / bm)
   float4 ra[NI], rb[NI];
-  auto load = [&](float4 (&xa)[NI], float4 (&xb)[NI], const umma::Cursor& c) {
-    const GemmPair pr = pairs[c.pi];
-    const cf* A = (const cf*)pr.A;
-    const cf* B = (const cf*)pr.B;
-    const bool at = (pr.opA == OP_T || pr.opA == OP_H), bt = (pr.opB == OP_T || pr.opB == OP_H);
+  unsigned am = 0, bm = 0;
+  auto elem = [](const cf* X, int ld, bool tr, int r, int k) -> const cf& {
+    return tr ? X[(size_t)k + (size_t)r * ld] : X[(size_t)r + (size_t)k * ld];
+  };
+  auto load = [&](const umma::Cursor& c) {
+    const bool at = (c.opA == OP_T || c.opA == OP_H), bt = (c.opB == OP_T || c.opB == OP_H);
+    am = bm = 0;
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       const int it = tid + r * NT;
       const int m = at ? it / KC : (it & 63), kp = at ? it % KC : (it >> 6);
       const int k = c.k0 + 2 * kp;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m0 + m < tk.M) {
-        if (k < c.kend) load_op<cf, float>(A, pr.lda, pr.opA, m0 + m, k, v.x, v.y);
-        if (k + 1 < c.kend) load_op<cf, float>(A, pr.lda, pr.opA, m0 + m, k + 1, v.z, v.w);
-      }
-      xa[r] = v;
+      const bool vm = m0 + m < tk.M, v0 = vm && k < c.kend, v1 = vm && k + 1 < c.kend;
+      am |= (v0 ? 1u : 0u) << (2 * r) | (v1 ? 1u : 0u) << (2 * r + 1);
+      const int mm = vm ? m0 + m : 0;
+      const cf x0 = elem(c.A, c.lda, at, mm, v0 ? k : c.k0), x1 = elem(c.A, c.lda, at, mm, v1 ? k + 1 : c.k0);
+      ra[r] = make_float4(x0.re, x0.im, x1.re, x1.im);
     }
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       const int it = tid + r * NT;
       const int n = bt ? (it & 63) : it / KC, kp = bt ? (it >> 6) : it % KC;
       const int k = c.k0 + 2 * kp;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (n0 + n < tk.N) {
-        if (k < c.kend) load_op<cf, float>(B, pr.ldb, pr.opB, k, n0 + n, v.x, v.y);
-        if (k + 1 < c.kend) load_op<cf, float>(B, pr.ldb, pr.opB, k + 1, n0 + n, v.z, v.w);
-      }
-      xb[r] = v;
+      const bool vn = n0 + n < tk.N, v0 = vn && k < c.kend, v1 = vn && k + 1 < c.kend;
+      bm |= (v0 ? 1u : 0u) << (2 * r) | (v1 ? 1u : 0u) << (2 * r + 1);
+      const int nn = vn ? n0 + n : 0;
+      // op(B)(k, n): B(k, n) stored (ld = ldb) or B^T's (n, k) when transposed
+      const cf x0 = elem(c.B, c.ldb, !bt, nn, v0 ? k : c.k0), x1 = elem(c.B, c.ldb, !bt, nn, v1 ? k + 1 : c.k0);
+      rb[r] = make_float4(x0.re, x0.im, x1.re, x1.im);
     }
   };
-  // split the staged registers into the hi / lo planes of stage st
-  auto store = [&](unsigned char* st, const float4 (&xa)[NI], const float4 (&xb)[NI], const umma::Cursor& c) {
-    const GemmPair& pr = pairs[c.pi];
-    const bool at = (pr.opA == OP_T || pr.opA == OP_H), bt = (pr.opB == OP_T || pr.opB == OP_H);
+  // mask, conjugate and split the staged registers into the hi / lo planes of stage st
+  auto store = [&](unsigned char* st, const umma::Cursor& c) {
+    const bool at = (c.opA == OP_T || c.opA == OP_H), bt = (c.opB == OP_T || c.opB == OP_H);
+    const float sa = (c.opA == OP_C || c.opA == OP_H) ? -1.f : 1.f, sb = (c.opB == OP_C || c.opB == OP_H) ? -1.f : 1.f;
 #pragma unroll
     for (int r = 0; r < NI; ++r) {
       const int it = tid + r * NT;
       const int m = at ? it / KC : (it & 63), kp = at ? it % KC : (it >> 6);
-      const float4 v = xa[r];
+      const bool v0 = (am >> (2 * r)) & 1u, v1 = (am >> (2 * r + 1)) & 1u;
+      const float4 v = make_float4(v0 ? ra[r].x : 0.f, v0 ? sa * ra[r].y : 0.f, v1 ? ra[r].z : 0.f,
+                                   v1 ? sa * ra[r].w : 0.f);
       const float4 h = make_float4(umma::tf(v.x), umma::tf(v.y), umma::tf(v.z), umma::tf(v.w));
       const float4 l = make_float4(umma::tf(v.x - h.x), umma::tf(v.y - h.y), umma::tf(v.z - h.z), umma::tf(v.w - h.w));
       const int o0 = kp * C_::LBO_A + (m >> 3) * 128 + (m & 7) * 16;
@@ -519,7 +535,9 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
     for (int r = 0; r < NI; ++r) {
       const int it = tid + r * NT;
       const int n = bt ? (it & 63) : it / KC, kp = bt ? (it >> 6) : it % KC;
-      const float4 v = xb[r];
+      const bool v0 = (bm >> (2 * r)) & 1u, v1 = (bm >> (2 * r + 1)) & 1u;
+      const float4 v = make_float4(v0 ? rb[r].x : 0.f, v0 ? sb * rb[r].y : 0.f, v1 ? rb[r].z : 0.f,
+                                   v1 ? sb * rb[r].w : 0.f);
       const float4 h = make_float4(umma::tf(v.x), umma::tf(v.y), umma::tf(v.z), umma::tf(v.w));
       const float4 l = make_float4(umma::tf(v.x - h.x), umma::tf(v.y - h.y), umma::tf(v.z - h.z), umma::tf(v.w - h.w));
       const int o = 2 * C_::PLANE_A + kp * C_::LBO_B + (n >> 3) * 128 + (n & 7) * 16;
@@ -548,7 +566,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
     }
   };
 
-  umma::Cursor cur{tk.p0 - 1, 0, 0, 0};
+  umma::Cursor cur{tk.p0 - 1, 0, 0, 0, nullptr, nullptr, 0, 0, 0, 0};
   if (!advance(cur)) {  // no K overlaps this tile: C = beta C (zero partial)
     for (int e = tid; e < 64 * 64; e += NT) {
       const int m = m0 + (e & 63), n = n0 + (e >> 6);
@@ -566,7 +584,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fail = 0;
   }
-  load(ra, rb, cur);
+  load(cur);
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
@@ -577,9 +595,9 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
   for (;;) {
     const int s = c % S;
     if (c >= S) umma::wait(umma::saddr(&bars[s]), (uint32_t)((c / S - 1) & 1), &fail);
-    store(sm + s * C_::STAGE, ra, rb, cur);
+    store(sm + s * C_::STAGE, cur);
     const bool more = advance(cur);
-    if (more) load(ra, rb, cur);  // next chunk's loads in flight across the barrier and the MMAs
+    if (more) load(cur);  // next chunk's loads in flight across the barrier and the MMAs
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
