@@ -148,6 +148,14 @@ def roofline(st, clocks):
         peak = bf16 * (1.1 / 2.25) / 3.0
         out.update(bound="tensor", peak=peak, peak_source="%s sustained bf16 %.0f TF/s x 1.1/2.25 (TF32) / 3 "
                    "(hi/lo split)" % (src, bf16))
+    elif pipe == "fp32_df":
+        # FP64-accurate products of complex64 operands on the FP32 pipe: 4
+        # exact real products summed in double-float per complex
+        # multiply-add, 9 FP32 operations each (36 per 8 algorithmic flops)
+        lanes = 152 * 128 * pk["mhz"] * 1e6
+        peak = lanes * 8.0 / 36.0 / 1e12
+        out.update(bound="alu", peak=peak, peak_source="derived: 152 SM x 128 FP32 lanes x %.0f MHz x 8 flops / "
+                   "36 FP32 operations per complex multiply-add (double-float, FP32 pipe)" % pk["mhz"])
     else:
         fp64 = pipe == "fp64"
         peak = pk["fp64"] if fp64 else pk["fp32"]

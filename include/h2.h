@@ -97,6 +97,10 @@ typedef struct {
                             in tensor memory; 1: warp-level TF32 MMAs; both
                             split each operand into TF32 hi + lo parts
                             (FP32 accuracy); 0: FP32 FMA pipe             */
+  int gram_emulation;    /* Step-0 Grams of complex64 operands (FP64
+                            accumulation): 1 (default) on the FP32 pipe, as
+                            exact products summed in double-float and
+                            flushed to FP64 every 8 terms; 0: FP64 FMAs   */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -286,8 +290,8 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 
 /*
  * h2_set_opts - change the run-time tunables of a context (apply_path,
- * solve_graph, split_target, cluster_max, tile_policy, tensor_cores, profile)
- * without
+ * solve_graph, split_target, cluster_max, tile_policy, tensor_cores,
+ * gram_emulation, profile) without
  * rebuilding it; the other fields of *opts are ignored.  They take effect at
  * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
  * counterpart in the paper: used by the autotuner.

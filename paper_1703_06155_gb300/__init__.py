@@ -35,7 +35,8 @@ class h2_opts(ctypes.Structure):
                 ("arena_cap_bytes", ctypes.c_size_t),
                 ("host_only", ctypes.c_int), ("profile", ctypes.c_int), ("apply_path", ctypes.c_int),
                 ("solve_graph", ctypes.c_int), ("split_target", ctypes.c_int), ("cluster_max", ctypes.c_int),
-                ("tile_policy", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("tile_policy", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("gram_emulation", ctypes.c_int)]
 
 
 class H2Error(RuntimeError):
@@ -270,7 +271,8 @@ class H2:
 
     def set_opts(self, **kw):
         """h2_set_opts: change run-time tunables (apply_path, solve_graph,
-        split_target, cluster_max, tile_policy, tensor_cores, profile) of this
+        split_target, cluster_max, tile_policy, tensor_cores, gram_emulation,
+        profile) of this
         context; tunables not given return to their defaults."""
         o = default_opts(**kw)
         self._check(lib().h2_set_opts(self._h, ctypes.byref(o)), "h2_set_opts")

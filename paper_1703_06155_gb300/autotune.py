@@ -10,6 +10,7 @@ for candidate settings of
   apply_path    Step-2 and panel applications (GEMM + copy / in place),
   tensor_cores  complex64 tiles on tcgen05 / warp-level tensor-core MMAs
                 (3xTF32) or on FP32 FMAs,
+  gram_emulation  FP64-accurate Step-0 Grams on the FP32 pipe / FP64 FMAs,
 
 one parameter at a time from the defaults (coordinate descent), keeps the
 fastest setting of each and leaves it set on the context.  Every timing runs
@@ -19,6 +20,7 @@ import torch
 
 DEFAULT_SPACE = {
     "tensor_cores": [2, 1, 0],
+    "gram_emulation": [1, 0],
     "tile_policy": [0, 1],
     "split_target": [0, 304, 1216],
     "cluster_max": [16, 8],

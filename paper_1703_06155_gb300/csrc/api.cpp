@@ -246,12 +246,13 @@ void h2_default_opts(h2_opts* o) {
   o->cluster_max = 0;
   o->tile_policy = 0;
   o->tensor_cores = 2;
+  o->gram_emulation = 1;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   if (!ctx || !o || o->apply_path < 0 || o->apply_path > 2 || o->split_target < 0 || o->cluster_max < 0 ||
       o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
-      o->tensor_cores < 0 || o->tensor_cores > 2)
+      o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -260,6 +261,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   c.cluster_max = o->cluster_max;
   c.tile_policy = o->tile_policy;
   c.tensor_cores = o->tensor_cores;
+  c.gram_emulation = o->gram_emulation;
   c.profile = o->profile;
   ctx->c.graphs.clear();
   return H2_OK;
@@ -293,7 +295,8 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   h2_ctx* x = new h2_ctx();
   h2_default_opts(&x->c.opts);
   if (opts) x->c.opts = *opts;
-  if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2) {
+  if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2 ||
+      x->c.opts.gram_emulation < 0 || x->c.opts.gram_emulation > 1) {
     delete x;
     g_err = "h2_build: bad options";
     return H2_EINVAL;

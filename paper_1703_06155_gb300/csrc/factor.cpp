@@ -48,10 +48,11 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   c.st.upload(c);
   const int pa = b.pina < 0 ? pin : b.pina;
   const int tc = (b.shape == 0 && pa == P32 && pin == P32 && pacc == P32 && pout == P32) ? c.opts.tensor_cores : 0;
-  const char* pipe = pacc == P64 ? "fp64" : tc == 2 ? "tcgen05_tf32x3" : tc == 1 ? "mma_tf32x3" : "fp32";
+  const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1 : 0;
+  const char* pipe = emul ? "fp32_df" : pacc == P64 ? "fp64" : tc == 2 ? "tcgen05_tf32x3" : tc == 1 ? "mma_tf32x3" : "fp32";
   ProfScope ps(c, std::string("gemm:") + what, b.alg_flops, pipe);
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
-          wsp, c.stream, b.shape, b.pina, c.opts.tensor_cores),
+          wsp, c.stream, b.shape, b.pina, c.opts.tensor_cores, emul),
      what);
   c.launches++;
   if (ws > 0) {

@@ -167,6 +167,162 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
   }
 }
 
+// ---- complex64 products accumulated to FP64 accuracy on the FP32 pipe ----
+//
+// For the Step-0 Grams of complex64 operands.  A product a b of two FP32
+// numbers is exact as p + e with p = fl(a b) and e = fma(a, b, -p).  The
+// products of one BK-long K slice are summed in double-float: hi takes p
+// through an error-free TwoSum and lo collects the TwoSum errors and the e
+// parts; the slice total hi + lo (error <= ~4 BK 2^-48 of the slice's
+// magnitude) is then added to an FP64 accumulator.  About ten FP32 operations
+// replace one FP64 FMA, on a pipe that runs 64x the FP64 rate here.  The
+// rounded operations are the _rn intrinsics, which the compiler never fuses
+// into FMAs.  (Operands below ~1e-19 in magnitude would lose the exactness of
+// their products to FP32 underflow; Gram operands are far above that.)
+__device__ __forceinline__ void df_madd(float& h, float& l, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  const float t = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(t, e));
+}
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tasks,
+                                               const GemmPair* __restrict__ pairs,
+                                               const GemmTile* __restrict__ tiles, cd* __restrict__ ws) {
+  constexpr int TN = BN / 16, TMR = BM / 16;
+  __shared__ float As_r[BK][BM], As_i[BK][BM];
+  __shared__ float Bs_r[BK][BN], Bs_i[BK][BN];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask tk = tasks[tl.task];
+  const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc_r[TMR][TN], acc_i[TMR][TN];
+#pragma unroll
+  for (int i = 0; i < TMR; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc_r[i][j] = acc_i[i][j] = 0.0;
+
+  const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
+  const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
+  int64_t koff = 0;
+  for (int pi = tk.p0; pi < tk.p0 + tk.np; ++pi) {
+    const GemmPair pr = pairs[pi];
+    const int64_t kb = koff;
+    koff += pr.K;
+    if (koff <= klo || kb >= khi) continue;
+    const int kbeg = (int)(klo > kb ? klo - kb : 0);
+    const int kend = (int)(khi - kb < pr.K ? khi - kb : pr.K);
+    const cf* A = (const cf*)pr.A;
+    const cf* B = (const cf*)pr.B;
+    const bool at = (pr.opA == OP_T || pr.opA == OP_H);
+    const bool bt = (pr.opB == OP_T || pr.opB == OP_H);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < (BM * BK + NT - 1) / NT; ++r) {
+        const int l = tid + r * NT;
+        if (l >= BM * BK) break;
+        int i, k;
+        if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
+        float re = 0, im = 0;
+        if (m0 + i < tk.M && k0 + k < kend) load_op<cf, float>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
+        As_r[k][i] = re;
+        As_i[k][i] = im;
+      }
+#pragma unroll
+      for (int r = 0; r < (BK * BN + NT - 1) / NT; ++r) {
+        const int l = tid + r * NT;
+        if (l >= BK * BN) break;
+        int k, j;
+        if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
+        float re = 0, im = 0;
+        if (n0 + j < tk.N && k0 + k < kend) load_op<cf, float>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
+        Bs_r[k][j] = re;
+        Bs_i[k][j] = im;
+      }
+      __syncthreads();
+      float hr[TMR][TN], lr[TMR][TN], hi[TMR][TN], li[TMR][TN];
+#pragma unroll
+      for (int i = 0; i < TMR; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) hr[i][j] = lr[i][j] = hi[i][j] = li[i][j] = 0.f;
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        float ar[TMR], ai[TMR], br[TN], bi[TN];
+#pragma unroll
+        for (int i = 0; i < TMR; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
+#pragma unroll
+        for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
+#pragma unroll
+        for (int i = 0; i < TMR; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            df_madd(hr[i][j], lr[i][j], ar[i], br[j]);
+            df_madd(hr[i][j], lr[i][j], -ai[i], bi[j]);
+            df_madd(hi[i][j], li[i][j], ar[i], bi[j]);
+            df_madd(hi[i][j], li[i][j], ai[i], br[j]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < TMR; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          acc_r[i][j] += (double)hr[i][j] + (double)lr[i][j];
+          acc_i[i][j] += (double)hi[i][j] + (double)li[i][j];
+        }
+      __syncthreads();
+    }
+  }
+  if (tk.nk > 1) {
+    cd* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
+#pragma unroll
+    for (int i = 0; i < TMR; ++i) {
+      const int m = m0 + ty + 16 * i;
+      if (m >= tk.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n >= tk.N) continue;
+        cd v;
+        v.re = acc_r[i][j];
+        v.im = acc_i[i][j];
+        W[(int64_t)m + (int64_t)n * tk.M] = v;
+      }
+    }
+    return;
+  }
+  cd* C = (cd*)tk.C;
+#pragma unroll
+  for (int i = 0; i < TMR; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= tk.M) continue;
+    cd old[TN];
+    if (tk.beta != 0.0) {
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n < tk.N) old[j] = C[(size_t)m + (size_t)n * tk.ldc];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= tk.N) continue;
+      cd v;
+      v.re = tk.alpha * acc_r[i][j];
+      v.im = tk.alpha * acc_i[i][j];
+      if (tk.beta != 0.0) {
+        v.re = fma(tk.beta, old[j].re, v.re);
+        v.im = fma(tk.beta, old[j].im, v.im);
+      }
+      C[(size_t)m + (size_t)n * tk.ldc] = v;
+    }
+  }
+}
+
 // ---- complex64 tiles on the tensor cores (3xTF32) ----------------------
 //
 // The same 64 x 64 tile / task / pair / split-K scheme as k_gemm, with the
@@ -735,8 +891,10 @@ int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : 16; }
 
 template <int BM, int BN>
 static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
-                             int pina, int pin, int pout, int pacc, void* ws, cudaStream_t s) {
-  if (pina == P64 && pin == P64 && pacc == P64 && pout == P64)
+                             int pina, int pin, int pout, int pacc, void* ws, cudaStream_t s, int emul) {
+  if (emul && pina == P32 && pin == P32 && pacc == P64 && pout == P64)
+    k_gemm_df<BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+  else if (pina == P64 && pin == P64 && pacc == P64 && pout == P64)
     k_gemm<cd, cd, double, cd, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pina == P32 && pin == P32 && pacc == P32 && pout == P32)
     k_gemm<cf, cf, float, cf, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
@@ -781,7 +939,7 @@ unsigned int gemm_umma_timeouts() {
 }
 
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles, int pin,
-                 int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina, int tensor) {
+                 int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina, int tensor, int emul) {
   if (ntiles <= 0) return cudaSuccess;
   if (pina < 0) pina = pin;
   if (tensor && shape == 0 && pina == P32 && pin == P32 && pacc == P32 && pout == P32) {
@@ -790,11 +948,11 @@ cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTil
     return cudaGetLastError();
   }
   switch (shape) {
-    case 0: return gemm_tile<64, 64>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
-    case 1: return gemm_tile<64, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
-    case 2: return gemm_tile<32, 32>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
-    case 3: return gemm_tile<32, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
-    case 4: return gemm_tile<16, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s);
+    case 0: return gemm_tile<64, 64>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
+    case 1: return gemm_tile<64, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
+    case 2: return gemm_tile<32, 32>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
+    case 3: return gemm_tile<32, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
+    case 4: return gemm_tile<16, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
     default: return cudaErrorInvalidValue;
   }
 }

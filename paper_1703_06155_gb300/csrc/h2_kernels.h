@@ -157,11 +157,13 @@ struct KGramTile { int task, tm, tn; };
 // it differs from B's (pin); supported: A complex128 with B complex64, FP64
 // accumulation into complex128 or FP32 accumulation into complex64.
 // tensor = 1: complex64 64 x 64 products on warp-level TF32 MMAs (3xTF32);
-// tensor = 2: the same on tcgen05 MMAs with TMEM accumulators (3xTF32)
+// tensor = 2: the same on tcgen05 MMAs with TMEM accumulators (3xTF32);
+// emul = 1: complex64 operands with FP64 accumulation run on the FP32 pipe
+// (exact products summed in double-float, flushed to FP64 per K slice)
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
                  int pacc, void* ws, cudaStream_t s, int shape = 0,
-                 int pina = -1, int tensor = 0);
+                 int pina = -1, int tensor = 0, int emul = 0);
 cudaError_t gemm_reduce(const GemmTask* d_tasks, int ntasks, int maxmn,
                         int pout, int pacc, const void* ws, cudaStream_t s);
 // C[i, j] = conj(C[j, i]) for the entries of bm x bm tiles below the diagonal

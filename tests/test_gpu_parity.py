@@ -207,6 +207,30 @@ def test_autotune_keeps_results(dev):
     assert rel(x, xe) < 1e-10
 
 
+def test_gram_emulation_matches_fp64_grams(dev):
+    # Step-0 Grams of complex64 operands as exact products summed in
+    # double-float on the FP32 pipe (flushed to FP64 every 8 terms) or with
+    # FP64 FMAs: the same Step-0 ranks on every level, FP32-close
+    # factorizations, and both refine to the exact H^2 solution
+    eps = 1e-6
+    n = 16
+    H = h2_problem(n, 64, eps)
+    A1 = gpu_ctx(H, gram_emulation=1)
+    A0 = gpu_ctx(H, gram_emulation=0)
+    A1.factorize(eps, "mixed")
+    A0.factorize(eps, "mixed")
+    e1 = [lv["eliminated"] for lv in A1.stats()["levels"]]
+    e0 = [lv["eliminated"] for lv in A0.stats()["levels"]]
+    assert e1 == e0
+    b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 2, 29)).to(dev)
+    x1, x0 = A1.solve(b).cpu().numpy(), A0.solve(b).cpu().numpy()
+    assert rel(x1, x0) < 1e-4
+    Zd = h2_dense(n, 64, eps)
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
+    xr = A1.solve(b, refine=True, tol=1e-12, max_iter=30).cpu().numpy()
+    assert rel(xr, xe) < 1e-10
+
+
 @pytest.mark.parametrize("tc", [1, 2])
 def test_tensor_core_bulk_matches_fma_bulk(dev, tc):
     # the complex64 bulk on the tensor cores (3xTF32: warp-level MMAs, or
