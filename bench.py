@@ -56,6 +56,8 @@ def parse():
                    help="Step 2 / panel applications: 0 auto, 1 in-place kernel, 2 GEMM + copy")
     p.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                    help="complex64 GEMM tiles: 2 tcgen05, 1 warp-level TF32 MMA, 0 FP32 FMA (default: library's)")
+    p.add_argument("--no-kernel-events", action="store_true",
+                   help="no per-launch CUDA events in the timed steps (no kernel table / roofline)")
     p.add_argument("--json-extra", action="store_true", help="print per-level stats")
     p.add_argument("--profile-step", action="store_true",
                    help="build, then exactly one factorize + refined solve (for profiler captures)")
@@ -431,7 +433,8 @@ def run_ours(args):
     pts = inputs.grid_points(args.grid, H)
     N = len(pts)
     t0 = time.perf_counter()
-    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream, profile=2 if args.profile_levels else 1,
+    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream,
+                 profile=2 if args.profile_levels else (0 if args.no_kernel_events else 1),
                  apply_path=args.apply_path, **tc_opts(args))
     t_build = time.perf_counter() - t0
     b_host = inputs.rhs_gaussian(N, args.nrhs, args.seed + rank)  # independent instance per rank

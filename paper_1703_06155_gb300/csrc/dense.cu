@@ -194,13 +194,26 @@ __global__ void __launch_bounds__(NT) k_jacobi(const EigTask* __restrict__ tasks
   fro = block_sum(fro, red);
   // rotations whose off-diagonal entry is below 4e-16 ||A||_F (or 1e-17 of
   // the geometric mean of the two diagonal entries) are skipped; the sweep
-  // loop ends after a sweep without any rotation.
+  // loop ends when a sweep would rotate nothing.
   const double gmin = fmax(1e-300, 4e-16 * sqrt(fro));
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (threadIdx.x == 0) any_rot = 0;
     __syncthreads();
     if (fro == 0.0) break;
+    // converged when no off-diagonal entry is above its rotation threshold
+    // (such a sweep would rotate nothing): one pass replaces that sweep
+    {
+      int any = 0;
+      for (int idx = threadIdx.x; idx < p * p && !any; idx += NT) {
+        const int row = idx % p, col = idx / p;
+        if (row >= col) continue;
+        const cd v = A[row + (size_t)col * p];
+        const double g = sqrt(v.re * v.re + v.im * v.im);
+        if (g > gmin && g > 1e-17 * sqrt(fabs(A[row + (size_t)row * p].re * A[col + (size_t)col * p].re))) any = 1;
+      }
+      if (!__syncthreads_or(any)) break;
+    }
     for (int r = 0; r < pe - 1; ++r) {
       for (int i = threadIdx.x; i < np; i += NT) {
         int a, b;

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
   double* rei = rer + np;
   int* pa = (int*)(rei + np);
   int* pb = pa + np;
-  int* flags = pb + np;  // one flag per sweep (zeroed by the host)
+  int* flags = pb + np;           // per sweep: a rotation happened (zeroed by the host)
+  int* open = flags + kMaxSweeps;  // per sweep: an entry above its threshold at the start
   cd* A = t.A;
   cd* U = t.U;
   __shared__ double red[32];
@@ -88,6 +89,23 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (fro == 0.0) break;
+    // converged when no off-diagonal entry is above its rotation threshold:
+    // such a sweep would rotate nothing, so one pass over the owned columns
+    // replaces it
+    {
+      int any = 0;
+      const int ncol = (p - rank + C - 1) / C;
+      for (int idx = threadIdx.x; idx < ncol * p && !any; idx += NT) {
+        const int col = rank + (idx / p) * C, row = idx % p;
+        if (row >= col) continue;
+        const cd v = A[row + (size_t)col * p];
+        const double g = sqrt(v.re * v.re + v.im * v.im);
+        if (g > gmin && g > 1e-17 * sqrt(fabs(A[row + (size_t)row * p].re * A[col + (size_t)col * p].re))) any = 1;
+      }
+      if (__syncthreads_or(any) && threadIdx.x == 0) open[sweep] = 1;
+      cluster_barrier();
+      if (!open[sweep]) break;
+    }
     for (int r = 0; r < pe - 1; ++r) {
       // 1a. rotations of own pairs (pair i is owned by CTA i mod C)
       for (int i = rank + threadIdx.x * C; i < np; i += NT * C) {
@@ -192,7 +210,7 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
 
 int64_t jacobi_cluster_scratch(int maxp) {
   const int np = (maxp + 1) / 2 + 1;
-  return (int64_t)np * 4 + (np * 2 + kMaxSweeps + 8) / 2 + 8;  // doubles
+  return (int64_t)np * 4 + (np * 2 + 2 * kMaxSweeps + 8) / 2 + 8;  // doubles
 }
 
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, double* d_scratch,
