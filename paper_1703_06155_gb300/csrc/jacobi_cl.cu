@@ -5,14 +5,16 @@
 // G = diag(1, e^{-i phi}) J with J the real Jacobi rotation of [[a, g],[g, d]]),
 // but each eigenproblem runs on one cluster of CTAs so that its FP64 work is
 // spread over several SMs.  Per round:
-//   1. each CTA computes the rotations of the pairs it owns (pair i is owned by
-//      CTA i mod C), publishes them in global scratch and rotates the columns
-//      of A and U of those pairs (no other CTA touches them in this phase);
-//   2. each CTA applies all row rotations to the columns it owns (col mod C).
-// Phases are separated by cluster barriers with release / acquire semantics
-// (hardware barrier.cluster; no software spin), which order the global-memory
-// traffic of the cluster's threads.  A matrix whose sweeps do not converge
-// within kMaxSweeps sets status bit 2 and returns its current state.
+//   1. every CTA computes all rotations of the round into its shared memory;
+//   2. the rotations form one block-diagonal unitary G, so each 2 x 2 block
+//      of G^H A G is G_P^H A[P, Q] G_Q: each CTA updates the two columns of
+//      the pairs Q it owns (pair q is owned by CTA q mod C), rows and columns
+//      rotated at once, and the same columns of U.
+// Rounds are separated by one cluster barrier with release / acquire
+// semantics (hardware barrier.cluster; no software spin), which orders the
+// global-memory traffic of the cluster's threads.  A matrix whose sweeps do
+// not converge within kMaxSweeps sets status bit 2 and returns its current
+// state.
 #include <cooperative_groups.h>
 
 #include "h2_kernels.h"
@@ -52,17 +54,27 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
   const int pe = p + (p & 1);
   const int np = pe / 2;
   double* base = scratch + ti * scratch_per_task;
-  double* rc = base;
-  double* rs = rc + np;
-  double* rer = rs + np;
-  double* rei = rer + np;
-  int* pa = (int*)(rei + np);
+  // entries that the next round's rotations read, double-buffered by round
+  // parity: Dd[k] = A(k, k), Do[b] = A(a, b) of the pair (a < b); written by
+  // the owner of column k / b after its updates, read by every CTA after the
+  // cluster barrier (so no CTA reads A while another one writes it)
+  double* Dd = base;                    // 2 x pe
+  cd* Do = (cd*)(base + 2 * (size_t)pe);  // 2 x pe
+  int* pa = (int*)(base + 6 * (size_t)pe);
   int* pb = pa + np;
   int* flags = pb + np;           // per sweep: a rotation happened (zeroed by the host)
   int* open = flags + kMaxSweeps;  // per sweep: an entry above its threshold at the start
   cd* A = t.A;
   cd* U = t.U;
   __shared__ double red[32];
+  // rotation parameters of the current round (all pairs), dynamic shared memory
+  extern __shared__ double jsh[];
+  double* jc = jsh;
+  double* js = jc + np;
+  double* jer = js + np;
+  double* jei = jer + np;
+  int* ja = (int*)(jei + np);
+  int* jb = ja + np;
   // U = I (columns owned by this CTA)
   for (int idx = threadIdx.x; idx < p * p; idx += NT) {
     const int col = idx / p;
@@ -85,8 +97,17 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
   fro = red[0];
   // off-diagonal entries at the rounding level of the matrix are not rotated
   const double gmin = fmax(1e-300, 4e-16 * sqrt(fro));
+  const int m = pe - 1;  // round-robin modulus
+  // partner of index k in round r (pair 0 = (pe - 1, r), pair i = (r + i, r - i) mod m)
+  auto partner = [&](int k, int r) { return k == pe - 1 ? r : k == r ? pe - 1 : ((2 * r - k) % m + m) % m; };
+  if (rank == 0)
+    for (int k = threadIdx.x; k < p; k += NT) {
+      Dd[k] = A[k + (size_t)k * p].re;
+      const int j = partner(k, 0);
+      if (j < k) Do[k] = A[j + (size_t)k * p];
+    }
   cluster_barrier();
-  int sweep = 0;
+  int sweep = 0, tr = 0;  // tr: rounds so far (buffer parity)
   for (; sweep < kMaxSweeps; ++sweep) {
     if (fro == 0.0) break;
     // converged when no off-diagonal entry is above its rotation threshold:
@@ -107,15 +128,17 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
       if (!open[sweep]) break;
     }
     for (int r = 0; r < pe - 1; ++r) {
-      // 1a. rotations of own pairs (pair i is owned by CTA i mod C)
-      for (int i = rank + threadIdx.x * C; i < np; i += NT * C) {
+      // 1. every CTA computes all rotations of the round (pair i = (a, b))
+      //    from the entries published for it, into shared memory
+      for (int i = threadIdx.x; i < np; i += NT) {
         int a, b;
         if (i == 0) { a = pe - 1; b = r; } else { a = (r + i) % (pe - 1); b = (r - i + pe - 1) % (pe - 1); }
         if (a > b) { const int x = a; a = b; b = x; }
         double c = 1, s = 0, er = 1, ei = 0;
         if (b < p) {
-          const double app = A[a + (size_t)a * p].re, aqq = A[b + (size_t)b * p].re;
-          const cd apq = A[a + (size_t)b * p];
+          const int bi = tr & 1;
+          const double app = Dd[bi * pe + a], aqq = Dd[bi * pe + b];
+          const cd apq = Do[bi * pe + b];
           const double g = sqrt(apq.re * apq.re + apq.im * apq.im);
           if (g > gmin && g > 1e-17 * sqrt(fabs(app * aqq))) {
             er = apq.re / g;
@@ -127,56 +150,117 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
             flags[sweep] = 1;
           }
         }
-        pa[i] = a;
-        pb[i] = b;
-        rc[i] = c;
-        rs[i] = s;
-        rer[i] = er;
-        rei[i] = ei;
+        ja[i] = a;
+        jb[i] = b;
+        jc[i] = c;
+        js[i] = s;
+        jer[i] = er;
+        jei[i] = ei;
       }
       __syncthreads();
-      // 1b. columns of A and U of own pairs (pair ii is owned by CTA ii mod C)
-      for (int ii = rank; ii < np; ii += C) {
-        const double s = rs[ii];
-        if (s == 0.0) continue;
-        const int a = pa[ii], b = pb[ii];
-        const double c = rc[ii], er = rer[ii], ei = -rei[ii];
-        for (int idx = threadIdx.x; idx < 2 * p; idx += NT) {
-          cd* M = idx < p ? A : U;
-          const int row = idx < p ? idx : idx - p;
-          const cd xa = M[row + (size_t)a * p], xb = M[row + (size_t)b * p];
-          const double ebr = er * xb.re - ei * xb.im, ebi = er * xb.im + ei * xb.re;
-          cd na, nb;
-          na.re = c * xa.re - s * ebr;
-          na.im = c * xa.im - s * ebi;
-          nb.re = s * xa.re + c * ebr;
-          nb.im = s * xa.im + c * ebi;
-          M[row + (size_t)a * p] = na;
-          M[row + (size_t)b * p] = nb;
+      // 2. the pair rotations form one block-diagonal unitary G, so every 2 x 2
+      //    block of G^H A G is G_P^H A[P, Q] G_Q.  This CTA updates the two
+      //    columns of its own pairs Q (pair q is owned by CTA q mod C) for all
+      //    row pairs P, and the same columns of U (U G_Q); no other CTA
+      //    touches them in this round.
+      {
+        const int nown = rank < np ? (np - rank + C - 1) / C : 0;
+        const int totA = nown * np, tot = totA + nown * p;
+        for (int idx = threadIdx.x; idx < tot; idx += NT) {
+          if (idx < totA) {
+            const int q = rank + (idx / np) * C, P = idx % np;
+            const double sq = js[q], sp = js[P];
+            if (sq == 0.0 && sp == 0.0) continue;
+            const int aq = ja[q], bq = jb[q], ap = ja[P], bp = jb[P];
+            const bool hq = bq < p, hp = bp < p;  // the padding index of an odd order has no row / column
+            cd x11 = A[ap + (size_t)aq * p], x21, x12, x22;
+            x21.re = x21.im = x12.re = x12.im = x22.re = x22.im = 0;
+            if (hp) x21 = A[bp + (size_t)aq * p];
+            if (hq) x12 = A[ap + (size_t)bq * p];
+            if (hp && hq) x22 = A[bp + (size_t)bq * p];
+            // columns: new a = c x_a - s conj(e) x_b ; new b = s x_a + c conj(e) x_b
+            if (sq != 0.0) {
+              const double c = jc[q], er = jer[q], ei = -jei[q];
+              const double e1r = er * x12.re - ei * x12.im, e1i = er * x12.im + ei * x12.re;
+              const double e2r = er * x22.re - ei * x22.im, e2i = er * x22.im + ei * x22.re;
+              cd n11, n12, n21, n22;
+              n11.re = c * x11.re - sq * e1r;
+              n11.im = c * x11.im - sq * e1i;
+              n12.re = sq * x11.re + c * e1r;
+              n12.im = sq * x11.im + c * e1i;
+              n21.re = c * x21.re - sq * e2r;
+              n21.im = c * x21.im - sq * e2i;
+              n22.re = sq * x21.re + c * e2r;
+              n22.im = sq * x21.im + c * e2i;
+              x11 = n11;
+              x12 = n12;
+              x21 = n21;
+              x22 = n22;
+            }
+            // rows: new a = c y_a - s e y_b ; new b = s y_a + c e y_b
+            if (sp != 0.0) {
+              const double c = jc[P], er = jer[P], ei = jei[P];
+              const double e1r = er * x21.re - ei * x21.im, e1i = er * x21.im + ei * x21.re;
+              const double e2r = er * x22.re - ei * x22.im, e2i = er * x22.im + ei * x22.re;
+              cd n11, n12, n21, n22;
+              n11.re = c * x11.re - sp * e1r;
+              n11.im = c * x11.im - sp * e1i;
+              n21.re = sp * x11.re + c * e1r;
+              n21.im = sp * x11.im + c * e1i;
+              n12.re = c * x12.re - sp * e2r;
+              n12.im = c * x12.im - sp * e2i;
+              n22.re = sp * x12.re + c * e2r;
+              n22.im = sp * x12.im + c * e2i;
+              x11 = n11;
+              x12 = n12;
+              x21 = n21;
+              x22 = n22;
+            }
+            // the rotated pair's off-diagonal entries are zero by construction
+            if (P == q) {
+              x12.re = x12.im = 0;
+              x21.re = x21.im = 0;
+              x11.im = 0;
+              x22.im = 0;
+            }
+            A[ap + (size_t)aq * p] = x11;
+            if (hp) A[bp + (size_t)aq * p] = x21;
+            if (hq) A[ap + (size_t)bq * p] = x12;
+            if (hp && hq) A[bp + (size_t)bq * p] = x22;
+          } else {
+            const int e = idx - totA;
+            const int q = rank + (e / p) * C, row = e % p;
+            const double sq = js[q];
+            if (sq == 0.0) continue;
+            const int aq = ja[q], bq = jb[q];
+            const double c = jc[q], er = jer[q], ei = -jei[q];
+            const cd xa = U[row + (size_t)aq * p], xb = U[row + (size_t)bq * p];
+            const double ebr = er * xb.re - ei * xb.im, ebi = er * xb.im + ei * xb.re;
+            cd na, nb;
+            na.re = c * xa.re - sq * ebr;
+            na.im = c * xa.im - sq * ebi;
+            nb.re = sq * xa.re + c * ebr;
+            nb.im = sq * xa.im + c * ebi;
+            U[row + (size_t)aq * p] = na;
+            U[row + (size_t)bq * p] = nb;
+          }
         }
       }
-      cluster_barrier();
-      // 2. rows of A, columns owned by this CTA, all pairs
-      const int ncol = (p - rank + C - 1) / C;
-      for (int idx = threadIdx.x; idx < np * ncol; idx += NT) {
-        const int i = idx / ncol, col = rank + (idx % ncol) * C;
-        const double s = rs[i];
-        if (s == 0.0) continue;
-        const int a = pa[i], b = pb[i];
-        const double c = rc[i], er = rer[i], ei = rei[i];
-        const cd ya = A[a + (size_t)col * p], yb = A[b + (size_t)col * p];
-        const double ebr = er * yb.re - ei * yb.im, ebi = er * yb.im + ei * yb.re;
-        cd na, nb;
-        na.re = c * ya.re - s * ebr;
-        na.im = c * ya.im - s * ebi;
-        nb.re = s * ya.re + c * ebr;
-        nb.im = s * ya.im + c * ebi;
-        // the rotated pair's off-diagonal entries are zero by construction
-        if (col == b) { na.re = 0; na.im = 0; nb.im = 0; }
-        if (col == a) { nb.re = 0; nb.im = 0; na.im = 0; }
-        A[a + (size_t)col * p] = na;
-        A[b + (size_t)col * p] = nb;
+      __syncthreads();
+      // 3. publish the entries of the own columns that the next round reads
+      {
+        const int rn = (r + 1) % m, nb = (tr + 1) & 1;
+        const int nown = rank < np ? (np - rank + C - 1) / C : 0;
+        for (int idx = threadIdx.x; idx < 2 * nown; idx += NT) {
+          const int q = rank + (idx >> 1) * C;
+          const int k = (idx & 1) ? jb[q] : ja[q];
+          if (k >= p) continue;
+          Dd[nb * pe + k] = A[k + (size_t)k * p].re;
+          const int j = partner(k, rn);
+          if (j < k) Do[nb * pe + k] = A[j + (size_t)k * p];
+        }
       }
+      ++tr;
       cluster_barrier();
     }
     if (!flags[sweep]) break;
@@ -210,7 +294,10 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
 
 int64_t jacobi_cluster_scratch(int maxp) {
   const int np = (maxp + 1) / 2 + 1;
-  return (int64_t)np * 4 + (np * 2 + 2 * kMaxSweeps + 8) / 2 + 8;  // doubles
+  // doubles; even, so that every task's block (which holds complex128
+  // entries) starts on a 16-byte boundary
+  const int64_t n = (int64_t)np * 12 + (np * 2 + 2 * kMaxSweeps + 8) / 2 + 8;
+  return (n + 1) & ~(int64_t)1;
 }
 
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, double* d_scratch,
@@ -219,12 +306,16 @@ cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int
   const int64_t per = jacobi_cluster_scratch(maxp);
   cudaError_t e = cudaMemsetAsync(d_scratch, 0, (size_t)per * ntasks * sizeof(double), s);
   if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)((maxp + 1) / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));
+  e = cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   if (csize > 8) {
     cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     // fall back to the portable size if the device cannot co-schedule csize CTAs
     cudaLaunchConfig_t q = {};
     q.gridDim = dim3(csize, 1, 1);
     q.blockDim = dim3(NT, 1, 1);
+    q.dynamicSmemBytes = smem;
     cudaLaunchAttribute qa[1];
     qa[0].id = cudaLaunchAttributeClusterDimension;
     qa[0].val.clusterDim.x = csize;
@@ -241,7 +332,7 @@ cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ntasks * csize, 1, 1);
   cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
