@@ -334,35 +334,59 @@ __device__ __forceinline__ void cvt(const ES& s, ED& d, double al) {
   d.im = (decltype(d.im))(al * (double)s.im);
 }
 
+// Work unit: 32 consecutive rows of one column (lane = row), units dealt to
+// the task's warps; each warp takes CU units at a time with all their loads
+// issued before any store (the destination may not alias the source, except
+// in accumulate mode where it is read first).
 template <class ES, class ED>
 __device__ void copy_body(const CopyTask& t) {
+  constexpr int CU = 4;
   const ES* S = (const ES*)t.src;
   ED* D = (ED*)t.dst;
-  const int n = t.rows * t.cols;
-  for (int idx = threadIdx.x + blockIdx.y * NT; idx < n; idx += NT * gridDim.y) {
-    const int r = idx % t.rows, c = idx / t.rows;
-    ED v;
-    if (t.mode == 2) {
-      v.re = (r == c) ? 1 : 0;
-      v.im = 0;
+  if (t.rows <= 0 || t.cols <= 0) return;
+  const int nrb = (t.rows + 31) >> 5;
+  const int units = nrb * t.cols;
+  const int lane = threadIdx.x & 31;
+  const int nw = (NT / 32) * gridDim.y;
+  const int gw = (threadIdx.x >> 5) + blockIdx.y * (NT / 32);
+  for (int u0 = gw; u0 < units; u0 += nw * CU) {
+    ES sv[CU];
+    ED ov[CU];
+    int rr[CU], cc[CU];
+    unsigned st = 0;  // per unit: bit 0 in range, bit 1 loaded from S
+#pragma unroll
+    for (int k = 0; k < CU; ++k) {
+      const int u = u0 + k * nw;
+      const int c = u / nrb, r = (u - c * nrb) * 32 + lane;
+      rr[k] = r;
+      cc[k] = c;
+      if (u >= units || r >= t.rows) continue;
+      st |= 1u << (2 * k);
+      if (t.mode != 2 && S && r < t.srows && c < t.scols) {
+        sv[k] = t.transpose ? S[(size_t)c + (size_t)r * t.lds] : S[(size_t)r + (size_t)c * t.lds];
+        st |= 2u << (2 * k);
+      }
+      if (t.mode == 1) ov[k] = D[(size_t)r + (size_t)c * t.ldd];
+    }
+#pragma unroll
+    for (int k = 0; k < CU; ++k) {
+      if (!((st >> (2 * k)) & 1u)) continue;
+      const int r = rr[k], c = cc[k];
+      ED v;
+      if (t.mode == 2) {
+        v.re = (r == c) ? 1 : 0;
+        v.im = 0;
+      } else if ((st >> (2 * k)) & 2u) {
+        cvt(sv[k], v, t.alpha);
+      } else {
+        v.re = 0;
+        v.im = 0;
+      }
+      if (t.mode == 1) {
+        v.re += ov[k].re;
+        v.im += ov[k].im;
+      }
       D[(size_t)r + (size_t)c * t.ldd] = v;
-      continue;
-    }
-    if (S && r < t.srows && c < t.scols) {
-      const ES s = t.transpose ? S[(size_t)c + (size_t)r * t.lds] : S[(size_t)r + (size_t)c * t.lds];
-      cvt(s, v, t.alpha);
-    } else {
-      v.re = 0;
-      v.im = 0;
-    }
-    ED* p = D + (size_t)r + (size_t)c * t.ldd;
-    if (t.mode == 1) {
-      ED o = *p;
-      o.re += v.re;
-      o.im += v.im;
-      *p = o;
-    } else {
-      *p = v;
     }
   }
 }
@@ -422,10 +446,14 @@ __global__ void k_frob2_part(const FrobBlock* __restrict__ blocks, double* __res
   const FrobBlock k = blocks[blockIdx.x];
   const E* A = (const E*)k.A;
   double s = 0;
-  const int64_t tot = (int64_t)k.rows * k.cols;
-  for (int64_t e = threadIdx.x; e < tot; e += NT) {
-    const E v = A[(e % k.rows) + (e / k.rows) * (int64_t)k.lda];
-    s += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+  // one warp per column, lanes over its rows (coalesced, no index division)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < k.cols; c += NT / 32) {
+    const E* col = A + (int64_t)c * k.lda;
+    for (int r = lane; r < k.rows; r += 32) {
+      const E v = col[r];
+      s += (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+    }
   }
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;

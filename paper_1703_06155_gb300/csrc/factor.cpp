@@ -291,7 +291,7 @@ struct Info {
   bool fill;
   bool proj = false;  // Gram formed in complement coordinates: X = Vp^H F, G' = X X^H
   int64_t wsum = 0;   // total fill-in width of the row (and column)
-  size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1, X, tr;
+  size_t M, T1, G, L, T, W, Qx, Z1, Gh, U, lam, W1, W2, Yf, Y1, X, tr, Vpf;
   std::vector<int> rowf, colf;
 };
 
@@ -359,6 +359,9 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         f.tr = take(1);
         if (f.proj) {
           f.X = take(p * (size_t)f.wsum);
+          // complex64 copy of Vp for the complex64 product X = Vp^H F (the
+          // product rounds Vp to FP32 either way)
+          if (prec == P32) f.Vpf = take((n * p + 1) / 2);
         } else {
           f.M = take(n * n);
           f.T1 = take(n * p);
@@ -390,6 +393,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   hsA.reset();
   if (anyfill) {
     GemmBatch gM, gX, gXX, gT, gG;
+    CopyBatch cvp;
     std::vector<PcholTask> pc;
     std::vector<FrobTask> ft;
     std::vector<FrobBlock> fb;
@@ -418,10 +422,15 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           // X = Vp^H [F_row ..., F_col^T ...]  (p x W, bulk precision), then G' = X X^H
           int64_t off = 0;
           char* Xb = (char*)(Sq + f.X);
+          const void* VA = Vp(q, f.i);
+          if (prec == P32) {
+            cvp.add(Vp(q, f.i), P64, n, n, p, Sq + f.Vpf, P32, n, n, p);
+            VA = Sq + f.Vpf;
+          }
           for (int id : f.rowf) {
             const int k = F.fill_pairs[id].second, lo = lo_of(q, k), w = F.n[k] - lo;
             gX.task(Xb + (size_t)off * p * es, p, p, w, 1.0, 0.0);
-            gX.pair(Vp(q, f.i), n, OP_H, FB(q, id) + (size_t)lo * n * es, n, OP_N, n);
+            gX.pair(VA, n, OP_H, FB(q, id) + (size_t)lo * n * es, n, OP_N, n);
             gX.close();
             off += w;
           }
@@ -429,7 +438,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
             for (int id : f.colf) {
               const int k = F.fill_pairs[id].first, lo = lo_of(q, k), w = F.n[k] - lo;
               gX.task(Xb + (size_t)off * p * es, p, p, w, 1.0, 0.0);
-              gX.pair(Vp(q, f.i), n, OP_H, FB(q, id) + (size_t)lo * es, F.n[k], OP_T, n);
+              gX.pair(VA, n, OP_H, FB(q, id) + (size_t)lo * es, F.n[k], OP_T, n);
               gX.close();
               off += w;
             }
@@ -481,10 +490,11 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
          "fill trace");
       lc.launches += 2;
     }
-    gX.pina = P64;
     run_gemm(lc, gM, prec, P64, P64, "gram");
-    // X = Vp^H F: complex128 result with the FP64 bulk, complex64 (FP32 pipe)
-    // with the complex64 bulk; then X X^H accumulates in FP64
+    // X = Vp^H F: complex128 result with the FP64 bulk, complex64 (from the
+    // complex64 copy of Vp, on the tensor cores) with the complex64 bulk; then
+    // X X^H accumulates to FP64 accuracy
+    run_copy(lc, cvp, "Vp to complex64");
     run_gemm(lc, gX, prec, prec, prec, "Vp^H*F");
     run_gemm(lc, gXX, P32, P64, P64, "X*X^H");
     run_gemm(lc, gT, P64, P64, P64, "gram*Vp");
