@@ -163,6 +163,15 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
       //    columns of its own pairs Q (pair q is owned by CTA q mod C) for all
       //    row pairs P, and the same columns of U (U G_Q); no other CTA
       //    touches them in this round.
+      // Entries that the next round's rotations read (A(k, k) and A(j, k) of
+      // its pairs j < k) are published by the thread that owns them here, from
+      // unrotated blocks too, into the other parity's buffer.
+      const int rn = (r + 1) % m, nbuf = (tr + 1) & 1;
+      auto publish = [&](int row, int col, const cd& v) {
+        if (row == col) Dd[nbuf * pe + col] = v.re;
+        else if (row < col && partner(col, rn) == row) Do[nbuf * pe + col] = v;
+      };
+      auto needed = [&](int row, int col) { return row == col || (row < col && partner(col, rn) == row); };
       {
         const int nown = rank < np ? (np - rank + C - 1) / C : 0;
         const int totA = nown * np, tot = totA + nown * p;
@@ -170,9 +179,15 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
           if (idx < totA) {
             const int q = rank + (idx / np) * C, P = idx % np;
             const double sq = js[q], sp = js[P];
-            if (sq == 0.0 && sp == 0.0) continue;
             const int aq = ja[q], bq = jb[q], ap = ja[P], bp = jb[P];
             const bool hq = bq < p, hp = bp < p;  // the padding index of an odd order has no row / column
+            if (sq == 0.0 && sp == 0.0) {
+              if (needed(ap, aq)) publish(ap, aq, A[ap + (size_t)aq * p]);
+              if (hp && needed(bp, aq)) publish(bp, aq, A[bp + (size_t)aq * p]);
+              if (hq && needed(ap, bq)) publish(ap, bq, A[ap + (size_t)bq * p]);
+              if (hp && hq && needed(bp, bq)) publish(bp, bq, A[bp + (size_t)bq * p]);
+              continue;
+            }
             cd x11 = A[ap + (size_t)aq * p], x21, x12, x22;
             x21.re = x21.im = x12.re = x12.im = x22.re = x22.im = 0;
             if (hp) x21 = A[bp + (size_t)aq * p];
@@ -227,6 +242,10 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
             if (hp) A[bp + (size_t)aq * p] = x21;
             if (hq) A[ap + (size_t)bq * p] = x12;
             if (hp && hq) A[bp + (size_t)bq * p] = x22;
+            publish(ap, aq, x11);
+            if (hp) publish(bp, aq, x21);
+            if (hq) publish(ap, bq, x12);
+            if (hp && hq) publish(bp, bq, x22);
           } else {
             const int e = idx - totA;
             const int q = rank + (e / p) * C, row = e % p;
@@ -244,20 +263,6 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
             U[row + (size_t)aq * p] = na;
             U[row + (size_t)bq * p] = nb;
           }
-        }
-      }
-      __syncthreads();
-      // 3. publish the entries of the own columns that the next round reads
-      {
-        const int rn = (r + 1) % m, nb = (tr + 1) & 1;
-        const int nown = rank < np ? (np - rank + C - 1) / C : 0;
-        for (int idx = threadIdx.x; idx < 2 * nown; idx += NT) {
-          const int q = rank + (idx >> 1) * C;
-          const int k = (idx & 1) ? jb[q] : ja[q];
-          if (k >= p) continue;
-          Dd[nb * pe + k] = A[k + (size_t)k * p].re;
-          const int j = partner(k, rn);
-          if (j < k) Do[nb * pe + k] = A[j + (size_t)k * p];
         }
       }
       ++tr;
