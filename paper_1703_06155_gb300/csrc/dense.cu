@@ -225,14 +225,16 @@ __global__ void __launch_bounds__(NT) k_jacobi(const EigTask* __restrict__ tasks
         if (b < p) {
           const double app = A[a + (size_t)a * p].re, aqq = A[b + (size_t)b * p].re;
           const cd apq = A[a + (size_t)b * p];
-          const double g = sqrt(apq.re * apq.re + apq.im * apq.im);
+          const double g2 = apq.re * apq.re + apq.im * apq.im;
+          const double g = sqrt(g2);  // the threshold test of the convergence check
+          const double rg = g2 > 0.0 ? rsqrt(g2) : 0.0;  // 1/g, issued beside the test
           if (g > gmin && g > 1e-17 * sqrt(fabs(app * aqq))) {
             any_rot = 1;
-            er = apq.re / g;
-            ei = apq.im / g;
-            const double zeta = (aqq - app) / (2.0 * g);
+            er = apq.re * rg;
+            ei = apq.im * rg;
+            const double zeta = (aqq - app) * 0.5 * rg;
             const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+            c = rsqrt(1.0 + tt * tt);
             s = tt * c;
           }
         }

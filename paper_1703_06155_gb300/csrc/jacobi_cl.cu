@@ -139,13 +139,17 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
           const int bi = tr & 1;
           const double app = Dd[bi * pe + a], aqq = Dd[bi * pe + b];
           const cd apq = Do[bi * pe + b];
-          const double g = sqrt(apq.re * apq.re + apq.im * apq.im);
+          const double g2 = apq.re * apq.re + apq.im * apq.im;
+          const double g = sqrt(g2);  // the threshold test of the convergence check
+          // one reciprocal square root (issued beside the test) gives 1/g for
+          // e^{i phi} and zeta; the dependent chain is rsqrt -> sqrt -> divide -> rsqrt
+          const double rg = g2 > 0.0 ? rsqrt(g2) : 0.0;
           if (g > gmin && g > 1e-17 * sqrt(fabs(app * aqq))) {
-            er = apq.re / g;
-            ei = apq.im / g;
-            const double zeta = (aqq - app) / (2.0 * g);
+            er = apq.re * rg;
+            ei = apq.im * rg;
+            const double zeta = (aqq - app) * 0.5 * rg;
             const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+            c = rsqrt(1.0 + tt * tt);
             s = tt * c;
             flags[sweep] = 1;
           }
