@@ -151,17 +151,39 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
       if (tid == 0) { cand_v[s] = bv; cand_i[s] = bi; cand_t[s] = ts; }
     }
   };
-  // reduce the C published candidates of slot s (all CTAs get the same)
+  // reduce the C published candidates of slot s (all CTAs get the same):
+  // lane q of warp 0 reads candidate q through distributed shared memory
+  // (one remote read per candidate and CTA), a warp reduction (the argmax
+  // rule is order-free: larger value, ties -> lower row; the trace sum runs
+  // in a fixed tree order), then the result to the CTA through shared memory
+  __shared__ double g_dv, g_trs;
+  __shared__ int g_pc;
   auto gather = [&](int s, double& dv, int& pc, double& trs) {
-    dv = -1;
-    pc = 0x7fffffff;
-    trs = 0;
-    for (int q = 0; q < C; ++q) {
-      const double v = *cl.map_shared_rank(&cand_v[s], q);
-      const int i = *cl.map_shared_rank(&cand_i[s], q);
-      trs += *cl.map_shared_rank(&cand_t[s], q);
-      if (better(v, i, dv, pc)) { dv = v; pc = i; }
+    if (warp == 0) {
+      dv = -1;
+      pc = 0x7fffffff;
+      trs = 0;
+      if (lane < C) {
+        dv = *cl.map_shared_rank(&cand_v[s], lane);
+        pc = *cl.map_shared_rank(&cand_i[s], lane);
+        trs = *cl.map_shared_rank(&cand_t[s], lane);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, dv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, pc, o);
+        trs += __shfl_xor_sync(0xffffffffu, trs, o);
+        if (better(ov, oi, dv, pc)) { dv = ov; pc = oi; }
+      }
+      if (lane == 0) {
+        g_dv = dv;
+        g_pc = pc;
+        g_trs = trs;
+      }
     }
+    __syncthreads();
+    dv = g_dv;
+    pc = g_pc;
+    trs = g_trs;
   };
 
   // ---------------------------------------------------- pivoted Cholesky
@@ -258,13 +280,47 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
       T[j + (size_t)j * r].im = ti_;
     }
   };
-  // apply H_j^H to column c (one warp)
+  // apply H_j^H to column c (one warp); vs = reflector j in shared memory
+  // (vs[j] = 1).  A column of up to 32 WR entries stays in registers between
+  // the dot product and the update, its loads all in flight together.
+  constexpr int WR = 12;
+  cd* vs = prow;  // the pivot-row buffer is free after the Cholesky
   auto apply_col = [&](int j, int c, double tr_, double ti_) {
     double dr = 0, di = 0;
+    if (p - j <= 32 * WR) {
+      cd w[WR];
+#pragma unroll
+      for (int u = 0; u < WR; ++u) {
+        const int i = j + lane + 32 * u;
+        if (i < p) w[u] = L[i + (size_t)c * p];
+      }
+#pragma unroll
+      for (int u = 0; u < WR; ++u) {
+        const int i = j + lane + 32 * u;
+        if (i < p) {
+          const cd v = vs[i];
+          dr += v.re * w[u].re + v.im * w[u].im;
+          di += v.re * w[u].im - v.im * w[u].re;
+        }
+      }
+      dr = wsum(dr);
+      di = wsum(di);
+      const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
+#pragma unroll
+      for (int u = 0; u < WR; ++u) {
+        const int i = j + lane + 32 * u;
+        if (i < p) {
+          const cd v = vs[i];
+          w[u].re -= v.re * fr - v.im * fi;
+          w[u].im -= v.re * fi + v.im * fr;
+          L[i + (size_t)c * p] = w[u];
+        }
+      }
+      return;
+    }
     for (int i = j + lane; i < p; i += 32) {
       const cd w = L[i + (size_t)c * p];
-      cd v;
-      if (i == j) { v.re = 1; v.im = 0; } else v = L[i + (size_t)j * p];
+      const cd v = vs[i];
       dr += v.re * w.re + v.im * w.im;
       di += v.re * w.im - v.im * w.re;
     }
@@ -272,8 +328,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
     di = wsum(di);
     const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
     for (int i = j + lane; i < p; i += 32) {
-      cd v;
-      if (i == j) { v.re = 1; v.im = 0; } else v = L[i + (size_t)j * p];
+      const cd v = vs[i];
       cd w = L[i + (size_t)c * p];
       w.re -= v.re * fr - v.im * fi;
       w.im -= v.re * fi + v.im * fr;
@@ -286,6 +341,16 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
   }
   for (int j = 0; j < r; ++j) {
     const double tr_ = T[j + (size_t)j * r].re, ti_ = T[j + (size_t)j * r].im;
+    // reflector j (written by its owner before the last cluster barrier) to shared memory
+    for (int i = j + tid; i < p; i += NT) {
+      if (i == j) {
+        vs[i].re = 1;
+        vs[i].im = 0;
+      } else {
+        vs[i] = L[i + (size_t)j * p];
+      }
+    }
+    __syncthreads();
     if (!(tr_ == 0.0 && ti_ == 0.0)) {
       // own columns c > j, c = rank (mod C)
       int first = j + 1 + ((rank - (j + 1)) % C + C) % C;
