@@ -19,7 +19,7 @@ trailing k~_c ("kept") stay in Z_cur.  Inadmissible blocks are dense; an
 admissible block carries its original coupling S (in the level's incoming
 bases) plus one summed fill-in F (eq. 15 and the paragraph after it).
 
-Readings of the paper (each listed in the design doc):
+Readings of the paper where it is silent or ambiguous:
   R1 one cluster basis per cluster serves rows and columns (eq. 2); for a
      general, non-symmetric matrix Step 0 adds the column fill-ins
      F_{k,i}^T conj(F_{k,i}) to the row Gram of eq. (16).

@@ -1,6 +1,6 @@
 """Cluster tree (Sec. II) and block partition by the admissibility test eq. (1).
 
-Readings (listed in the design doc):
+Readings of what the paper leaves open:
   * bisection of the cluster's points along the longest axis of their bounding
     box (ties -> lowest axis), stable order by (coordinate, global index), the
     left child takes the first ceil(n/2) points;
