@@ -1,0 +1,51 @@
+"""Host logic of bench.py (CPU): the roofline entry takes the flop-counted
+kernel class with the most device time and measures it against the peak of
+the arithmetic unit the library recorded for that class."""
+import bench
+
+
+def _stats(kernels):
+    return {"prec": "mixed", "kernels": kernels}
+
+
+CLOCKS = {"sm_max_mhz": 2070.0}
+
+
+def test_roofline_picks_longest_flop_counted_class():
+    st = _stats({
+        "jacobi_cluster": {"launches": 17, "ms": 100.0, "flops": 0},       # no flop count: not a candidate
+        "gemm:schur": {"launches": 33, "ms": 25.0, "flops": 1.0e12, "pipe": "tcgen05_tf32x3"},
+        "gemm:matvec couple": {"launches": 2, "ms": 36.0, "flops": 3.3e10, "pipe": "fp64"},
+    })
+    r = bench.roofline(st, CLOCKS)
+    assert r["kernel"] == "gemm:matvec couple" and r["launches"] == 2
+    assert abs(r["avg_launch_ms"] - 18.0) < 1e-12
+
+
+def test_roofline_peak_follows_the_recorded_pipe():
+    pk = bench.fp_peaks(CLOCKS)
+    fp64 = bench.roofline(_stats({"g": {"launches": 1, "ms": 1.0, "flops": 1e9, "pipe": "fp64"}}), CLOCKS)
+    assert fp64["bound"] == "alu" and abs(fp64["peak"] - pk["fp64"]) < 1e-12
+    assert abs(pk["fp64"] - 152 * 2 * 2 * 2070e6 / 1e12) < 1e-12
+    fp32 = bench.roofline(_stats({"g": {"launches": 1, "ms": 1.0, "flops": 1e9, "pipe": "fp32"}}), CLOCKS)
+    assert abs(fp32["peak"] - pk["fp32"]) < 1e-12
+    # FP64-accurate Grams on the FP32 pipe: 36 FP32 operations per 8 algorithmic flops
+    df = bench.roofline(_stats({"g": {"launches": 1, "ms": 1.0, "flops": 1e9, "pipe": "fp32_df"}}), CLOCKS)
+    assert abs(df["peak"] - 152 * 128 * 2070e6 * 8 / 36 / 1e12) < 1e-9
+    # tensor-core tiles: the measured bf16 rate x TF32/bf16 ratio / 3 (hi / lo split)
+    tc = bench.roofline(_stats({"g": {"launches": 1, "ms": 1.0, "flops": 1e9, "pipe": "tcgen05_tf32x3"}}), CLOCKS)
+    pv, _ = bench.peaks()
+    bf16 = pv.get("bf16_tflops_sustained", pv["bf16_tflops"])
+    assert tc["bound"] == "tensor" and abs(tc["peak"] - bf16 * (1.1 / 2.25) / 3.0) < 1e-9
+    for r in (fp64, fp32, df, tc):
+        assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15 and abs(r["achieved"] - 1.0) < 1e-12
+
+
+def test_roofline_without_flop_counts_is_absent():
+    assert bench.roofline(_stats({"jacobi": {"launches": 3, "ms": 5.0, "flops": 0}}), CLOCKS) is None
+
+
+def test_grid_workload_names_match_between_arms():
+    class A:
+        grid, chi, eps, nrhs = 32, 3.0, 1e-6, 16
+    assert bench.grid_workload(A) == "grid32 (N=32768), chi=3, eps=1e-06, nrhs=16, leaf 64, eta 1"

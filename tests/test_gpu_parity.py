@@ -207,6 +207,28 @@ def test_autotune_keeps_results(dev):
     assert rel(x, xe) < 1e-10
 
 
+@pytest.mark.parametrize("tc", [2, 0])
+def test_split_k_tiles_match_direct_tiles(dev, tc):
+    # a split-K target far above the GPU's CTA count cuts the long products of
+    # every GEMM launch into K chunks whose partial tiles (tensor-core or FMA
+    # kernels) are summed by the reduction pass: FP32-close to the default plan,
+    # and both refine to the exact H^2 solution
+    eps = 1e-6
+    n = 16
+    H = h2_problem(n, 64, eps)
+    A1 = gpu_ctx(H, tensor_cores=tc, split_target=20000)
+    A0 = gpu_ctx(H, tensor_cores=tc)
+    A1.factorize(eps, "mixed")
+    A0.factorize(eps, "mixed")
+    b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 2, 31)).to(dev)
+    x1, x0 = A1.solve(b).cpu().numpy(), A0.solve(b).cpu().numpy()
+    assert rel(x1, x0) < 1e-4
+    Zd = h2_dense(n, 64, eps)
+    xe = from_tree(H, np.linalg.solve(Zd, to_tree(H, b.cpu().numpy())))
+    xr = A1.solve(b, refine=True, tol=1e-12, max_iter=30).cpu().numpy()
+    assert rel(xr, xe) < 1e-10
+
+
 def test_gram_emulation_matches_fp64_grams(dev):
     # Step-0 Grams of complex64 operands as exact products summed in
     # double-float on the FP32 pipe (flushed to FP64 every 8 terms) or with
