@@ -86,7 +86,7 @@ typedef struct {
                             0 (default): launched one by one              */
   int split_target;      /* batched GEMM: split the K range of long products
                             until a launch has about this many CTAs
-                            (0 = default, 4 per SM)                         */
+                            (0 = default, 8 per SM)                         */
   int cluster_max;       /* Step 0: most CTAs in the thread-block cluster of
                             one subspace / eigen problem (1..16; 0 = 16)    */
   int tile_policy;       /* batched GEMM tile shape: 0 (default) least padded

@@ -22,7 +22,7 @@ DEFAULT_SPACE = {
     "tensor_cores": [2, 1, 0],
     "gram_emulation": [1, 0],
     "tile_policy": [0, 1],
-    "split_target": [0, 304, 1216],
+    "split_target": [0, 608, 2432],
     "cluster_max": [16, 8],
     "apply_path": [2, 1],
 }

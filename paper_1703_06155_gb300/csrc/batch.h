@@ -40,7 +40,7 @@ struct GemmBatch {
   int pina = -1;         // precision of the A operands if it differs from B's
   // fp64: FP64-accumulating launch (the FP64 pipe bounds it, so padding is
   // what costs); FP32 launches keep 64-wide tiles unless padding dominates
-  int64_t plan(int target_ctas = 4 * 152, bool fp64 = true, int policy = 0) {
+  int64_t plan(int target_ctas = 8 * 152, bool fp64 = true, int policy = 0) {
     tl.clear();
     alg_flops = 0;
     std::vector<int64_t> kt(t.size(), 0);

@@ -40,7 +40,7 @@ using namespace h2k;
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what) {
   if (b.empty()) return;
   HostScope hs(c, "run_gemm");
-  const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 4 * 152, pacc == P64, c.opts.tile_policy);
+  const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 8 * 152, pacc == P64, c.opts.tile_policy);
   if (b.tl.empty()) return;
   void* wsp = nullptr;
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
