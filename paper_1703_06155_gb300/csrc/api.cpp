@@ -175,8 +175,6 @@ std::vector<std::vector<double>> col_norms_group(const std::vector<h2_ctx*>& xs,
 void gpu_gram(h2_ctx* x, double k, double w, const std::vector<std::vector<int64_t>>& rows,
               const std::vector<std::vector<int64_t>>& ranges, std::vector<std::vector<cplx>>& G) {
   Ctx& c = x->c;
-  const H2Host& H = c.H;
-  const int64_t N = H.tree.N;
   const int nc = (int)rows.size();
   std::vector<int64_t> flat;
   std::vector<size_t> roff(nc), goff(nc);
