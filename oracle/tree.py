@@ -7,7 +7,8 @@ Readings of what the paper leaves open:
   * every cluster is split down to one depth L, the smallest with
     ceil(N / 2^L) <= leafsize, so level l holds exactly 2^l clusters as the
     paper's Algorithm 1 assumes;
-  * admissibility uses centres and radii: ||c_t - c_s|| >= eta (r_t + r_s),
+  * admissibility uses centres and radii: ||c_t - c_s|| >= eta (r_t + r_s)
+    for t != s (a cluster is never admissible with itself),
     c = bounding-box centre, r = max distance from c to a point of the cluster.
 Clusters at level l are numbered 0..2^l-1; children of c are 2c and 2c+1.
 """
@@ -77,7 +78,10 @@ class Partition:
             nxt = []
             for t, s in cur:
                 d = np.linalg.norm(tree.centre[l][t] - tree.centre[l][s])
-                if d >= eta * (tree.radius[l][t] + tree.radius[l][s]):
+                # a cluster is never admissible with itself (eq. (1) holds for
+                # it only when its diameter is zero, and its block holds the
+                # singular self term)
+                if t != s and d >= eta * (tree.radius[l][t] + tree.radius[l][s]):
                     self.adm[l].append((t, s))
                 else:
                     self.inad[l].append((t, s))

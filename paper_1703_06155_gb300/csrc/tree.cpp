@@ -5,8 +5,9 @@
 //    ceil(n/2) go to the left child;
 //  * all clusters split to one depth L = min{L : ceil(N/2^L) <= leafsize}, so
 //    level l has exactly 2^l clusters;
-//  * (t, s) admissible iff ||c_t - c_s|| >= eta (r_t + r_s), c = bounding-box
-//    centre, r = largest distance from c to a point of the cluster.
+//  * (t, s) admissible iff t != s and ||c_t - c_s|| >= eta (r_t + r_s),
+//    c = bounding-box centre, r = largest distance from c to a point of the
+//    cluster.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -93,7 +94,9 @@ void build_partition(const Tree& t, double eta, Partition& p) {
         const double v = t.centre[l][3 * a + q] - t.centre[l][3 * b + q];
         d2 += v * v;
       }
-      if (std::sqrt(d2) >= eta * (t.radius[l][a] + t.radius[l][b])) {
+      // a cluster is never admissible with itself (eq. (1) holds for it only
+      // when its diameter is zero, and its block holds the singular self term)
+      if (a != b && std::sqrt(d2) >= eta * (t.radius[l][a] + t.radius[l][b])) {
         p.adm[l].push_back({a, b});
       } else {
         p.inad[l].push_back({a, b});

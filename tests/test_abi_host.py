@@ -164,3 +164,23 @@ def test_set_opts_validates(libh2):
     o = default_opts()
     assert (o.leafsize, o.tensor_cores, o.gram_emulation, o.profile) == (64, 2, 1, 0)
     a.close()
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 64, 65, 129])
+def test_degenerate_sizes_build(libh2, N):
+    # one point, fewer points than a leaf, exactly one leaf, one point past a
+    # leaf (a ragged split): the host build still matches the oracle's tree and
+    # reproduces the dense matrix
+    from paper_1703_06155_gb300 import H2
+    pts = np.ascontiguousarray(inputs.grid_points(6, H)[:N])
+    chi = inputs.chi_uniform(N, 3.0)
+    eps = 1e-6
+    A = H2.build(pts, K, H, chi, eps, host_only=1)
+    r = A.export()
+    T = otree.ClusterTree(pts, 64)
+    assert np.array_equal(T.perm, r["perm"]) and r["L"] == T.L
+    Z, _ = dense_from_rep(r)
+    idx = r["perm"]
+    Zex = kernel.entries(pts, chi, idx, idx, K, H)
+    assert np.linalg.norm(Z - Zex) <= 10 * eps * np.linalg.norm(Zex)
+    A.close()

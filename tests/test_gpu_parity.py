@@ -273,3 +273,28 @@ def test_tensor_core_bulk_matches_fma_bulk(dev, tc):
     assert rel(x1, xe) < 1e-4
     xr = A1.solve(b, refine=True, tol=1e-12, max_iter=30).cpu().numpy()
     assert rel(xr, xe) < 1e-10
+
+
+@pytest.mark.parametrize("N", [1, 7, 65, 129])
+def test_degenerate_sizes_solve(dev, N):
+    # one point, fewer points than a leaf (the whole matrix is the final block),
+    # one point past a leaf and a ragged two-level tree: GPU build (library
+    # construction), FP64 and mixed factorizations, solves against the exact
+    # dense solution of the same points
+    from oracle import kernel
+    from paper_1703_06155_gb300 import H2
+    pts = np.ascontiguousarray(inputs.grid_points(6, 1.0 / 16.0)[:N])
+    chi = inputs.chi_uniform(N, 3.0)
+    eps = 1e-8
+    A = H2.build(pts, 2 * np.pi, 1.0 / 16.0, chi, eps)
+    idx = np.arange(N)
+    Z = kernel.entries(pts, chi, idx, idx, 2 * np.pi, 1.0 / 16.0)
+    b = inputs.rhs_gaussian(N, 2, 37)
+    xe = np.linalg.solve(Z, b)
+    A.factorize(eps, "fp64")
+    x = A.solve(torch.from_numpy(b).to(dev)).cpu().numpy()
+    assert rel(x, xe) < 1e-6
+    A.factorize(eps, "mixed")
+    xm = A.solve(torch.from_numpy(b).to(dev), refine=True, tol=1e-12, max_iter=30).cpu().numpy()
+    assert rel(xm, xe) < 1e-6
+    A.close()
