@@ -11,6 +11,7 @@ from oracle import dense, factor, h2, kernel, tree
 from paper_1703_06155_gb300 import inputs
 
 from _problems import H, K, factorization, h2_dense, h2_problem
+from _h2io import from_tree, to_tree
 
 # --------------------------------------------------------------- kernel ----
 
@@ -256,6 +257,29 @@ def test_trivial_cases():
     T = ClusterTree(pts, 16)
     P = Partition(T, 1e9)
     assert sum(len(a) for a in P.adm) == 0
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 65, 129])
+def test_degenerate_sizes(N):
+    # one point (never admissible with itself), fewer points than a leaf (the
+    # whole matrix is one near-field block), one point past a leaf and a
+    # ragged two-level tree: exact at eps = 0, within eps of the dense solve
+    from oracle import kernel
+    from oracle.tree import ClusterTree, Partition
+    pts = np.ascontiguousarray(inputs.grid_points(6, H)[:N])
+    chi = inputs.chi_uniform(N, 3.0)
+    T = ClusterTree(pts, 64)
+    P = Partition(T, 1.0)
+    assert all((t, t) not in P.adm[l] for l in range(T.L + 1) for t in range(2 ** l))
+    idx = np.arange(N)
+    Z = kernel.entries(pts, chi, idx, idx, K, H)
+    b = inputs.rhs_gaussian(N, 1, 3)[:, 0]
+    xe = np.linalg.solve(Z, b)
+    for eps, tol in ((0.0, 1e-12), (1e-6, 1e-5)):
+        Hm = h2.build(pts, chi, K, H, leafsize=64, eps=max(eps, 1e-12))
+        Fz = factor.factorize(Hm, eps)
+        x = from_tree(Hm, factor.solve(Fz, to_tree(Hm, b)))
+        assert np.linalg.norm(x - xe) <= tol * np.linalg.norm(xe), (eps, np.linalg.norm(x - xe))
 
 
 # ---------------------------------------------- planted mistakes (CPU) ----
