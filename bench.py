@@ -110,7 +110,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def grid_workload(args):
+def workload_name(args):
     """The grid workload's name (both arms)."""
     n = args.grid
     return "grid%d (N=%d), chi=%g, eps=%g, nrhs=%d, leaf 64, eta 1" % (n, n ** 3, args.chi, args.eps, args.nrhs)
@@ -236,7 +236,7 @@ def run_reference(args):
         "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128", "data": "synthetic",
-        "config": {"workload": grid_workload(args), "precision": "fp64 (oracle)",
+        "config": {"workload": workload_name(args), "precision": "fp64 (oracle)",
                    "sample": "16^3 sub-grid of the workload, same h, chi, eps (N=%d)" % N},
         "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": "oracle factorize + refined solve of the 16^3 sub-grid (N=%d)" % N},
@@ -542,7 +542,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 bulk + c128 rank/refine" if args.prec == "mixed" else "c128",
         "data": "synthetic",
-        "config": {"workload": grid_workload(args), "precision": args.prec,
+        "config": {"workload": workload_name(args), "precision": args.prec,
             "l2": "inputs larger than L2 (near-field arena %.0f MB)" % (st.get("dev_bytes", 0) / 1e6)},
         "factorize_ms": float(np.mean(fac_ms)), "solve_iters": solve_info.get("iters"),
         "final_residual": res, "fp64": fp64,
