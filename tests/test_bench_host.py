@@ -45,7 +45,7 @@ def test_roofline_without_flop_counts_is_absent():
     assert bench.roofline(_stats({"jacobi": {"launches": 3, "ms": 5.0, "flops": 0}}), CLOCKS) is None
 
 
-def test_both_arms_name_the_same_workload():
+def test_reference_arm_names_our_config():
     class A:
         grid, chi, eps, nrhs = 32, 3.0, 1e-6, 16
     assert bench.workload_name(A) == "grid32 (N=32768), chi=3, eps=1e-06, nrhs=16, leaf 64, eta 1"
