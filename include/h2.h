@@ -215,14 +215,20 @@ h2_status h2_matvec(h2_ctx* ctx, const void* x, void* y, int nrhs,
  *   flags     0 or H2_ADJOINT
  * All temporaries (permuted vectors, level coefficients, task descriptors)
  * live in one static device array of 32 MiB that every GPU which loads the
- * library holds until the process exits.  Sizes whose temporaries exceed it
- * (about 2 N nrhs + 2 (sum of ranks) nrhs complex128 plus the task lists)
- * are rejected with H2_EINVAL and a message.  The call makes no cudaMalloc,
- * cudaFree or other allocating call.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array, which keeps the last
- * call's contents (every entry a call reads it writes first), so calls that
- * overlap on the GPU (other streams, other threads) race: serialize them.
+ * library's module holds until the process exits.  Sizes whose temporaries
+ * exceed it (about 2 N nrhs + 2 (sum of ranks) nrhs complex128 plus the task
+ * lists) are rejected with H2_EINVAL and a message before any work is
+ * enqueued.  The call makes no cudaMalloc, cudaFree or other allocating call.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress).  Under CUDA's lazy module loading (the default
+ * since CUDA 12.2) that lookup also loads the module that holds the array,
+ * so the 32 MiB are reserved on that device at this first call: make it
+ * during set-up, before device memory is reserved up front, and before any
+ * stream capture.  x or y in host memory: H2_EINVAL.  A stream that is being
+ * captured: H2_ESTATE, nothing enqueued.  All calls share the array, which
+ * keeps the last call's contents (every entry a call reads it writes
+ * first), so calls that overlap on the GPU (other streams, other threads)
+ * race: serialize them.
  */
 h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* x, void* y, int nrhs,
                             unsigned flags, void* stream);

@@ -45,8 +45,6 @@ def build(force=False, verbose=False, jobs=None):
                 and os.path.getmtime(obj) >= hmt):
             return obj, None
         cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
-        if src.endswith(".cpp"):
-            cmd[1:1] = ["-x", "cu"] if False else []
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             return obj, "%s\n%s\n%s" % (" ".join(cmd), r.stdout, r.stderr)

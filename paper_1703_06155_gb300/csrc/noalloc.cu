@@ -9,7 +9,10 @@
 //
 // The array's host-side name is only a stand-in: its device address is taken
 // once per device with cudaGetSymbolAddress (with that device current) and
-// passed to the kernels.
+// passed to the kernels.  With CUDA's lazy module loading (the default since
+// CUDA 12.2) that lookup is also what loads this file's module on the device,
+// so the 32 MiB are reserved at the first call on each device, not when the
+// library is loaded.
 #include <mutex>
 #include <unordered_map>
 
@@ -53,8 +56,7 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 using namespace h2;
 using namespace h2k;
 
-extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout, int nrhs, unsigned flags,
-                                       void* stream) {
+static h2_status matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout, int nrhs, unsigned flags, void* stream) {
   if (!ctx) return H2_EINVAL;
   Ctx& c = *ctx_core(ctx);
   if (c.opts.host_only) {
@@ -65,11 +67,33 @@ extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout,
     c.err = "h2_matvec_noalloc: bad argument (device x, y distinct; nrhs > 0; flags: H2_ADJOINT only)";
     return H2_EINVAL;
   }
+  for (const void* v : {xin, (const void*)yout}) {
+    cudaPointerAttributes at{};
+    const cudaError_t pe = cudaPointerGetAttributes(&at, v);
+    if (pe != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      c.err = "h2_matvec_noalloc: x and y must be device (or managed) memory";
+      return H2_EINVAL;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      c.err = "h2_matvec_noalloc: cudaStreamIsCapturing failed";
+      return H2_ECUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) {
+      c.err = "h2_matvec_noalloc: the stream is being captured (the call uploads its task lists from host memory "
+              "and synchronizes the stream); nothing was enqueued";
+      return H2_ESTATE;
+    }
+  }
   const bool adj = flags & H2_ADJOINT;
   const H2Host& H = c.H;
   const int L = H.L, l0 = H.l0;
   const int64_t N = H.tree.N;
-  cudaStream_t s = (cudaStream_t)stream;
   std::string err;
   unsigned char* base = (unsigned char*)scratch_address(err);
   if (!base) {
@@ -101,11 +125,6 @@ extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout,
   cd* yhb = (cd*)(base + off);
   off += hbytes;
   const size_t task_base = off;
-  if (task_base > kNoAllocBytes) {
-    c.err = "h2_matvec_noalloc: N * nrhs too large for the " + std::to_string(kNoAllocBytes >> 20) +
-            " MiB static scratch (needs " + std::to_string(task_base >> 20) + " MiB before task lists)";
-    return H2_EINVAL;
-  }
   auto xh = [&](int l, int t) { return xhb + lb[l] + koff[l][t]; };
   auto yh = [&](int l, int t) { return yhb + lb[l] + koff[l][t]; };
   const cd* Vd = (const cd*)c.dV.p;
@@ -203,9 +222,14 @@ extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout,
     o.tl = put(g.tl.data(), g.tl.size() * sizeof(GemmTile));
     offs.push_back(o);
   }
+  // one bound on the whole layout (vectors, level coefficients, task lists),
+  // checked before anything is enqueued; the stage pointers computed above
+  // are not dereferenced on the host
   if (task_base + host.size() > kNoAllocBytes) {
     c.err = "h2_matvec_noalloc: problem too large for the " + std::to_string(kNoAllocBytes >> 20) +
-            " MiB static scratch (needs " + std::to_string((task_base + host.size()) >> 20) + " MiB)";
+            " MiB static scratch (needs " + std::to_string((task_base + host.size() + (1 << 20) - 1) >> 20) +
+            " MiB: " + std::to_string(task_base >> 20) + " MiB of vectors, " + std::to_string(host.size() >> 10) +
+            " KiB of task lists)";
     return H2_EINVAL;
   }
   unsigned char* dtask = base + task_base;
@@ -234,4 +258,25 @@ extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout,
   if (e != cudaSuccess) return fail_cuda(e, "sync");
   c.err.clear();
   return H2_OK;
+}
+
+// Exceptions of the host-side planning (allocation of the host task lists,
+// message strings) become an h2_status here: nothing throws across the ABI.
+extern "C" h2_status h2_matvec_noalloc(h2_ctx* ctx, const void* xin, void* yout, int nrhs, unsigned flags,
+                                       void* stream) {
+  try {
+    return matvec_noalloc(ctx, xin, yout, nrhs, flags, stream);
+  } catch (const Err& e) {
+    if (ctx) ctx_core(ctx)->err = "h2_matvec_noalloc: " + e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx_core(ctx)->err = "h2_matvec_noalloc: host allocation of the task lists failed";
+    return H2_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx_core(ctx)->err = std::string("h2_matvec_noalloc: internal: ") + e.what();
+    return H2_EINTERNAL;
+  } catch (...) {
+    if (ctx) ctx_core(ctx)->err = "h2_matvec_noalloc: internal error";
+    return H2_EINTERNAL;
+  }
 }
