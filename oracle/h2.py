@@ -40,6 +40,15 @@ def _far_columns(tree, part):
     return far
 
 
+def eps_rank(sv, eps):
+    """Number of singular values kept at relative accuracy eps: sigma > eps * sigma_1
+    (sv in descending order; 0 for an empty or zero block)."""
+    sv = np.asarray(sv)
+    if sv.size == 0 or sv[0] == 0.0:
+        return 0
+    return int(np.sum(sv > eps * sv[0]))
+
+
 def build(pts, chi, k, h, leafsize=64, eta=1.0, eps=1e-6, sign=1.0):
     """Exact nested-basis H^2 approximation of Z (see module docstring)."""
     tree = ClusterTree(pts, leafsize)
@@ -57,10 +66,7 @@ def build(pts, chi, k, h, leafsize=64, eta=1.0, eps=1e-6, sign=1.0):
         if M.shape[1] == 0 or M.shape[0] == 0:
             return np.zeros((M.shape[0], 0), dtype=np.complex128)
         U, sg, _ = np.linalg.svd(M, full_matrices=False)
-        if sg[0] == 0.0:
-            return np.zeros((M.shape[0], 0), dtype=np.complex128)
-        r = int(np.sum(sg > eps * sg[0]))
-        return U[:, :r].copy()
+        return U[:, :eps_rank(sg, eps)].copy()
 
     full = [dict() for _ in range(L + 1)]  # full basis per level (pins only)
     H.V = {}
