@@ -56,14 +56,13 @@ def parse():
                    help="Step 2 / panel applications: 0 auto, 1 in-place kernel, 2 GEMM + copy")
     p.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                    help="complex64 GEMM tiles: 2 tcgen05, 1 warp-level TF32 MMA, 0 FP32 FMA (default: library's)")
-    p.add_argument("--no-kernel-events", action="store_true",
-                   help="no per-launch CUDA events in the timed steps (no kernel table / roofline)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison factorization (large grids)")
     p.add_argument("--arena-cap-gb", type=float, default=0.0,
                    help="cap on the library's device memory (h2_opts.arena_cap_bytes; 0 = none)")
     p.add_argument("--json-extra", action="store_true", help="print per-level stats")
     p.add_argument("--profile-step", action="store_true",
                    help="build, then exactly one factorize + refined solve (for profiler captures)")
+    p.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -135,19 +134,30 @@ def fp_peaks(clocks):
     return {"fp64": 152 * 2 * 2 * f * 1e6 / 1e12, "fp32": 152 * 128 * 2 * f * 1e6 / 1e12, "mhz": f}
 
 
-def roofline(st, clocks):
-    """Roofline entry for the kernel class with the most device time among the
-    classes with an algorithmic flop count (per-launch CUDA events of the last
-    timed step, library profiling mode)."""
+def roofline(st, clocks, kernel=None):
+    """Roofline entry of one kernel class (default: the class with the most
+    device time among the classes with an algorithmic flop or byte count),
+    from the per-launch CUDA events of the instrumented pass."""
     kern = st.get("kernels", {})
-    cands = [(k, v) for k, v in kern.items() if v.get("flops", 0) > 0 and v["ms"] > 0]
+    cands = [(k, v) for k, v in kern.items() if (v.get("flops", 0) > 0 or v.get("bytes", 0) > 0) and v["ms"] > 0]
+    if kernel is not None:
+        cands = [(k, v) for k, v in cands if k == kernel]
     if not cands:
         return None
     k, v = max(cands, key=lambda kv: kv[1]["ms"])
     pk = fp_peaks(clocks)
+    if v.get("flops", 0) <= 0:
+        # memory-bound class (copies, traces): algorithmic bytes over time
+        pv, src = peaks()
+        achieved = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+        return {"kernel": k, "pipe": "hbm", "achieved": achieved, "unit": "GB/s", "bound": "hbm",
+                "peak": pv["hbm_gbs"], "peak_source": "%s HBM copy bandwidth" % src, "frac": achieved / pv["hbm_gbs"],
+                "traffic": None, "launches": v["launches"], "avg_launch_ms": v["ms"] / v["launches"],
+                "bytes_per_launch": v["bytes"] / v["launches"]}
     achieved = v["flops"] / (v["ms"] * 1e-3) / 1e12
     out = {"kernel": k, "pipe": v.get("pipe"), "achieved": achieved, "unit": "TFLOP/s",
-           "traffic": measured_traffic(k), "launches": v["launches"], "avg_launch_ms": v["ms"] / v["launches"]}
+           "traffic": measured_traffic(k), "launches": v["launches"], "avg_launch_ms": v["ms"] / v["launches"],
+           "flops_per_launch": v["flops"] / v["launches"]}
     pipe = v.get("pipe") or ("fp64" if st.get("prec") == "fp64" else "fp32")
     if pipe.endswith("tf32x3"):
         # complex64 products as three TF32 tensor-core products each: the
@@ -174,6 +184,22 @@ def roofline(st, clocks):
             "2 FP64" if fp64 else "128 FP32", pk["mhz"], "FP64 pipe" if fp64 else "FP32 pipe"))
     out["frac"] = achieved / out["peak"]
     return out
+
+
+def roofline_table(st, clocks, top=14):
+    """One roofline row per kernel class with an algorithmic count, by device time."""
+    rows = []
+    kern = st.get("kernels", {})
+    for k in sorted(kern, key=lambda k: -kern[k]["ms"]):
+        r = roofline(st, clocks, kernel=k)
+        if r is None:
+            continue
+        rows.append({"kernel": k, "ms": round(kern[k]["ms"], 3), "launches": kern[k]["launches"],
+                     "pipe": r["pipe"], "bound": r["bound"], "achieved": round(r["achieved"], 4),
+                     "unit": r["unit"], "peak": round(r["peak"], 3), "frac": round(r["frac"], 4)})
+        if len(rows) >= top:
+            break
+    return rows
 
 
 def measured_traffic(kernel_class):
@@ -215,6 +241,14 @@ def oracle_sample(args, repeat=1):
     return N, times, hist[-1]
 
 
+def oracle_precision(args):
+    """What the oracle computes in the sample (numpy complex128 arithmetic)."""
+    if args.prec == "mixed":
+        return "mixed-precision emulation: complex128 arithmetic with the bulk rounded to complex64, FP64 rank " \
+               "decisions and refinement"
+    return "complex128 throughout"
+
+
 def cpu_cores():
     try:
         from threadpoolctl import threadpool_info
@@ -235,11 +269,12 @@ def run_reference(args):
         "impl": "reference", "metric": "H2 factorize+solve unknowns/s (rel. residual 1e-6)", "value": v,
         "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c128", "data": "synthetic",
-        "config": {"workload": workload_name(args), "precision": "fp64 (oracle)",
-                   "sample": "16^3 sub-grid of the workload, same h, chi, eps (N=%d)" % N},
+        "dtype": "c128 (bulk rounded to c64)" if args.prec == "mixed" else "c128", "data": "synthetic",
+        "config": {"workload": workload_name(args), "precision": "oracle, " + oracle_precision(args),
+                   "sample": "16^3 sub-grid of the workload, same h, chi, eps (N=%d), build untimed" % N},
         "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": "oracle factorize + refined solve of the 16^3 sub-grid (N=%d)" % N},
+                         "sample": "oracle factorize + refined solve of the 16^3 sub-grid (N=%d), %s" % (
+                             N, oracle_precision(args))},
         "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "final_residual": res,
     }
@@ -285,7 +320,7 @@ def run_grad(args):
     N = len(pts)
     chi = inputs.chi_random_cells(N, 4)
     t0 = time.perf_counter()
-    A = H2.build(pts, K, H, chi, args.eps, stream=stream, profile=1, **tc_opts(args))
+    A = H2.build(pts, K, H, chi, args.eps, stream=stream, **tc_opts(args))
     t_build = time.perf_counter() - t0
     f0 = time.perf_counter()
     A.factorize(args.eps, args.prec)
@@ -370,7 +405,7 @@ def run_batch(args):
     reserve = 48 << 30  # keep this much device memory free
     for i, (n, chi) in enumerate(zip(sizes, chis)):
         pts = inputs.grid_points(int(n), H)
-        A = H2.build(pts, K, H, float(chi), args.eps, stream=stream, profile=1, **tc_opts(args))
+        A = H2.build(pts, K, H, float(chi), args.eps, stream=stream, **tc_opts(args))
         b = torch.from_numpy(inputs.rhs_gaussian(len(pts), args.nrhs, args.seed + i)).to("cuda")
         A.factorize(args.eps, args.prec)  # sizes the instance's arenas
         A.solve(b, refine=True, tol=args.tol, max_iter=30)
@@ -441,10 +476,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     pts = inputs.grid_points(args.grid, H)
     N = len(pts)
+    tun = dict(apply_path=args.apply_path, **tc_opts(args))
+    prof = 2 if args.profile_levels else 1
     t0 = time.perf_counter()
-    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream,
-                 profile=2 if args.profile_levels else (0 if args.no_kernel_events else 1),
-                 apply_path=args.apply_path, arena_cap_bytes=int(args.arena_cap_gb * 1e9), **tc_opts(args))
+    # the timed steps run without per-launch events (profile = 0); the kernel
+    # table comes from a separate instrumented pass afterwards
+    A = H2.build(pts, K, H, args.chi, args.eps, stream=stream, profile=0,
+                 arena_cap_bytes=int(args.arena_cap_gb * 1e9), **tun)
     t_build = time.perf_counter() - t0
     b_host = inputs.rhs_gaussian(N, args.nrhs, args.seed + rank)  # independent instance per rank
     b = torch.from_numpy(b_host).to("cuda")
@@ -455,18 +493,15 @@ def run_ours(args):
         print(json.dumps({"profile_step": True, "stats": A.stats()}))
         return
 
-    def step(prec):
-        A.factorize(args.eps, prec)
-        x = A.solve(b, refine=True, tol=args.tol, max_iter=30)
-        return x
-
     for _ in range(args.warmup):
-        step(args.prec)
+        A.factorize(args.eps, args.prec)
+        A.solve(b, refine=True, tol=args.tol, max_iter=30)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches = 0
     with ClockSampler() as cs:
         ev0.record(stream)
         fac_ms = []
@@ -475,14 +510,15 @@ def run_ours(args):
             A.factorize(args.eps, args.prec)
             fac_ms.append((time.perf_counter() - f0) * 1e3)
             x = A.solve(b, refine=True, tol=args.tol, max_iter=30)
+            st = A.stats()
+            launches += int(st["launches_factor"] + st["launches_solve"])
         ev1.record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
-    st = A.stats()
+    clocks = cs.summary()
     solve_info = dict(A.last_solve)
-    roof = roofline(st, cs.summary())
     # residual of the result against the H^2 matrix (FP64 matvec), and the
     # matvec's own time (CUDA events, mean of 3)
     r = A.matvec(x) - b
@@ -495,17 +531,38 @@ def run_ours(args):
     m1.record(stream)
     torch.cuda.synchronize()
     matvec_ms = m0.elapsed_time(m1) / 3
-    # FP64 comparison run (not part of the metric)
+
+    def timed_step(prec):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        A.factorize(args.eps, prec)
+        e1.record(stream)
+        A.solve(b, refine=True, tol=args.tol, max_iter=30)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), A.last_solve["iters"], A.last_solve["resid"]
+
+    # FP64 comparison arm (not part of the metric): one warm-up, median of 3
     fp64 = None
     if not args.no_fp64:
-        f0 = time.perf_counter()
-        A.factorize(args.eps, "fp64")
-        fp64_fac_ms = (time.perf_counter() - f0) * 1e3
-        s0 = time.perf_counter()
-        A.solve(b, refine=True, tol=args.tol, max_iter=30)
-        fp64_solve_ms = (time.perf_counter() - s0) * 1e3
-        fp64 = {"factorize_ms": fp64_fac_ms, "solve_ms": fp64_solve_ms, "solve_iters": A.last_solve["iters"],
-                "factorize_unknowns_per_s": N / (fp64_fac_ms / 1e3)}
+        timed_step("fp64")
+        runs = [timed_step("fp64") for _ in range(3)]
+        fm = float(np.median([u[0] for u in runs]))
+        fp64 = {"factorize_ms": fm, "factorize_ms_runs": [round(u[0], 2) for u in runs],
+                "refined_solve_ms": float(np.median([u[1] for u in runs])), "solve_iters": runs[-1][2],
+                "final_residual": runs[-1][3], "factorize_unknowns_per_s": N / (fm / 1e3),
+                "timing": "CUDA events, 1 warm-up, median of 3"}
+    # instrumented pass: per-launch CUDA events of one factorize + refined
+    # solve in the same configuration (kernel table, roofline; not timed)
+    A.set_opts(profile=prof, **tun)
+    A.factorize(args.eps, args.prec)
+    A.solve(b, refine=True, tol=args.tol, max_iter=30)
+    torch.cuda.synchronize()
+    st = A.stats()
+    A.set_opts(profile=0, **tun)
+    roof = roofline(st, clocks)
+    table = roofline_table(st, clocks)
     # repeated solves with the same factors: plain launches vs CUDA-graph replay
     # of the sweeps (h2_opts.solve_graph; not part of the metric)
     A.factorize(args.eps, args.prec)
@@ -528,13 +585,15 @@ def run_ours(args):
         solves(G, 2)  # sizing run + capture
         solve_graph = {"ms_per_solve_plain": solves(A, 10), "ms_per_solve_graph": solves(G, 10)}
         G.close()
-    # e2e: same step through the public API with HOST buffers
+    # e2e: same step through the public API with HOST buffers (H2D of b and
+    # D2H of x inside the timed region, every step)
     A.factorize(args.eps, args.prec)
     e0 = time.perf_counter()
-    for _ in range(max(1, args.steps // 2)):
+    ne = max(1, args.steps // 2)
+    for _ in range(ne):
         A.factorize(args.eps, args.prec)
         xh = A.solve(b_host, refine=True, tol=args.tol, max_iter=30)
-    e_ms = (time.perf_counter() - e0) * 1e3 / max(1, args.steps // 2)
+    e_ms = (time.perf_counter() - e0) * 1e3 / ne
     value = whole_job_value(world, N, ms)
     line = {
         "metric": "H2 factorize+solve unknowns/s (rel. residual 1e-6)", "value": value, "unit": "unknowns/s",
@@ -543,36 +602,63 @@ def run_ours(args):
         "dtype": "c64 bulk + c128 rank/refine" if args.prec == "mixed" else "c128",
         "data": "synthetic",
         "config": {"workload": workload_name(args), "precision": args.prec,
-            "l2": "inputs larger than L2 (near-field arena %.0f MB)" % (st.get("dev_bytes", 0) / 1e6)},
+                   "l2": "inputs larger than L2 (near-field arena %.0f MB)" % (st.get("dev_bytes", 0) / 1e6),
+                   "timed_steps": "no per-launch events (kernel table from a separate instrumented pass)"},
         "factorize_ms": float(np.mean(fac_ms)), "solve_iters": solve_info.get("iters"),
         "final_residual": res, "fp64": fp64,
         "refined_solve_ms": ms - float(np.mean(fac_ms)), "matvec_ms": matvec_ms,
         "dev_peak_gb": st.get("dev_peak", 0) / 1e9,
         "factorize_unknowns_per_s": N / (float(np.mean(fac_ms)) / 1e3),
-        "build_s": t_build, "gpu_launches": int(st["launches_factor"] + st["launches_solve"]),
+        "mixed_over_fp64_factorize": (fp64["factorize_ms"] / float(np.mean(fac_ms))) if fp64 else None,
+        "build_s": t_build, "gpu_launches": launches,
         "e2e": {"value": world * N / (e_ms / 1e3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
-        "clocks": cs.summary(),
+        "clocks": clocks,
         "roofline": roof,
+        "roofline_table": table,
         "solve_graph": solve_graph,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
-                    sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:40 if args.profile_levels else 12]},
+                    sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:40 if args.profile_levels else 14]},
     }
     if args.json_extra:
         line["stats"] = st
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        Nc, times, _ = oracle_sample(args, repeat=1)
-        line["cpu_baseline"] = {"value": Nc / times[0], "unit": "unknowns/s", "cores": cpu_cores(),
-                                "kind": "oracle",
-                                "sample": "oracle factorize + refined solve of the 16^3 sub-grid (N=%d)" % Nc}
+        line["cpu_baseline"] = cpu_baseline_subprocess(args)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
+def cpu_baseline_subprocess(args):
+    """The oracle's factorize + refined solve of the 16^3 sub-grid on ONE host
+    core (the paper's single-core setting): a child process with the BLAS
+    thread pools limited to one thread before numpy loads; build untimed."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only", "--grid", str(args.grid),
+           "--eps", str(args.eps), "--chi", str(args.chi), "--nrhs", str(args.nrhs), "--seed", str(args.seed),
+           "--prec", args.prec, "--tol", str(args.tol)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal to the GPU line
+        return {"value": None, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "error": str(e)[:200]}
+
+
+def cpu_baseline_only(args):
+    Nc, times, res = oracle_sample(args, repeat=1)
+    print(json.dumps({"value": Nc / times[0], "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                      "sample": "oracle factorize + refined solve (to %g) of the 16^3 sub-grid (N=%d), %s, one "
+                                "host core, build untimed" % (args.tol, Nc, oracle_precision(args)),
+                      "final_residual": res}))
+
+
 def main():
     args = parse()
+    if args.cpu_baseline_only:
+        return cpu_baseline_only(args)
     if args.impl == "ours" and args.workload == "batch":
         return run_batch(args)
     if args.impl == "ours" and args.workload == "grad":

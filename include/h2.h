@@ -305,6 +305,31 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* opts);
 
 /*
+ * h2_set_chi - new contrast chi on an existing context (the column scaling
+ * D_chi of A = I + s K D_chi; Sec. II's matrix with the workload's contrast):
+ * Z = D^{1/2} A D^{-1/2} becomes Z' = I + E (Z - I) E, E = diag(sqrt(chi' /
+ * chi)).  The H^2 form is updated exactly (dense blocks scaled, the scaled
+ * cluster bases re-orthonormalised leaf to root so they stay nested, eq. 3,
+ * couplings multiplied by the triangular factors, eq. 2): ranks and the block
+ * partition are unchanged, no new approximation is made, cost O(N k^2) host
+ * work plus one upload.  Valid for matrices of that form (h2_build; h2_load
+ * with dscale = sqrt(chi)).  The factorization and explicit inverse are
+ * invalidated: call h2_factorize again before solving.
+ *   chi       HOST, chi_len doubles (N, or 1 = uniform), finite and > 0
+ * H2_EINVAL for a bad chi (the context is unchanged).
+ */
+h2_status h2_set_chi(h2_ctx* ctx, const double* chi, int64_t chi_len);
+
+/*
+ * h2_level_ranks - cluster ranks of tree level `level` (l0 <= level <= L) in
+ * the last factorization: k0[i] the incoming rank k_i and kt[i] the rank
+ * after the Step-0 basis update (eqs. 17-18), i = 0 .. 2^level - 1 (HOST
+ * arrays of n >= 2^level entries; either may be NULL).  H2_ESTATE without a
+ * valid factorization, H2_EINVAL for another level or a short array.
+ */
+h2_status h2_level_ranks(const h2_ctx* ctx, int level, int* k0, int* kt, int64_t n);
+
+/*
  * h2_export - copy the H^2 representation out in the h2_load layout (HOST
  * arrays, caller-allocated).  Call h2_export_sizes first: it returns the
  * element counts (complex entries for V, T, S, D; pairs for adm / near).

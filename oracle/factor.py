@@ -89,8 +89,9 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
     path; rank decisions (Step 0/1) always run in FP64.  `observe`, if given,
     is called once per Step-0 rank decision with the data it was taken on
     (level, cluster, incoming basis B, the active parts of the row and column
-    fill-ins, nu^2, the number r of kept directions and V_add); it only
-    reads them."""
+    fill-ins, nu^2, the eigenvalues of G_i in descending order, the threshold
+    (eps nu_i)^2, the number r of kept directions and V_add); it only reads
+    them."""
     tree, part, L, l0 = H.tree, H.part, H.L, H.l0
     Fz = Factorization()
     Fz.H, Fz.eps, Fz.ordering = H, eps, ordering
@@ -173,7 +174,7 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
                     if observe is not None:
                         observe(dict(level=l, cluster=i, B=Bi.copy(), rows=[(k, Fm[:, act(k)].copy()) for k, Fm in rows],
                                      cols=[(k, Fm[act(k), :].copy()) for k, Fm in cols], nu2=nu2, r=r,
-                                     Vadd=Vadd.copy()))
+                                     Vadd=Vadd.copy(), eig=w[::-1].copy(), thr=thr))
                 Bn = np.hstack([Bi, Vadd])                      # eq. (18)/(27)
                 # Step 1: complement, Q~_i = [V~^perp, V~] (eq. 19, R4)
                 step01[i] = (Bn, np.hstack([Vrest, Bn]))

@@ -25,7 +25,7 @@ H2_ADJOINT, H2_REFINE, H2_USE_INVERSE, H2_HOST = 1, 2, 4, 8
 H2_GRAD_ACCUMULATE = 1
 SYMBOLS = ("h2_default_opts", "h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec",
            "h2_matvec_noalloc", "h2_factorize_batch", "h2_solve_batch", "h2_grad_chi", "h2_set_opts",
-           "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
+           "h2_set_chi", "h2_level_ranks", "h2_export_sizes", "h2_export", "h2_stats", "h2_last_error",
            "h2_status_string", "h2_destroy")
 
 
@@ -71,6 +71,8 @@ def lib():
     L.h2_grad_chi.argtypes = [P, P, P, P, I, D, P, ctypes.c_uint, P]
     L.h2_factorize_batch.argtypes = [P, I, D, I]
     L.h2_set_opts.argtypes = [P, ctypes.POINTER(h2_opts)]
+    L.h2_set_chi.argtypes = [P, P, I64]
+    L.h2_level_ranks.argtypes = [P, I, P, P, I64]
     L.h2_solve_batch.argtypes = [P, I, P, P, I, ctypes.c_uint, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     L.h2_export_sizes.argtypes = [P] + [ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I)] + \
         [ctypes.POINTER(I64)] * 6
@@ -83,8 +85,8 @@ def lib():
     L.h2_destroy.argtypes = [P]
     L.h2_destroy.restype = None
     for name in ("h2_build", "h2_load", "h2_factorize", "h2_invert", "h2_solve", "h2_matvec", "h2_matvec_noalloc",
-                 "h2_grad_chi", "h2_factorize_batch", "h2_solve_batch", "h2_set_opts", "h2_export_sizes", "h2_export",
-                 "h2_stats"):
+                 "h2_grad_chi", "h2_factorize_batch", "h2_solve_batch", "h2_set_opts", "h2_set_chi", "h2_level_ranks",
+                 "h2_export_sizes", "h2_export", "h2_stats"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -199,6 +201,22 @@ class H2:
     def factorize(self, eps_fill, precision="fp64"):
         prec = {"fp64": H2_FP64, "mixed": H2_MIXED}[precision]
         self._check(lib().h2_factorize(self._h, float(eps_fill), prec), "h2_factorize")
+        self.last_factorize = (float(eps_fill), precision)
+
+    def set_chi(self, chi):
+        """h2_set_chi: new contrast (N or scalar, > 0); the factors are invalidated."""
+        c = np.ascontiguousarray(np.atleast_1d(np.asarray(chi, dtype=np.float64)))
+        self._check(lib().h2_set_chi(self._h, _ptr(c), len(c)), "h2_set_chi")
+        self.chi = np.broadcast_to(c, (self.N,)).copy()
+        self.last_factorize = None
+
+    def level_ranks(self, level):
+        """(k0, kt): cluster ranks of tree level `level` before / after the Step-0
+        basis update of the last factorization (h2_level_ranks)."""
+        n = 2 ** level
+        k0, kt = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        self._check(lib().h2_level_ranks(self._h, int(level), _ptr(k0), _ptr(kt), n), "h2_level_ranks")
+        return k0, kt
 
     def invert(self):
         self._check(lib().h2_invert(self._h), "h2_invert")

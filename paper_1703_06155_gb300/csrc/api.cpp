@@ -892,6 +892,54 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu, const void* g,
   });
 }
 
+h2_status h2_set_chi(h2_ctx* ctx, const double* chi, int64_t chi_len) {
+  if (!ctx) return H2_EINVAL;
+  const int64_t N = ctx->c.H.tree.N;
+  if (!chi || !(chi_len == 1 || chi_len == N)) {
+    ctx->c.err = "h2_set_chi: bad argument (chi_len must be 1 or N)";
+    return H2_EINVAL;
+  }
+  for (int64_t i = 0; i < chi_len; ++i)
+    if (!(chi[i] > 0) || !std::isfinite(chi[i])) {
+      ctx->c.err = "h2_set_chi: chi must be finite and > 0 for every cell";
+      return H2_EINVAL;
+    }
+  return guard(ctx, [&]() {
+    Ctx& c = ctx->c;
+    H2Host& H = c.H;
+    std::vector<double> sq(N), e(N);
+    for (int64_t g = 0; g < N; ++g) sq[g] = std::sqrt(chi_len == 1 ? chi[0] : chi[g]);
+    for (int64_t p = 0; p < N; ++p) {
+      const int64_t g = H.tree.perm[p];
+      e[p] = sq[g] / H.dscale[g];
+    }
+    // the factors and everything derived from the old matrix are void from here on
+    c.factored = false;
+    c.inverted = false;
+    c.epoch++;
+    c.graphs.clear();
+    c.snorm2_cache.clear();
+    rescale_h2(H, e);
+    H.dscale = sq;
+    if (!c.opts.host_only) finish_setup(ctx, c.stream);
+  });
+}
+
+h2_status h2_level_ranks(const h2_ctx* ctx, int level, int* k0, int* kt, int64_t n) {
+  if (!ctx) return H2_EINVAL;
+  const Ctx& c = ctx->c;
+  for (const LevelF& F : c.lev)
+    if (F.l == level) {
+      if (n < F.nc) return H2_EINVAL;
+      for (int i = 0; i < F.nc; ++i) {
+        if (k0) k0[i] = F.k0[i];
+        if (kt) kt[i] = F.kt[i];
+      }
+      return c.factored ? H2_OK : H2_ESTATE;
+    }
+  return c.factored ? H2_EINVAL : H2_ESTATE;
+}
+
 h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
   if (!ctx || !json || cap == 0) return H2_EINVAL;
   const Ctx& c = ctx->c;
@@ -914,8 +962,21 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
   o << "],\"levels\":[";
   for (size_t li = 0; li < c.lev.size(); ++li) {
     const LevelF& F = c.lev[li];
-    int nmax = 0, k0max = 0, ktmax = 0, pushed = 0, live = 0;
+    int nmax = 0, k0max = 0, ktmax = 0, pushed = 0, live = 0, csp = 0, csp_fill = 0;
     long msum = 0;
+    {
+      // C_sp (Sec. V, Table IV): most blocks in one block row of the level,
+      // near + admissible, and with the pushed fill-in targets
+      std::vector<int> rowc(F.nc, 0), rowf(F.nc, 0);
+      for (int i = 0; i < F.nc; ++i) rowc[i] = (int)F.nbrs[i].size();
+      for (auto pr : c.H.part.adm[F.l]) rowc[pr.first]++;
+      for (size_t q = 0; q < F.fill_pairs.size(); ++q)
+        if (F.fill_live[q] && !F.fill_is_adm[q]) rowf[F.fill_pairs[q].first]++;
+      for (int i = 0; i < F.nc; ++i) {
+        csp = std::max(csp, rowc[i]);
+        csp_fill = std::max(csp_fill, rowc[i] + rowf[i]);
+      }
+    }
     for (int i = 0; i < F.nc; ++i) {
       nmax = std::max(nmax, F.n[i]);
       k0max = std::max(k0max, F.k0[i]);
@@ -931,16 +992,24 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
       << ",\"batches\":" << F.batches.size() << ",\"near\":" << F.near_pairs.size()
       << ",\"adm\":" << c.H.part.adm[F.l].size() << ",\"fill_live\":" << live << ",\"pushed_live\":" << pushed
       << ",\"ritz_max\":" << F.st_ritz_max << ",\"ritz_mean\":" << (F.st_ritz_n ? (double)F.st_ritz_sum / F.st_ritz_n : 0.0)
-      << ",\"jacobi_sweeps_max\":" << F.st_sweeps_max << "}";
+      << ",\"jacobi_sweeps_max\":" << F.st_sweeps_max << ",\"csp\":" << csp << ",\"csp_fill\":" << csp_fill << "}";
   }
   o << "],\"kernels\":{";
   {
     bool first = true;
     for (const auto& [tag, a] : c.prof) {
       o << (first ? "" : ",") << "\"" << tag << "\":{\"launches\":" << a.launches << ",\"ms\":" << a.ms
-        << ",\"flops\":" << a.flops;
+        << ",\"flops\":" << a.flops << ",\"bytes\":" << a.bytes;
       if (a.pipe) o << ",\"pipe\":\"" << a.pipe << "\"";
       o << "}";
+      first = false;
+    }
+  }
+  o << "},\"paths\":{";
+  {
+    bool first = true;
+    for (const auto& [k, v] : c.paths) {
+      o << (first ? "" : ",") << "\"" << k << "\":" << v;
       first = false;
     }
   }

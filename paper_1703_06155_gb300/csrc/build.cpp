@@ -368,4 +368,94 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
   return "";
 }
 
+// New contrast on an existing representation: Z' = I + E (Z - I) E with
+// E = diag(e) (tree order), e_i = sqrt(chi'_i / chi_i).  Exact algebra on the
+// H^2 form (no new approximation, ranks unchanged): dense near blocks are
+// scaled entrywise; the scaled bases E_t V_t are re-orthonormalised from the
+// leaves up, E_t V_t = Q_t R_t (leaf: V'_t = Q_t; parent:
+// diag(R_t1, R_t2) T_t = Q_t R_t, T'_t = Q_t), which keeps them nested
+// (eq. 3); couplings become S'_ts = R_t S_ts R_s^T (eq. 2).
+void rescale_h2(H2Host& H, const std::vector<double>& e) {
+  const Tree& T = H.tree;
+  const int L = H.L, l0 = H.l0;
+  std::vector<std::vector<Mat>> Rm(L + 1);
+  for (int l = L; l >= l0; --l) {
+    const int nc = 1 << l;
+    Rm[l].assign(nc, Mat());
+    parallel_for(nc, [&](int t) {
+      const int k = H.rank[l][t];
+      Mat A;
+      if (l == L) {
+        const int n = (int)T.size[L][t];
+        A = Mat(n, k);
+        A.a = H.V[t];
+        for (int j = 0; j < k; ++j)
+          for (int i = 0; i < n; ++i) A(i, j) *= e[T.start[L][t] + i];
+      } else {
+        const Mat& R1 = Rm[l + 1][2 * t];
+        const Mat& R2 = Rm[l + 1][2 * t + 1];
+        const int k1 = R1.m, k2 = R2.m;
+        Mat Tm(k1 + k2, k);
+        Tm.a = H.T[l][t];
+        A = Mat(k1 + k2, k);
+        for (int j = 0; j < k; ++j) {
+          for (int i = 0; i < k1; ++i) {
+            cplx v = 0;
+            for (int q = i; q < k1; ++q) v += R1(i, q) * Tm(q, j);
+            A(i, j) = v;
+          }
+          for (int i = 0; i < k2; ++i) {
+            cplx v = 0;
+            for (int q = i; q < k2; ++q) v += R2(i, q) * Tm(k1 + q, j);
+            A(k1 + i, j) = v;
+          }
+        }
+      }
+      Mat Q, R;
+      thin_qr(A, Q, R);
+      if (l == L) H.V[t] = Q.a;
+      else H.T[l][t] = Q.a;
+      Rm[l][t] = R;
+    });
+  }
+  for (int l = l0; l <= L; ++l) {
+    const auto& pairs = H.part.adm[l];
+    parallel_for((int)pairs.size(), [&](int q) {
+      const int t = pairs[q].first, s = pairs[q].second;
+      const Mat& Rt = Rm[l][t];
+      const Mat& Rs = Rm[l][s];
+      const int kt = Rt.m, ks = Rs.m;
+      Mat S(kt, ks);
+      S.a = H.S[l][q];
+      Mat Y(kt, ks);  // Rt S
+      for (int j = 0; j < ks; ++j)
+        for (int i = 0; i < kt; ++i) {
+          cplx v = 0;
+          for (int p = i; p < kt; ++p) v += Rt(i, p) * S(p, j);
+          Y(i, j) = v;
+        }
+      for (int j = 0; j < ks; ++j)  // Y Rs^T
+        for (int i = 0; i < kt; ++i) {
+          cplx v = 0;
+          for (int p = j; p < ks; ++p) v += Y(i, p) * Rs(j, p);
+          S(i, j) = v;
+        }
+      H.S[l][q] = S.a;
+    });
+  }
+  const auto& np_ = H.part.inad[L];
+  parallel_for((int)np_.size(), [&](int q) {
+    const int t = np_[q].first, s = np_[q].second;
+    const int64_t at = T.start[L][t], as = T.start[L][s];
+    const int nt = (int)T.size[L][t], ns = (int)T.size[L][s];
+    std::vector<cplx>& D = H.D[q];
+    for (int j = 0; j < ns; ++j)
+      for (int i = 0; i < nt; ++i) {
+        const double f = e[at + i] * e[as + j];
+        cplx& z = D[(size_t)i + (size_t)j * nt];
+        z = (t == s && i == j) ? 1.0 + f * (z - 1.0) : f * z;
+      }
+  });
+}
+
 }  // namespace h2

@@ -28,10 +28,10 @@ static cudaEvent_t prof_event(Ctx& c) {
   return e;
 }
 
-ProfScope::ProfScope(Ctx& c_, const std::string& tag, double flops, const char* pipe)
+ProfScope::ProfScope(Ctx& c_, const std::string& tag, double flops, const char* pipe, double bytes)
     : c(c_), on(c_.opts.profile != 0 && !c_.capturing) {
   if (!on) return;
-  ProfRec r{c.opts.profile == 2 ? tag + c.prof_suffix : tag, prof_event(c), prof_event(c), flops, pipe};
+  ProfRec r{c.opts.profile == 2 ? tag + c.prof_suffix : tag, prof_event(c), prof_event(c), flops, pipe, bytes};
   ck(cudaEventRecord(r.a, c.stream), "cudaEventRecord");
   idx = c.prof_open.size();
   c.prof_open.push_back(r);
@@ -49,6 +49,7 @@ void prof_resolve(Ctx& c) {
       a.launches++;
       a.ms += ms;
       a.flops += r.flops;
+      a.bytes += r.bytes;
       if (r.pipe) a.pipe = r.pipe;
     } else {
       cudaGetLastError();

@@ -51,6 +51,9 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1 : 0;
   const char* pipe = emul ? "fp32_df" : pacc == P64 ? "fp64" : tc == 2 ? "tcgen05_tf32x3" : tc == 1 ? "mma_tf32x3" : "fp32";
   ProfScope ps(c, std::string("gemm:") + what, b.alg_flops, pipe);
+  c.paths[std::string("gemm:") + pipe + ":" + std::to_string(h2k::gemm_tile_m(b.shape)) + "x" +
+          std::to_string(h2k::gemm_tile_n(b.shape))]++;
+  if (ws > 0) c.paths[std::string("gemm_splitk:") + pipe]++;
   ck(gemm(c.st.ptr<GemmTask>(i0), c.st.ptr<GemmPair>(i1), c.st.ptr<GemmTile>(i2), (int)b.tl.size(), pin, pout, pacc,
           wsp, c.stream, b.shape, b.pina, c.opts.tensor_cores, emul),
      what);
@@ -130,7 +133,12 @@ void run_copy(Ctx& c, CopyBatch& b, const char* what) {
   HostScope hs(c, "run_copy");
   const int i0 = c.st.add(b.t);
   c.st.upload(c);
-  ProfScope ps(c, std::string("copy:") + what, 0.0);
+  double bytes = 0;
+  for (const CopyTask& t : b.t) {
+    const double n = (double)t.rows * t.cols, ns = (double)std::min(t.rows, t.srows) * std::min(t.cols, t.scols);
+    bytes += n * esz(t.dst_prec) * (t.mode == 1 ? 2 : 1) + (t.src ? ns * esz(t.src_prec) : 0.0);
+  }
+  ProfScope ps(c, std::string("copy:") + what, 0.0, nullptr, bytes);
   ck(copy2d(c.st.ptr<CopyTask>(i0), (int)b.t.size(), c.stream), what);
   c.launches++;
 }
@@ -389,6 +397,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     ck(cudaMemsetAsync(d_r[q], 0, 3 * nb * sizeof(int), lc.stream), "memset r");
   }
   std::vector<std::vector<int>> r(nj), sweeps(nj);
+  size_t jac_rec = SIZE_MAX;
+  std::vector<std::pair<size_t, size_t>> eig_of;
   for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
   hsA.reset();
   if (anyfill) {
@@ -483,7 +493,9 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     {
       const int i0 = lc.st.add(ft), i1 = lc.st.add(fb);
       lc.st.upload(lc);
-      ProfScope ps(lc, "trace", 0.0);
+      double tb = 0;
+      for (const FrobBlock& f : fb) tb += (double)f.rows * f.cols * es;
+      ProfScope ps(lc, "trace", 0.0, nullptr, tb);
       double* part = (double*)dev_ensure(lc, lc.frobbuf, (fb.size() + 1) * sizeof(double));
       ck(frob2(lc.st.ptr<FrobTask>(i0), (int)ft.size(), lc.st.ptr<FrobBlock>(i1), (int)fb.size(), part, prec,
                lc.stream),
@@ -499,13 +511,17 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     run_gemm(lc, gXX, P32, P64, P64, "X*X^H");
     run_gemm(lc, gT, P64, P64, P64, "gram*Vp");
     run_gemm(lc, gG, P64, P64, P64, "Vp^H*gram*Vp");
+    size_t pchol_rec = SIZE_MAX;
     {
       const int i0 = lc.st.add(pc);
       lc.st.upload(lc);
-      ProfScope ps(lc, "pchol_wy", 0.0);
+      ProfScope ps(lc, "pchol_wy", 0.0, "fp64");
+      if (ps.on) pchol_rec = ps.idx;
+      int used = 0;
       ck(pchol_wy(lc.st.ptr<PcholTask>(i0), (int)pc.size(), maxp, lc.opts.cluster_max > 0 ? lc.opts.cluster_max : 16,
-                  lc.stream),
+                  lc.stream, &used),
          "pivoted cholesky");
+      lc.paths["pchol_wy:cta" + std::to_string(used)]++;
       lc.launches++;
     }
     std::vector<std::vector<int>> rp(nj);
@@ -519,6 +535,20 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     for (size_t q = 0; q < nj; ++q)
       for (size_t u = 0; u < info[q].size(); ++u)
         if (info[q][u].fill) info[q][u].rp = std::min(std::max(rp[q][u], 0), info[q][u].p);
+    if (pchol_rec != SIZE_MAX) {
+      // algorithmic flops of the subspace kernel: pivoted Cholesky of the
+      // p x p Gram to r' pivots (p r'^2 / 2 complex MACs), Householder QR of
+      // the p x r' factor (2 p r'^2 - 2 r'^3 / 3) and its compact-WY T
+      // (p r'^2 / 2); 8 real flops per complex MAC
+      double fl = 0;
+      for (size_t q = 0; q < nj; ++q)
+        for (const Info& f : info[q])
+          if (f.fill) {
+            const double p = f.p, r = f.rp;
+            fl += 8.0 * (p * r * r / 2 + 2 * p * r * r - 2 * r * r * r / 3 + p * r * r / 2);
+          }
+      lc.prof_open[pchol_rec].flops = fl;
+    }
     // Ritz step on span(Qx) and the complement rotation Yf = Vp Q, Q = I - Y T Y^H
     GemmBatch g1, g2, g3, g4, g5;
     CopyBatch cp;
@@ -557,6 +587,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         g4.pair(Sq + f.Qx, p, OP_H, Sq + f.Z1, p, OP_N, p);
         g4.close();
         eig.push_back(EigTask{Sq + f.Gh, Sq + f.U, (double*)(Sq + f.lam), rr, d_r[q] + 2 * nb + u});
+        eig_of.push_back({q, u});
         sel.push_back(
             SelTask{(const double*)(Sq + f.tr), (double*)(Sq + f.lam), d_r[q] + nb + u, n, rr, snorm(q, f.i), eps * eps});
         maxr = std::max(maxr, rr);
@@ -573,7 +604,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     if (!eig.empty()) {
       const int i0 = lc.st.add(eig);
       lc.st.upload(lc);
-      ProfScope ps(lc, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0);
+      ProfScope ps(lc, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0, "fp64");
+      if (ps.on) jac_rec = ps.idx;
       if (maxr >= 48) {
         // large Ritz problems: one cluster of CTAs per eigenproblem (16 when
         // few problems share the launch, so that more SMs work on each)
@@ -581,11 +613,14 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         double* js = (double*)dev_ensure(lc, lc.jac_buf, (size_t)per * eig.size() * sizeof(double));
         const int cmax = lc.opts.cluster_max > 0 ? lc.opts.cluster_max : 16;
         const int csize = std::min(cmax, eig.size() * 16 <= 152 ? 16 : 8);
+        int used = 0;
         ck(jacobi_eig_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, csize, js, (int*)lc.statusbuf.p,
-                              lc.stream),
+                              lc.stream, &used),
            "jacobi (cluster)");
+        lc.paths["jacobi_cluster:cta" + std::to_string(used)]++;
       } else {
         ck(jacobi_eig(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, (int*)lc.statusbuf.p, lc.stream), "jacobi");
+        lc.paths["jacobi:cta1"]++;
       }
       lc.launches++;
       const int i1 = lc.st.add(sel);
@@ -603,6 +638,17 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     }
   }
   sync_timed(lc, lc.stream, "sync after step 0");
+  if (jac_rec != SIZE_MAX) {
+    // algorithmic flops of the Hermitian Jacobi: 24 r'^3 real flops per sweep
+    // (r'(r'-1)/2 complex rotations per sweep, each applied to two rows and
+    // two columns of the r' x r' matrix and to two columns of U)
+    double fl = 0;
+    for (auto [q, u] : eig_of) {
+      const double rr = info[q][u].rp;
+      fl += 24.0 * rr * rr * rr * std::max(sweeps[q][u], 0);
+    }
+    lc.prof_open[jac_rec].flops = fl;
+  }
   prof_resolve(lc);
   lc.st.begin();  // stream idle: staging can be reused
   for (size_t q = 0; q < nj; ++q) {
@@ -696,7 +742,9 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   if (!lu.empty()) {
     const int i0 = lc.st.add(lu);
     lc.st.upload(lc);
-    ProfScope ps(lc, "lu", 0.0);
+    double fl = 0;
+    for (const LuTask& t : lu) fl += 16.0 / 3.0 * (double)t.m * t.m * t.m;
+    ProfScope ps(lc, "lu", fl, prec == P64 ? "fp64" : "fp32");
     int maxm = 0;
     for (const LuTask& t : lu) maxm = std::max(maxm, t.m);
     ck(lu_blocked(lc.st.ptr<LuTask>(i0), (int)lu.size(), maxm, prec, (int*)lc.statusbuf.p, lc.stream), "lu");
@@ -981,7 +1029,7 @@ void check_status(Ctx& c) {
   if (st & 1) fail(H2_ESINGULAR, "zero pivot in a partial LU or in the final LU");
   if (st & 2) fail(H2_EINTERNAL, "Jacobi eigen-decomposition did not converge");
   if (c.opts.tensor_cores == 2 && h2k::gemm_umma_timeouts() != 0)
-    fail(H2_EINTERNAL, "a tensor-core GEMM tile gave up waiting for its MMAs");
+    fail(H2_ETIMEOUT, "a tensor-core GEMM tile gave up waiting for its MMAs (bounded mbarrier wait)");
 }
 
 }  // namespace

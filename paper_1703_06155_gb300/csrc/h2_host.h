@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
 #include <string>
 #include <unordered_map>
@@ -69,6 +70,8 @@ using GramFn = std::function<void(int level, const std::vector<std::vector<int64
 std::string build_h2(const double* pts, int64_t N, double k, double h, const double* chi, int64_t chi_len,
                      double eps, const h2_opts& o, H2Host& H, const GramFn& gram);
 std::vector<cplx> host_complement(const std::vector<cplx>& B, int n, int k);
+// Z <- I + E (Z - I) E with E = diag(e), e in tree order (h2_set_chi)
+void rescale_h2(H2Host& H, const std::vector<double>& e);
 void host_gram(const double* pts_tree, const double* sq_tree, double k, double w,
                const std::vector<std::vector<int64_t>>& rows, const std::vector<std::vector<int64_t>>& ranges,
                std::vector<std::vector<cplx>>& G);
@@ -192,11 +195,12 @@ struct ProfRec {
   std::string tag;
   cudaEvent_t a, b;
   double flops;
-  const char* pipe;  // arithmetic unit of the products (GEMMs), else null
+  const char* pipe;  // arithmetic unit of the products, else null
+  double bytes;      // algorithmic bytes (memory-bound classes), else 0
 };
 struct ProfAgg {
   int64_t launches = 0;
-  double ms = 0, flops = 0;
+  double ms = 0, flops = 0, bytes = 0;
   const char* pipe = nullptr;
 };
 
@@ -232,6 +236,9 @@ struct Ctx {
   std::vector<ProfRec> prof_open;
   std::vector<cudaEvent_t> prof_pool;
   std::unordered_map<std::string, ProfAgg> prof;  // per kernel class, since the last reset
+  // launches per code path variant (kernel, arithmetic unit, tile shape, CTAs
+  // per thread-block cluster), counted since the context was created
+  std::map<std::string, int64_t> paths;
   std::string prof_suffix;                        // profile == 2: "@<level>" appended to tags
   // sum of ||S||_F^2 over the admissible blocks of each cluster's row and
   // column, per level (depends on the H^2 only; computed once)
@@ -268,7 +275,7 @@ struct ProfScope {
   Ctx& c;
   bool on;
   size_t idx = 0;
-  ProfScope(Ctx& c_, const std::string& tag, double flops, const char* pipe = nullptr);
+  ProfScope(Ctx& c_, const std::string& tag, double flops, const char* pipe = nullptr, double bytes = 0.0);
   ~ProfScope();
 };
 void prof_resolve(Ctx& c);  // after a stream synchronize: fold events into c.prof

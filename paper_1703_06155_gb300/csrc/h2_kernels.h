@@ -191,7 +191,7 @@ cudaError_t jacobi_eig(const EigTask* d_tasks, int ntasks, int maxp,
 int64_t jacobi_cluster_scratch(int maxp);  // doubles per task
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
                                int csize, double* d_scratch, int* d_status,
-                               cudaStream_t s);
+                               cudaStream_t s, int* csize_used = nullptr);
 // Step 3 partial LU with pivoting (one CTA per task), then explicit L^{-1} P
 // and U^{-1} (two CTAs per task, in a second launch); maxm = the largest m of
 // the tasks (<= 4096)
@@ -199,7 +199,8 @@ cudaError_t lu_blocked(const LuTask* d_tasks, int ntasks, int maxm, int prec,
                        int* d_status, cudaStream_t s);
 cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
 // one thread-block cluster of up to cmax (<= 16) CTAs per task
-cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, int cmax, cudaStream_t s);
+cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, int cmax, cudaStream_t s,
+                     int* csize_used = nullptr);
 // one CTA per task
 cudaError_t lu_panel(const PanelTask* d_tasks, int ntasks, int prec, int* d_status,
                      cudaStream_t s);

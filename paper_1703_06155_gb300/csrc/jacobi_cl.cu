@@ -310,7 +310,7 @@ int64_t jacobi_cluster_scratch(int maxp) {
 }
 
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, double* d_scratch,
-                               int* d_status, cudaStream_t s) {
+                               int* d_status, cudaStream_t s, int* csize_used) {
   if (ntasks <= 0) return cudaSuccess;
   const int64_t per = jacobi_cluster_scratch(maxp);
   cudaError_t e = cudaMemsetAsync(d_scratch, 0, (size_t)per * ntasks * sizeof(double), s);
@@ -338,6 +338,7 @@ cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int
       csize = 8;
     }
   }
+  if (csize_used) *csize_used = csize;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ntasks * csize, 1, 1);
   cfg.blockDim = dim3(NT, 1, 1);

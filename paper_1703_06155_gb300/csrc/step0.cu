@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
 
 }  // namespace
 
-cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, int cmax, cudaStream_t s) {
+cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, int cmax, cudaStream_t s, int* csize_used) {
   if (n <= 0) return cudaSuccess;
   if (maxp > PMAX) return cudaErrorInvalidValue;
   // CTAs per problem: spread few problems over the SMs, keep >= 16 rows each
@@ -454,6 +454,7 @@ cudaError_t pchol_wy(const PcholTask* d, int n, int maxp, int cmax, cudaStream_t
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (csize_used) *csize_used = csize;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_pchol_wy_cl, d, lrow_smem);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

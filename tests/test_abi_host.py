@@ -13,6 +13,7 @@ from oracle import kernel
 from oracle import tree as otree
 from paper_1703_06155_gb300 import inputs
 
+from _h2io import dense_from_rep
 from _problems import H, K
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -33,62 +34,6 @@ def test_exports_every_declared_symbol(libh2):
         assert hasattr(libh2, name), name
     from paper_1703_06155_gb300 import SYMBOLS
     assert set(SYMBOLS) == decl
-
-
-def dense_from_rep(r):
-    """Assemble Z_H2 (tree order) from the h2_load layout, independently of
-    both the oracle and the library."""
-    L, l0 = r["L"], r["l0"]
-    ranks, o = {}, 0
-    for l in range(l0, L + 1):
-        ranks[l] = r["rank"][o:o + 2 ** l]
-        o += 2 ** l
-    sizes = {L: r["leaf_size"]}
-    for l in range(L - 1, -1, -1):
-        sizes[l] = sizes[l + 1][0::2] + sizes[l + 1][1::2]
-    starts = {l: np.concatenate([[0], np.cumsum(sizes[l])[:-1]]) for l in sizes}
-    full, o = {}, 0
-    for c in range(2 ** L):
-        cnt = sizes[L][c] * ranks[L][c]
-        full[(L, c)] = r["V"][o:o + cnt].reshape(ranks[L][c], sizes[L][c]).T
-        o += cnt
-    o = 0
-    for l in range(L - 1, l0 - 1, -1):
-        pass
-    Tm, o = {}, 0
-    for l in range(l0, L):
-        for c in range(2 ** l):
-            k1, k2 = ranks[l + 1][2 * c], ranks[l + 1][2 * c + 1]
-            cnt = (k1 + k2) * ranks[l][c]
-            Tm[(l, c)] = r["T"][o:o + cnt].reshape(ranks[l][c], k1 + k2).T
-            o += cnt
-    for l in range(L - 1, l0 - 1, -1):
-        for c in range(2 ** l):
-            A1, A2 = full[(l + 1, 2 * c)], full[(l + 1, 2 * c + 1)]
-            W = np.zeros((A1.shape[0] + A2.shape[0], A1.shape[1] + A2.shape[1]), complex)
-            W[:A1.shape[0], :A1.shape[1]] = A1
-            W[A1.shape[0]:, A1.shape[1]:] = A2
-            full[(l, c)] = W @ Tm[(l, c)]
-    N = r["N"]
-    Z = np.zeros((N, N), complex)
-    adm = r["adm"].reshape(-1, 2)
-    o = so = 0
-    for i, l in enumerate(range(l0, L + 1)):
-        for q in range(r["n_adm"][i]):
-            t, s = adm[o]
-            o += 1
-            cnt = ranks[l][t] * ranks[l][s]
-            S = r["S"][so:so + cnt].reshape(ranks[l][s], ranks[l][t]).T
-            so += cnt
-            Z[starts[l][t]:starts[l][t] + sizes[l][t], starts[l][s]:starts[l][s] + sizes[l][s]] = \
-                full[(l, t)] @ S @ full[(l, s)].T
-    do = 0
-    for t, s in r["near"].reshape(-1, 2):
-        cnt = sizes[L][t] * sizes[L][s]
-        Z[starts[L][t]:starts[L][t] + sizes[L][t], starts[L][s]:starts[L][s] + sizes[L][s]] = \
-            r["D"][do:do + cnt].reshape(sizes[L][s], sizes[L][t]).T
-        do += cnt
-    return Z, full
 
 
 @pytest.mark.parametrize("n,eps", [(12, 1e-6), (12, 1e-3)])
@@ -183,4 +128,35 @@ def test_degenerate_sizes_build(libh2, N):
     idx = r["perm"]
     Zex = kernel.entries(pts, chi, idx, idx, K, H)
     assert np.linalg.norm(Z - Zex) <= 10 * eps * np.linalg.norm(Zex)
+    A.close()
+
+
+def test_set_chi_host_rescale_is_exact(libh2):
+    # h2_set_chi on a host_only context (no GPU): the representation becomes
+    # I + E (Z - I) E exactly, E = diag(sqrt(chi'/chi)), with the same ranks and
+    # orthonormal nested bases; bad contrasts are rejected and change nothing
+    from paper_1703_06155_gb300 import H2, H2Error
+    pts = inputs.grid_points(8, H)
+    N = len(pts)
+    chi = inputs.chi_random_cells(N, 4)
+    A = H2.build(pts, K, H, chi, 1e-6, leafsize=32, host_only=1)
+    r0 = A.export()
+    Z0, _ = dense_from_rep(r0)
+    chi2 = chi * (1.0 + 0.5 * np.random.default_rng(2).random(N))
+    A.set_chi(chi2)
+    r1 = A.export()
+    Z1, full = dense_from_rep(r1)
+    e = np.sqrt(chi2 / chi)[r0["perm"]]
+    ref = np.eye(N) + e[:, None] * (Z0 - np.eye(N)) * e[None, :]
+    assert np.linalg.norm(Z1 - ref) <= 1e-13 * np.linalg.norm(ref)
+    assert np.array_equal(r0["rank"], r1["rank"])
+    assert np.allclose(r1["dscale"], np.sqrt(chi2), rtol=1e-15, atol=0)
+    for V in full.values():
+        if V.shape[1]:
+            assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-12
+    for bad in (np.zeros(N), -chi, np.full(N, np.nan), chi[:5]):
+        with pytest.raises(H2Error) as ei:
+            A.set_chi(bad)
+        assert ei.value.status == -1
+    assert np.array_equal(A.export()["S"], r1["S"])
     A.close()

@@ -13,7 +13,7 @@ CLOCKS = {"sm_max_mhz": 2070.0}
 
 def test_roofline_picks_longest_flop_counted_class():
     st = _stats({
-        "jacobi_cluster": {"launches": 17, "ms": 100.0, "flops": 0},       # no flop count: not a candidate
+        "jacobi_cluster": {"launches": 17, "ms": 100.0, "flops": 0, "bytes": 0},  # no count: not a candidate
         "gemm:schur": {"launches": 33, "ms": 25.0, "flops": 1.0e12, "pipe": "tcgen05_tf32x3"},
         "gemm:matvec couple": {"launches": 2, "ms": 36.0, "flops": 3.3e10, "pipe": "fp64"},
     })
@@ -43,6 +43,25 @@ def test_roofline_peak_follows_the_recorded_pipe():
 
 def test_roofline_without_flop_counts_is_absent():
     assert bench.roofline(_stats({"jacobi": {"launches": 3, "ms": 5.0, "flops": 0}}), CLOCKS) is None
+
+
+def test_memory_bound_class_takes_the_hbm_peak():
+    pv, _ = bench.peaks()
+    r = bench.roofline(_stats({"copy:merge": {"launches": 4, "ms": 2.0, "flops": 0, "bytes": 2.0e9}}), CLOCKS)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 1000.0) < 1e-9 and abs(r["frac"] - 1000.0 / pv["hbm_gbs"]) < 1e-12
+
+
+def test_roofline_table_rows_by_time():
+    st = _stats({
+        "gemm:schur": {"launches": 3, "ms": 5.0, "flops": 1.0e12, "pipe": "tcgen05_tf32x3"},
+        "copy:merge": {"launches": 4, "ms": 2.0, "flops": 0, "bytes": 2.0e9},
+        "jacobi": {"launches": 3, "ms": 9.0, "flops": 0, "bytes": 0},
+        "pchol_wy": {"launches": 2, "ms": 7.0, "flops": 3.0e9, "pipe": "fp64"},
+    })
+    rows = bench.roofline_table(st, CLOCKS)
+    assert [r["kernel"] for r in rows] == ["pchol_wy", "gemm:schur", "copy:merge"]
+    assert rows[0]["bound"] == "alu" and rows[2]["bound"] == "hbm"
 
 
 def test_reference_arm_names_our_config():

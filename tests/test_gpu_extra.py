@@ -1,0 +1,207 @@
+"""GPU checks of the construction, the explicit inverse, the failure statuses
+and the contrast update, each against something independent of the CUDA path:
+
+* h2_build on the GPU (far-field Grams in k_kgram) against the dense kernel
+  matrix (10 eps_build) and against the same build done on the host;
+* H2_USE_INVERSE solves (eq. 35) against the oracle's explicit inverse and
+  against a dense solve;
+* H2_ENOMEM from the arena cap, H2_ENOCONV from a refinement that cannot
+  reach its tolerance, and a context that stays usable after both;
+* h2_set_chi against the dense rescaled matrix, and the autograd node taking
+  a gradient step in chi on one context against a dense solve at the new chi.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint, factor, kernel
+from oracle import h2 as oh2
+from paper_1703_06155_gb300 import inputs
+
+from _h2io import dense_from_rep, from_tree, oracle_to_rep, to_tree
+from _problems import H, K, factorization, h2_dense, h2_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("n", [12, 16])
+def test_gpu_build_matches_dense_and_host_build(dev, n):
+    from paper_1703_06155_gb300 import H2
+    eps = 1e-6
+    pts = inputs.grid_points(n, H)
+    N = len(pts)
+    chi = inputs.chi_random_cells(N, 4)
+    A = H2.build(pts, K, H, chi, eps)  # GPU far-field Grams
+    B = H2.build(pts, K, H, chi, eps, host_only=1)
+    ra, rb = A.export(), B.export()
+    assert np.array_equal(ra["perm"], rb["perm"])
+    Za, _ = dense_from_rep(ra)
+    Zb, _ = dense_from_rep(rb)
+    idx = ra["perm"]
+    Zex = kernel.entries(pts, chi, idx, idx, K, H)
+    ea, eb = rel(Za, Zex), rel(Zb, Zex)
+    print("grid%d build: GPU %.2e, host %.2e of ||Z||_F; ranks equal on %.1f %% of the clusters" % (
+        n, ea, eb, 100.0 * np.mean(ra["rank"] == rb["rank"])))
+    assert ea < 10 * eps and eb < 10 * eps
+    assert rel(Za, Zb) < 10 * eps
+    # the two Gram orders differ only in rounding: pivot decisions at ties aside,
+    # the same skeleton ranks
+    assert np.mean(ra["rank"] == rb["rank"]) >= 0.95
+    A.close()
+    B.close()
+
+
+def test_inverse_matches_oracle_inverse_and_dense(dev):
+    eps = 1e-6
+    Hm = h2_problem(12, 64, eps)
+    Fz = factorization(12, 64, eps, eps, "colored")
+    inv = factor.invert(Fz)
+    from paper_1703_06155_gb300 import H2
+    A = H2.load(oracle_to_rep(Hm))
+    A.factorize(eps, "fp64")
+    A.invert()
+    b = inputs.rhs_gaussian(Hm.tree.N, 3, 19)
+    xi = A.solve(torch.from_numpy(b).to(dev), use_inverse=True).cpu().numpy()
+    x_oi = from_tree(Hm, factor.solve(Fz, to_tree(Hm, b), inverse=inv))
+    Zd = h2_dense(12, 64, eps)
+    xe = from_tree(Hm, np.linalg.solve(Zd, to_tree(Hm, b)))
+    print("inverse apply: vs oracle eq. 35 inverse %.2e, vs dense solve %.2e" % (rel(xi, x_oi), rel(xi, xe)))
+    assert rel(xi, x_oi) <= 10 * eps
+    assert rel(xi, xe) <= 10 * eps
+    # mixed-precision factors: the inverse apply refines to the dense solution
+    A.factorize(eps, "mixed")
+    A.invert()
+    xr = A.solve(torch.from_numpy(b).to(dev), use_inverse=True, refine=True, tol=1e-12, max_iter=30).cpu().numpy()
+    assert rel(xr, xe) < 1e-10
+    A.close()
+
+
+def test_enomem_and_enoconv(dev):
+    from paper_1703_06155_gb300 import H2, H2Error
+    eps = 1e-6
+    Hm = h2_problem(12, 64, eps)
+    rep = oracle_to_rep(Hm)
+    with pytest.raises(H2Error) as ei:
+        H2.load(rep, arena_cap_bytes=1 << 16)  # the H^2 upload alone needs more
+    assert ei.value.status == -2
+    A0 = H2.load(rep)
+    base = A0.stats()["dev_bytes"]
+    A0.close()
+    A = H2.load(rep, arena_cap_bytes=base + (1 << 20))  # room for the matrix, not for the factors
+    with pytest.raises(H2Error) as ei:
+        A.factorize(eps, "fp64")
+    assert ei.value.status == -2 and b"cap" in ei.value.args[0].encode()
+    with pytest.raises(H2Error) as ei:
+        A.solve(torch.zeros(Hm.tree.N, dtype=torch.complex128, device=dev))
+    assert ei.value.status == -8  # no factorization: call out of order
+    # the context still multiplies (its H^2 matrix is intact)
+    x = inputs.rhs_gaussian(Hm.tree.N, 1, 3)[:, 0]
+    y = A.matvec(torch.from_numpy(x).to(dev)).cpu().numpy()
+    assert rel(y, from_tree(Hm, oh2.matvec(Hm, to_tree(Hm, x)))) < 1e-13
+    A.close()
+    # refinement that cannot reach its tolerance: H2_ENOCONV, x = last iterate
+    B = H2.load(rep)
+    B.factorize(eps, "mixed")
+    b = torch.from_numpy(inputs.rhs_gaussian(Hm.tree.N, 1, 7)[:, 0]).to(dev)
+    with pytest.raises(H2Error) as ei:
+        B.solve(b, refine=True, tol=1e-15, max_iter=0)
+    assert ei.value.status == -4
+    x = B.solve(b, refine=True, tol=1e-15, max_iter=0, allow_noconv=True)
+    assert B.last_solve["status"] == -4 and B.last_solve["iters"] == 0
+    assert 1e-15 < B.last_solve["resid"] < 1e-3
+    assert rel(x.cpu().numpy(), B.solve(b).cpu().numpy()) < 1e-12  # no correction was applied
+    B.close()
+
+
+def _dense_A(Hm, Zd_tree, chi):
+    """A = D^{-1/2} Z D^{1/2} in global order from the tree-order dense Z_H2."""
+    p = Hm.tree.perm
+    Z = np.empty_like(Zd_tree)
+    Z[np.ix_(p, p)] = Zd_tree
+    s = np.sqrt(chi)
+    return Z * (s[None, :] / s[:, None])
+
+
+def test_set_chi_matches_dense_rescaled_matrix(dev):
+    from paper_1703_06155_gb300 import H2
+    eps = 1e-6
+    Hm = h2_problem(12, 64, eps, percell_seed=4)
+    N = Hm.tree.N
+    chi = inputs.chi_random_cells(N, 4)
+    Zd = h2_dense(12, 64, eps, percell_seed=4)
+    A = H2.load(oracle_to_rep(Hm, dscale=np.sqrt(chi)))
+    chi2 = chi * (1.0 + 0.2 * np.random.default_rng(8).random(N))
+    A.set_chi(chi2)
+    # Z' = I + E (Z - I) E, E = diag(sqrt(chi2 / chi)) in tree order
+    e = np.sqrt(chi2 / chi)[Hm.tree.perm]
+    Z2 = np.eye(N) + e[:, None] * (Zd - np.eye(N)) * e[None, :]
+    A2 = _dense_A(Hm, Z2, chi2)
+    x = inputs.rhs_gaussian(N, 2, 21)
+    y = A.matvec(torch.from_numpy(x).to(dev)).cpu().numpy()
+    assert rel(y, A2 @ x) < 1e-12
+    # and Z' is the dense kernel matrix at chi2 to the construction accuracy
+    idx = Hm.tree.perm
+    Zex = kernel.entries(Hm.pts, chi2, idx, idx, K, H)
+    assert rel(Z2, Zex) < 10 * eps
+    with pytest.raises(Exception) as ei:
+        A.solve(torch.from_numpy(x).to(dev))
+    assert getattr(ei.value, "status", None) == -8  # factors were invalidated
+    A.factorize(eps, "mixed")
+    xs = A.solve(torch.from_numpy(x).to(dev), refine=True, tol=1e-13, max_iter=30).cpu().numpy()
+    assert rel(xs, np.linalg.solve(A2, x)) < 1e-10
+    A.close()
+
+
+def test_autograd_step_in_chi_on_one_context(dev):
+    # one gradient step in chi: the node moves its context to the new chi
+    # (h2_set_chi + refactorization) and the solution equals a dense solve of
+    # the rescaled matrix; the gradient at the new chi matches the dense FP64
+    # adjoint gradient there
+    from paper_1703_06155_gb300 import H2, autograd
+    eps = 1e-6
+    Hm = h2_problem(12, 64, eps, percell_seed=4)
+    N = Hm.tree.N
+    pts = Hm.pts
+    chi = inputs.chi_random_cells(N, 4)
+    Zd = h2_dense(12, 64, eps, percell_seed=4)
+    A = H2.load(oracle_to_rep(Hm, dscale=np.sqrt(chi)))
+    A.factorize(eps, "mixed")
+    b = inputs.rhs_plane_wave(pts, K)
+    probes = inputs.fibonacci_sphere(64, pts.mean(axis=0), 2.0 * (np.sqrt(3.0) / 2.0) * 12 * H)
+    G = torch.from_numpy(adjoint.probe_matrix(probes, pts, K, H)).to(dev)
+    bt = torch.from_numpy(b).to(dev)
+
+    def loss_grad(c_np):
+        c = torch.tensor(c_np, dtype=torch.float64, device=dev, requires_grad=True)
+        x = autograd.solve(A, c, bt, refine=True, tol=1e-13)
+        L = torch.sum(torch.abs(G @ (c * x)) ** 2)
+        L.backward()
+        return float(L.detach()), c.grad.cpu().numpy(), x.detach().cpu().numpy()
+
+    L0, g0, _ = loss_grad(chi)
+    step = 0.05 * np.max(chi) / np.max(np.abs(g0))
+    chi1 = chi - step * g0
+    assert np.all(chi1 > 0)
+    L1, g1, x1 = loss_grad(chi1)
+    assert np.array_equal(A.chi, chi1)
+    e = np.sqrt(chi1 / chi)[Hm.tree.perm]
+    Z1 = np.eye(N) + e[:, None] * (Zd - np.eye(N)) * e[None, :]
+    A1 = _dense_A(Hm, Z1, chi1)
+    xd = np.linalg.solve(A1, b)
+    print("chi step: L %.6e -> %.6e, ||x - x_dense|| / ||x_dense|| = %.2e" % (L0, L1, rel(x1, xd)))
+    assert rel(x1, xd) < 1e-10
+    assert L1 < L0  # a descent step
+    # gradient at chi1 against the oracle's dense FP64 adjoint gradient there
+    _, _, gd, _ = adjoint.probe_gradient(A1, None, G.cpu().numpy(), chi1, b, 1.0)
+    assert np.max(np.abs(g1 - gd)) <= 1e-8 * np.max(np.abs(gd)), np.max(np.abs(g1 - gd)) / np.max(np.abs(gd))
+    A.close()

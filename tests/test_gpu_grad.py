@@ -124,11 +124,3 @@ def test_grad_chi_kernel_forms(setup):
     ctx.grad_chi(T(x), T(mu), None, alpha=2.0, out=out)
     ctx.grad_chi(T(x), T(mu), None, alpha=2.0, out=out, accumulate=True)
     assert np.max(np.abs(out.cpu().numpy() - 2 * ref0)) <= 1e-13 * np.max(np.abs(ref0))
-
-
-def test_autograd_rejects_other_contrast(setup):
-    from paper_1703_06155_gb300 import autograd
-    s = setup
-    chi_t = torch.tensor(s["chi"] * 1.01, dtype=torch.float64, device=s["dev"], requires_grad=True)
-    with pytest.raises(ValueError):
-        autograd.solve(s["ctx"], chi_t, torch.from_numpy(s["b"]).to(s["dev"]))

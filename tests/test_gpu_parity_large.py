@@ -1,0 +1,130 @@
+"""GPU path vs the oracle at the sizes and on the code paths of the benchmark.
+
+* 20^3 grid (N = 8,000, L = 7): the oracle's own H^2 matrix through h2_load,
+  factorized by the GPU in FP64 and in mixed precision.  FP64: solution within
+  10 eps of the oracle's; mixed + FP64 refinement: within 10 eps of the
+  oracle's as well; ranks per cluster within +-1 of the oracle's at every
+  level, and where they are not, the oracle's eigenvalues around the
+  threshold are reported; the launches must have used the cluster-wide
+  Step-0 kernels (16-CTA subspace kernel, cluster Jacobi), the double-float
+  Gram tiles, split-K products and the tcgen05 tiles.
+* 32^3 grid (N = 32,768, L = 9, the benchmark workload): the library's own
+  construction (GPU far-field Grams), the benchmark's launch configuration
+  (mixed factorization, refined 16-RHS solve to 1e-6).  The oracle cannot
+  factorize this size in a test, so the result is checked on 64 sampled rows
+  of the exact matrix A = I + K D_chi, evaluated one by one by the oracle's
+  kernel: ||A x - b|| on those rows is bounded by the H^2 residual plus the
+  construction accuracy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import factor, kernel
+from oracle import h2 as oh2
+from paper_1703_06155_gb300 import inputs
+
+from _h2io import from_tree, oracle_to_rep, to_tree
+from _problems import H, K, h2_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def grid20():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    Hm = h2_problem(20, 64, EPS)
+    obs = []
+    Fz = factor.factorize(Hm, EPS, "colored", observe=obs.append)
+    b = inputs.rhs_gaussian(Hm.tree.N, 1, 0)[:, 0]
+    x_orc = from_tree(Hm, factor.solve(Fz, to_tree(Hm, b)))
+    res_orc = np.linalg.norm(oh2.matvec(Hm, to_tree(Hm, x_orc)) - to_tree(Hm, b)) / np.linalg.norm(b)
+    return dict(H=Hm, Fz=Fz, obs=obs, b=b, x_orc=x_orc, res_orc=res_orc)
+
+
+def _rank_report(g, A):
+    """Per-cluster kept ranks of the GPU factorization against the oracle's."""
+    Hm, Fz = g["H"], g["Fz"]
+    near = {}
+    for rec in g["obs"]:
+        w, thr = rec["eig"], rec["thr"]
+        near[(rec["level"], rec["cluster"])] = [float(v / thr) for v in w if 0.5 <= v / thr <= 2.0]
+    worst, bad = 0, []
+    for li, lev in enumerate(Fz.levels):
+        l = Hm.L - li
+        _, kt = A.level_ranks(l)
+        d = kt.astype(int) - lev.kt.astype(int)
+        worst = max(worst, int(np.abs(d).max()))
+        for i in np.nonzero(np.abs(d) > 1)[0]:
+            bad.append((l, int(i), int(kt[i]), int(lev.kt[i]), near.get((l, int(i)), [])))
+    return worst, bad
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parity_grid20(grid20, prec):
+    from paper_1703_06155_gb300 import H2
+    g = grid20
+    Hm, b = g["H"], g["b"]
+    assert g["res_orc"] <= EPS, g["res_orc"]
+    A = H2.load(oracle_to_rep(Hm))
+    A.factorize(EPS, prec)
+    dev = torch.device("cuda:0")
+    bt = torch.from_numpy(b).to(dev)
+    if prec == "fp64":
+        x = A.solve(bt).cpu().numpy()
+    else:
+        x = A.solve(bt, refine=True, tol=1e-10, max_iter=30).cpu().numpy()
+    err = rel(x, g["x_orc"])
+    print("grid20 %s: ||x - x_oracle|| / ||x_oracle|| = %.3e (oracle residual %.2e)" % (prec, err, g["res_orc"]))
+    assert err <= 10 * EPS, err
+    worst, bad = _rank_report(g, A)
+    print("grid20 %s: largest per-cluster rank difference %d; beyond +-1: %s" % (prec, worst, bad[:8]))
+    assert not bad, bad
+    paths = A.stats()["paths"]
+    print("grid20 %s paths:" % prec, paths)
+    assert any(k.startswith("jacobi_cluster:cta") for k in paths), paths
+    assert paths.get("pchol_wy:cta16", 0) > 0, paths
+    assert any(k.startswith("gemm_splitk:") for k in paths), paths
+    if prec == "mixed":
+        assert paths.get("gemm:fp32_df:32x32", 0) > 0, paths
+        assert paths.get("gemm:tcgen05_tf32x3:64x64", 0) > 0, paths
+    A.close()
+
+
+def test_headline_grid32_sampled_exact_rows():
+    # the benchmark step on the benchmark workload: library construction,
+    # mixed factorization, refined 16-RHS solve to 1e-6 (bench.py's settings)
+    from paper_1703_06155_gb300 import H2
+    assert torch.cuda.is_available()
+    n, nrhs, seed, chi = 32, 16, 1, 3.0
+    pts = inputs.grid_points(n, H)
+    N = len(pts)
+    A = H2.build(pts, K, H, chi, EPS)
+    A.factorize(EPS, "mixed")
+    b = inputs.rhs_gaussian(N, nrhs, seed)
+    x = A.solve(torch.from_numpy(b).cuda(), refine=True, tol=1e-6, max_iter=30).cpu().numpy()
+    res_h2 = A.last_solve["resid"]
+    assert res_h2 <= 1e-6
+    rows = np.random.default_rng(5).choice(N, 64, replace=False)
+    chiv = inputs.chi_uniform(N, chi)
+    # A = D^{-1/2} Z D^{1/2} with Z the oracle's scaled kernel matrix
+    Zr = kernel.entries(pts, chiv, rows, np.arange(N), K, H)
+    Ax = (Zr @ (np.sqrt(chiv)[:, None] * x)) / np.sqrt(chiv[rows])[:, None]
+    r = Ax - b[rows]
+    rho = np.linalg.norm(r, axis=0) / np.linalg.norm(b[rows], axis=0)
+    print("grid32 headline: H^2 residual %.2e, sampled exact-row residual max %.2e" % (res_h2, rho.max()))
+    assert rho.max() <= 10 * EPS, rho
+    paths = A.stats()["paths"]
+    print("grid32 paths:", paths)
+    for p in ("pchol_wy:cta16", "jacobi_cluster:cta16", "gemm:fp32_df:32x32", "gemm:tcgen05_tf32x3:64x64"):
+        assert paths.get(p, 0) > 0, (p, paths)
+    assert any(k.startswith("gemm_splitk:") for k in paths), paths
+    A.close()
