@@ -56,6 +56,8 @@ def parse():
                    help="Step 2 / panel applications: 0 auto, 1 in-place kernel, 2 GEMM + copy")
     p.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                    help="complex64 GEMM tiles: 2 tcgen05, 1 warp-level TF32 MMA, 0 FP32 FMA (default: library's)")
+    p.add_argument("--eig-solver", type=int, default=None, choices=[0, 1],
+                   help="Step-0 eigen-decomposition: 0 tridiagonal + QL, 1 cyclic Jacobi (default: library's)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison factorization (large grids)")
     p.add_argument("--arena-cap-gb", type=float, default=0.0,
                    help="cap on the library's device memory (h2_opts.arena_cap_bytes; 0 = none)")
@@ -116,7 +118,10 @@ def workload_name(args):
 
 
 def tc_opts(args):
-    return {} if args.tensor_cores is None else {"tensor_cores": args.tensor_cores}
+    o = {} if args.tensor_cores is None else {"tensor_cores": args.tensor_cores}
+    if args.eig_solver is not None:
+        o["eig_solver"] = args.eig_solver
+    return o
 
 
 def peaks():

@@ -101,6 +101,11 @@ typedef struct {
                             accumulation): 1 (default) on the FP32 pipe, as
                             exact products summed in double-float and
                             flushed to FP64 every 8 terms; 0: FP64 FMAs   */
+  int eig_solver;        /* Step-0 eigen-decomposition of the Ritz matrix
+                            (eq. 17): 0 (default) Householder reduction to
+                            real tridiagonal form + implicit QL with
+                            accumulated rotations (orders up to 452, cyclic
+                            Jacobi above); 1 cyclic Jacobi throughout      */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -297,7 +302,7 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 /*
  * h2_set_opts - change the run-time tunables of a context (apply_path,
  * solve_graph, split_target, cluster_max, tile_policy, tensor_cores,
- * gram_emulation, profile) without
+ * gram_emulation, eig_solver, profile) without
  * rebuilding it; the other fields of *opts are ignored.  They take effect at
  * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
  * counterpart in the paper: used by the autotuner.

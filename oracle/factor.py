@@ -83,7 +83,22 @@ def _round(X, dtype):
     return X if dtype == np.complex128 else X.astype(dtype).astype(np.complex128)
 
 
-def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
+def ancestor_map(H, l, a, lv):
+    """E with V_A(rows of a) = V_a E for the ancestor A of cluster a (level l)
+    at level lv < l: the product of the transfer blocks on the path from a up
+    to A (eq. 3 applied once per level)."""
+    E = np.eye(int(H.rank[l][a]), dtype=np.complex128)
+    c = a
+    for ll in range(l - 1, lv - 1, -1):
+        p = c // 2
+        k1 = int(H.rank[ll + 1][2 * p])
+        Tp = H.T[ll][p]
+        E = E @ (Tp[:k1] if c % 2 == 0 else Tp[k1:])
+        c = p
+    return E
+
+
+def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop_level=None):
     """Factorize Z_H2 (Algorithm 1).  `bulk`=np.complex64 rounds the Schur /
     LU / transform products to FP32 complex, emulating the mixed-precision
     path; rank decisions (Step 0/1) always run in FP64.  `observe`, if given,
@@ -91,8 +106,14 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
     (level, cluster, incoming basis B, the active parts of the row and column
     fill-ins, nu^2, the eigenvalues of G_i in descending order, the threshold
     (eps nu_i)^2, the number r of kept directions and V_add); it only reads
-    them."""
+    them.  `stop_level` (Sec. III-C, last paragraph: the factorization may
+    stop at a level before l0 is reached): levels L .. stop_level are
+    processed, and the remaining matrix of all pairs at stop_level is
+    factorized as the final block; a pair that lies inside an ancestor's
+    admissible block enters it as pad(E_a S E_b^T) + F, E from
+    `ancestor_map` (the coupling in the level's incoming bases, eq. 20)."""
     tree, part, L, l0 = H.tree, H.part, H.L, H.l0
+    ls = l0 if stop_level is None else max(l0, min(L, int(stop_level)))
     Fz = Factorization()
     Fz.H, Fz.eps, Fz.ordering = H, eps, ordering
     Fz.levels = []
@@ -101,7 +122,7 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
     B = {c: H.V[c].copy() for c in range(2 ** L)}
     near = {p: H.D[p].copy() for p in part.inad[L]}
     fill = {}
-    for l in range(L, l0 - 1, -1):
+    for l in range(L, ls - 1, -1):
         near_set = set(part.inad[l])
         adm_set = set(part.adm[l])
         nbrs = part.near_lists(l)
@@ -263,11 +284,20 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
             if (a, b) in adm_set:
                 S = H.S[l][(a, b)]
                 X[:S.shape[0], :S.shape[1]] = S                 # eq. (20)
+            elif l > l0:
+                # inside the admissible block of an ancestor pair (final block
+                # of an early stop): that coupling in the level's bases
+                for lv in range(l - 1, l0 - 1, -1):
+                    A_, B_ = a >> (l - lv), b >> (l - lv)
+                    if (A_, B_) in H.S[lv]:
+                        S = ancestor_map(H, l, a, lv) @ H.S[lv][(A_, B_)] @ ancestor_map(H, l, b, lv).T
+                        X[:S.shape[0], :S.shape[1]] = S
+                        break
             if (a, b) in fill:
                 X += fill[(a, b)][m[a]:, m[b]:]                 # eq. (22)/(33)
             return X
 
-        if l > l0:
+        if l > ls:
             # ---- merge to level l-1 (eq. 23, eq. 24, Fig. 2 g-i) ----
             npar = np.array([kt[2 * p] + kt[2 * p + 1] for p in range(2 ** (l - 1))], dtype=np.int64)
             Bn = {}
@@ -298,12 +328,13 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None):
                 fill_n[(pa, pb)][ro:ro + kt[a], co:co + kt[b]] += Fm[m[a]:, m[b]:]
             n, B, near, fill = npar, Bn, near_n, fill_n
         else:
-            # ---- final block: all pairs at level l0 (Alg. 1, last line) ----
+            # ---- final block: all pairs at level l0, or at the stop level
+            # (Alg. 1, last line; Sec. III-C) ----
             off = np.concatenate([[0], np.cumsum(kt)])
             R = np.zeros((off[-1], off[-1]), dtype=np.complex128)
             for a in range(nc):
                 for b in range(nc):
-                    assert (a, b) in near_set or (a, b) in adm_set
+                    assert l > l0 or (a, b) in near_set or (a, b) in adm_set
                     R[off[a]:off[a + 1], off[b]:off[b + 1]] = kept(a, b)
             Fz.root_size = int(off[-1])
             Fz.root_off = off

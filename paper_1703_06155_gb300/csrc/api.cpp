@@ -245,12 +245,14 @@ void h2_default_opts(h2_opts* o) {
   o->tile_policy = 0;
   o->tensor_cores = 2;
   o->gram_emulation = 1;
+  o->eig_solver = 0;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   if (!ctx || !o || o->apply_path < 0 || o->apply_path > 2 || o->split_target < 0 || o->cluster_max < 0 ||
       o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
-      o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1)
+      o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1 ||
+      o->eig_solver < 0 || o->eig_solver > 1)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -260,6 +262,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   c.tile_policy = o->tile_policy;
   c.tensor_cores = o->tensor_cores;
   c.gram_emulation = o->gram_emulation;
+  c.eig_solver = o->eig_solver;
   c.profile = o->profile;
   ctx->c.graphs.clear();
   return H2_OK;
@@ -648,7 +651,7 @@ h2_status h2_factorize(h2_ctx* ctx, double eps_fill, int prec) {
     try {
       factorize(ctx->c, eps_fill, prec == H2_FP64 ? P64 : P32);
     } catch (...) {
-      ctx->c.factored = false;
+      drop_factors(ctx->c);
       throw;
     }
   });
@@ -760,7 +763,7 @@ h2_status h2_factorize_batch(h2_ctx* const* ctxs, int count, double eps_fill, in
     try {
       factorize_group(cores(xs), eps_fill, prec == H2_FP64 ? P64 : P32);
     } catch (...) {
-      for (h2_ctx* x : xs) x->c.factored = false;
+      for (h2_ctx* x : xs) drop_factors(x->c);
       throw;
     }
   });

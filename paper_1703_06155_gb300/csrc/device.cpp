@@ -108,6 +108,28 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
   return p;
 }
 
+void dev_free(Ctx& c, DevBuf& b) {
+  if (!b.p) return;
+  c.dev_bytes -= b.bytes;
+  b.release();
+  c.gen++;
+}
+
+void drop_factors(Ctx& c) {
+  cudaStreamSynchronize(c.stream);  // nothing of the failed call may still use the buffers
+  cudaGetLastError();
+  for (LevelF& F : c.lev)
+    for (DevBuf* b : {&F.near_buf, &F.fill_buf, &F.B_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf, &F.Vp_buf})
+      dev_free(c, *b);
+  c.lev.clear();
+  for (DevBuf* b : {&c.root.R, &c.root.piv, &c.root.Linv, &c.root.Uinv, &c.root.Rinv}) dev_free(c, *b);
+  c.root = RootF();
+  for (DevBuf* b : {&c.scratch, &c.scratch2, &c.gemm_ws, &c.jac_buf, &c.applybuf, &c.frobbuf}) dev_free(c, *b);
+  c.factored = false;
+  c.inverted = false;
+  c.graphs.clear();
+}
+
 Stager::~Stager() {
   if (pinned) cudaFreeHost(pinned);
 }

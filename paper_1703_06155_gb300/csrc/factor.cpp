@@ -398,6 +398,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   }
   std::vector<std::vector<int>> r(nj), sweeps(nj);
   size_t jac_rec = SIZE_MAX;
+  bool heev_used = false;
   std::vector<std::pair<size_t, size_t>> eig_of;
   for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
   hsA.reset();
@@ -601,7 +602,28 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     run_gemm(lc, g2, P64, P64, P64, "WY 2");
     run_gemm(lc, g3, P64, P64, P64, "WY 3");
     run_gemm(lc, g4, P64, P64, P64, "ritz matrix");
-    if (!eig.empty()) {
+    const bool use_heev = lc.opts.eig_solver == 0 && maxr <= heev_max_order();
+    if (!eig.empty() && use_heev) {
+      const int i0 = lc.st.add(eig);
+      lc.st.upload(lc);
+      ProfScope ps(lc, "heev_cluster", 0.0, "fp64");
+      if (ps.on) jac_rec = ps.idx;
+      heev_used = true;
+      const int cmax = lc.opts.cluster_max > 0 ? lc.opts.cluster_max : 16;
+      const int csize = heev_cluster_size((int)eig.size(), maxr, cmax);
+      const int64_t per = heev_cluster_scratch(maxr);
+      double* js = (double*)dev_ensure(lc, lc.jac_buf, (size_t)per * eig.size() * sizeof(double));
+      int used = 0;
+      ck(heev_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, csize, js, (int*)lc.statusbuf.p, lc.stream,
+                      &used),
+         "tridiagonal QL eigen-decomposition");
+      lc.paths["heev_cluster:cta" + std::to_string(used)]++;
+      lc.launches++;
+      const int i1 = lc.st.add(sel);
+      lc.st.upload(lc);
+      ck(select_rank(lc.st.ptr<SelTask>(i1), (int)sel.size(), lc.stream), "select");
+      lc.launches++;
+    } else if (!eig.empty()) {
       const int i0 = lc.st.add(eig);
       lc.st.upload(lc);
       ProfScope ps(lc, maxr >= 48 ? "jacobi_cluster" : "jacobi", 0.0, "fp64");
@@ -639,13 +661,17 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   }
   sync_timed(lc, lc.stream, "sync after step 0");
   if (jac_rec != SIZE_MAX) {
-    // algorithmic flops of the Hermitian Jacobi: 24 r'^3 real flops per sweep
+    // algorithmic flops.  Hermitian Jacobi: 24 r'^3 real flops per sweep
     // (r'(r'-1)/2 complex rotations per sweep, each applied to two rows and
-    // two columns of the r' x r' matrix and to two columns of U)
+    // two columns of the r' x r' matrix and to two columns of U).
+    // Tridiagonal path: (16/3) r'^3 (Householder reduction) + 8 r'^3
+    // (back-transformation of r' vectors) + 3 r'^2 per QL sweep (a sweep's
+    // rotations, r'/2 of them on average, applied to the r' rows of Z)
     double fl = 0;
     for (auto [q, u] : eig_of) {
       const double rr = info[q][u].rp;
-      fl += 24.0 * rr * rr * rr * std::max(sweeps[q][u], 0);
+      const double sw = std::max(sweeps[q][u], 0);
+      fl += heev_used ? (16.0 / 3.0 + 8.0) * rr * rr * rr + 3.0 * rr * rr * sw : 24.0 * rr * rr * rr * sw;
     }
     lc.prof_open[jac_rec].flops = fl;
   }
@@ -1066,6 +1092,9 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
       const int L = H.L, l0 = H.l0;
       depth = std::max(depth, L - l0 + 1);
       if ((int)c.lev.size() != L - l0 + 1) {
+        for (LevelF& F : c.lev)
+          for (DevBuf* b : {&F.near_buf, &F.fill_buf, &F.B_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf, &F.Vp_buf})
+            dev_free(c, *b);
         c.lev.clear();
         c.lev.resize(L - l0 + 1);
       }

@@ -106,6 +106,11 @@ void ck(cudaError_t e, const char* what);
 
 // Grow-only device buffer allocation with arena accounting.
 void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes);
+// Frees a buffer of the context's arena accounting.
+void dev_free(Ctx& c, DevBuf& b);
+// Frees the factors of the last factorization and the factorization scratch
+// (after a failed factorization: the context keeps its H^2 matrix only).
+void drop_factors(Ctx& c);
 
 // Task staging: host task arrays are appended into one growing byte buffer,
 // copied into pinned memory and uploaded with cudaMemcpyAsync just before the

@@ -192,6 +192,13 @@ int64_t jacobi_cluster_scratch(int maxp);  // doubles per task
 cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
                                int csize, double* d_scratch, int* d_status,
                                cudaStream_t s, int* csize_used = nullptr);
+// the same decomposition by Householder tridiagonalization, implicit QL with
+// accumulated rotations and back-transformation (orders <= heev_max_order())
+int heev_max_order();
+int64_t heev_cluster_scratch(int maxp);  // doubles per task
+int heev_cluster_size(int ntasks, int maxp, int cmax);
+cudaError_t heev_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, double* d_scratch, int* d_status,
+                         cudaStream_t s, int* csize_used = nullptr);
 // Step 3 partial LU with pivoting (one CTA per task), then explicit L^{-1} P
 // and U^{-1} (two CTAs per task, in a second launch); maxm = the largest m of
 // the tasks (<= 4096)
