@@ -106,6 +106,12 @@ typedef struct {
                             real tridiagonal form + implicit QL with
                             accumulated rotations (orders up to 452, cyclic
                             Jacobi above); 1 cyclic Jacobi throughout      */
+  int stop_level;        /* early stop (Sec. III-C, last paragraph): 0
+                            (default) factorize levels L .. l0; s > l0:
+                            levels L .. s only, the remaining matrix of all
+                            level-s pairs (couplings of ancestor blocks
+                            expressed in the level-s bases) is the final
+                            dense block; clamped to [l0, L]                 */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -302,7 +308,7 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 /*
  * h2_set_opts - change the run-time tunables of a context (apply_path,
  * solve_graph, split_target, cluster_max, tile_policy, tensor_cores,
- * gram_emulation, eig_solver, profile) without
+ * gram_emulation, eig_solver, stop_level, profile) without
  * rebuilding it; the other fields of *opts are ignored.  They take effect at
  * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
  * counterpart in the paper: used by the autotuner.

@@ -11,6 +11,9 @@ for candidate settings of
   tensor_cores  complex64 tiles on tcgen05 / warp-level tensor-core MMAs
                 (3xTF32) or on FP32 FMAs,
   gram_emulation  FP64-accurate Step-0 Grams on the FP32 pipe / FP64 FMAs,
+  eig_solver    Step-0 eigen-decomposition: tridiagonal + QL / cyclic Jacobi,
+  stop_level    early stop of the factorization (Sec. III-C): l0 (0) or one
+                to three levels below it, the rest as one dense final block,
 
 one parameter at a time from the defaults (coordinate descent), keeps the
 fastest setting of each and leaves it set on the context.  Every timing runs
@@ -25,7 +28,14 @@ DEFAULT_SPACE = {
     "split_target": [0, 608, 2432],
     "cluster_max": [16, 8],
     "apply_path": [2, 1],
+    "eig_solver": [0, 1],
 }
+
+
+def stop_levels(ctx, extra=3):
+    """Candidate stop levels of a context: 0 (= l0) and l0 + 1 .. l0 + extra (<= L)."""
+    L, l0 = ctx._sizes()[1:3]
+    return [0] + [s for s in range(l0 + 1, min(L, l0 + extra) + 1)]
 
 
 def _time_step(ctx, b, eps, precision, tol, stream, repeats):
@@ -45,7 +55,10 @@ def _time_step(ctx, b, eps, precision, tol, stream, repeats):
 def autotune(ctx, b, eps, precision="mixed", tol=1e-6, space=None, repeats=2, stream=None, profile=0):
     """Returns (best settings, list of (settings, ms per step)); the best
     settings are left applied to `ctx`."""
-    space = dict(DEFAULT_SPACE if space is None else space)
+    if space is None:
+        space = dict(DEFAULT_SPACE)
+        space["stop_level"] = stop_levels(ctx)
+    space = dict(space)
     stream = stream or torch.cuda.current_stream()
     best = {k: v[0] for k, v in space.items()}
     log = []

@@ -246,13 +246,14 @@ void h2_default_opts(h2_opts* o) {
   o->tensor_cores = 2;
   o->gram_emulation = 1;
   o->eig_solver = 0;
+  o->stop_level = 0;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   if (!ctx || !o || o->apply_path < 0 || o->apply_path > 2 || o->split_target < 0 || o->cluster_max < 0 ||
       o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
       o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1 ||
-      o->eig_solver < 0 || o->eig_solver > 1)
+      o->eig_solver < 0 || o->eig_solver > 1 || o->stop_level < 0)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -263,6 +264,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   c.tensor_cores = o->tensor_cores;
   c.gram_emulation = o->gram_emulation;
   c.eig_solver = o->eig_solver;
+  c.stop_level = o->stop_level;
   c.profile = o->profile;
   ctx->c.graphs.clear();
   return H2_OK;
@@ -297,7 +299,8 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   h2_default_opts(&x->c.opts);
   if (opts) x->c.opts = *opts;
   if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2 ||
-      x->c.opts.gram_emulation < 0 || x->c.opts.gram_emulation > 1) {
+      x->c.opts.gram_emulation < 0 || x->c.opts.gram_emulation > 1 || x->c.opts.eig_solver < 0 ||
+      x->c.opts.eig_solver > 1 || x->c.opts.stop_level < 0) {
     delete x;
     g_err = "h2_build: bad options";
     return H2_EINVAL;
@@ -922,6 +925,7 @@ h2_status h2_set_chi(h2_ctx* ctx, const double* chi, int64_t chi_len) {
     c.epoch++;
     c.graphs.clear();
     c.snorm2_cache.clear();
+    c.cov_level = -1;
     rescale_h2(H, e);
     H.dscale = sq;
     if (!c.opts.host_only) finish_setup(ctx, c.stream);
@@ -950,7 +954,8 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
   o.precision(10);
   o << "{\"N\":" << c.H.tree.N << ",\"L\":" << c.H.L << ",\"l0\":" << c.H.l0 << ",\"factored\":" << (c.factored ? 1 : 0)
     << ",\"prec\":\"" << (c.prec == P64 ? "fp64" : "mixed") << "\",\"eps_fill\":" << c.eps_fill
-    << ",\"t_build_ms\":" << c.stats.t_build_ms << ",\"t_factor_ms\":" << c.stats.t_factor_ms
+    << ",\"stop_level\":" << c.stats.stop_level << ",\"t_build_ms\":" << c.stats.t_build_ms
+    << ",\"t_factor_ms\":" << c.stats.t_factor_ms
     << ",\"t_solve_ms\":" << c.stats.t_solve_ms << ",\"t_factor_sync_ms\":" << c.stats.t_sync_ms
     << ",\"flops_factor\":" << c.stats.flops_factor
     << ",\"launches_factor\":" << c.stats.launches_factor << ",\"launches_solve\":" << c.stats.launches_solve

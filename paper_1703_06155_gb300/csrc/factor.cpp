@@ -145,6 +145,8 @@ void run_copy(Ctx& c, CopyBatch& b, const char* what) {
 
 namespace {
 
+void ensure_covered(Ctx& lc, Ctx& c, int ls);
+
 // Step 2 / panel applications: in-place kernel or GEMM + copy (h2_opts.apply_path)
 void run_apply_auto(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
   if (c.opts.apply_path == 1) run_apply(c, b, left, prec, what);
@@ -922,6 +924,7 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
   const size_t es = esz(prec);
   CopyBatch as, ac;
   int npan_max = 0;
+  for (Ctx* cp : cs) ensure_covered(lc, *cp, cp->lev.back().l);
   for (Ctx* cp : cs) {
     Ctx& c = *cp;
     LevelF& F = c.lev.back();
@@ -944,9 +947,17 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
                  F.n[a], F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b]);
         } else {
           auto ai = c.adm_id[l].find(key);
-          if (ai == c.adm_id[l].end()) fail(H2_EINTERNAL, "final block: pair neither near nor admissible");
-          as.add((char*)c.dS.p + c.S_off[l][ai->second] * sizeof(cd), P64, F.k0[a], F.k0[a], F.k0[b], d, prec, n,
-                 F.kt[a], F.kt[b]);
+          if (ai != c.adm_id[l].end()) {
+            as.add((char*)c.dS.p + c.S_off[l][ai->second] * sizeof(cd), P64, F.k0[a], F.k0[a], F.k0[b], d, prec, n,
+                   F.kt[a], F.kt[b]);
+          } else {
+            // early stop: the pair lies inside an ancestor's admissible block
+            auto ci = c.cov_off.find(key);
+            if (c.cov_level != l || ci == c.cov_off.end())
+              fail(H2_EINTERNAL, "final block: pair neither near nor admissible");
+            as.add((char*)c.cov_buf.p + ci->second * sizeof(cd), P64, F.k0[a], F.k0[a], F.k0[b], d, prec, n,
+                   F.kt[a], F.kt[b]);
+          }
           auto it = F.fill_id.find(key);
           if (it != F.fill_id.end() && F.fill_live[it->second])
             ac.add(S.fill + (F.fill_off[it->second] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a],
@@ -1047,6 +1058,99 @@ void root_inverse_group(Ctx& lc, const std::vector<Ctx*>& cs) {
   }
 }
 
+// The last factorized level: l0, or the early-stop level of the options.
+int stop_of(const Ctx& c) {
+  const int l0 = c.H.l0, L = c.H.L;
+  return c.opts.stop_level > 0 ? std::max(l0, std::min(L, c.opts.stop_level)) : l0;
+}
+
+// Couplings of the pairs (a, b) of level ls > l0 that lie inside the
+// admissible block (A, B) of an ancestor level lv: in the level-ls bases of a
+// and b they are E_a S_AB E_b^T, where V_A(rows of a) = V_a E_a and E_a is the
+// product of the transfer blocks on the path from a up to A (eq. 3).  They
+// depend on the H^2 matrix only and are kept until it changes.  Launches go
+// to lc's stream; the buffers belong to c.
+void ensure_covered(Ctx& lc, Ctx& c, int ls) {
+  const H2Host& H = c.H;
+  const int l0 = H.l0;
+  if (ls <= l0 || c.cov_level == ls) return;
+  const int nc = 1 << ls;
+  const std::vector<int>& kl = H.rank[ls];
+  std::vector<std::vector<size_t>> eoff(nc, std::vector<size_t>(ls, 0));
+  size_t etot = 0;
+  for (int a = 0; a < nc; ++a)
+    for (int lv = ls - 1; lv >= l0; --lv) {
+      eoff[a][lv] = etot;
+      etot += (size_t)kl[a] * H.rank[lv][a >> (ls - lv)];
+    }
+  cd* E = (cd*)dev_ensure(c, c.cov_E, (etot + 1) * sizeof(cd));
+  const cd* T = (const cd*)c.dT.p;
+  auto tslice = [&](int lv, int child) {  // rows of `child` (level lv+1) in the transfer of its parent
+    const int p = child >> 1, k1 = H.rank[lv + 1][2 * p];
+    return T + c.T_off[lv][p] + ((child & 1) ? k1 : 0);
+  };
+  auto tld = [&](int lv, int child) { const int p = child >> 1; return H.rank[lv + 1][2 * p] + H.rank[lv + 1][2 * p + 1]; };
+  {
+    CopyBatch cb;
+    for (int a = 0; a < nc; ++a) {
+      const int kp = H.rank[ls - 1][a >> 1];
+      cb.add(tslice(ls - 1, a), P64, tld(ls - 1, a), kl[a], kp, E + eoff[a][ls - 1], P64, kl[a], kl[a], kp);
+    }
+    run_copy(lc, cb, "ancestor maps");
+  }
+  for (int lv = ls - 2; lv >= l0; --lv) {
+    GemmBatch g;
+    for (int a = 0; a < nc; ++a) {
+      const int c1 = a >> (ls - lv - 1), kc = H.rank[lv + 1][c1], kp = H.rank[lv][c1 >> 1];
+      g.task(E + eoff[a][lv], kl[a], kl[a], kp, 1.0, 0.0);
+      g.pair(E + eoff[a][lv + 1], kl[a], OP_N, tslice(lv, c1), tld(lv, c1), OP_N, kc);
+      g.close();
+    }
+    run_gemm(lc, g, P64, P64, P64, "ancestor maps");
+  }
+  std::set<Pair> near(H.part.inad[ls].begin(), H.part.inad[ls].end());
+  struct Cov { int a, b, lv, q; };
+  std::vector<Cov> cov;
+  for (int a = 0; a < nc; ++a)
+    for (int b = 0; b < nc; ++b) {
+      if (near.count({a, b}) || c.adm_id[ls].count(pkey(a, b))) continue;
+      int found = -1, q = -1;
+      for (int lv = ls - 1; lv >= l0 && found < 0; --lv) {
+        auto it = c.adm_id[lv].find(pkey(a >> (ls - lv), b >> (ls - lv)));
+        if (it != c.adm_id[lv].end()) { found = lv; q = it->second; }
+      }
+      if (found < 0) fail(H2_EINTERNAL, "early stop: a level pair lies in no block of the partition");
+      cov.push_back(Cov{a, b, found, q});
+    }
+  size_t ytot = 0, stot = 0;
+  std::vector<size_t> yoff(cov.size());
+  c.cov_off.clear();
+  for (size_t u = 0; u < cov.size(); ++u) {
+    const Cov& v = cov[u];
+    yoff[u] = ytot;
+    ytot += (size_t)kl[v.a] * H.rank[v.lv][v.b >> (ls - v.lv)];
+    c.cov_off[pkey(v.a, v.b)] = stot;
+    stot += (size_t)kl[v.a] * kl[v.b];
+  }
+  cd* Y = (cd*)dev_ensure(c, c.cov_Y, (ytot + 1) * sizeof(cd));
+  cd* S = (cd*)dev_ensure(c, c.cov_buf, (stot + 1) * sizeof(cd));
+  GemmBatch g1, g2;
+  for (size_t u = 0; u < cov.size(); ++u) {
+    const Cov& v = cov[u];
+    const int A = v.a >> (ls - v.lv), B = v.b >> (ls - v.lv);
+    const int kA = H.rank[v.lv][A], kB = H.rank[v.lv][B], ka = kl[v.a], kb = kl[v.b];
+    g1.task(Y + yoff[u], ka, ka, kB, 1.0, 0.0);  // Y = E_a S_AB
+    g1.pair(E + eoff[v.a][v.lv], ka, OP_N, (const cd*)c.dS.p + c.S_off[v.lv][v.q], kA, OP_N, kA);
+    g1.close();
+    g2.task(S + c.cov_off[pkey(v.a, v.b)], ka, ka, kb, 1.0, 0.0);  // Y E_b^T
+    g2.pair(Y + yoff[u], ka, OP_N, E + eoff[v.b][v.lv], kb, OP_T, kB);
+    g2.close();
+  }
+  run_gemm(lc, g1, P64, P64, P64, "ancestor couplings");
+  run_gemm(lc, g2, P64, P64, P64, "ancestor couplings");
+  c.cov_level = ls;
+}
+
 void check_status(Ctx& c) {
   int st = 0;
   ck(cudaMemcpyAsync(&st, c.statusbuf.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "read status");
@@ -1083,13 +1187,13 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
   ck(cudaMemsetAsync(lc.statusbuf.p, 0, 64, lc.stream), "status memset");
   ck(cudaStreamSynchronize(lc.stream), "sync");
   lc.st.begin();
-  int depth = 0;  // levels L .. l0 of the deepest instance
+  int depth = 0;  // levels L .. (l0 or the stop level) of the deepest instance
   {
     CopyBatch cb;
     for (Ctx* cp : cs) {
       Ctx& c = *cp;
       H2Host& H = c.H;
-      const int L = H.L, l0 = H.l0;
+      const int L = H.L, l0 = stop_of(c);
       depth = std::max(depth, L - l0 + 1);
       if ((int)c.lev.size() != L - l0 + 1) {
         for (LevelF& F : c.lev)
@@ -1098,6 +1202,7 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
         c.lev.clear();
         c.lev.resize(L - l0 + 1);
       }
+      c.stats.stop_level = l0;
       // leaf level: dense near blocks and leaf bases
       std::vector<int> n(1 << L);
       for (int t = 0; t < (1 << L); ++t) n[t] = (int)H.tree.size[L][t];

@@ -185,6 +185,7 @@ struct RootF {
 };
 
 struct Stats {
+  int stop_level = -1;  // last factorized level of the last factorization
   double t_factor_ms = 0, t_solve_ms = 0, t_build_ms = 0;
   double t_sync_ms = 0;  // factorization: host time blocked in stream synchronizes
   double flops_factor = 0;
@@ -249,6 +250,11 @@ struct Ctx {
   // column, per level (depends on the H^2 only; computed once)
   std::vector<std::vector<double>> snorm2_cache;
   std::vector<std::vector<int>> colour_cache;  // near-field colouring per level
+  // early stop at level cov_level > l0: couplings of the level's pairs that
+  // lie inside an ancestor's admissible block, E_a S E_b^T (FP64, k_a x k_b)
+  int cov_level = -1;
+  DevBuf cov_buf, cov_E, cov_Y;
+  std::unordered_map<int64_t, size_t> cov_off;
 };
 
 // A captured forward / backward (or adjoint) sweep of a group of instances:

@@ -207,3 +207,40 @@ def test_autograd_step_in_chi_on_one_context(dev):
     _, _, gd, _ = adjoint.probe_gradient(A1, None, G.cpu().numpy(), chi1, b, 1.0)
     assert np.max(np.abs(g1 - gd)) <= 1e-8 * np.max(np.abs(gd)), np.max(np.abs(g1 - gd)) / np.max(np.abs(gd))
     A.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_early_stop_matches_oracle(dev, prec):
+    # Sec. III-C: stop at a level above l0 and factorize the rest as one dense
+    # block.  eps_fill = 0: exact block LU; eps_fill = eps: within 10 eps of the
+    # oracle's factorization with the same stop level (FP64), or refined to the
+    # dense solution (mixed); the explicit inverse applies the same factors.
+    from paper_1703_06155_gb300 import H2
+    eps = 1e-6
+    Hm = h2_problem(12, 64, eps)
+    Zd = h2_dense(12, 64, eps)
+    b = inputs.rhs_gaussian(Hm.tree.N, 2, 29)
+    bt = torch.from_numpy(b).to(dev)
+    xe = from_tree(Hm, np.linalg.solve(Zd, to_tree(Hm, b)))
+    A = H2.load(oracle_to_rep(Hm))
+    for ls in range(Hm.l0 + 1, Hm.L + 1):
+        A.set_opts(stop_level=ls)
+        A.factorize(0.0, "fp64")
+        assert A.stats()["stop_level"] == ls
+        assert rel(A.solve(bt).cpu().numpy(), xe) < 1e-10, ls
+        A.factorize(eps, prec)
+        if prec == "fp64":
+            Fz = factor.factorize(Hm, eps, "colored", stop_level=ls)
+            x_orc = from_tree(Hm, factor.solve(Fz, to_tree(Hm, b)))
+            x = A.solve(bt).cpu().numpy()
+            print("stop level %d: vs oracle %.2e, vs dense %.2e" % (ls, rel(x, x_orc), rel(x, xe)))
+            assert rel(x, x_orc) <= 10 * eps
+            k0, kt = A.level_ranks(ls)
+            assert np.all(np.abs(kt.astype(int) - Fz.levels[-1].kt.astype(int)) <= 1)
+        else:
+            x = A.solve(bt, refine=True, tol=1e-12, max_iter=30).cpu().numpy()
+            assert rel(x, xe) < 1e-10
+        A.invert()
+        xi = A.solve(bt, use_inverse=True).cpu().numpy()
+        assert rel(xi, A.solve(bt).cpu().numpy()) < 1e-12 if prec == "fp64" else 1e-5
+    A.close()

@@ -128,3 +128,33 @@ def test_complex64_bulk_emulation():
     Fm = factor.factorize(H, 1e-6, "colored", bulk=np.complex64)
     x, hist = factor.refine(Fm, bt, tol=1e-13, max_iter=30)
     assert hist[-1] <= 1e-13 and rel(x, xe) < 1e-10, (hist, rel(x, xe))
+
+
+def test_early_stop_levels():
+    # Sec. III-C, last paragraph: the factorization may stop at any level
+    # above l0, the rest being factorized as one dense block.  With
+    # eps_fill = 0 every stop level gives an exact block LU of Z_H2; with
+    # eps_fill > 0 the residual stays at the eps level and decreases as the
+    # stop level moves towards the leaves (fewer truncations), and the final
+    # block grows.
+    eps = 1e-6
+    H = h2_problem(12, 64, eps)
+    Zd = h2_dense(12, 64, eps)
+    b = inputs.rhs_gaussian(H.tree.N, 2, 17)[H.tree.perm]
+    xe = np.linalg.solve(Zd, b)
+    sizes, res = [], []
+    for ls in range(H.l0, H.L + 1):
+        F0 = factor.factorize(H, 0.0, "colored", stop_level=ls)
+        assert len(F0.levels) == H.L - ls + 1
+        assert rel(factor.solve(F0, b), xe) < 1e-11, ls
+        Fe = factor.factorize(H, eps, "colored", stop_level=ls)
+        x = factor.solve(Fe, b)
+        res.append(np.linalg.norm(Zd @ x - b) / np.linalg.norm(b))
+        sizes.append(Fe.root_size)
+        # the explicit inverse (eq. 35) and the adjoint traversal work on the same factors
+        xi = factor.solve(Fe, b, inverse=factor.invert(Fe))
+        assert rel(xi, x) < 1e-12
+        xa = factor.solve_adjoint(Fe, b)
+        assert rel(xa, np.linalg.solve(Zd.conj().T, b)) < 10 * eps
+    assert max(res) <= 10 * eps and res[-1] <= res[0], res
+    assert all(s1 > s0 for s0, s1 in zip(sizes, sizes[1:])), sizes
