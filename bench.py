@@ -46,7 +46,9 @@ def parse():
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="grid", choices=["grid", "batch", "grad"],
+    p.add_argument("--rod-lengths", default="25,50,100,200,400",
+                   help="rod workload: lengths in wavelengths (cross-section 0.4 x 0.4, h = 0.1)")
+    p.add_argument("--workload", default="grid", choices=["grid", "batch", "grad", "rod"],
                    help="grid: one instance (default); batch: many independent instances in shared launches")
     p.add_argument("--instances", type=int, default=64, help="batch workload: number of instances")
     p.add_argument("--solve-graph-check", action="store_true",
@@ -57,7 +59,7 @@ def parse():
     p.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                    help="complex64 GEMM tiles: 2 tcgen05, 1 warp-level TF32 MMA, 0 FP32 FMA (default: library's)")
     p.add_argument("--eig-solver", type=int, default=None, choices=[0, 1],
-                   help="Step-0 eigen-decomposition: 0 tridiagonal + QL, 1 cyclic Jacobi (default: library's)")
+                   help="Step-0 eigen-decomposition: 0 cyclic Jacobi, 1 tridiagonal + QL (default: library's)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison factorization (large grids)")
     p.add_argument("--arena-cap-gb", type=float, default=0.0,
                    help="cap on the library's device memory (h2_opts.arena_cap_bytes; 0 = none)")
@@ -391,6 +393,64 @@ def run_grad(args):
     }))
 
 
+def run_rod(args):
+    """The rod workload of Sec. VI-B on a regular grid: cross-section 0.4 x 0.4
+    wavelengths, cells of 0.1 wavelength (4 x 4 per layer), eps_r = 2.54
+    (chi = 1.54), eps = 1e-4, length growing (--rod-lengths, wavelengths).
+    A 1-D configuration: the ranks stay bounded as it grows, so factorization,
+    solve and memory should grow linearly in N (eq. 44, Fig. 5).  Per length:
+    h2_build untimed, factorization and refined solve timed with CUDA events
+    (one warm-up, median of 3), peak device memory; the log-log slope of the
+    times against N is reported."""
+    import torch
+    from paper_1703_06155_gb300 import H2, inputs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    h, chi, eps = 0.1, 1.54, args.eps if args.eps != 1e-6 else 1e-4
+    rows = []
+    for length in [float(v) for v in args.rod_lengths.split(",")]:
+        pts = inputs.rod_points(length, h)
+        N = len(pts)
+        A = H2.build(pts, K, h, chi, eps, stream=stream, **tc_opts(args))
+        b = torch.from_numpy(inputs.rhs_gaussian(N, args.nrhs, args.seed)).to("cuda")
+        A.factorize(eps, args.prec)
+        A.solve(b, refine=True, tol=args.tol, max_iter=30)
+        fac, sol = [], []
+        for _ in range(3):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            e0.record(stream)
+            A.factorize(eps, args.prec)
+            e1.record(stream)
+            x = A.solve(b, refine=True, tol=args.tol, max_iter=30)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            fac.append(e0.elapsed_time(e1))
+            sol.append(e1.elapsed_time(e2))
+        st = A.stats()
+        res = float(torch.linalg.norm(A.matvec(x) - b) / torch.linalg.norm(b))
+        rows.append({"length_wavelengths": length, "N": N, "factorize_ms": float(np.median(fac)),
+                     "refined_solve_ms": float(np.median(sol)), "dev_peak_gb": st["dev_peak"] / 1e9,
+                     "kt_max": max(lv["kt_max"] for lv in st["levels"]), "final_residual": res,
+                     "refine_iters": A.last_solve["iters"]})
+        A.close()
+    Ns = np.array([r["N"] for r in rows], dtype=float)
+
+    def slope(key):
+        return float(np.polyfit(np.log(Ns), np.log([r[key] for r in rows]), 1)[0]) if len(rows) > 1 else None
+
+    print(json.dumps({
+        "metric": "H2 factorize unknowns/s on the rod workload (1-D, constant rank)",
+        "value": rows[-1]["N"] / (rows[-1]["factorize_ms"] / 1e3), "unit": "unknowns/s", "higher_is_better": True,
+        "n_gpus": 1, "dtype": "c64 bulk + c128 rank/refine" if args.prec == "mixed" else "c128", "data": "synthetic",
+        "config": {"workload": "rod 0.4 x 0.4 x L wavelengths, h = 0.1, eps_r = 2.54, eps = %g, nrhs = %d, leaf 64"
+                   % (eps, args.nrhs), "precision": args.prec},
+        "rows": rows, "loglog_slope": {"factorize": slope("factorize_ms"), "solve": slope("refined_solve_ms"),
+                                       "memory": slope("dev_peak_gb")},
+    }))
+
+
 def run_batch(args):
     """Independent instances: grids drawn from {12..32}^3 (cube sides 0.75-2
     wavelengths at h = 1/16), eps_r ~ U[2, 6] per instance (chi = eps_r - 1),
@@ -668,6 +728,8 @@ def main():
         return run_batch(args)
     if args.impl == "ours" and args.workload == "grad":
         return run_grad(args)
+    if args.impl == "ours" and args.workload == "rod":
+        return run_rod(args)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -102,10 +102,10 @@ typedef struct {
                             exact products summed in double-float and
                             flushed to FP64 every 8 terms; 0: FP64 FMAs   */
   int eig_solver;        /* Step-0 eigen-decomposition of the Ritz matrix
-                            (eq. 17): 0 (default) Householder reduction to
-                            real tridiagonal form + implicit QL with
-                            accumulated rotations (orders up to 452, cyclic
-                            Jacobi above); 1 cyclic Jacobi throughout      */
+                            (eq. 17): 0 (default) cyclic Jacobi; 1
+                            Householder reduction to real tridiagonal form
+                            + implicit QL with accumulated rotations
+                            (orders up to 452, Jacobi above)               */
   int stop_level;        /* early stop (Sec. III-C, last paragraph): 0
                             (default) factorize levels L .. l0; s > l0:
                             levels L .. s only, the remaining matrix of all

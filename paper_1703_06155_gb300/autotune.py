@@ -11,7 +11,7 @@ for candidate settings of
   tensor_cores  complex64 tiles on tcgen05 / warp-level tensor-core MMAs
                 (3xTF32) or on FP32 FMAs,
   gram_emulation  FP64-accurate Step-0 Grams on the FP32 pipe / FP64 FMAs,
-  eig_solver    Step-0 eigen-decomposition: tridiagonal + QL / cyclic Jacobi,
+  eig_solver    Step-0 eigen-decomposition: cyclic Jacobi / tridiagonal + QL,
   stop_level    early stop of the factorization (Sec. III-C): l0 (0) or one
                 to three levels below it, the rest as one dense final block,
 

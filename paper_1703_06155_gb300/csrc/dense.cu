@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(NT) k_jacobi(const EigTask* __restrict__ tasks
   // rotations whose off-diagonal entry is below 4e-16 ||A||_F (or 1e-17 of
   // the geometric mean of the two diagonal entries) are skipped; the sweep
   // loop ends when a sweep would rotate nothing.
-  const double gmin = fmax(1e-300, 4e-16 * sqrt(fro));
+  // entries at the rounding level of the matrix are not rotated, nor entries
+  // far below the truncation threshold of the rank decision (eq. 17), whose
+  // rotation would move the eigenvalues by less than that floor
+  const double gmin = fmax(fmax(1e-300, 4e-16 * sqrt(fro)), t.trM ? t.tol_rel * t.eps2 * (t.snorm2 + *t.trM) : 0.0);
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (threadIdx.x == 0) any_rot = 0;

@@ -589,7 +589,10 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         g4.task(Sq + f.Gh, rr, rr, rr, 1.0, 0.0);  // Ritz matrix Qx^H G' Qx
         g4.pair(Sq + f.Qx, p, OP_H, Sq + f.Z1, p, OP_N, p);
         g4.close();
-        eig.push_back(EigTask{Sq + f.Gh, Sq + f.U, (double*)(Sq + f.lam), rr, d_r[q] + 2 * nb + u});
+        // the Jacobi leaves entries below 1e-4 of the threshold unrotated: with
+        // r' of them per row, the eigenvalues move by at most r' 1e-4 thr
+        eig.push_back(EigTask{Sq + f.Gh, Sq + f.U, (double*)(Sq + f.lam), rr, d_r[q] + 2 * nb + u,
+                              (const double*)(Sq + f.tr), snorm(q, f.i), eps * eps, 1e-4});
         eig_of.push_back({q, u});
         sel.push_back(
             SelTask{(const double*)(Sq + f.tr), (double*)(Sq + f.lam), d_r[q] + nb + u, n, rr, snorm(q, f.i), eps * eps});
@@ -604,7 +607,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     run_gemm(lc, g2, P64, P64, P64, "WY 2");
     run_gemm(lc, g3, P64, P64, P64, "WY 3");
     run_gemm(lc, g4, P64, P64, P64, "ritz matrix");
-    const bool use_heev = lc.opts.eig_solver == 0 && maxr <= heev_max_order();
+    const bool use_heev = lc.opts.eig_solver == 1 && maxr <= heev_max_order();
     if (!eig.empty() && use_heev) {
       const int i0 = lc.st.add(eig);
       lc.st.upload(lc);

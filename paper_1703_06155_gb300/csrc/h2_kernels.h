@@ -81,6 +81,10 @@ struct EigTask {
   double* lam;
   int p;
   int* sweeps;  // may be NULL: number of sweeps used
+  // Jacobi: off-diagonal entries at or below tol_rel * eps2 * (snorm2 + *trM)
+  // are not rotated (trM NULL: no such floor)
+  const double* trM;
+  double snorm2, eps2, tol_rel;
 };
 
 // ---- partial-pivoting LU of one m x m block + explicit triangular inverses

@@ -96,7 +96,10 @@ __global__ void __launch_bounds__(NT) k_jacobi_cl(const EigTask* __restrict__ ta
   __syncthreads();
   fro = red[0];
   // off-diagonal entries at the rounding level of the matrix are not rotated
-  const double gmin = fmax(1e-300, 4e-16 * sqrt(fro));
+  // entries at the rounding level of the matrix are not rotated, nor entries
+  // far below the truncation threshold of the rank decision (eq. 17), whose
+  // rotation would move the eigenvalues by less than that floor
+  const double gmin = fmax(fmax(1e-300, 4e-16 * sqrt(fro)), t.trM ? t.tol_rel * t.eps2 * (t.snorm2 + *t.trM) : 0.0);
   const int m = pe - 1;  // round-robin modulus
   // partner of index k in round r (pair 0 = (pe - 1, r), pair i = (r + i, r - i) mod m)
   auto partner = [&](int k, int r) { return k == pe - 1 ? r : k == r ? pe - 1 : ((2 * r - k) % m + m) % m; };

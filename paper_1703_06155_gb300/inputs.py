@@ -27,6 +27,19 @@ def grid_points(n, h=1.0 / 16.0):
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1).copy()
 
 
+def rod_points(length, h=0.1, side=0.4):
+    """Cell centres of a dielectric rod: a (side x side x length) box of cells of
+    edge h (wavelength units), index i + nx*(j + nx*l), nx = round(side / h).
+    The rod workload of Sec. VI-B (cross-section 0.4 x 0.4 wavelengths, mesh
+    0.1 wavelength, length growing) on a regular grid."""
+    nx = int(round(side / h))
+    nz = int(round(length / h))
+    cx = (np.arange(nx, dtype=np.float64) + 0.5) * h
+    cz = (np.arange(nz, dtype=np.float64) + 0.5) * h
+    z, y, x = np.meshgrid(cz, cx, cx, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1).copy()
+
+
 def chi_uniform(N, chi):
     """Uniform contrast chi = eps_r - 1 for all N cells."""
     return np.full(N, float(chi), dtype=np.float64)

@@ -158,3 +158,25 @@ def test_early_stop_levels():
         assert rel(xa, np.linalg.solve(Zd.conj().T, b)) < 10 * eps
     assert max(res) <= 10 * eps and res[-1] <= res[0], res
     assert all(s1 > s0 for s0, s1 in zip(sizes, sizes[1:])), sizes
+
+
+def test_rod_ranks_stay_bounded():
+    # Sec. VI-B: a rod (fixed 0.4 x 0.4 wavelength cross-section, growing
+    # length) has 1-D rank characteristics: the rank does not grow with the
+    # electric length, which is what makes the solver strictly O(N) there.
+    # The oracle's construction on rods of 8, 16 and 32 wavelengths (h = 0.1):
+    # the largest rank at each distance from the leaves is the same to within
+    # a few directions, whatever the length.
+    eps = 1e-4
+    tops = []
+    for length in (8.0, 16.0, 32.0):
+        pts = inputs.rod_points(length, 0.1)
+        Hm = h2.build(pts, inputs.chi_uniform(len(pts), 1.54), K, 0.1, leafsize=64, eps=eps)
+        per = [int(Hm.rank[l].max()) for l in range(Hm.L, Hm.l0 - 1, -1)]  # leaf level first
+        tops.append(per)
+    print("rod ranks by level from the leaves:", tops)
+    depth = min(len(t) for t in tops)
+    for d in range(depth - 1):  # the top level of the shortest rod has the smallest far field
+        vals = [t[d] for t in tops]
+        assert max(vals) - min(vals) <= max(3, 0.1 * max(vals)), (d, vals)
+    assert max(max(t) for t in tops) <= 1.15 * max(tops[0])
