@@ -673,6 +673,7 @@ def run_ours(args):
         "final_residual": res, "fp64": fp64,
         "refined_solve_ms": ms - float(np.mean(fac_ms)), "matvec_ms": matvec_ms,
         "dev_peak_gb": st.get("dev_peak", 0) / 1e9,
+        "dev_bytes_by_kind_gb": {k: round(v / 1e9, 3) for k, v in st.get("mem", {}).items()},
         "factorize_unknowns_per_s": N / (float(np.mean(fac_ms)) / 1e3),
         "mixed_over_fp64_factorize": (fp64["factorize_ms"] / float(np.mean(fac_ms))) if fp64 else None,
         "build_s": t_build, "gpu_launches": launches,

@@ -967,7 +967,21 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
     for (int v : c.H.rank[l]) mx = std::max(mx, v);
     o << (l > c.H.l0 ? "," : "") << mx;
   }
-  o << "],\"levels\":[";
+  o << "],\"mem\":{";
+  {
+    // device bytes by kind: the H^2 matrix (FP64), the factors kept for the
+    // solves, the per-level working arenas, and other scratch
+    size_t h2 = 0, kept = 0, work = 0;
+    for (const DevBuf* b : {&c.dV, &c.dT, &c.dS, &c.dD, &c.dperm, &c.dscale, &c.dVp, &c.dTp}) h2 += b->bytes;
+    for (const LevelF& F : c.lev)
+      for (const DevBuf* b : {&F.near_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf}) kept += b->bytes;
+    for (const DevBuf* b : {&c.root.R, &c.root.piv, &c.root.Linv, &c.root.Uinv, &c.root.Rinv}) kept += b->bytes;
+    for (const DevBuf* b : {&c.fill_pp[0], &c.fill_pp[1], &c.B_pp[0], &c.B_pp[1], &c.Vp_pp[0], &c.Vp_pp[1]})
+      work += b->bytes;
+    o << "\"h2\":" << h2 << ",\"factors\":" << kept << ",\"level_work\":" << work
+      << ",\"other\":" << (c.dev_bytes > h2 + kept + work ? c.dev_bytes - h2 - kept - work : 0);
+  }
+  o << "},\"levels\":[";
   for (size_t li = 0; li < c.lev.size(); ++li) {
     const LevelF& F = c.lev[li];
     int nmax = 0, k0max = 0, ktmax = 0, pushed = 0, live = 0, csp = 0, csp_fill = 0;

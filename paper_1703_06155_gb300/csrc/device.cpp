@@ -119,12 +119,13 @@ void drop_factors(Ctx& c) {
   cudaStreamSynchronize(c.stream);  // nothing of the failed call may still use the buffers
   cudaGetLastError();
   for (LevelF& F : c.lev)
-    for (DevBuf* b : {&F.near_buf, &F.fill_buf, &F.B_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf, &F.Vp_buf})
-      dev_free(c, *b);
+    for (DevBuf* b : {&F.near_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf}) dev_free(c, *b);
   c.lev.clear();
   for (DevBuf* b : {&c.root.R, &c.root.piv, &c.root.Linv, &c.root.Uinv, &c.root.Rinv}) dev_free(c, *b);
   c.root = RootF();
-  for (DevBuf* b : {&c.scratch, &c.scratch2, &c.gemm_ws, &c.jac_buf, &c.applybuf, &c.frobbuf}) dev_free(c, *b);
+  for (DevBuf* b : {&c.scratch, &c.scratch2, &c.gemm_ws, &c.jac_buf, &c.applybuf, &c.frobbuf, &c.lu_scr,
+                    &c.fill_pp[0], &c.fill_pp[1], &c.B_pp[0], &c.B_pp[1], &c.Vp_pp[0], &c.Vp_pp[1]})
+    dev_free(c, *b);
   c.factored = false;
   c.inverted = false;
   c.graphs.clear();

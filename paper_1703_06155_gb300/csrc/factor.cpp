@@ -158,17 +158,14 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   const int nc = 1 << l;
   {
     // keep the device arenas of an earlier factorization (grow-only)
-    DevBuf b1 = std::move(F.near_buf), b2 = std::move(F.fill_buf), b3 = std::move(F.B_buf), b4 = std::move(F.Q_buf),
-           b5 = std::move(F.inv_buf), b6 = std::move(F.piv_buf), b7 = std::move(F.Ub_buf), b8 = std::move(F.Vp_buf);
+    DevBuf b1 = std::move(F.near_buf), b4 = std::move(F.Q_buf), b5 = std::move(F.inv_buf), b6 = std::move(F.piv_buf),
+           b7 = std::move(F.Ub_buf);
     F = LevelF();
     F.near_buf = std::move(b1);
-    F.fill_buf = std::move(b2);
-    F.B_buf = std::move(b3);
     F.Q_buf = std::move(b4);
     F.inv_buf = std::move(b5);
     F.piv_buf = std::move(b6);
     F.Ub_buf = std::move(b7);
-    F.Vp_buf = std::move(b8);
   }
   F.l = l;
   F.nc = nc;
@@ -228,8 +225,9 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.fill_row[F.fill_pairs[q].first].push_back((int)q);
     F.fill_col[F.fill_pairs[q].second].push_back((int)q);
   }
-  dev_ensure(c, F.fill_buf, tot * es);
-  if (tot) ck(cudaMemsetAsync(F.fill_buf.p, 0, tot * es, c.stream), "fill memset");
+  const int pp = l & 1;
+  F.fill_ptr = (char*)dev_ensure(c, c.fill_pp[pp], tot * es);
+  if (tot) ck(cudaMemsetAsync(F.fill_ptr, 0, tot * es, c.stream), "fill memset");
   // bases (FP64), Q (bulk), L^{-1}P and U^{-1} (bulk), pivots
   size_t tb = 0, tq = 0, ti = 0, tp = 0, tvp = 0;
   F.voff.assign(nc, 0);
@@ -243,7 +241,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.Q_off.push_back(tq);
     tq += (size_t)n[i] * n[i];
     F.inv_off.push_back(ti);
-    ti += 3 * (size_t)n[i] * n[i];  // L^{-1}P, U^{-1}, scratch of the inversion
+    ti += 2 * (size_t)n[i] * n[i];  // L^{-1}P, U^{-1}
     F.piv_off.push_back(tp);
     tp += n[i];
     F.Vp_off.push_back(tvp);
@@ -251,11 +249,11 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.voff[i] = F.vlen;
     F.vlen += n[i];
   }
-  dev_ensure(c, F.B_buf, tb * sizeof(cd));
+  F.B_ptr = (cd*)dev_ensure(c, c.B_pp[pp], tb * sizeof(cd));
   dev_ensure(c, F.Q_buf, tq * es);
   dev_ensure(c, F.inv_buf, ti * es);
   dev_ensure(c, F.piv_buf, tp * sizeof(int));
-  dev_ensure(c, F.Vp_buf, tvp * sizeof(cd));
+  F.Vp_ptr = (cd*)dev_ensure(c, c.Vp_pp[pp], tvp * sizeof(cd));
   // sum of ||S||_F^2 over the admissible blocks of each row and column
   if ((int)c.snorm2_cache.size() <= l) c.snorm2_cache.resize(l + 1);
   std::vector<double>& sn = c.snorm2_cache[l];
@@ -282,7 +280,7 @@ struct Ptrs {
 };
 
 Ptrs ptrs(Ctx& c, LevelF& F) {
-  return Ptrs{(char*)F.near_buf.p, (char*)F.fill_buf.p, (cd*)F.B_buf.p, (char*)F.Q_buf.p, (char*)F.inv_buf.p,
+  return Ptrs{(char*)F.near_buf.p, F.fill_ptr, F.B_ptr, (char*)F.Q_buf.p, (char*)F.inv_buf.p,
               (int*)F.piv_buf.p, esz(c.prec)};
 }
 
@@ -321,7 +319,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   };
   auto FB = [&](size_t q, int id) -> char* { return P[q].fill + jobs[q].F->fill_off[id] * es; };
   auto lo_of = [&](size_t q, int j) { return (*jobs[q].done)[j] ? jobs[q].F->m[j] : 0; };
-  auto Vp = [&](size_t q, int i) { return (cd*)jobs[q].F->Vp_buf.p + jobs[q].F->Vp_off[i]; };
+  auto Vp = [&](size_t q, int i) { return jobs[q].F->Vp_ptr + jobs[q].F->Vp_off[i]; };
   // With a symmetric Z the column fill-ins are the transposed row fill-ins and
   // the column Gram equals the row Gram: only the row side is formed, and the
   // admissible-row norm is halved to match (the decisions are unchanged).
@@ -759,6 +757,12 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
 
   // Step 3: LU + explicit inverses, panels, Schur
   std::vector<LuTask> lu;
+  size_t lscr = 0;
+  for (size_t q = 0; q < nj; ++q)
+    for (int i : *jobs[q].bt)
+      if (jobs[q].F->m[i] > 0) lscr += (size_t)jobs[q].F->n[i] * jobs[q].F->n[i];
+  char* lsc = (char*)dev_ensure(lc, lc.lu_scr, (lscr + 1) * es);
+  lscr = 0;
   for (size_t q = 0; q < nj; ++q) {
     const LevelF& F = *jobs[q].F;
     for (int i : *jobs[q].bt) {
@@ -766,7 +770,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       if (m <= 0) continue;
       char* inv = P[q].inv + F.inv_off[i] * es;
       lu.push_back(LuTask{NB(q, i, i), inv, inv + (size_t)n * n * es, P[q].piv + F.piv_off[i], n, m,
-                          inv + 2 * (size_t)n * n * es});
+                          lsc + lscr * es});
+      lscr += (size_t)n * n;
       jobs[q].c->stats.flops_factor += 8.0 / 3.0 * m * (double)m * m + 8.0 / 3.0 * m * (double)m * m;
     }
   }
@@ -894,7 +899,7 @@ void merge_level(Ctx& c, LevelF& F, LevelF& Pn, CopyBatch& as, CopyBatch& ac) {
   for (int p = 0; p < Pn.nc; ++p) {
     const int c1 = 2 * p, c2 = 2 * p + 1, kp = Pn.k0[p], np_ = Pn.n[p], pp = np_ - kp;
     if (pp <= 0) continue;
-    cd* V = (cd*)Pn.Vp_buf.p + Pn.Vp_off[p];
+    cd* V = Pn.Vp_ptr + Pn.Vp_off[p];
     as.add(nullptr, P64, np_, 0, 0, V, P64, np_, np_, pp);
     const int q = F.k0[c1] + F.k0[c2] - kp, pad1 = F.kt[c1] - F.k0[c1], pad2 = F.kt[c2] - F.k0[c2];
     const cd* Tp = (const cd*)c.dTp.p + c.Tp_off[l - 1][p];
@@ -1200,8 +1205,7 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
       depth = std::max(depth, L - l0 + 1);
       if ((int)c.lev.size() != L - l0 + 1) {
         for (LevelF& F : c.lev)
-          for (DevBuf* b : {&F.near_buf, &F.fill_buf, &F.B_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf, &F.Vp_buf})
-            dev_free(c, *b);
+          for (DevBuf* b : {&F.near_buf, &F.Q_buf, &F.inv_buf, &F.piv_buf, &F.Ub_buf}) dev_free(c, *b);
         c.lev.clear();
         c.lev.resize(L - l0 + 1);
       }
@@ -1219,10 +1223,10 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
       }
       for (int t = 0; t < (1 << L); ++t) {
         if (F.k0[t] > 0)
-          cb.add((const cd*)c.dV.p + c.V_off[t], P64, n[t], n[t], F.k0[t], (cd*)F.B_buf.p + F.B_off[t], P64, n[t],
+          cb.add((const cd*)c.dV.p + c.V_off[t], P64, n[t], n[t], F.k0[t], F.B_ptr + F.B_off[t], P64, n[t],
                  n[t], F.k0[t]);
         if (n[t] > F.k0[t])
-          cb.add((const cd*)c.dVp.p + c.Vp_off[t], P64, n[t], n[t], n[t] - F.k0[t], (cd*)F.Vp_buf.p + F.Vp_off[t], P64,
+          cb.add((const cd*)c.dVp.p + c.Vp_off[t], P64, n[t], n[t], n[t] - F.k0[t], F.Vp_ptr + F.Vp_off[t], P64,
                  n[t], n[t], n[t] - F.k0[t]);
       }
     }

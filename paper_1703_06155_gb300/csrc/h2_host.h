@@ -166,7 +166,14 @@ struct LevelF {
   std::vector<char> fill_is_adm;
   std::vector<size_t> B_off, Q_off, inv_off, piv_off, Vp_off;
   std::vector<double> snorm2;
-  DevBuf near_buf, fill_buf, B_buf, Q_buf, inv_buf, piv_buf, Ub_buf, Vp_buf;
+  // near field, Q~, L^{-1}P and U^{-1}, pivots, eq. 35 panels: kept for the
+  // solves; the fill-ins and the FP64 incoming bases / complements are only
+  // needed while the level (and its merge) runs and live in the context's
+  // ping-pong arenas (slot = level parity), shared by all levels
+  DevBuf near_buf, Q_buf, inv_buf, piv_buf, Ub_buf;
+  char* fill_ptr = nullptr;
+  h2k::cd* B_ptr = nullptr;
+  h2k::cd* Vp_ptr = nullptr;
   std::vector<size_t> Ub_off;                  // per (cluster, nbr) for eq. 35
   std::vector<int> nbr_first;                  // first (cluster, nbr) index
   // Step-0 statistics: Ritz subspace sizes and Jacobi sweeps
@@ -236,6 +243,8 @@ struct Ctx {
   RootF root;
   // scratch
   DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf, applybuf, frobbuf;
+  DevBuf fill_pp[2], B_pp[2], Vp_pp[2];  // per-level working arenas, by level parity
+  DevBuf lu_scr;                         // partial-LU inversion scratch of one batch
   Stager st;
   Stats stats;
   int64_t launches = 0;
