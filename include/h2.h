@@ -65,8 +65,14 @@ typedef struct {
   double eta;            /* admissibility ||c_t-c_s|| >= eta (r_t+r_s) (1.0) */
   double sign;           /* s in A = I + s K D_chi (default +1)             */
   int ordering;          /* h2_order (default H2_ORDER_COLORED)             */
-  int proxy_min;         /* minimum proxy points per sphere (default 64)    */
-  double proxy_radius;   /* proxy sphere radius / cluster radius (3.0)      */
+  int proxy_min;         /* construction of h2_build: 0 (default) samples
+                            each cluster's whole far field (O(N^2) kernel
+                            evaluations); > 0 samples the far-field points
+                            within proxy_radius * r_t of the cluster centre
+                            plus proxy points on two spheres (radii R and
+                            0.8 R, R = proxy_radius * r_t), at least
+                            proxy_min per sphere (O(N k^2))                */
+  double proxy_radius;   /* proxy sphere radius / cluster radius (1.5)      */
   size_t arena_cap_bytes;/* 0 = unlimited; else H2_ENOMEM beyond it         */
   int host_only;         /* 1: h2_build keeps the representation on the host
                             only (no GPU needed); such a context allows

@@ -233,8 +233,8 @@ void h2_default_opts(h2_opts* o) {
   o->eta = 1.0;
   o->sign = 1.0;
   o->ordering = H2_ORDER_COLORED;
-  o->proxy_min = 64;
-  o->proxy_radius = 3.0;
+  o->proxy_min = 0;
+  o->proxy_radius = 1.5;
   o->arena_cap_bytes = 0;
   o->host_only = 0;
   o->profile = 0;
@@ -321,6 +321,9 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
         for (int d = 0; d < 3; ++d) pts_tree[3 * p + d] = pts[3 * g + d];
         sq_tree[p] = c.H.dscale[g];
       }
+      // proxy sample points (positions N, N + 1, ...) of the proxy construction
+      pts_tree.insert(pts_tree.end(), c.H.proxy_pts.begin(), c.H.proxy_pts.end());
+      sq_tree.insert(sq_tree.end(), c.H.proxy_w.begin(), c.H.proxy_w.end());
     };
     GramFn gram = [&](int, const std::vector<std::vector<int64_t>>& rows,
                       const std::vector<std::vector<int64_t>>& ranges, std::vector<std::vector<cplx>>& G) {
@@ -955,6 +958,8 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
   o << "{\"N\":" << c.H.tree.N << ",\"L\":" << c.H.L << ",\"l0\":" << c.H.l0 << ",\"factored\":" << (c.factored ? 1 : 0)
     << ",\"prec\":\"" << (c.prec == P64 ? "fp64" : "mixed") << "\",\"eps_fill\":" << c.eps_fill
     << ",\"stop_level\":" << c.stats.stop_level << ",\"t_build_ms\":" << c.stats.t_build_ms
+    << ",\"t_build_phases_ms\":{\"gram\":" << c.H.t_gram_ms << ",\"id\":" << c.H.t_id_ms
+    << ",\"couplings\":" << c.H.t_coupling_ms << ",\"near\":" << c.H.t_near_ms << "}"
     << ",\"t_factor_ms\":" << c.stats.t_factor_ms
     << ",\"t_solve_ms\":" << c.stats.t_solve_ms << ",\"t_factor_sync_ms\":" << c.stats.t_sync_ms
     << ",\"flops_factor\":" << c.stats.flops_factor

@@ -19,6 +19,7 @@
 //            with Z symmetric so Z_ts = Z(s, t)^T).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <thread>
 
@@ -250,6 +251,136 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
     admp[l].assign(size_t(1) << l, {});
     for (auto [t, s] : Pt.adm[l]) admp[l][t].push_back(s);
   }
+  // proxy construction (h2_opts.proxy_min > 0): the far field F*(t) of a
+  // cluster is sampled by the points of F*(t) inside the sphere of radius
+  // R = proxy_radius * r_t around c_t plus proxy points on two concentric
+  // spheres (radii R and 0.8 R, both enclosing t) that stand for the sources
+  // outside R; per sphere max(proxy_min, ceil(2 (k R + 10)^2)) Fibonacci
+  // points, weighted so that their sample matches the far field's strength
+  // sum_s n_s chi / |c_t - c_s|^2.  O(N k^2) in all instead of O(N^2).
+  const bool proxy = o.proxy_min > 0;
+  double chimean = 0;
+  for (int64_t i = 0; i < N; ++i) chimean += chiv[i];
+  chimean /= (double)N;
+  std::vector<std::vector<int64_t>> proxy_off(L + 1);  // first proxy position of each cluster
+  std::vector<std::vector<int>> proxy_cnt(L + 1);
+  if (proxy) {
+    H.proxy_pts.clear();
+    H.proxy_w.clear();
+    for (int l = l0; l <= L; ++l) {
+      proxy_off[l].assign(size_t(1) << l, 0);
+      proxy_cnt[l].assign(size_t(1) << l, 0);
+      for (int t = 0; t < (1 << l); ++t) {
+        // far-field strength estimate from the admissible partners of t and its ancestors
+        double far = 0;
+        for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
+          for (int s : admp[lv][anc]) {
+            double d2 = 0;
+            for (int q = 0; q < 3; ++q) {
+              const double v = T.centre[l][3 * t + q] - T.centre[lv][3 * s + q];
+              d2 += v * v;
+            }
+            far += (double)T.size[lv][s] * chimean / std::max(d2, 1e-300);
+          }
+        if (far == 0) continue;  // no far field: rank 0
+        const double R = o.proxy_radius * T.radius[l][t];
+        // no proxies when every far-field point lies inside the sphere (the
+        // far field is then sampled exactly, point by point): descend the
+        // partners' subtrees until a node is wholly inside or a point outside
+        bool outside = false;
+        {
+          std::vector<std::pair<int, int>> st;
+          for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
+            for (int s : admp[lv][anc]) st.push_back({lv, s});
+          while (!st.empty() && !outside) {
+            const auto [ll, u] = st.back();
+            st.pop_back();
+            double d2 = 0;
+            for (int q = 0; q < 3; ++q) {
+              const double v = T.centre[l][3 * t + q] - T.centre[ll][3 * u + q];
+              d2 += v * v;
+            }
+            const double d = std::sqrt(d2);
+            if (d + T.radius[ll][u] <= R) continue;     // wholly inside
+            if (d - T.radius[ll][u] > R) { outside = true; break; }
+            if (ll == L) {
+              for (int64_t p = T.start[L][u]; p < T.start[L][u] + T.size[L][u] && !outside; ++p) {
+                double e2 = 0;
+                for (int q = 0; q < 3; ++q) {
+                  const double v = T.centre[l][3 * t + q] - pts[3 * T.perm[p] + q];
+                  e2 += v * v;
+                }
+                outside = e2 > R * R;
+              }
+            } else {
+              st.push_back({ll + 1, 2 * u});
+              st.push_back({ll + 1, 2 * u + 1});
+            }
+          }
+        }
+        proxy_cnt[l][t] = -1;  // far field present (sampled inside R only)
+        if (!outside) continue;
+        const int np = std::max(o.proxy_min, (int)std::ceil(2.0 * (k * R + 10.0) * (k * R + 10.0)));
+        proxy_off[l][t] = N + (int64_t)H.proxy_w.size();
+        proxy_cnt[l][t] = 2 * np;
+        // weight: sum over the 2 np proxies of w^2 / R_p^2 equals `far`
+        const double wgt = std::sqrt(far / (np / (R * R) + np / (0.64 * R * R)));
+        for (int sph = 0; sph < 2; ++sph) {
+          const double rad = sph == 0 ? R : 0.8 * R;
+          for (int i = 0; i < np; ++i) {
+            const double z = 1.0 - 2.0 * (i + 0.5) / np, rr = std::sqrt(std::max(0.0, 1.0 - z * z));
+            const double th = M_PI * (1.0 + std::sqrt(5.0)) * (i + 0.5);
+            H.proxy_pts.push_back(T.centre[l][3 * t] + rad * rr * std::cos(th));
+            H.proxy_pts.push_back(T.centre[l][3 * t + 1] + rad * rr * std::sin(th));
+            H.proxy_pts.push_back(T.centre[l][3 * t + 2] + rad * z);
+            H.proxy_w.push_back(wgt);
+          }
+        }
+      }
+    }
+  }
+  // far-field tree positions of t inside the sphere (c_t, R): descend the
+  // admissible partners' subtrees, pruning by bounding spheres
+  auto inside_runs = [&](int l, int t, std::vector<int64_t>& out) {
+    const double R = o.proxy_radius * T.radius[l][t];
+    const double* ct = &T.centre[l][3 * t];
+    std::vector<int64_t> pos;
+    std::vector<std::pair<int, int>> stack;
+    for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
+      for (int s : admp[lv][anc]) stack.push_back({lv, s});
+    while (!stack.empty()) {
+      const auto [ll, u] = stack.back();
+      stack.pop_back();
+      double d2 = 0;
+      for (int q = 0; q < 3; ++q) {
+        const double v = ct[q] - T.centre[ll][3 * u + q];
+        d2 += v * v;
+      }
+      if (std::sqrt(d2) - T.radius[ll][u] > R) continue;
+      if (ll == L) {
+        for (int64_t p = T.start[L][u]; p < T.start[L][u] + T.size[L][u]; ++p) {
+          const int64_t g = T.perm[p];
+          double e2 = 0;
+          for (int q = 0; q < 3; ++q) {
+            const double v = ct[q] - pts[3 * g + q];
+            e2 += v * v;
+          }
+          if (e2 <= R * R) pos.push_back(p);
+        }
+      } else {
+        stack.push_back({ll + 1, 2 * u});
+        stack.push_back({ll + 1, 2 * u + 1});
+      }
+    }
+    std::sort(pos.begin(), pos.end());
+    for (size_t i = 0; i < pos.size();) {
+      size_t j = i + 1;
+      while (j < pos.size() && pos[j] == pos[j - 1] + 1) ++j;
+      out.push_back(pos[i]);
+      out.push_back((int64_t)(j - i));
+      i = j;
+    }
+  };
   H.rank.assign(L + 1, {});
   H.V.assign(size_t(1) << L, {});
   H.T.assign(L + 1, {});
@@ -271,15 +402,26 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
         rows[t] = skel[l + 1][2 * t];
         rows[t].insert(rows[t].end(), skel[l + 1][2 * t + 1].begin(), skel[l + 1][2 * t + 1].end());
       }
-      for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
-        for (int s : admp[lv][anc]) {
-          ranges[t].push_back(T.start[lv][s]);
-          ranges[t].push_back(T.size[lv][s]);
+      if (proxy) {
+        if (proxy_cnt[l][t] > 0) {
+          ranges[t].push_back(proxy_off[l][t]);
+          ranges[t].push_back(proxy_cnt[l][t]);
         }
+        if (proxy_cnt[l][t] != 0) inside_runs(l, t, ranges[t]);
+      } else {
+        for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
+          for (int s : admp[lv][anc]) {
+            ranges[t].push_back(T.start[lv][s]);
+            ranges[t].push_back(T.size[lv][s]);
+          }
+      }
       if (ranges[t].empty()) rows[t].clear();  // no far field: rank 0
     }
     std::vector<std::vector<cplx>> G;
+    auto tg = std::chrono::steady_clock::now();
     gram(l, rows, ranges, G);
+    H.t_gram_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tg).count();
+    tg = std::chrono::steady_clock::now();
     parallel_for(nc, [&](int t) {
       const int nr = (int)rows[t].size();
       std::vector<int> sk;
@@ -321,8 +463,10 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
       }
       Rm[l][t] = R;
     });
+    H.t_id_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tg).count();
   }
   // couplings of admissible pairs, levels l0..L
+  auto tc = std::chrono::steady_clock::now();
   for (int l = l0; l <= L; ++l) {
     const auto& pairs = Pt.adm[l];
     H.S[l].assign(pairs.size(), {});
@@ -353,6 +497,8 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
       H.S[l][q] = Sm.a;
     });
   }
+  H.t_coupling_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc).count();
+  tc = std::chrono::steady_clock::now();
   // dense near-field blocks at the leaf level
   const auto& np_ = Pt.inad[L];
   H.D.assign(np_.size(), {});
@@ -365,6 +511,7 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
       for (int i = 0; i < nt; ++i) Dm[(size_t)i + (size_t)j * nt] = zentry(K, T.perm[at + i], T.perm[as + j]);
     H.D[q] = std::move(Dm);
   });
+  H.t_near_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc).count();
   return "";
 }
 

@@ -56,6 +56,12 @@ struct H2Host {
   std::vector<std::vector<cplx>> D;                  // [inad[L] idx]
   std::vector<double> dscale;                        // global order (size N)
   bool symmetric = false;                            // Z^T = Z (h2_build; checked by h2_load)
+  // construction phase times (h2_build), ms: far-field Grams, interpolative
+  // decompositions + bases, couplings, dense near blocks
+  double t_gram_ms = 0, t_id_ms = 0, t_coupling_ms = 0, t_near_ms = 0;
+  // proxy construction: extra sample points after the N tree positions
+  // (3 coordinates each) and their column weights (the sqrt(chi) slot)
+  std::vector<double> proxy_pts, proxy_w;
 };
 
 // Far-field sample Grams of one level: G[t] = Z(rows[t], F) Z(rows[t], F)^H,
