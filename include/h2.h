@@ -72,7 +72,7 @@ typedef struct {
                             plus proxy points on two spheres (radii R and
                             0.8 R, R = proxy_radius * r_t), at least
                             proxy_min per sphere (O(N k^2))                */
-  double proxy_radius;   /* proxy sphere radius / cluster radius (1.5)      */
+  double proxy_radius;   /* proxy sphere radius / cluster radius (3.0)      */
   size_t arena_cap_bytes;/* 0 = unlimited; else H2_ENOMEM beyond it         */
   int host_only;         /* 1: h2_build keeps the representation on the host
                             only (no GPU needed); such a context allows
@@ -118,6 +118,10 @@ typedef struct {
                             level-s pairs (couplings of ancestor blocks
                             expressed in the level-s bases) is the final
                             dense block; clamped to [l0, L]                 */
+  double proxy_margin;   /* proxy construction: a proxy point is placed only
+                            within this angle (radians, default 0.3) of the
+                            angular extent of some far-field node outside
+                            the proxy sphere, as seen from the cluster centre */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */

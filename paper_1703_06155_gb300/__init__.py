@@ -36,7 +36,8 @@ class h2_opts(ctypes.Structure):
                 ("host_only", ctypes.c_int), ("profile", ctypes.c_int), ("apply_path", ctypes.c_int),
                 ("solve_graph", ctypes.c_int), ("split_target", ctypes.c_int), ("cluster_max", ctypes.c_int),
                 ("tile_policy", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("gram_emulation", ctypes.c_int), ("eig_solver", ctypes.c_int), ("stop_level", ctypes.c_int)]
+                ("gram_emulation", ctypes.c_int), ("eig_solver", ctypes.c_int), ("stop_level", ctypes.c_int),
+                ("proxy_margin", ctypes.c_double)]
 
 
 class H2Error(RuntimeError):

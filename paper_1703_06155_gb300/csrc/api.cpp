@@ -234,7 +234,7 @@ void h2_default_opts(h2_opts* o) {
   o->sign = 1.0;
   o->ordering = H2_ORDER_COLORED;
   o->proxy_min = 0;
-  o->proxy_radius = 1.5;
+  o->proxy_radius = 3.0;
   o->arena_cap_bytes = 0;
   o->host_only = 0;
   o->profile = 0;
@@ -247,6 +247,7 @@ void h2_default_opts(h2_opts* o) {
   o->gram_emulation = 1;
   o->eig_solver = 0;
   o->stop_level = 0;
+  o->proxy_margin = 0.3;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {

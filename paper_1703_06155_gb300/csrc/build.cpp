@@ -18,6 +18,7 @@
 //            (eq. 3); couplings S_ts = R_t Z(skel_t, skel_s) R_s^T (eq. 2,
 //            with Z symmetric so Z_ts = Z(s, t)^T).
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -284,34 +285,43 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
           }
         if (far == 0) continue;  // no far field: rank 0
         const double R = o.proxy_radius * T.radius[l][t];
-        // no proxies when every far-field point lies inside the sphere (the
-        // far field is then sampled exactly, point by point): descend the
-        // partners' subtrees until a node is wholly inside or a point outside
-        bool outside = false;
+        // the far-field nodes with points outside the sphere: descend the
+        // partners' subtrees until a node is wholly inside (sampled exactly,
+        // point by point) or wholly outside, or is a leaf with points on both
+        // sides; their directions and angular radii seen from c_t decide
+        // which proxy points are placed (a proxy stands for the outside
+        // sources near its direction); none at all when every far point is
+        // inside
+        std::vector<std::array<double, 4>> cones;  // unit direction, angular radius
         {
           std::vector<std::pair<int, int>> st;
           for (int lv = l, anc = t; lv >= 0; --lv, anc >>= 1)
             for (int s : admp[lv][anc]) st.push_back({lv, s});
-          while (!st.empty() && !outside) {
+          while (!st.empty()) {
             const auto [ll, u] = st.back();
             st.pop_back();
-            double d2 = 0;
+            double dv[3], d2 = 0;
             for (int q = 0; q < 3; ++q) {
-              const double v = T.centre[l][3 * t + q] - T.centre[ll][3 * u + q];
-              d2 += v * v;
+              dv[q] = T.centre[ll][3 * u + q] - T.centre[l][3 * t + q];
+              d2 += dv[q] * dv[q];
             }
-            const double d = std::sqrt(d2);
-            if (d + T.radius[ll][u] <= R) continue;     // wholly inside
-            if (d - T.radius[ll][u] > R) { outside = true; break; }
-            if (ll == L) {
-              for (int64_t p = T.start[L][u]; p < T.start[L][u] + T.size[L][u] && !outside; ++p) {
+            const double d = std::sqrt(d2), ru = T.radius[ll][u];
+            if (d + ru <= R) continue;  // wholly inside
+            bool rec = d - ru > R;      // wholly outside
+            if (!rec && ll == L) {
+              for (int64_t p = T.start[L][u]; p < T.start[L][u] + T.size[L][u] && !rec; ++p) {
                 double e2 = 0;
                 for (int q = 0; q < 3; ++q) {
                   const double v = T.centre[l][3 * t + q] - pts[3 * T.perm[p] + q];
                   e2 += v * v;
                 }
-                outside = e2 > R * R;
+                rec = e2 > R * R;
               }
+              if (!rec) continue;
+            }
+            if (rec) {
+              const double ang = d > ru ? std::asin(std::min(1.0, ru / d)) : M_PI;
+              cones.push_back({dv[0] / d, dv[1] / d, dv[2] / d, ang});
             } else {
               st.push_back({ll + 1, 2 * u});
               st.push_back({ll + 1, 2 * u + 1});
@@ -319,23 +329,36 @@ std::string build_h2(const double* pts, int64_t N, double k, double h, const dou
           }
         }
         proxy_cnt[l][t] = -1;  // far field present (sampled inside R only)
-        if (!outside) continue;
+        if (cones.empty()) continue;
         const int np = std::max(o.proxy_min, (int)std::ceil(2.0 * (k * R + 10.0) * (k * R + 10.0)));
         proxy_off[l][t] = N + (int64_t)H.proxy_w.size();
-        proxy_cnt[l][t] = 2 * np;
         // weight: sum over the 2 np proxies of w^2 / R_p^2 equals `far`
         const double wgt = std::sqrt(far / (np / (R * R) + np / (0.64 * R * R)));
+        int kept = 0;
         for (int sph = 0; sph < 2; ++sph) {
           const double rad = sph == 0 ? R : 0.8 * R;
           for (int i = 0; i < np; ++i) {
             const double z = 1.0 - 2.0 * (i + 0.5) / np, rr = std::sqrt(std::max(0.0, 1.0 - z * z));
             const double th = M_PI * (1.0 + std::sqrt(5.0)) * (i + 0.5);
-            H.proxy_pts.push_back(T.centre[l][3 * t] + rad * rr * std::cos(th));
-            H.proxy_pts.push_back(T.centre[l][3 * t + 1] + rad * rr * std::sin(th));
-            H.proxy_pts.push_back(T.centre[l][3 * t + 2] + rad * z);
+            const double u[3] = {rr * std::cos(th), rr * std::sin(th), z};
+            bool use = false;
+            for (const auto& cn : cones) {
+              const double cosa = u[0] * cn[0] + u[1] * cn[1] + u[2] * cn[2];
+              if (std::acos(std::max(-1.0, std::min(1.0, cosa))) <= cn[3] + o.proxy_margin) {
+                use = true;
+                break;
+              }
+            }
+            if (!use) continue;
+            H.proxy_pts.push_back(T.centre[l][3 * t] + rad * u[0]);
+            H.proxy_pts.push_back(T.centre[l][3 * t + 1] + rad * u[1]);
+            H.proxy_pts.push_back(T.centre[l][3 * t + 2] + rad * u[2]);
             H.proxy_w.push_back(wgt);
+            ++kept;
           }
         }
+        proxy_cnt[l][t] = kept > 0 ? kept : -1;
+        if (kept == 0) continue;
       }
     }
   }

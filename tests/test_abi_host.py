@@ -160,3 +160,29 @@ def test_set_chi_host_rescale_is_exact(libh2):
         assert ei.value.status == -1
     assert np.array_equal(A.export()["S"], r1["S"])
     A.close()
+
+
+@pytest.mark.parametrize("n,eps", [(12, 1e-6), (16, 1e-4)])
+def test_proxy_construction_matches_dense(libh2, n, eps):
+    # the proxy-point construction (far field sampled exactly inside three
+    # cluster radii, through direction-filtered proxy points beyond) keeps the
+    # construction accuracy (<= 10 eps against the dense kernel matrix) and
+    # ranks close to those of the exact far-field sample
+    from paper_1703_06155_gb300 import H2
+    pts = inputs.grid_points(n, H)
+    N = len(pts)
+    chi = inputs.chi_random_cells(N, 4)
+    Ap = H2.build(pts, K, H, chi, eps, host_only=1, proxy_min=64)
+    Ae = H2.build(pts, K, H, chi, eps, host_only=1)
+    rp, re_ = Ap.export(), Ae.export()
+    Zp, full = dense_from_rep(rp)
+    idx = rp["perm"]
+    Zex = kernel.entries(pts, chi, idx, idx, K, H)
+    assert np.linalg.norm(Zp - Zex) <= 10 * eps * np.linalg.norm(Zex)
+    for V in full.values():
+        if V.shape[1]:
+            assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-12
+    kp, ke = Ap.stats()["build_rank_max"], Ae.stats()["build_rank_max"]
+    assert all(a <= 1.15 * b + 4 for a, b in zip(kp, ke)), (kp, ke)
+    Ap.close()
+    Ae.close()
