@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--workload", default="grid", choices=["grid", "batch", "grad", "rod"],
                    help="grid: one instance (default); batch: many independent instances in shared launches")
     p.add_argument("--instances", type=int, default=64, help="batch workload: number of instances")
+    p.add_argument("--batch-reserve-gb", type=float, default=24.0,
+                   help="batch workload: stop adding instances when less device memory than this is free")
     p.add_argument("--solve-graph-check", action="store_true",
                    help="also time repeated solves with CUDA-graph replay (builds a second context)")
     p.add_argument("--profile-levels", action="store_true", help="kernel classes kept apart per tree level")
@@ -61,6 +63,8 @@ def parse():
     p.add_argument("--eig-solver", type=int, default=None, choices=[0, 1],
                    help="Step-0 eigen-decomposition: 0 cyclic Jacobi, 1 tridiagonal + QL (default: library's)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison factorization (large grids)")
+    p.add_argument("--proxy", type=int, default=0,
+                   help="construction with proxy points (h2_opts.proxy_min; 0 = exact far-field sample)")
     p.add_argument("--arena-cap-gb", type=float, default=0.0,
                    help="cap on the library's device memory (h2_opts.arena_cap_bytes; 0 = none)")
     p.add_argument("--json-extra", action="store_true", help="print per-level stats")
@@ -141,7 +145,7 @@ def fp_peaks(clocks):
     return {"fp64": 152 * 2 * 2 * f * 1e6 / 1e12, "fp32": 152 * 128 * 2 * f * 1e6 / 1e12, "mhz": f}
 
 
-def roofline(st, clocks, kernel=None):
+def roofline(st, clocks, kernel=None, workload=None):
     """Roofline entry of one kernel class (default: the class with the most
     device time among the classes with an algorithmic flop or byte count),
     from the per-launch CUDA events of the instrumented pass."""
@@ -163,8 +167,8 @@ def roofline(st, clocks, kernel=None):
                 "bytes_per_launch": v["bytes"] / v["launches"]}
     achieved = v["flops"] / (v["ms"] * 1e-3) / 1e12
     out = {"kernel": k, "pipe": v.get("pipe"), "achieved": achieved, "unit": "TFLOP/s",
-           "traffic": measured_traffic(k), "launches": v["launches"], "avg_launch_ms": v["ms"] / v["launches"],
-           "flops_per_launch": v["flops"] / v["launches"]}
+           "traffic": measured_traffic(k, workload), "launches": v["launches"],
+           "avg_launch_ms": v["ms"] / v["launches"], "flops_per_launch": v["flops"] / v["launches"]}
     pipe = v.get("pipe") or ("fp64" if st.get("prec") == "fp64" else "fp32")
     if pipe.endswith("tf32x3"):
         # complex64 products as three TF32 tensor-core products each: the
@@ -209,19 +213,21 @@ def roofline_table(st, clocks, top=14):
     return rows
 
 
-def measured_traffic(kernel_class):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken for this kernel class with the current GEMM
-    source (else None: the counters no longer describe the kernel)."""
+def measured_traffic(kernel_class, workload=None):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary,
+    if it was taken for this class, on this workload, with the kernel's
+    current source (else None: the counters do not describe this run)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             d = json.load(f)
-        with open(os.path.join(ROOT, "paper_1703_06155_gb300", "csrc", "gemm.cu"), "rb") as f:
+        with open(os.path.join(ROOT, d["source"]), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
     except Exception:
         return None
-    if d.get("kernel_class") != kernel_class.split("@")[0] or d.get("gemm_cu_sha256") != sha:
+    if d.get("kernel_class") != kernel_class.split("@")[0] or d.get("source_sha256") != sha:
+        return None
+    if workload is not None and d.get("workload") != workload:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -467,7 +473,7 @@ def run_batch(args):
     chis = rng.uniform(2.0, 6.0, args.instances) - 1.0
     ctxs, bs, Ns = [], [], []
     t0 = time.perf_counter()
-    reserve = 48 << 30  # keep this much device memory free
+    reserve = int(args.batch_reserve_gb * (1 << 30))  # keep this much device memory free
     for i, (n, chi) in enumerate(zip(sizes, chis)):
         pts = inputs.grid_points(int(n), H)
         A = H2.build(pts, K, H, float(chi), args.eps, stream=stream, **tc_opts(args))
@@ -547,7 +553,7 @@ def run_ours(args):
     # the timed steps run without per-launch events (profile = 0); the kernel
     # table comes from a separate instrumented pass afterwards
     A = H2.build(pts, K, H, args.chi, args.eps, stream=stream, profile=0,
-                 arena_cap_bytes=int(args.arena_cap_gb * 1e9), **tun)
+                 arena_cap_bytes=int(args.arena_cap_gb * 1e9), proxy_min=args.proxy, **tun)
     t_build = time.perf_counter() - t0
     b_host = inputs.rhs_gaussian(N, args.nrhs, args.seed + rank)  # independent instance per rank
     b = torch.from_numpy(b_host).to("cuda")
@@ -626,7 +632,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     st = A.stats()
     A.set_opts(profile=0, **tun)
-    roof = roofline(st, clocks)
+    roof = roofline(st, clocks, workload=workload_name(args))
     table = roofline_table(st, clocks)
     # repeated solves with the same factors: plain launches vs CUDA-graph replay
     # of the sweeps (h2_opts.solve_graph; not part of the metric)
@@ -667,6 +673,7 @@ def run_ours(args):
         "dtype": "c64 bulk + c128 rank/refine" if args.prec == "mixed" else "c128",
         "data": "synthetic",
         "config": {"workload": workload_name(args), "precision": args.prec,
+                   "construction": "proxy points (min %d per sphere)" % args.proxy if args.proxy else "exact far field",
                    "l2": "inputs larger than L2 (near-field arena %.0f MB)" % (st.get("dev_bytes", 0) / 1e6),
                    "timed_steps": "no per-launch events (kernel table from a separate instrumented pass)"},
         "factorize_ms": float(np.mean(fac_ms)), "solve_iters": solve_info.get("iters"),
@@ -676,7 +683,7 @@ def run_ours(args):
         "dev_bytes_by_kind_gb": {k: round(v / 1e9, 3) for k, v in st.get("mem", {}).items()},
         "factorize_unknowns_per_s": N / (float(np.mean(fac_ms)) / 1e3),
         "mixed_over_fp64_factorize": (fp64["factorize_ms"] / float(np.mean(fac_ms))) if fp64 else None,
-        "build_s": t_build, "gpu_launches": launches,
+        "build_s": t_build, "build_phases_ms": st.get("t_build_phases_ms"), "gpu_launches": launches,
         "e2e": {"value": world * N / (e_ms / 1e3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
         "clocks": clocks,
