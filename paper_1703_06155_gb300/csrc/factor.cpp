@@ -40,15 +40,16 @@ using namespace h2k;
 void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* what) {
   if (b.empty()) return;
   HostScope hs(c, "run_gemm");
-  const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 8 * 152, pacc == P64, c.opts.tile_policy);
+  const int pa = b.pina < 0 ? pin : b.pina;
+  const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1 : 0;
+  const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 8 * 152, pacc == P64, c.opts.tile_policy,
+                            !emul);
   if (b.tl.empty()) return;
   void* wsp = nullptr;
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
   c.st.upload(c);
-  const int pa = b.pina < 0 ? pin : b.pina;
   const int tc = (b.shape == 0 && pa == P32 && pin == P32 && pacc == P32 && pout == P32) ? c.opts.tensor_cores : 0;
-  const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1 : 0;
   const char* pipe = emul ? "fp32_df" : pacc == P64 ? "fp64" : tc == 2 ? "tcgen05_tf32x3" : tc == 1 ? "mma_tf32x3" : "fp32";
   ProfScope ps(c, std::string("gemm:") + what, b.alg_flops, pipe);
   c.paths[std::string("gemm:") + pipe + ":" + std::to_string(h2k::gemm_tile_m(b.shape)) + "x" +

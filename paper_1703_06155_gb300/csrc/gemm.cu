@@ -47,13 +47,14 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
                                             const GemmPair* __restrict__ pairs,
                                             const GemmTile* __restrict__ tiles,
                                             typename CxOf<R>::T* __restrict__ ws) {
-  constexpr int TN = BN / 16, TMR = BM / 16;
+  constexpr int TX = BN >= 16 ? 16 : BN, TY = NT / TX, TN = BN / TX, TMR = BM / TY;
+  static_assert(BN % TX == 0 && BM % TY == 0, "tile shape");
   __shared__ R As_r[BK][BM], As_i[BK][BM];
   __shared__ R Bs_r[BK][BN], Bs_i[BK][BN];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmTask tk = tasks[tl.task];
   const int m0 = tl.tm * BM, n0 = tl.tn * BN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   R acc_r[TMR][TN], acc_i[TMR][TN];
 #pragma unroll
   for (int i = 0; i < TMR; ++i)
@@ -105,9 +106,9 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
       for (int k = 0; k < BK; ++k) {
         R ar[TMR], ai[TMR], br[TN], bi[TN];
 #pragma unroll
-        for (int i = 0; i < TMR; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
+        for (int i = 0; i < TMR; ++i) { ar[i] = As_r[k][ty + TY * i]; ai[i] = As_i[k][ty + TY * i]; }
 #pragma unroll
-        for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
+        for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + TX * j]; bi[j] = Bs_i[k][tx + TX * j]; }
 #pragma unroll
         for (int i = 0; i < TMR; ++i)
 #pragma unroll
@@ -124,11 +125,11 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
     typename CxOf<R>::T* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
 #pragma unroll
     for (int i = 0; i < TMR; ++i) {
-      const int m = m0 + ty + 16 * i;
+      const int m = m0 + ty + TY * i;
       if (m >= tk.M) continue;
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int n = n0 + tx + 16 * j;
+        const int n = n0 + tx + TX * j;
         if (n >= tk.N) continue;
         typename CxOf<R>::T v;
         v.re = acc_r[i][j];
@@ -142,20 +143,20 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
   const R al = (R)tk.alpha, be = (R)tk.beta;
 #pragma unroll
   for (int i = 0; i < TMR; ++i) {
-    const int m = m0 + ty + 16 * i;
+    const int m = m0 + ty + TY * i;
     if (m >= tk.M) continue;
     // a row's C values in flight together, then the updates
     EO old[TN];
     if (tk.beta != 0.0) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int n = n0 + tx + 16 * j;
+        const int n = n0 + tx + TX * j;
         if (n < tk.N) old[j] = C[(size_t)m + (size_t)n * tk.ldc];
       }
     }
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int n = n0 + tx + 16 * j;
+      const int n = n0 + tx + TX * j;
       if (n >= tk.N) continue;
       R re = al * acc_r[i][j], im = al * acc_i[i][j];
       if (tk.beta != 0.0) {
@@ -193,13 +194,14 @@ template <int BM, int BN>
 __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tasks,
                                                const GemmPair* __restrict__ pairs,
                                                const GemmTile* __restrict__ tiles, cd* __restrict__ ws) {
-  constexpr int TN = BN / 16, TMR = BM / 16;
+  constexpr int TX = BN >= 16 ? 16 : BN, TY = NT / TX, TN = BN / TX, TMR = BM / TY;
+  static_assert(BN % TX == 0 && BM % TY == 0, "tile shape");
   __shared__ float As_r[BK][BM], As_i[BK][BM];
   __shared__ float Bs_r[BK][BN], Bs_i[BK][BN];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmTask tk = tasks[tl.task];
   const int m0 = tl.tm * BM, n0 = tl.tn * BN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   double acc_r[TMR][TN], acc_i[TMR][TN];
 #pragma unroll
   for (int i = 0; i < TMR; ++i)
@@ -253,9 +255,9 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tas
       for (int k = 0; k < BK; ++k) {
         float ar[TMR], ai[TMR], br[TN], bi[TN];
 #pragma unroll
-        for (int i = 0; i < TMR; ++i) { ar[i] = As_r[k][ty + 16 * i]; ai[i] = As_i[k][ty + 16 * i]; }
+        for (int i = 0; i < TMR; ++i) { ar[i] = As_r[k][ty + TY * i]; ai[i] = As_i[k][ty + TY * i]; }
 #pragma unroll
-        for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + 16 * j]; bi[j] = Bs_i[k][tx + 16 * j]; }
+        for (int j = 0; j < TN; ++j) { br[j] = Bs_r[k][tx + TX * j]; bi[j] = Bs_i[k][tx + TX * j]; }
 #pragma unroll
         for (int i = 0; i < TMR; ++i)
 #pragma unroll
@@ -280,11 +282,11 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tas
     cd* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
 #pragma unroll
     for (int i = 0; i < TMR; ++i) {
-      const int m = m0 + ty + 16 * i;
+      const int m = m0 + ty + TY * i;
       if (m >= tk.M) continue;
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int n = n0 + tx + 16 * j;
+        const int n = n0 + tx + TX * j;
         if (n >= tk.N) continue;
         cd v;
         v.re = acc_r[i][j];
@@ -297,19 +299,19 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tas
   cd* C = (cd*)tk.C;
 #pragma unroll
   for (int i = 0; i < TMR; ++i) {
-    const int m = m0 + ty + 16 * i;
+    const int m = m0 + ty + TY * i;
     if (m >= tk.M) continue;
     cd old[TN];
     if (tk.beta != 0.0) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int n = n0 + tx + 16 * j;
+        const int n = n0 + tx + TX * j;
         if (n < tk.N) old[j] = C[(size_t)m + (size_t)n * tk.ldc];
       }
     }
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int n = n0 + tx + 16 * j;
+      const int n = n0 + tx + TX * j;
       if (n >= tk.N) continue;
       cd v;
       v.re = tk.alpha * acc_r[i][j];
@@ -886,8 +888,10 @@ __global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks, int bm) {
 }  // namespace
 
 // tile shapes: 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16, 4 = 16 x 16
-int gemm_tile_m(int shape) { return shape == 4 ? 16 : shape >= 2 ? 32 : 64; }
-int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : 16; }
+// shapes 0 64x64, 1 64x16, 2 32x32, 3 32x16, 4 16x16, 5 64x8, 6 64x4 (the
+// narrow ones for products with a few right-hand sides; plain FP tiles only)
+int gemm_tile_m(int shape) { return shape == 4 ? 16 : (shape == 2 || shape == 3) ? 32 : 64; }
+int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : shape == 5 ? 8 : shape == 6 ? 4 : 16; }
 
 template <int BM, int BN>
 static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
@@ -953,6 +957,8 @@ cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTil
     case 2: return gemm_tile<32, 32>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
     case 3: return gemm_tile<32, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
     case 4: return gemm_tile<16, 16>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, emul);
+    case 5: return emul ? cudaErrorInvalidValue : gemm_tile<64, 8>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, 0);
+    case 6: return emul ? cudaErrorInvalidValue : gemm_tile<64, 4>(d_tasks, d_pairs, d_tiles, ntiles, pina, pin, pout, pacc, ws, s, 0);
     default: return cudaErrorInvalidValue;
   }
 }
