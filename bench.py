@@ -138,11 +138,36 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+MEASURED = {}  # FP64 / FP32 / DMMA rates measured by the peak probes in this run
+
+
+def probe_peaks():
+    """FP64 FMA, FP32 FMA and FP64 tensor-core (DMMA) throughput measured on
+    this GPU with the probe kernels of libh2peaks.so (CUDA events)."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_1703_06155_gb300", "libh2peaks.so")
+    if not os.path.exists(path):
+        return {}
+    lib = ctypes.CDLL(path)
+    lib.h2_peak_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for kind, name in ((0, "fp64"), (1, "fp32"), (2, "dmma_fp64")):
+        v = ctypes.c_double()
+        if lib.h2_peak_probe(kind, ctypes.byref(v)) == 0:
+            out[name] = v.value
+    return out
+
+
 def fp_peaks(clocks):
-    """Peak FP64 / FP32 (non-tensor) rates of the GB300 from unit counts and
-    the SM clock: 152 SMs, 2 FP64 FMA and 128 FP32 FMA per SM per clock."""
+    """Peak FP64 / FP32 (non-tensor) rates: measured by the probes of this run
+    when they ran, else derived from unit counts and the SM clock (152 SMs, 2
+    FP64 FMA and 128 FP32 FMA per SM per clock)."""
     f = (clocks or {}).get("sm_max_mhz") or 2070.0
-    return {"fp64": 152 * 2 * 2 * f * 1e6 / 1e12, "fp32": 152 * 128 * 2 * f * 1e6 / 1e12, "mhz": f}
+    out = {"fp64": 152 * 2 * 2 * f * 1e6 / 1e12, "fp32": 152 * 128 * 2 * f * 1e6 / 1e12, "mhz": f,
+           "source": "derived"}
+    if MEASURED.get("fp64") and MEASURED.get("fp32"):
+        out.update(fp64=MEASURED["fp64"], fp32=MEASURED["fp32"], source="measured")
+    return out
 
 
 def roofline(st, clocks, kernel=None, workload=None):
@@ -184,15 +209,18 @@ def roofline(st, clocks, kernel=None, workload=None):
         # FP64-accurate products of complex64 operands on the FP32 pipe: 4
         # exact real products summed in double-float per complex
         # multiply-add, 9 FP32 operations each (36 per 8 algorithmic flops)
-        lanes = 152 * 128 * pk["mhz"] * 1e6
-        peak = lanes * 8.0 / 36.0 / 1e12
-        out.update(bound="alu", peak=peak, peak_source="derived: 152 SM x 128 FP32 lanes x %.0f MHz x 8 flops / "
-                   "36 FP32 operations per complex multiply-add (double-float, FP32 pipe)" % pk["mhz"])
+        peak = pk["fp32"] / 2.0 * 8.0 / 36.0
+        out.update(bound="alu", peak=peak, peak_source="%s FP32 lane rate x 8 flops / 36 FP32 operations per "
+                   "complex multiply-add (double-float, FP32 pipe)" % pk["source"])
     else:
         fp64 = pipe == "fp64"
         peak = pk["fp64"] if fp64 else pk["fp32"]
-        out.update(bound="alu", peak=peak, peak_source="derived: 152 SM x %s FMA/clk x 2 flops x %.0f MHz (%s)" % (
-            "2 FP64" if fp64 else "128 FP32", pk["mhz"], "FP64 pipe" if fp64 else "FP32 pipe"))
+        if pk["source"] == "measured":
+            src = "measured in this run by the %s FMA probe (libh2peaks)" % ("FP64" if fp64 else "FP32")
+        else:
+            src = "derived: 152 SM x %s FMA/clk x 2 flops x %.0f MHz (%s)" % (
+                "2 FP64" if fp64 else "128 FP32", pk["mhz"], "FP64 pipe" if fp64 else "FP32 pipe")
+        out.update(bound="alu", peak=peak, peak_source=src)
     out["frac"] = achieved / out["peak"]
     return out
 
@@ -545,6 +573,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
+    MEASURED.update(probe_peaks())
     pts = inputs.grid_points(args.grid, H)
     N = len(pts)
     tun = dict(apply_path=args.apply_path, **tc_opts(args))
@@ -689,6 +718,7 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "roofline_table": table,
+        "measured_peaks_tflops": {k: round(v, 3) for k, v in MEASURED.items()},
         "solve_graph": solve_graph,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
                     sorted(st.get("kernels", {}).items(), key=lambda kv: -kv[1]["ms"])[:40 if args.profile_levels else 14]},

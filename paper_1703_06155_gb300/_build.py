@@ -1,4 +1,5 @@
-"""Compile libh2.so (all of csrc/) for sm_103a with nvcc, in place.
+"""Compile libh2.so (all of csrc/) and the peak probes libh2peaks.so
+(peaks/) for sm_103a with nvcc, in place.
 
 Translation units are compiled in parallel and only when a source or header
 changed; objects go to paper_1703_06155_gb300/_build/ (git-ignored).
@@ -14,6 +15,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libh2.so")
+PEAKS_SRC = os.path.join(PKG, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(PKG, "libh2peaks.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -66,6 +69,14 @@ def build(force=False, verbose=False, jobs=None):
         if r.returncode != 0:
             raise RuntimeError("libh2 link failed:\n%s\n%s\n%s" % (" ".join(cmd), r.stdout, r.stderr))
         os.replace(tmp, LIB)
+    # arithmetic peak probes (measurement only; not part of libh2)
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_SRC) > os.path.getmtime(PEAKS_LIB):
+        tmp = PEAKS_LIB + ".tmp"
+        cmd = [nvcc] + ARCH + ["-O3", "-shared", "-Xcompiler", "-fPIC", "-o", tmp, PEAKS_SRC]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("libh2peaks build failed:\n%s\n%s\n%s" % (" ".join(cmd), r.stdout, r.stderr))
+        os.replace(tmp, PEAKS_LIB)
     return LIB
 
 
