@@ -60,8 +60,9 @@ def parse():
                    help="Step 2 / panel applications: 0 auto, 1 in-place kernel, 2 GEMM + copy")
     p.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                    help="complex64 GEMM tiles: 2 tcgen05, 1 warp-level TF32 MMA, 0 FP32 FMA (default: library's)")
-    p.add_argument("--eig-solver", type=int, default=None, choices=[0, 1],
-                   help="Step-0 eigen-decomposition: 0 cyclic Jacobi, 1 tridiagonal + QL (default: library's)")
+    p.add_argument("--eig-solver", type=int, default=None, choices=[0, 1, 2],
+                   help="Step-0 eigen-decomposition: 0 cyclic Jacobi, 1 tridiagonal + QL, "
+                        "2 one-sided Jacobi SVD of the Cholesky factor (default: library's)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison factorization (large grids)")
     p.add_argument("--proxy", type=int, default=0,
                    help="construction with proxy points (h2_opts.proxy_min; 0 = exact far-field sample)")
@@ -212,6 +213,23 @@ def roofline(st, clocks, kernel=None, workload=None):
         peak = pk["fp32"] / 2.0 * 8.0 / 36.0
         out.update(bound="alu", peak=peak, peak_source="%s FP32 lane rate x 8 flops / 36 FP32 operations per "
                    "complex multiply-add (double-float, FP32 pipe)" % pk["source"])
+    elif pipe == "fp64_dd":
+        # complex128 products in double-float on the FP32 pipe: per real
+        # product a split multiply (4 FP32 operations) and a TwoSum
+        # accumulation (8), 48 per complex multiply-add of 8 algorithmic flops
+        peak = pk["fp32"] / 2.0 * 8.0 / 48.0
+        out.update(bound="alu", peak=peak, peak_source="%s FP32 lane rate x 8 flops / 48 FP32 operations per "
+                   "complex multiply-add (double-float products of FP64 operands, FP32 pipe)" % pk["source"])
+    elif pipe == "fp32_dfr":
+        # one-sided Jacobi rotations in double-float on the FP32 pipe: per
+        # entry of a rotated column pair, the complex dot product (4
+        # double-float multiply-adds of 15 FP32 operations) and the rotation
+        # of the entry pair of W and of J (2 double-float multiplies of 7 and
+        # 8 multiply-adds of 15 operations each, twice): 328 FP32 operations
+        # for 48 algorithmic flops
+        peak = pk["fp32"] / 2.0 * 48.0 / 328.0
+        out.update(bound="alu", peak=peak, peak_source="%s FP32 lane rate x 48 flops / 328 FP32 operations per "
+                   "rotated entry pair (double-float, FP32 pipe)" % pk["source"])
     else:
         fp64 = pipe == "fp64"
         peak = pk["fp64"] if fp64 else pk["fp32"]

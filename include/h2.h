@@ -107,11 +107,17 @@ typedef struct {
                             accumulation): 1 (default) on the FP32 pipe, as
                             exact products summed in double-float and
                             flushed to FP64 every 8 terms; 0: FP64 FMAs   */
-  int eig_solver;        /* Step-0 eigen-decomposition of the Ritz matrix
-                            (eq. 17): 0 (default) cyclic Jacobi; 1
-                            Householder reduction to real tridiagonal form
-                            + implicit QL with accumulated rotations
-                            (orders up to 452, Jacobi above)               */
+  int eig_solver;        /* Step-0 eigen-decomposition (eq. 17): 0
+                            cyclic Jacobi of the Ritz matrix; 1
+                            Householder reduction of the Ritz matrix to
+                            real tridiagonal form + implicit QL with
+                            accumulated rotations (orders up to 452,
+                            Jacobi above); 2 (default) one-sided Jacobi
+                            SVD of the
+                            Cholesky factor R (squared singular values =
+                            eigenvalues of L L^H, within trace(E) of those
+                            of G'), double-float on the FP32 pipe (orders
+                            up to 327, Jacobi above)                      */
   int stop_level;        /* early stop (Sec. III-C, last paragraph): 0
                             (default) factorize levels L .. l0; s > l0:
                             levels L .. s only, the remaining matrix of all
@@ -122,6 +128,12 @@ typedef struct {
                             within this angle (radians, default 0.3) of the
                             angular extent of some far-field node outside
                             the proxy sphere, as seen from the cluster centre */
+  int matvec_emulation;  /* products of the FP64 H^2 matvec: 1 (default)
+                            in double-float on the FP32 pipe (operands split
+                            into two FP32 parts, ~1e-13 relative error) for
+                            the residuals of refined solves with tol >=
+                            1e-11, FP64 FMAs elsewhere; 2: also h2_matvec;
+                            0: FP64 FMAs everywhere                        */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -318,7 +330,7 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 /*
  * h2_set_opts - change the run-time tunables of a context (apply_path,
  * solve_graph, split_target, cluster_max, tile_policy, tensor_cores,
- * gram_emulation, eig_solver, stop_level, profile) without
+ * gram_emulation, eig_solver, stop_level, matvec_emulation, profile) without
  * rebuilding it; the other fields of *opts are ignored.  They take effect at
  * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
  * counterpart in the paper: used by the autotuner.

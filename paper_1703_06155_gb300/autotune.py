@@ -11,7 +11,8 @@ for candidate settings of
   tensor_cores  complex64 tiles on tcgen05 / warp-level tensor-core MMAs
                 (3xTF32) or on FP32 FMAs,
   gram_emulation  FP64-accurate Step-0 Grams on the FP32 pipe / FP64 FMAs,
-  eig_solver    Step-0 eigen-decomposition: cyclic Jacobi / tridiagonal + QL,
+  eig_solver    Step-0 eigen-decomposition: cyclic Jacobi / tridiagonal + QL /
+                one-sided Jacobi SVD of the Cholesky factor,
   stop_level    early stop of the factorization (Sec. III-C): l0 (0) or one
                 to three levels below it, the rest as one dense final block,
 
@@ -28,7 +29,7 @@ DEFAULT_SPACE = {
     "split_target": [0, 608, 2432],
     "cluster_max": [16, 8],
     "apply_path": [2, 1],
-    "eig_solver": [0, 1],
+    "eig_solver": [2, 0, 1],
 }
 
 

@@ -245,16 +245,18 @@ void h2_default_opts(h2_opts* o) {
   o->tile_policy = 0;
   o->tensor_cores = 2;
   o->gram_emulation = 1;
-  o->eig_solver = 0;
+  o->eig_solver = 2;
   o->stop_level = 0;
   o->proxy_margin = 0.3;
+  o->matvec_emulation = 1;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   if (!ctx || !o || o->apply_path < 0 || o->apply_path > 2 || o->split_target < 0 || o->cluster_max < 0 ||
       o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
       o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1 ||
-      o->eig_solver < 0 || o->eig_solver > 1 || o->stop_level < 0)
+      o->eig_solver < 0 || o->eig_solver > 2 || o->stop_level < 0 || o->matvec_emulation < 0 ||
+      o->matvec_emulation > 2)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -266,6 +268,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   c.gram_emulation = o->gram_emulation;
   c.eig_solver = o->eig_solver;
   c.stop_level = o->stop_level;
+  c.matvec_emulation = o->matvec_emulation;
   c.profile = o->profile;
   ctx->c.graphs.clear();
   return H2_OK;
@@ -301,7 +304,8 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   if (opts) x->c.opts = *opts;
   if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2 ||
       x->c.opts.gram_emulation < 0 || x->c.opts.gram_emulation > 1 || x->c.opts.eig_solver < 0 ||
-      x->c.opts.eig_solver > 1 || x->c.opts.stop_level < 0) {
+      x->c.opts.eig_solver > 2 || x->c.opts.stop_level < 0 || x->c.opts.matvec_emulation < 0 ||
+      x->c.opts.matvec_emulation > 2) {
     delete x;
     g_err = "h2_build: bad options";
     return H2_EINVAL;
@@ -715,8 +719,13 @@ h2_status h2_solve(h2_ctx* ctx, const void* b, void* xo, int nrhs, unsigned flag
       const std::vector<double> nb = col_norms(ctx, db, nrhs);
       int it = 0;
       double rel = 0;
+      const bool emul = c.opts.matvec_emulation >= 1 && tol >= 1e-11;
       for (;;) {
-        apply_A(ctx, dxx, r, nrhs, adj);
+        {
+          // the residual's products in double-float (h2_opts.matvec_emulation)
+          MvEmul me(c, emul);
+          apply_A(ctx, dxx, r, nrhs, adj);
+        }
         ck(axpby(db, r, r, (int64_t)N * nrhs, 1.0, -1.0, c.stream), "residual");
         const std::vector<double> nr = col_norms(ctx, r, nrhs);
         rel = 0;
@@ -828,8 +837,12 @@ h2_status h2_solve_batch(h2_ctx* const* ctxs, int count, const void* const* b, v
       int it = 0;
       double rel = 0;
       std::vector<const cd*> cx(dx.begin(), dx.end()), cr(r.begin(), r.end());
+      const bool emul = lc.opts.matvec_emulation >= 1 && tol >= 1e-11;
       for (;;) {
-        apply_A_group(xs, cx, r, nrhs, adj);
+        {
+          MvEmul me(lc, emul);
+          apply_A_group(xs, cx, r, nrhs, adj);
+        }
         for (int q = 0; q < count; ++q)
           ck(axpby(db[q], r[q], r[q], xs[q]->c.H.tree.N * (int64_t)nrhs, 1.0, -1.0, lc.stream), "residual");
         const auto nr = col_norms_group(xs, cr, nrhs);
@@ -878,6 +891,7 @@ h2_status h2_matvec(h2_ctx* ctx, const void* xi, void* y, int nrhs, unsigned fla
       dy = (cd*)dev_ensure(c, ctx->hx, bytes);
       ck(cudaMemcpyAsync((void*)dx, xi, bytes, cudaMemcpyHostToDevice, c.stream), "x H2D");
     }
+    MvEmul me(c, c.opts.matvec_emulation == 2);
     apply_A(ctx, dx, dy, nrhs, flags & H2_ADJOINT);
     if (flags & H2_HOST) ck(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, c.stream), "y D2H");
     ck(cudaStreamSynchronize(c.stream), "matvec sync");

@@ -90,6 +90,7 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
   // the old contents are not kept: grow-only scratch / per-factorization arenas
   if (b.p) {
     ck(cudaStreamSynchronize(c.stream), "sync before realloc");
+    if (c.side.s) ck(cudaStreamSynchronize(c.side.s), "sync before realloc");
     cudaFree(b.p);
     b.p = nullptr;
     c.dev_bytes -= old;
@@ -145,6 +146,7 @@ void Stager::upload(Ctx& c) {
     // everything uploaded so far has been consumed by launches already in
     // the stream: wait for them, grow, and upload the whole range again
     ck(cudaStreamSynchronize(c.stream), "stager sync");
+    if (c.side.s) ck(cudaStreamSynchronize(c.side.s), "stager sync");
     if (pinned) cudaFreeHost(pinned);
     pinned = nullptr;
     cap = std::max(host.size() * 2, (size_t)1 << 20);

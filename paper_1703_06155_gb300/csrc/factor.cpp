@@ -41,7 +41,9 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   if (b.empty()) return;
   HostScope hs(c, "run_gemm");
   const int pa = b.pina < 0 ? pin : b.pina;
-  const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1 : 0;
+  const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1
+                   : (c.mv_emul && pa == P64 && pin == P64 && pacc == P64 && pout == P64)   ? 2
+                                                                                            : 0;
   const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 8 * 152, pacc == P64, c.opts.tile_policy,
                             !emul);
   if (b.tl.empty()) return;
@@ -50,7 +52,12 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
   c.st.upload(c);
   const int tc = (b.shape == 0 && pa == P32 && pin == P32 && pacc == P32 && pout == P32) ? c.opts.tensor_cores : 0;
-  const char* pipe = emul ? "fp32_df" : pacc == P64 ? "fp64" : tc == 2 ? "tcgen05_tf32x3" : tc == 1 ? "mma_tf32x3" : "fp32";
+  const char* pipe = emul == 1      ? "fp32_df"
+                     : emul == 2    ? "fp64_dd"
+                     : pacc == P64  ? "fp64"
+                     : tc == 2      ? "tcgen05_tf32x3"
+                     : tc == 1      ? "mma_tf32x3"
+                                    : "fp32";
   ProfScope ps(c, std::string("gemm:") + what, b.alg_flops, pipe);
   c.paths[std::string("gemm:") + pipe + ":" + std::to_string(h2k::gemm_tile_m(b.shape)) + "x" +
           std::to_string(h2k::gemm_tile_n(b.shape))]++;
@@ -404,6 +411,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   for (size_t q = 0; q < nj; ++q) r[q].assign(jobs[q].bt->size(), 0);
   hsA.reset();
   if (anyfill) {
+    bool trace_forked = false;
     GemmBatch gM, gX, gXX, gT, gG;
     CopyBatch cvp;
     std::vector<PcholTask> pc;
@@ -487,8 +495,11 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           gG.pair(Vp(q, f.i), n, OP_H, Sq + f.T1, n, OP_N, n);
           gG.close();
         }
+        // the one-sided solver works on the Cholesky factor R, written into
+        // the Ritz-matrix slot
         pc.push_back(PcholTask{Sq + f.G, (const double*)(Sq + f.tr), Sq + f.L, Sq + f.T, d_r[q] + u, p, n,
-                               snorm(q, f.i), eps * eps, Sq + f.W});
+                               snorm(q, f.i), eps * eps, Sq + f.W, lc.opts.eig_solver == 2 ? Sq + f.Gh : nullptr,
+                               prec == P32 ? 1 : 0});
         maxp = std::max(maxp, p);
       }
     }
@@ -497,11 +508,28 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
       lc.st.upload(lc);
       double tb = 0;
       for (const FrobBlock& f : fb) tb += (double)f.rows * f.cols * es;
-      ProfScope ps(lc, "trace", 0.0, nullptr, tb);
       double* part = (double*)dev_ensure(lc, lc.frobbuf, (fb.size() + 1) * sizeof(double));
-      ck(frob2(lc.st.ptr<FrobTask>(i0), (int)ft.size(), lc.st.ptr<FrobBlock>(i1), (int)fb.size(), part, prec,
-               lc.stream),
-         "fill trace");
+      if (lc.opts.profile == 0) {
+        // the trace only reads the fill-ins: it runs on the side stream beside
+        // the Gram products and joins before the subspace kernel reads it
+        if (!lc.side.s) {
+          ck(cudaStreamCreateWithFlags(&lc.side.s, cudaStreamNonBlocking), "side stream");
+          ck(cudaEventCreateWithFlags(&lc.side.a, cudaEventDisableTiming), "side event");
+          ck(cudaEventCreateWithFlags(&lc.side.b, cudaEventDisableTiming), "side event");
+        }
+        ck(cudaEventRecord(lc.side.a, lc.stream), "side fork");
+        ck(cudaStreamWaitEvent(lc.side.s, lc.side.a, 0), "side fork");
+        ck(frob2(lc.st.ptr<FrobTask>(i0), (int)ft.size(), lc.st.ptr<FrobBlock>(i1), (int)fb.size(), part, prec,
+                 lc.side.s),
+           "fill trace");
+        ck(cudaEventRecord(lc.side.b, lc.side.s), "side join");
+        trace_forked = true;
+      } else {
+        ProfScope ps(lc, "trace", 0.0, nullptr, tb);
+        ck(frob2(lc.st.ptr<FrobTask>(i0), (int)ft.size(), lc.st.ptr<FrobBlock>(i1), (int)fb.size(), part, prec,
+                 lc.stream),
+           "fill trace");
+      }
       lc.launches += 2;
     }
     run_gemm(lc, gM, prec, P64, P64, "gram");
@@ -514,6 +542,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     run_gemm(lc, gT, P64, P64, P64, "gram*Vp");
     run_gemm(lc, gG, P64, P64, P64, "Vp^H*gram*Vp");
     size_t pchol_rec = SIZE_MAX;
+    if (trace_forked) ck(cudaStreamWaitEvent(lc.stream, lc.side.b, 0), "side join");
     {
       const int i0 = lc.st.add(pc);
       lc.st.upload(lc);
@@ -557,6 +586,11 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     std::vector<EigTask> eig;
     std::vector<SelTask> sel;
     int maxr = 0;
+    for (size_t q = 0; q < nj; ++q)
+      for (const Info& f : info[q])
+        if (f.fill) maxr = std::max(maxr, f.rp);
+    // one-sided Jacobi on R: no Ritz matrix (and no explicit Qx) is formed
+    const bool use_osj = lc.opts.eig_solver == 2 && maxr <= osj_max_order();
     for (size_t q = 0; q < nj; ++q) {
       const size_t nb = jobs[q].bt->size();
       cd* Sq = S[q];
@@ -571,23 +605,29 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         g1.task(Sq + f.W1, n, n, rr, 1.0, 0.0);  // W1 = Vp Y
         g1.pair(Vp(q, f.i), n, OP_N, Y, p, OP_N, p);
         g1.close();
-        cp.add(nullptr, P64, p, 0, 0, Sq + f.Qx, P64, p, p, rr, 2);        // Qx = E
-        cp.add(Vp(q, f.i), P64, n, n, p, Sq + f.Yf, P64, n, n, p, 0);      // Yf = Vp
-        g2.task(Sq + f.Qx, p, p, rr, -1.0, 1.0);  // Qx = E - W Y(0:r',:)^H
-        g2.pair(Sq + f.W, p, OP_N, Y, p, OP_H, rr);
-        g2.close();
+        if (!use_osj) cp.add(nullptr, P64, p, 0, 0, Sq + f.Qx, P64, p, p, rr, 2);  // Qx = E
+        cp.add(Vp(q, f.i), P64, n, n, p, Sq + f.Yf, P64, n, n, p, 0);                // Yf = Vp
+        if (!use_osj) {
+          g2.task(Sq + f.Qx, p, p, rr, -1.0, 1.0);  // Qx = E - W Y(0:r',:)^H
+          g2.pair(Sq + f.W, p, OP_N, Y, p, OP_H, rr);
+          g2.close();
+        }
         g2.task(Sq + f.W2, n, n, rr, 1.0, 0.0);  // W2 = W1 T
         g2.pair(Sq + f.W1, n, OP_N, Sq + f.T, rr, OP_N, rr);
         g2.close();
-        g3.task(Sq + f.Z1, p, p, rr, 1.0, 0.0);  // Z1 = G' Qx
-        g3.pair(Sq + f.G, p, OP_N, Sq + f.Qx, p, OP_N, p);
-        g3.close();
+        if (!use_osj) {
+          g3.task(Sq + f.Z1, p, p, rr, 1.0, 0.0);  // Z1 = G' Qx
+          g3.pair(Sq + f.G, p, OP_N, Sq + f.Qx, p, OP_N, p);
+          g3.close();
+        }
         g3.task(Sq + f.Yf, n, n, p, -1.0, 1.0);  // Yf = Vp - W2 Y^H
         g3.pair(Sq + f.W2, n, OP_N, Y, p, OP_H, rr);
         g3.close();
-        g4.task(Sq + f.Gh, rr, rr, rr, 1.0, 0.0);  // Ritz matrix Qx^H G' Qx
-        g4.pair(Sq + f.Qx, p, OP_H, Sq + f.Z1, p, OP_N, p);
-        g4.close();
+        if (!use_osj) {
+          g4.task(Sq + f.Gh, rr, rr, rr, 1.0, 0.0);  // Ritz matrix Qx^H G' Qx
+          g4.pair(Sq + f.Qx, p, OP_H, Sq + f.Z1, p, OP_N, p);
+          g4.close();
+        }
         // the Jacobi leaves entries below 1e-4 of the threshold unrotated: with
         // r' of them per row, the eigenvalues move by at most r' 1e-4 thr
         eig.push_back(EigTask{Sq + f.Gh, Sq + f.U, (double*)(Sq + f.lam), rr, d_r[q] + 2 * nb + u,
@@ -595,7 +635,6 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         eig_of.push_back({q, u});
         sel.push_back(
             SelTask{(const double*)(Sq + f.tr), (double*)(Sq + f.lam), d_r[q] + nb + u, n, rr, snorm(q, f.i), eps * eps});
-        maxr = std::max(maxr, rr);
         g5.task(Sq + f.Y1, n, n, rr, 1.0, 0.0);  // Y1 = Yf(:, 0:r') U
         g5.pair(Sq + f.Yf, n, OP_N, Sq + f.U, rr, OP_N, rr);
         g5.close();
@@ -607,7 +646,26 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     run_gemm(lc, g3, P64, P64, P64, "WY 3");
     run_gemm(lc, g4, P64, P64, P64, "ritz matrix");
     const bool use_heev = lc.opts.eig_solver == 1 && maxr <= heev_max_order();
-    if (!eig.empty() && use_heev) {
+    if (!eig.empty() && use_osj) {
+      const int i0 = lc.st.add(eig);
+      lc.st.upload(lc);
+      ProfScope ps(lc, "osj_cluster", 0.0, "fp32_dfr");
+      if (ps.on) jac_rec = ps.idx;
+      const int cmax = lc.opts.cluster_max > 0 ? lc.opts.cluster_max : 16;
+      const int csize = osj_cluster_size((int)eig.size(), maxr, cmax);
+      const int64_t per = osj_cluster_scratch(maxr);
+      void* js = dev_ensure(lc, lc.jac_buf, (size_t)per * eig.size());
+      int used = 0;
+      ck(osj_eig_cluster(lc.st.ptr<EigTask>(i0), (int)eig.size(), maxr, csize, js, (int*)lc.statusbuf.p, lc.stream,
+                         &used),
+         "one-sided Jacobi (cluster)");
+      lc.paths["osj_cluster:cta" + std::to_string(used)]++;
+      lc.launches++;
+      const int i1 = lc.st.add(sel);
+      lc.st.upload(lc);
+      ck(select_rank(lc.st.ptr<SelTask>(i1), (int)sel.size(), lc.stream), "select");
+      lc.launches++;
+    } else if (!eig.empty() && use_heev) {
       const int i0 = lc.st.add(eig);
       lc.st.upload(lc);
       ProfScope ps(lc, "heev_cluster", 0.0, "fp64");
@@ -675,6 +733,9 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     for (auto [q, u] : eig_of) {
       const double rr = info[q][u].rp;
       const double sw = std::max(sweeps[q][u], 0);
+      // one-sided Jacobi: per sweep r'(r'-1)/2 pairs, each a complex dot
+      // product of two columns of W (8 r' flops) and the rotation of two
+      // columns of W and of J (20 r' flops each): 24 r'^3 per sweep as well
       fl += heev_used ? (16.0 / 3.0 + 8.0) * rr * rr * rr + 3.0 * rr * rr * sw : 24.0 * rr * rr * rr * sw;
     }
     lc.prof_open[jac_rec].flops = fl;

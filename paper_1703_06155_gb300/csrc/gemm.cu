@@ -325,6 +325,183 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tas
   }
 }
 
+// ---- complex128 products in double-float on the FP32 pipe ---------------
+//
+// For the FP64 stages of the H^2 matvec that refinement residuals run
+// through.  Each FP64 operand is split on load into hi = fl32(x) and
+// lo = fl32(x - hi) (48 of its 53 bits); a product (ah + al)(bh + bl) is
+// taken as the exact ah bh = p + e (e = fma(ah, bh, -p)) plus ah bl + al bh
+// (al bl, 2^-48 of the product, is dropped); one BK-long K slice is summed in
+// double-float as in k_gemm_df and the slice totals are added to a
+// double-float accumulator (TwoSum), which becomes FP64 at the end.  About 12
+// FP32 operations per real product: the relative error of an output is a few
+// 2^-47 per term (~1e-13 of its magnitude for thousands of terms), against
+// ~1e-16 with FP64 FMAs, at about a fifth of the FP64 pipe time.
+__device__ __forceinline__ void dd_madd(float& h, float& l, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  const float t = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(t, e));
+}
+
+// (H, L) += (h, l) in double-float
+__device__ __forceinline__ void dd_acc(float& H, float& L, float h, float l) {
+  const float s = __fadd_rn(H, h);
+  const float bb = __fsub_rn(s, H);
+  const float t = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bb)), __fsub_rn(h, bb));
+  const float lo = __fadd_rn(__fadd_rn(L, l), t);
+  H = __fadd_rn(s, lo);
+  L = __fsub_rn(lo, __fsub_rn(H, s));
+}
+
+__device__ __forceinline__ void dd_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT) k_gemm_dd(const GemmTask* __restrict__ tasks,
+                                               const GemmPair* __restrict__ pairs,
+                                               const GemmTile* __restrict__ tiles, cd* __restrict__ ws) {
+  constexpr int TX = BN >= 16 ? 16 : BN, TY = NT / TX, TN = BN / TX, TMR = BM / TY;
+  static_assert(BN % TX == 0 && BM % TY == 0, "tile shape");
+  __shared__ float As_rh[BK][BM], As_rl[BK][BM], As_ih[BK][BM], As_il[BK][BM];
+  __shared__ float Bs_rh[BK][BN], Bs_rl[BK][BN], Bs_ih[BK][BN], Bs_il[BK][BN];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask tk = tasks[tl.task];
+  const int m0 = tl.tm * BM, n0 = tl.tn * BN;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  float Hr[TMR][TN], Lr[TMR][TN], Hi[TMR][TN], Li[TMR][TN];
+#pragma unroll
+  for (int i = 0; i < TMR; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) Hr[i][j] = Lr[i][j] = Hi[i][j] = Li[i][j] = 0.f;
+
+  const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
+  const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
+  int64_t koff = 0;
+  for (int pi = tk.p0; pi < tk.p0 + tk.np; ++pi) {
+    const GemmPair pr = pairs[pi];
+    const int64_t kb = koff;
+    koff += pr.K;
+    if (koff <= klo || kb >= khi) continue;
+    const int kbeg = (int)(klo > kb ? klo - kb : 0);
+    const int kend = (int)(khi - kb < pr.K ? khi - kb : pr.K);
+    const cd* A = (const cd*)pr.A;
+    const cd* B = (const cd*)pr.B;
+    const bool at = (pr.opA == OP_T || pr.opA == OP_H);
+    const bool bt = (pr.opB == OP_T || pr.opB == OP_H);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+      for (int r = 0; r < (BM * BK + NT - 1) / NT; ++r) {
+        const int l = tid + r * NT;
+        if (l >= BM * BK) break;
+        int i, k;
+        if (!at) { i = l % BM; k = l / BM; } else { k = l % BK; i = l / BK; }
+        double re = 0, im = 0;
+        if (m0 + i < tk.M && k0 + k < kend) load_op<cd, double>(A, pr.lda, pr.opA, m0 + i, k0 + k, re, im);
+        dd_split(re, As_rh[k][i], As_rl[k][i]);
+        dd_split(im, As_ih[k][i], As_il[k][i]);
+      }
+#pragma unroll
+      for (int r = 0; r < (BK * BN + NT - 1) / NT; ++r) {
+        const int l = tid + r * NT;
+        if (l >= BK * BN) break;
+        int k, j;
+        if (!bt) { k = l % BK; j = l / BK; } else { j = l % BN; k = l / BN; }
+        double re = 0, im = 0;
+        if (n0 + j < tk.N && k0 + k < kend) load_op<cd, double>(B, pr.ldb, pr.opB, k0 + k, n0 + j, re, im);
+        dd_split(re, Bs_rh[k][j], Bs_rl[k][j]);
+        dd_split(im, Bs_ih[k][j], Bs_il[k][j]);
+      }
+      __syncthreads();
+      float hr[TMR][TN], lr[TMR][TN], hi[TMR][TN], li[TMR][TN];
+#pragma unroll
+      for (int i = 0; i < TMR; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) hr[i][j] = lr[i][j] = hi[i][j] = li[i][j] = 0.f;
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        float arh[TMR], arl[TMR], aih[TMR], ail[TMR], brh[TN], brl[TN], bih[TN], bil[TN];
+#pragma unroll
+        for (int i = 0; i < TMR; ++i) {
+          arh[i] = As_rh[k][ty + TY * i];
+          arl[i] = As_rl[k][ty + TY * i];
+          aih[i] = As_ih[k][ty + TY * i];
+          ail[i] = As_il[k][ty + TY * i];
+        }
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          brh[j] = Bs_rh[k][tx + TX * j];
+          brl[j] = Bs_rl[k][tx + TX * j];
+          bih[j] = Bs_ih[k][tx + TX * j];
+          bil[j] = Bs_il[k][tx + TX * j];
+        }
+#pragma unroll
+        for (int i = 0; i < TMR; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            dd_madd(hr[i][j], lr[i][j], arh[i], arl[i], brh[j], brl[j]);
+            dd_madd(hr[i][j], lr[i][j], -aih[i], -ail[i], bih[j], bil[j]);
+            dd_madd(hi[i][j], li[i][j], arh[i], arl[i], bih[j], bil[j]);
+            dd_madd(hi[i][j], li[i][j], aih[i], ail[i], brh[j], brl[j]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < TMR; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          dd_acc(Hr[i][j], Lr[i][j], hr[i][j], lr[i][j]);
+          dd_acc(Hi[i][j], Li[i][j], hi[i][j], li[i][j]);
+        }
+      __syncthreads();
+    }
+  }
+  if (tk.nk > 1) {
+    cd* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
+#pragma unroll
+    for (int i = 0; i < TMR; ++i) {
+      const int m = m0 + ty + TY * i;
+      if (m >= tk.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + TX * j;
+        if (n >= tk.N) continue;
+        cd v;
+        v.re = (double)Hr[i][j] + (double)Lr[i][j];
+        v.im = (double)Hi[i][j] + (double)Li[i][j];
+        W[(int64_t)m + (int64_t)n * tk.M] = v;
+      }
+    }
+    return;
+  }
+  cd* C = (cd*)tk.C;
+#pragma unroll
+  for (int i = 0; i < TMR; ++i) {
+    const int m = m0 + ty + TY * i;
+    if (m >= tk.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx + TX * j;
+      if (n >= tk.N) continue;
+      cd v;
+      v.re = tk.alpha * ((double)Hr[i][j] + (double)Lr[i][j]);
+      v.im = tk.alpha * ((double)Hi[i][j] + (double)Li[i][j]);
+      if (tk.beta != 0.0) {
+        const cd old = C[(size_t)m + (size_t)n * tk.ldc];
+        v.re = fma(tk.beta, old.re, v.re);
+        v.im = fma(tk.beta, old.im, v.im);
+      }
+      C[(size_t)m + (size_t)n * tk.ldc] = v;
+    }
+  }
+}
+
 // ---- complex64 tiles on the tensor cores (3xTF32) ----------------------
 //
 // The same 64 x 64 tile / task / pair / split-K scheme as k_gemm, with the
@@ -896,8 +1073,10 @@ int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : shape ==
 template <int BM, int BN>
 static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
                              int pina, int pin, int pout, int pacc, void* ws, cudaStream_t s, int emul) {
-  if (emul && pina == P32 && pin == P32 && pacc == P64 && pout == P64)
+  if (emul == 1 && pina == P32 && pin == P32 && pacc == P64 && pout == P64)
     k_gemm_df<BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
+  else if (emul == 2 && pina == P64 && pin == P64 && pacc == P64 && pout == P64)
+    k_gemm_dd<BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pina == P64 && pin == P64 && pacc == P64 && pout == P64)
     k_gemm<cd, cd, double, cd, BM, BN><<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cd*)ws);
   else if (pina == P32 && pin == P32 && pacc == P32 && pout == P32)

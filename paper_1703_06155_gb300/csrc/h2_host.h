@@ -223,9 +223,27 @@ struct ProfAgg {
   const char* pipe = nullptr;
 };
 
+// A second stream of the context for work that overlaps the main stream's
+// (the fill-in trace of Step 0), with the two events that order it.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  SideStream() = default;
+  SideStream(const SideStream&) = delete;
+  SideStream& operator=(const SideStream&) = delete;
+  ~SideStream() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 struct Ctx {
   H2Host H;
   cudaStream_t stream = nullptr;
+  SideStream side;
+  // the FP64 matvec's products in double-float while set (MvEmul)
+  bool mv_emul = false;
   h2_opts opts;
   std::string err;
   size_t dev_bytes = 0, dev_peak = 0;
@@ -304,6 +322,17 @@ struct ProfScope {
   ProfScope(Ctx& c_, const std::string& tag, double flops, const char* pipe = nullptr, double bytes = 0.0);
   ~ProfScope();
 };
+// Scope in which the FP64 H^2 matvec stages of `c` run their products in
+// double-float on the FP32 pipe (h2_opts.matvec_emulation).
+struct MvEmul {
+  Ctx& c;
+  bool old;
+  MvEmul(Ctx& cc, bool on) : c(cc), old(cc.mv_emul) { c.mv_emul = on; }
+  ~MvEmul() { c.mv_emul = old; }
+  MvEmul(const MvEmul&) = delete;
+  MvEmul& operator=(const MvEmul&) = delete;
+};
+
 void prof_resolve(Ctx& c);  // after a stream synchronize: fold events into c.prof
 // cudaStreamSynchronize with the blocked host time added to c.stats.t_sync_ms
 void sync_timed(Ctx& c, cudaStream_t s, const char* what);

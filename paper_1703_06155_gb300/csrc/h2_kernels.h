@@ -127,6 +127,8 @@ struct PcholTask {
   int p, n;
   double snorm2, eps2;
   cd* W;          // p x p scratch (Y^H Y)
+  cd* R;          // NULL, or r' x r' (ld r'): the upper triangle receives R of L = Q [R; 0]
+  int dfqr;       // 1: Householder QR and Y^H Y in double-float on the FP32 pipe
 };
 
 // ---- blocked LU of the final block: one tall panel with partial pivoting --
@@ -164,7 +166,9 @@ struct KGramTile { int task, tm, tn; };
 // tensor = 1: complex64 64 x 64 products on warp-level TF32 MMAs (3xTF32);
 // tensor = 2: the same on tcgen05 MMAs with TMEM accumulators (3xTF32);
 // emul = 1: complex64 operands with FP64 accumulation run on the FP32 pipe
-// (exact products summed in double-float, flushed to FP64 per K slice)
+// (exact products summed in double-float, flushed to FP64 per K slice);
+// emul = 2: complex128 operands and output, products in double-float on the
+// FP32 pipe (operands split into two FP32 parts)
 cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs,
                  const GemmTile* d_tiles, int ntiles, int pin, int pout,
                  int pacc, void* ws, cudaStream_t s, int shape = 0,
@@ -200,6 +204,15 @@ cudaError_t jacobi_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp,
 // the same decomposition by Householder tridiagonalization, implicit QL with
 // accumulated rotations and back-transformation (orders <= heev_max_order())
 int heev_max_order();
+// the Step-0 truncation from the Cholesky factor: one-sided Jacobi SVD of R
+// (EigTask.A = R, r' x r' upper triangular, ld r') in double-float on the
+// FP32 pipe; lam = squared singular values (decreasing), U = left singular
+// vectors.  Orders <= osj_max_order(); scratch in bytes per task.
+int osj_max_order();
+int64_t osj_cluster_scratch(int maxp);
+int osj_cluster_size(int ntasks, int maxp, int cmax);
+cudaError_t osj_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, void* d_scratch, int* d_status,
+                            cudaStream_t s, int* csize_used = nullptr);
 int64_t heev_cluster_scratch(int maxp);  // doubles per task
 int heev_cluster_size(int ntasks, int maxp, int cmax);
 cudaError_t heev_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, double* d_scratch, int* d_status,

@@ -34,9 +34,11 @@
 
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "h2_kernels.h"
 
 namespace cg = cooperative_groups;
+namespace D = h2k::dfl;
 
 namespace h2k {
 namespace {
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
   __shared__ double red[32];
   __shared__ double dl[PMAX];            // diagonal residuals of the own rows
   __shared__ unsigned char used[PMAX];   // own rows already pivoted
-  __shared__ cd prow[PMAX];              // pivot row L[pc, 0:j]
+  __shared__ __align__(16) cd prow[PMAX];  // pivot row L[pc, 0:j]
   __shared__ double cand_v[2], cand_t[2];
   __shared__ int cand_i[2];
   __shared__ double wv[NT / 32];
@@ -251,139 +253,356 @@ __global__ void __launch_bounds__(NT) k_pchol_wy_cl(const PcholTask* __restrict_
   }
   // ---------------------------------------- Householder QR of L(:, 0:r)
   cd* T = t.T;  // r x r (ld r): tau_j on the diagonal while the QR runs
-  auto reflector = [&](int j) {
-    double s = 0;
-    for (int i = j + 1 + tid; i < p; i += NT) {
-      const cd v = L[i + (size_t)j * p];
-      s += v.re * v.re + v.im * v.im;
-    }
-    s = bsum(s, red);
-    const cd al = L[j + (size_t)j * p];
-    double tr_ = 0, ti_ = 0;
-    if (!(s == 0.0 && al.im == 0.0)) {
-      const double nrm = sqrt(al.re * al.re + al.im * al.im + s);
-      const double beta = al.re >= 0 ? -nrm : nrm;
-      tr_ = (beta - al.re) / beta;
-      ti_ = -al.im / beta;
-      const double dr = al.re - beta, di = al.im, dd = dr * dr + di * di;
-      const double scr = dr / dd, sci = -di / dd;
+  cd* W = t.W;
+  if (t.dfqr) {
+    // The QR in double-float on the FP32 pipe.  L's entries are of the order
+    // of the square roots of G's: the directions at the truncation threshold
+    // have singular values near eps ||L||, which double-float's ~48 bits
+    // carry to ~1e-9 relative at eps = 1e-6, while Q stays unitary to ~1e-13.
+    // The columns are held as {re.h, re.l, im.h, im.l} in L's own storage.
+    float4* Lf = reinterpret_cast<float4*>(L);
+    float4* vsf = reinterpret_cast<float4*>(prow);  // reflector j (pivot-row buffer, free now)
+    __shared__ float2 redf[NT / 32];
+    auto bsum_df = [&](D::df v) {
+      v = D::wsum(v);
+      __syncthreads();
+      if (lane == 0) redf[warp] = make_float2(v.h, v.l);
+      __syncthreads();
+      D::df s = {0.0f, 0.0f};
+      for (int w = 0; w < nw; ++w) s = D::dadd(s, D::df{redf[w].x, redf[w].y});
+      __syncthreads();
+      return s;
+    };
+    // power-of-two scaling to max |L| in [0.5, 1) (Q, Y and T do not change;
+    // R is scaled back): with diagonal pivoting |L(i, j)| <= L(p_0, 0), the
+    // largest entry of column 0, which every CTA reads
+    double mx = 0;
+    if (r > 0)
+      for (int i = tid; i < p; i += NT) {
+        const cd v = L[i];
+        mx = fmax(mx, fmax(fabs(v.re), fabs(v.im)));
+      }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = 0;
+    for (int w = 0; w < nw; ++w) mx = fmax(mx, red[w]);
+    int ex = 0;
+    if (mx > 0) frexp(mx, &ex);
+    cluster_barrier();  // column 0 read by all before its owner converts it
+    for (int c = rank; c < r; c += C)
+      for (int i = tid; i < p; i += NT) {
+        const cd v = L[i + (size_t)c * p];
+        Lf[i + (size_t)c * p] = D::pack(D::dsplit(ldexp(v.re, -ex)), D::dsplit(ldexp(v.im, -ex)));
+      }
+    __syncthreads();
+    auto reflector_df = [&](int j) {
+      D::df s = {0.0f, 0.0f};
       for (int i = j + 1 + tid; i < p; i += NT) {
-        cd v = L[i + (size_t)j * p];
-        const double vr = v.re * scr - v.im * sci, vi = v.re * sci + v.im * scr;
-        v.re = vr;
-        v.im = vi;
-        L[i + (size_t)j * p] = v;
+        const float4 v = Lf[i + (size_t)j * p];
+        s = D::dfma(D::re_of(v), D::re_of(v), s);
+        s = D::dfma(D::im_of(v), D::im_of(v), s);
       }
-    }
-    if (tid == 0) {
-      T[j + (size_t)j * r].re = tr_;
-      T[j + (size_t)j * r].im = ti_;
-    }
-  };
-  // apply H_j^H to column c (one warp); vs = reflector j in shared memory
-  // (vs[j] = 1).  A column of up to 32 WR entries stays in registers between
-  // the dot product and the update, its loads all in flight together.
-  constexpr int WR = 12;
-  cd* vs = prow;  // the pivot-row buffer is free after the Cholesky
-  auto apply_col = [&](int j, int c, double tr_, double ti_) {
-    double dr = 0, di = 0;
-    if (p - j <= 32 * WR) {
-      cd w[WR];
-#pragma unroll
-      for (int u = 0; u < WR; ++u) {
-        const int i = j + lane + 32 * u;
-        if (i < p) w[u] = L[i + (size_t)c * p];
-      }
-#pragma unroll
-      for (int u = 0; u < WR; ++u) {
-        const int i = j + lane + 32 * u;
-        if (i < p) {
-          const cd v = vs[i];
-          dr += v.re * w[u].re + v.im * w[u].im;
-          di += v.re * w[u].im - v.im * w[u].re;
+      s = bsum_df(s);
+      const float4 alv = Lf[j + (size_t)j * p];
+      const D::df ar = D::re_of(alv), ai = D::im_of(alv);
+      D::df tr = {0.0f, 0.0f}, ti = {0.0f, 0.0f};
+      // R(j, j) (unscaled): beta of the reflection, or the entry itself when none is needed
+      double rjj = ldexp(D::djoin(ar), ex);
+      if (!(s.h == 0.0f && ai.h == 0.0f)) {
+        const D::df nrm = D::dsqrt(D::dfma(ar, ar, D::dfma(ai, ai, s)));
+        const D::df beta = ar.h >= 0.0f ? D::dneg(nrm) : nrm;
+        rjj = ldexp(D::djoin(beta), ex);
+        const D::df ib = D::drcp(beta);
+        tr = D::dmul(D::dsub(beta, ar), ib);  // tau = (beta - alpha) / beta
+        ti = D::dneg(D::dmul(ai, ib));
+        // v = x / (alpha - beta) = x conj(d) / |d|^2, d = alpha - beta
+        const D::df dr = D::dsub(ar, beta), di = ai;
+        const D::df idd = D::drcp(D::dfma(dr, dr, D::dmul(di, di)));
+        const D::df scr = D::dmul(dr, idd), sci = D::dneg(D::dmul(di, idd));
+        for (int i = j + 1 + tid; i < p; i += NT) {
+          const float4 v = Lf[i + (size_t)j * p];
+          const D::df vr = D::re_of(v), vi = D::im_of(v);
+          Lf[i + (size_t)j * p] =
+              D::pack(D::dfma(vr, scr, D::dneg(D::dmul(vi, sci))), D::dfma(vr, sci, D::dmul(vi, scr)));
         }
+      }
+      if (tid == 0) {
+        T[j + (size_t)j * r].re = D::djoin(tr);
+        T[j + (size_t)j * r].im = D::djoin(ti);
+        if (t.R) {
+          t.R[j + (size_t)j * r].re = rjj;
+          t.R[j + (size_t)j * r].im = 0;
+        }
+      }
+    };
+    // apply H_j^H to column c (one warp): w -= v conj(tau) (v^H w); up to 32 WRD
+    // entries of the column stay in registers between the two passes
+    constexpr int WRD = 12;
+    auto apply_col_df = [&](int j, int c, D::df tr, D::df ti) {
+      D::df dr = {0.0f, 0.0f}, di = {0.0f, 0.0f};
+      float4* col = Lf + (size_t)c * p;
+      if (p - j <= 32 * WRD) {
+        float4 w[WRD];
+#pragma unroll
+        for (int u = 0; u < WRD; ++u) {
+          const int i = j + lane + 32 * u;
+          if (i < p) w[u] = col[i];
+        }
+#pragma unroll
+        for (int u = 0; u < WRD; ++u) {
+          const int i = j + lane + 32 * u;
+          if (i < p) {
+            const float4 v = vsf[i];
+            dr = D::dfma(D::re_of(v), D::re_of(w[u]), dr);
+            dr = D::dfma(D::im_of(v), D::im_of(w[u]), dr);
+            di = D::dfma(D::re_of(v), D::im_of(w[u]), di);
+            di = D::dfma(D::dneg(D::im_of(v)), D::re_of(w[u]), di);
+          }
+        }
+        dr = D::wsum(dr);
+        di = D::wsum(di);
+        const D::df fr = D::dfma(tr, dr, D::dmul(ti, di)), fi = D::dfma(tr, di, D::dneg(D::dmul(ti, dr)));
+#pragma unroll
+        for (int u = 0; u < WRD; ++u) {
+          const int i = j + lane + 32 * u;
+          if (i < p) {
+            const float4 v = vsf[i];
+            const D::df vr = D::re_of(v), vi = D::im_of(v);
+            const D::df nr = D::dsub(D::re_of(w[u]), D::dfma(vr, fr, D::dneg(D::dmul(vi, fi))));
+            const D::df ni = D::dsub(D::im_of(w[u]), D::dfma(vr, fi, D::dmul(vi, fr)));
+            col[i] = D::pack(nr, ni);
+          }
+        }
+        return;
+      }
+      for (int i = j + lane; i < p; i += 32) {
+        const float4 v = vsf[i], x = col[i];
+        dr = D::dfma(D::re_of(v), D::re_of(x), dr);
+        dr = D::dfma(D::im_of(v), D::im_of(x), dr);
+        di = D::dfma(D::re_of(v), D::im_of(x), di);
+        di = D::dfma(D::dneg(D::im_of(v)), D::re_of(x), di);
+      }
+      dr = D::wsum(dr);
+      di = D::wsum(di);
+      const D::df fr = D::dfma(tr, dr, D::dmul(ti, di)), fi = D::dfma(tr, di, D::dneg(D::dmul(ti, dr)));
+      for (int i = j + lane; i < p; i += 32) {
+        const float4 v = vsf[i], x = col[i];
+        const D::df vr = D::re_of(v), vi = D::im_of(v);
+        const D::df nr = D::dsub(D::re_of(x), D::dfma(vr, fr, D::dneg(D::dmul(vi, fi))));
+        const D::df ni = D::dsub(D::im_of(x), D::dfma(vr, fi, D::dmul(vi, fr)));
+        col[i] = D::pack(nr, ni);
+      }
+    };
+    if (r > 0) {
+      if (rank == 0) reflector_df(0);
+      cluster_barrier();
+    }
+    for (int j = 0; j < r; ++j) {
+      const D::df tr = D::dsplit(T[j + (size_t)j * r].re), ti = D::dsplit(T[j + (size_t)j * r].im);
+      for (int i = j + tid; i < p; i += NT) vsf[i] = (i == j) ? make_float4(1.0f, 0.0f, 0.0f, 0.0f) : Lf[i + (size_t)j * p];
+      __syncthreads();
+      if (!(tr.h == 0.0f && ti.h == 0.0f)) {
+        int first = j + 1 + ((rank - (j + 1)) % C + C) % C;
+        for (int c = first + warp * C; c < r; c += nw * C) apply_col_df(j, c, tr, ti);
+      }
+      __syncthreads();
+      if (j + 1 < r && (j + 1) % C == rank) reflector_df(j + 1);
+      cluster_barrier();
+    }
+    // strict upper triangle of R, and W(k, c) = Y(:, k)^H Y(:, c) for k < c
+    // (Y unit lower trapezoidal: Y(c, c) = 1, Y(i, c) = 0 for i < c), by
+    // column owners, summed in double-float
+    for (int c = rank; c < r; c += C) {
+      if (t.R)
+        for (int i = tid; i < c; i += NT) {
+          const float4 v = Lf[i + (size_t)c * p];
+          t.R[i + (size_t)c * r].re = ldexp(D::djoin(D::re_of(v)), ex);
+          t.R[i + (size_t)c * r].im = ldexp(D::djoin(D::im_of(v)), ex);
+        }
+      for (int k = warp; k < c; k += nw) {
+        D::df sr = {0.0f, 0.0f}, si = {0.0f, 0.0f};
+        for (int i = c + lane; i < p; i += 32) {
+          const float4 a = Lf[i + (size_t)k * p];
+          if (i == c) {
+            sr = D::dadd(sr, D::re_of(a));
+            si = D::dsub(si, D::im_of(a));
+          } else {
+            const float4 bv = Lf[i + (size_t)c * p];
+            sr = D::dfma(D::re_of(a), D::re_of(bv), sr);
+            sr = D::dfma(D::im_of(a), D::im_of(bv), sr);
+            si = D::dfma(D::re_of(a), D::im_of(bv), si);
+            si = D::dfma(D::dneg(D::im_of(a)), D::re_of(bv), si);
+          }
+        }
+        sr = D::wsum(sr);
+        si = D::wsum(si);
+        if (lane == 0) {
+          W[k + (size_t)c * r].re = D::djoin(sr);
+          W[k + (size_t)c * r].im = D::djoin(si);
+        }
+      }
+    }
+    cluster_barrier();
+    // own columns back to complex128: Y
+    for (int c = rank; c < r; c += C)
+      for (int i = tid; i < p; i += NT) {
+        cd y;
+        if (i < c) {
+          y.re = 0;
+          y.im = 0;
+        } else if (i == c) {
+          y.re = 1;
+          y.im = 0;
+        } else {
+          const float4 v = Lf[i + (size_t)c * p];
+          y.re = D::djoin(D::re_of(v));
+          y.im = D::djoin(D::im_of(v));
+        }
+        L[i + (size_t)c * p] = y;
+      }
+  } else {
+    auto reflector = [&](int j) {
+      double s = 0;
+      for (int i = j + 1 + tid; i < p; i += NT) {
+        const cd v = L[i + (size_t)j * p];
+        s += v.re * v.re + v.im * v.im;
+      }
+      s = bsum(s, red);
+      const cd al = L[j + (size_t)j * p];
+      double tr_ = 0, ti_ = 0;
+      double rjj = al.re;  // R(j, j): beta of the reflection, or the entry itself when none is needed
+      if (!(s == 0.0 && al.im == 0.0)) {
+        const double nrm = sqrt(al.re * al.re + al.im * al.im + s);
+        const double beta = al.re >= 0 ? -nrm : nrm;
+        rjj = beta;
+        tr_ = (beta - al.re) / beta;
+        ti_ = -al.im / beta;
+        const double dr = al.re - beta, di = al.im, dd = dr * dr + di * di;
+        const double scr = dr / dd, sci = -di / dd;
+        for (int i = j + 1 + tid; i < p; i += NT) {
+          cd v = L[i + (size_t)j * p];
+          const double vr = v.re * scr - v.im * sci, vi = v.re * sci + v.im * scr;
+          v.re = vr;
+          v.im = vi;
+          L[i + (size_t)j * p] = v;
+        }
+      }
+      if (tid == 0) {
+        T[j + (size_t)j * r].re = tr_;
+        T[j + (size_t)j * r].im = ti_;
+        if (t.R) {
+          t.R[j + (size_t)j * r].re = rjj;
+          t.R[j + (size_t)j * r].im = 0;
+        }
+      }
+    };
+    // apply H_j^H to column c (one warp); vs = reflector j in shared memory
+    // (vs[j] = 1).  A column of up to 32 WR entries stays in registers between
+    // the dot product and the update, its loads all in flight together.
+    constexpr int WR = 12;
+    cd* vs = prow;  // the pivot-row buffer is free after the Cholesky
+    auto apply_col = [&](int j, int c, double tr_, double ti_) {
+      double dr = 0, di = 0;
+      if (p - j <= 32 * WR) {
+        cd w[WR];
+  #pragma unroll
+        for (int u = 0; u < WR; ++u) {
+          const int i = j + lane + 32 * u;
+          if (i < p) w[u] = L[i + (size_t)c * p];
+        }
+  #pragma unroll
+        for (int u = 0; u < WR; ++u) {
+          const int i = j + lane + 32 * u;
+          if (i < p) {
+            const cd v = vs[i];
+            dr += v.re * w[u].re + v.im * w[u].im;
+            di += v.re * w[u].im - v.im * w[u].re;
+          }
+        }
+        dr = wsum(dr);
+        di = wsum(di);
+        const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
+  #pragma unroll
+        for (int u = 0; u < WR; ++u) {
+          const int i = j + lane + 32 * u;
+          if (i < p) {
+            const cd v = vs[i];
+            w[u].re -= v.re * fr - v.im * fi;
+            w[u].im -= v.re * fi + v.im * fr;
+            L[i + (size_t)c * p] = w[u];
+          }
+        }
+        return;
+      }
+      for (int i = j + lane; i < p; i += 32) {
+        const cd w = L[i + (size_t)c * p];
+        const cd v = vs[i];
+        dr += v.re * w.re + v.im * w.im;
+        di += v.re * w.im - v.im * w.re;
       }
       dr = wsum(dr);
       di = wsum(di);
       const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
-#pragma unroll
-      for (int u = 0; u < WR; ++u) {
-        const int i = j + lane + 32 * u;
-        if (i < p) {
-          const cd v = vs[i];
-          w[u].re -= v.re * fr - v.im * fi;
-          w[u].im -= v.re * fi + v.im * fr;
-          L[i + (size_t)c * p] = w[u];
+      for (int i = j + lane; i < p; i += 32) {
+        const cd v = vs[i];
+        cd w = L[i + (size_t)c * p];
+        w.re -= v.re * fr - v.im * fi;
+        w.im -= v.re * fi + v.im * fr;
+        L[i + (size_t)c * p] = w;
+      }
+    };
+    if (r > 0) {
+      if (rank == 0) reflector(0);
+      cluster_barrier();
+    }
+    for (int j = 0; j < r; ++j) {
+      const double tr_ = T[j + (size_t)j * r].re, ti_ = T[j + (size_t)j * r].im;
+      // reflector j (written by its owner before the last cluster barrier) to shared memory
+      for (int i = j + tid; i < p; i += NT) {
+        if (i == j) {
+          vs[i].re = 1;
+          vs[i].im = 0;
+        } else {
+          vs[i] = L[i + (size_t)j * p];
         }
       }
-      return;
-    }
-    for (int i = j + lane; i < p; i += 32) {
-      const cd w = L[i + (size_t)c * p];
-      const cd v = vs[i];
-      dr += v.re * w.re + v.im * w.im;
-      di += v.re * w.im - v.im * w.re;
-    }
-    dr = wsum(dr);
-    di = wsum(di);
-    const double fr = tr_ * dr + ti_ * di, fi = tr_ * di - ti_ * dr;  // conj(tau) d
-    for (int i = j + lane; i < p; i += 32) {
-      const cd v = vs[i];
-      cd w = L[i + (size_t)c * p];
-      w.re -= v.re * fr - v.im * fi;
-      w.im -= v.re * fi + v.im * fr;
-      L[i + (size_t)c * p] = w;
-    }
-  };
-  if (r > 0) {
-    if (rank == 0) reflector(0);
-    cluster_barrier();
-  }
-  for (int j = 0; j < r; ++j) {
-    const double tr_ = T[j + (size_t)j * r].re, ti_ = T[j + (size_t)j * r].im;
-    // reflector j (written by its owner before the last cluster barrier) to shared memory
-    for (int i = j + tid; i < p; i += NT) {
-      if (i == j) {
-        vs[i].re = 1;
-        vs[i].im = 0;
-      } else {
-        vs[i] = L[i + (size_t)j * p];
+      __syncthreads();
+      if (!(tr_ == 0.0 && ti_ == 0.0)) {
+        // own columns c > j, c = rank (mod C)
+        int first = j + 1 + ((rank - (j + 1)) % C + C) % C;
+        for (int c = first + warp * C; c < r; c += nw * C) apply_col(j, c, tr_, ti_);
       }
+      __syncthreads();
+      if (j + 1 < r && (j + 1) % C == rank) reflector(j + 1);
+      cluster_barrier();
     }
-    __syncthreads();
-    if (!(tr_ == 0.0 && ti_ == 0.0)) {
-      // own columns c > j, c = rank (mod C)
-      int first = j + 1 + ((rank - (j + 1)) % C + C) % C;
-      for (int c = first + warp * C; c < r; c += nw * C) apply_col(j, c, tr_, ti_);
-    }
-    __syncthreads();
-    if (j + 1 < r && (j + 1) % C == rank) reflector(j + 1);
+    // Y: unit lower trapezoidal reflectors (upper part zeroed, v_0 = 1), own
+    // columns; the strict upper triangle of R is saved first when asked for
+    for (int c = rank; c < r; c += C)
+      for (int i = tid; i <= c && i < p; i += NT) {
+        if (t.R && i < c) t.R[i + (size_t)c * r] = L[i + (size_t)c * p];
+        L[i + (size_t)c * p].re = (i == c) ? 1 : 0;
+        L[i + (size_t)c * p].im = 0;
+      }
     cluster_barrier();
-  }
-  // Y: unit lower trapezoidal reflectors (upper part zeroed, v_0 = 1), own columns
-  for (int c = rank; c < r; c += C)
-    for (int i = tid; i <= c && i < p; i += NT) {
-      L[i + (size_t)c * p].re = (i == c) ? 1 : 0;
-      L[i + (size_t)c * p].im = 0;
-    }
-  cluster_barrier();
 
-  // ------------------------------------------------------- compact WY T
-  // W(k, j) = Y(:, k)^H Y(:, j), k < j, into the scratch (ld r), by column owners
-  cd* W = t.W;
-  for (int c = rank; c < r; c += C)
-    for (int k = warp; k < c; k += nw) {
-      double sr = 0, si = 0;
-      for (int i = c + lane; i < p; i += 32) {  // Y(i, c) = 0 for i < c
-        const cd a = L[i + (size_t)k * p], b = L[i + (size_t)c * p];
-        sr += a.re * b.re + a.im * b.im;
-        si += a.re * b.im - a.im * b.re;
+    // ------------------------------------------------------- compact WY T
+    // W(k, j) = Y(:, k)^H Y(:, j), k < j, into the scratch (ld r), by column owners
+    for (int c = rank; c < r; c += C)
+      for (int k = warp; k < c; k += nw) {
+        double sr = 0, si = 0;
+        for (int i = c + lane; i < p; i += 32) {  // Y(i, c) = 0 for i < c
+          const cd a = L[i + (size_t)k * p], b = L[i + (size_t)c * p];
+          sr += a.re * b.re + a.im * b.im;
+          si += a.re * b.im - a.im * b.re;
+        }
+        sr = wsum(sr);
+        si = wsum(si);
+        if (lane == 0) { W[k + (size_t)c * r].re = sr; W[k + (size_t)c * r].im = si; }
       }
-      sr = wsum(sr);
-      si = wsum(si);
-      if (lane == 0) { W[k + (size_t)c * r].re = sr; W[k + (size_t)c * r].im = si; }
-    }
-  cluster_barrier();
+    cluster_barrier();
+  }
   // rows of T: T(i, i) = tau_i, T(i, j) = -tau_j sum_{k=i}^{j-1} T(i, k) W(k, j);
   // one warp per own row (rows i = rank mod C), strictly lower part zeroed
   for (int i = rank + warp * C; i < r; i += nw * C) {
