@@ -299,3 +299,41 @@ def test_proxy_construction_on_gpu(dev):
     assert np.linalg.norm(Zg @ x - b) / np.linalg.norm(b) < 10 * eps
     A.close()
     B.close()
+
+
+def test_matvec_emulation_against_fp64_and_oracle(dev):
+    # the FP64 H^2 matvec with its products in double-float on the FP32 pipe
+    # (h2_opts.matvec_emulation) against FP64 FMAs and the oracle's matvec,
+    # and a refined solve whose residuals ran emulated, checked with FP64
+    from paper_1703_06155_gb300 import H2
+    eps = 1e-6
+    Hm = h2_problem(16, 64, eps)
+    A = H2.load(oracle_to_rep(Hm))
+    N = Hm.tree.N
+    x = inputs.rhs_gaussian(N, 4, 3)
+    xt = torch.from_numpy(x).to(dev)
+    A.set_opts(matvec_emulation=0)
+    y64 = A.matvec(xt).cpu().numpy()
+    A.set_opts(matvec_emulation=2, profile=1)
+    y2 = A.matvec(xt).cpu().numpy()
+    paths = A.stats()["paths"]
+    y_orc = np.stack([from_tree(Hm, oh2.matvec(Hm, to_tree(Hm, x[:, q]))) for q in range(4)], axis=1)
+    e_fp64, e_orc = rel(y2, y64), rel(y2, y_orc)
+    print("matvec emulation: vs FP64 FMAs %.2e, vs oracle %.2e (FP64 FMAs vs oracle %.2e)"
+          % (e_fp64, e_orc, rel(y64, y_orc)))
+    assert any(k.startswith("gemm:fp64_dd:") for k in paths), paths
+    assert e_fp64 <= 1e-12 and e_orc <= 1e-12
+    # refined solve to 1e-10 with emulated residuals (default 1), residual
+    # re-evaluated with FP64 FMAs
+    A.set_opts(matvec_emulation=1, profile=0)
+    A.factorize(eps, "mixed")
+    b = inputs.rhs_gaussian(N, 4, 4)
+    bt = torch.from_numpy(b).to(dev)
+    xs = A.solve(bt, refine=True, tol=1e-10, max_iter=30)
+    res_emul = A.last_solve["resid"]
+    A.set_opts(matvec_emulation=0)
+    r = A.matvec(xs).cpu().numpy() - b
+    res64 = float(np.max(np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0)))
+    print("refined solve: emulated residual %.2e, FP64 residual %.2e" % (res_emul, res64))
+    assert res_emul <= 1e-10 and res64 <= 2e-10
+    A.close()
