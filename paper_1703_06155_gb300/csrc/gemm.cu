@@ -174,12 +174,27 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmTask* __restrict__ tasks,
 // numbers is exact as p + e with p = fl(a b) and e = fma(a, b, -p).  The
 // products of one BK-long K slice are summed in double-float: hi takes p
 // through an error-free TwoSum and lo collects the TwoSum errors and the e
-// parts; the slice total hi + lo (error <= ~4 BK 2^-48 of the slice's
-// magnitude) is then added to an FP64 accumulator.  About ten FP32 operations
-// replace one FP64 FMA, on a pipe that runs 64x the FP64 rate here.  The
+// parts; the slice totals hi + lo (error <= ~4 BK 2^-48 of the slice's
+// magnitude) are summed in a double-float chunk accumulator (TwoSum, as
+// dd_acc below), which is added to an FP64 accumulator every kDfFlush
+// slices (FP64 adds run at 1/64 of the FP32 rate here: one per slice would
+// cost as much as the slice's products).  About ten FP32 operations replace
+// one FP64 FMA, on a pipe that runs 64x the FP64 rate here.  The
 // rounded operations are the _rn intrinsics, which the compiler never fuses
 // into FMAs.  (Operands below ~1e-19 in magnitude would lose the exactness of
 // their products to FP32 underflow; Gram operands are far above that.)
+constexpr int kDfFlush = 8;
+
+// (H, L) += (h, l) in double-float
+__device__ __forceinline__ void dd_acc(float& H, float& L, float h, float l) {
+  const float s = __fadd_rn(H, h);
+  const float bb = __fsub_rn(s, H);
+  const float t = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bb)), __fsub_rn(h, bb));
+  const float lo = __fadd_rn(__fadd_rn(L, l), t);
+  H = __fadd_rn(s, lo);
+  L = __fsub_rn(lo, __fsub_rn(H, s));
+}
+
 __device__ __forceinline__ void df_madd(float& h, float& l, float a, float b) {
   const float p = __fmul_rn(a, b);
   const float e = fmaf(a, b, -p);
@@ -203,10 +218,26 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tas
   const int m0 = tl.tm * BM, n0 = tl.tn * BN;
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   double acc_r[TMR][TN], acc_i[TMR][TN];
+  float Hr[TMR][TN], Lr[TMR][TN], Hi[TMR][TN], Li[TMR][TN];  // chunk accumulators
 #pragma unroll
   for (int i = 0; i < TMR; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc_r[i][j] = acc_i[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) {
+      acc_r[i][j] = acc_i[i][j] = 0.0;
+      Hr[i][j] = Lr[i][j] = Hi[i][j] = Li[i][j] = 0.f;
+    }
+  int nsl = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int i = 0; i < TMR; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        acc_r[i][j] += (double)Hr[i][j] + (double)Lr[i][j];
+        acc_i[i][j] += (double)Hi[i][j] + (double)Li[i][j];
+        Hr[i][j] = Lr[i][j] = Hi[i][j] = Li[i][j] = 0.f;
+      }
+    nsl = 0;
+  };
 
   const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
   const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
@@ -272,12 +303,14 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmTask* __restrict__ tas
       for (int i = 0; i < TMR; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          acc_r[i][j] += (double)hr[i][j] + (double)lr[i][j];
-          acc_i[i][j] += (double)hi[i][j] + (double)li[i][j];
+          dd_acc(Hr[i][j], Lr[i][j], hr[i][j], lr[i][j]);
+          dd_acc(Hi[i][j], Li[i][j], hi[i][j], li[i][j]);
         }
+      if (++nsl == kDfFlush) flush();
       __syncthreads();
     }
   }
+  flush();
   if (tk.nk > 1) {
     cd* W = ws + tk.ws_off + (int64_t)tl.kc * tk.M * tk.N;
 #pragma unroll
@@ -347,16 +380,6 @@ __device__ __forceinline__ void dd_madd(float& h, float& l, float ah, float al, 
   const float t = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   h = s;
   l = __fadd_rn(l, __fadd_rn(t, e));
-}
-
-// (H, L) += (h, l) in double-float
-__device__ __forceinline__ void dd_acc(float& H, float& L, float h, float l) {
-  const float s = __fadd_rn(H, h);
-  const float bb = __fsub_rn(s, H);
-  const float t = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bb)), __fsub_rn(h, bb));
-  const float lo = __fadd_rn(__fadd_rn(L, l), t);
-  H = __fadd_rn(s, lo);
-  L = __fsub_rn(lo, __fsub_rn(H, s));
 }
 
 __device__ __forceinline__ void dd_split(double x, float& h, float& l) {

@@ -3,22 +3,27 @@
 // the column, ties to the lowest row), followed by the explicit L^{-1} P and
 // U^{-1} that the panels, the Schur updates' operands and the solve apply.
 //
-// One CTA per task, blocked:
-//   * panels of nb columns are factorized in shared memory (pivot search by
-//     warp shuffles, one row swap, scaling, rank-1 update per column);
+// One thread-block cluster per task, blocked:
+//   * panels of nb columns are factorized in shared memory by the cluster's
+//     first CTA (pivot search by warp shuffles, one row swap, scaling, rank-1
+//     update per column);
 //   * the row swaps are then applied to the other columns, U12 = L11^{-1} A12
 //     with the inverse of the 32 x 32 diagonal block (formed in shared
-//     memory), and the trailing block is updated by a CTA-wide tiled GEMM
-//     (64 x 64 output tiles, 32-deep K slices staged in shared memory, 4 x 4
-//     complex micro-tiles);
-//   * in a second launch (two CTAs per task, concurrently) L^{-1} and U^{-1}
-//     are formed block row by block row with the same GEMM
-//     (X[I, :I] = -L[I,I]^{-1} L[I, :I] X[:I, :I]); L^{-1} P is L^{-1} with
-//     its columns permuted.
+//     memory), and the trailing block is updated, these by all CTAs of the
+//     cluster over 64-column / 64 x 64 tiles with a CTA-wide tiled GEMM
+//     (32-deep K slices staged in shared memory, 4 x 4 complex micro-tiles);
+//   * in two more launches (one CTA per task, L or U and 32-column block) the
+//     inverses of the diagonal blocks, then every column block of L^{-1} and
+//     U^{-1} by block forward / back substitution with the same GEMM;
+//     L^{-1} P is L^{-1} with its columns permuted.
 // A zero pivot sets status bit 1 and the CTA returns.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "h2_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace h2k {
 namespace {
@@ -179,199 +184,271 @@ __device__ void diag_inverse(const E* Ls, int ib, E* Ds, bool upper) {
   }
 }
 
+// cluster-wide barrier: arrive with release, wait with acquire (cluster scope)
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One thread-block cluster of C CTAs per task.  Per panel of nb columns:
+//   1. CTA 0 factorizes the panel in its shared memory (pivot search, swap,
+//      scaling, rank-1 updates) and writes it back; its pivots and a failure
+//      flag stay in its shared memory;
+//   2. after a cluster barrier every CTA reads the pivots through distributed
+//      shared memory and, for the 64-column tiles it owns (tile q belongs to
+//      CTA q mod C), applies the row swaps and forms U12 = L11^{-1} A12 (L11^{-1}
+//      computed by each CTA from the panel);
+//   3. after a cluster barrier the 64 x 64 tiles of A22 -= L21 U12 are dealt
+//      round-robin over the CTAs; a third barrier precedes the next panel.
 template <class E>
-__global__ void __launch_bounds__(NT) k_lu_blk(const LuTask* __restrict__ tasks, int nb, int maxm, int* status) {
+__global__ void __launch_bounds__(NT) k_lu_cl(const LuTask* __restrict__ tasks, int nb, int maxm, int* status) {
   using R = typename RealOf<E>::T;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
   extern __shared__ __align__(16) unsigned char smraw[];
   GemmSmem<R>& gs = *reinterpret_cast<GemmSmem<R>*>(smraw);
   E* Ls = reinterpret_cast<E*>(smraw + sizeof(GemmSmem<R>));  // NBMAX x NBMAX, ld NBMAX
   E* Ds = Ls + NBMAX * NBMAX;                                  // NBMAX x NBMAX, ld NBMAX
-  E* Pn = Ds + NBMAX * NBMAX;                                  // panel, (m - j0) x nb
-  int* perm = reinterpret_cast<int*>(Pn + (size_t)maxm * nb);  // m
-  const LuTask t = tasks[blockIdx.x];
+  E* Pn = Ds + NBMAX * NBMAX;                                  // panel, (m - j0) x nb (CTA 0)
+  int* perm = reinterpret_cast<int*>(Pn + (size_t)maxm * nb);  // m (CTA 0)
+  const LuTask t = tasks[blockIdx.x / C];
   const int m = t.m, ld = t.lda;
   __shared__ R wv[NT / 32];
   __shared__ int wi[NT / 32];
-  __shared__ int spiv[NBMAX];
+  __shared__ int spiv[NBMAX], lpiv[NBMAX];
+  __shared__ int fail;
   const int tid = threadIdx.x;
   E* A = (E*)t.A;
-  for (int i = tid; i < m; i += NT) perm[i] = i;
+  if (rank == 0) {
+    for (int i = tid; i < m; i += NT) perm[i] = i;
+    if (tid == 0) fail = 0;
+  }
   __syncthreads();
+  int* spiv0 = cl.map_shared_rank(spiv, 0);
+  int* fail0 = cl.map_shared_rank(&fail, 0);
 
-  // ------------------------------------------------------------ LU ------
   for (int j0 = 0; j0 < m; j0 += nb) {
     const int jb = min(nb, m - j0), pl = m - j0;
-    for (int idx = tid; idx < pl * jb; idx += NT) {
-      const int r = idx % pl, c = idx / pl;
-      Pn[idx] = A[(size_t)(j0 + r) + (size_t)(j0 + c) * ld];
-    }
-    __syncthreads();
-    for (int jj = 0; jj < jb; ++jj) {
-      R best = -1;
-      int bi = 0x7fffffff;
-      for (int r = jj + tid; r < pl; r += NT) {
-        const E v = Pn[r + jj * pl];
-        const R a = (R)v.re * (R)v.re + (R)v.im * (R)v.im;
-        if (a > best) { best = a; bi = r; }
+    // ------------------------------------------------ 1. panel (CTA 0)
+    if (rank == 0) {
+      for (int idx = tid; idx < pl * jb; idx += NT) {
+        const int r = idx % pl, c = idx / pl;
+        Pn[idx] = A[(size_t)(j0 + r) + (size_t)(j0 + c) * ld];
       }
-      cta_argmax<R>(best, bi, wv, wi);
-      const int pr = wi[0];
-      const R pv = wv[0];
       __syncthreads();
-      if (!(pv > (R)0)) {
-        if (tid == 0 && status) atomicMax(status, 1);
-        return;
-      }
-      if (tid == 0) {
-        spiv[jj] = pr;
-        if (pr != jj) {
-          const int x = perm[j0 + jj];
-          perm[j0 + jj] = perm[j0 + pr];
-          perm[j0 + pr] = x;
+      for (int jj = 0; jj < jb; ++jj) {
+        R best = -1;
+        int bi = 0x7fffffff;
+        for (int r = jj + tid; r < pl; r += NT) {
+          const E v = Pn[r + jj * pl];
+          const R a = (R)v.re * (R)v.re + (R)v.im * (R)v.im;
+          if (a > best) { best = a; bi = r; }
         }
-      }
-      if (pr != jj && tid < jb) {
-        const E a = Pn[jj + tid * pl];
-        Pn[jj + tid * pl] = Pn[pr + tid * pl];
-        Pn[pr + tid * pl] = a;
+        cta_argmax<R>(best, bi, wv, wi);
+        const int pr = wi[0];
+        const R pv = wv[0];
+        __syncthreads();
+        if (!(pv > (R)0)) {
+          if (tid == 0) {
+            fail = 1;
+            if (status) atomicMax(status, 1);
+          }
+          break;
+        }
+        if (tid == 0) {
+          spiv[jj] = pr;
+          if (pr != jj) {
+            const int x = perm[j0 + jj];
+            perm[j0 + jj] = perm[j0 + pr];
+            perm[j0 + pr] = x;
+          }
+        }
+        if (pr != jj && tid < jb) {
+          const E a = Pn[jj + tid * pl];
+          Pn[jj + tid * pl] = Pn[pr + tid * pl];
+          Pn[pr + tid * pl] = a;
+        }
+        __syncthreads();
+        const E d = Pn[jj + jj * pl];
+        const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
+        const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
+        for (int r = jj + 1 + tid; r < pl; r += NT) {
+          E v = Pn[r + jj * pl];
+          const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
+          v.re = vr;
+          v.im = vi;
+          Pn[r + jj * pl] = v;
+        }
+        __syncthreads();
+        const int rem = pl - jj - 1, pc = jb - jj - 1;
+        for (int idx = tid; idx < rem * pc; idx += NT) {
+          const int r = jj + 1 + idx % rem, c = jj + 1 + idx / rem;
+          E v = Pn[r + c * pl];
+          cmul_sub<E, R>(v, Pn[r + jj * pl], Pn[jj + c * pl]);
+          Pn[r + c * pl] = v;
+        }
+        __syncthreads();
       }
       __syncthreads();
-      const E d = Pn[jj + jj * pl];
-      const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
-      const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
-      for (int r = jj + 1 + tid; r < pl; r += NT) {
-        E v = Pn[r + jj * pl];
-        const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
-        v.re = vr;
-        v.im = vi;
-        Pn[r + jj * pl] = v;
-      }
-      __syncthreads();
-      const int rem = pl - jj - 1, pc = jb - jj - 1;
-      for (int idx = tid; idx < rem * pc; idx += NT) {
-        const int r = jj + 1 + idx % rem, c = jj + 1 + idx / rem;
-        E v = Pn[r + c * pl];
-        cmul_sub<E, R>(v, Pn[r + jj * pl], Pn[jj + c * pl]);
-        Pn[r + c * pl] = v;
-      }
-      __syncthreads();
+      if (!fail)
+        for (int idx = tid; idx < pl * jb; idx += NT) {
+          const int r = idx % pl, c = idx / pl;
+          A[(size_t)(j0 + r) + (size_t)(j0 + c) * ld] = Pn[idx];
+        }
     }
-    for (int idx = tid; idx < pl * jb; idx += NT) {
-      const int r = idx % pl, c = idx / pl;
-      A[(size_t)(j0 + r) + (size_t)(j0 + c) * ld] = Pn[idx];
-    }
-    // the panel's row swaps on every other column
-    for (int c = tid; c < m; c += NT) {
-      if (c >= j0 && c < j0 + jb) continue;
-      for (int q = 0; q < jb; ++q) {
-        const int pr = spiv[q];
-        if (pr == q) continue;
-        E* x = A + (size_t)c * ld;
-        const E a = x[j0 + q];
-        x[j0 + q] = x[j0 + pr];
-        x[j0 + pr] = a;
-      }
-    }
+    cluster_barrier();
+    if (*fail0) break;
+    // ----------------------- 2. swaps and U12 on the own 64-column tiles
+    if (tid < jb) lpiv[tid] = spiv0[tid];
     __syncthreads();
     const int rest = m - j0 - jb;
+    const int ntile = (m + 63) / 64;
+    for (int q = rank; q < ntile; q += C) {
+      const int c0 = q * 64, c1 = min(m, c0 + 64);
+      for (int c = c0 + tid; c < c1; c += NT) {
+        if (c >= j0 && c < j0 + jb) continue;
+        E* x = A + (size_t)c * ld;
+        for (int u = 0; u < jb; ++u) {
+          const int pr = lpiv[u];
+          if (pr == u) continue;
+          const E a = x[j0 + u];
+          x[j0 + u] = x[j0 + pr];
+          x[j0 + pr] = a;
+        }
+      }
+    }
     if (rest > 0) {
-      for (int idx = tid; idx < jb * jb; idx += NT) Ls[(idx % jb) + (idx / jb) * NBMAX] = Pn[(idx % jb) + (idx / jb) * pl];
+      for (int idx = tid; idx < jb * jb; idx += NT)
+        Ls[(idx % jb) + (idx / jb) * NBMAX] = A[(size_t)(j0 + idx % jb) + (size_t)(j0 + idx / jb) * ld];
       __syncthreads();
-      // U12 = L11^{-1} A12 (unit lower L11), in place
       diag_inverse<E, R>(Ls, jb, Ds, false);
       __syncthreads();
-      cta_gemm<E, R>(A + (size_t)j0 + (size_t)(j0 + jb) * ld, ld, Ds, NBMAX, A + (size_t)j0 + (size_t)(j0 + jb) * ld,
-                     ld, jb, rest, jb, (R)1, true, gs);
-      __syncthreads();
-      cta_gemm<E, R>(A + (size_t)(j0 + jb) + (size_t)(j0 + jb) * ld, ld, A + (size_t)(j0 + jb) + (size_t)j0 * ld, ld,
-                     A + (size_t)j0 + (size_t)(j0 + jb) * ld, ld, rest, rest, jb, (R)-1, false, gs);
-      __syncthreads();
+      // U12 = L11^{-1} A12 (unit lower L11), in place, own tiles of the
+      // columns j0 + jb .. m (the swaps above touched the same columns)
+      const int cb = j0 + jb;
+      for (int q = rank; q < ntile; q += C) {
+        const int c0 = max(q * 64, cb), c1 = min(m, q * 64 + 64);
+        if (c0 >= c1) continue;
+        cta_gemm<E, R>(A + (size_t)j0 + (size_t)c0 * ld, ld, Ds, NBMAX, A + (size_t)j0 + (size_t)c0 * ld, ld, jb,
+                       c1 - c0, jb, (R)1, true, gs);
+        __syncthreads();
+      }
     }
+    cluster_barrier();
+    // ------------------------------------ 3. A22 -= L21 U12, dealt by tiles
+    if (rest > 0) {
+      const int cb = j0 + jb;
+      const int nt = (rest + 63) / 64;
+      for (int q = rank; q < nt * nt; q += C) {
+        const int tm = q % nt, tn = q / nt;
+        const int r0 = cb + tm * 64, c0 = cb + tn * 64;
+        cta_gemm<E, R>(A + (size_t)r0 + (size_t)c0 * ld, ld, A + (size_t)r0 + (size_t)j0 * ld, ld,
+                       A + (size_t)j0 + (size_t)c0 * ld, ld, min(64, m - r0), min(64, m - c0), jb, (R)-1, false, gs);
+        __syncthreads();
+      }
+    }
+    cluster_barrier();
   }
-  for (int i = tid; i < m; i += NT) t.piv[i] = perm[i];
+  if (rank == 0 && !fail)
+    for (int i = tid; i < m; i += NT) t.piv[i] = perm[i];
+  // no CTA leaves while another may still read CTA 0's shared memory
+  cluster_barrier();
 }
 
-// L^{-1} P (even CTA of the task's pair) or U^{-1} (odd CTA) from the packed
-// LU of k_lu_blk; both run at once.
+// The explicit inverses from the packed LU of k_lu_cl, in two launches over
+// (task, L or U, 32-column block J):
+//   1. k_lu_dinv: the inverse of the diagonal block J of the unit lower L or
+//      of U, into the diagonal block of X (the L^{-1} scratch) or of U^{-1};
+//   2. k_lu_inv_cols: the rest of column block J, independently of the other
+//      blocks -- L^{-1} E_J by forward substitution over the block rows below
+//      J, X[I, J] = -D_I L[I, J0:I0] X[J0:I0, J] (D_I = L_II^{-1} from launch
+//      1); U^{-1} E_J by back substitution over the block rows above J,
+//      Y[I, J] = -D_I U[I, I1:J1] Y[I1:J1, J] (D_I = U_II^{-1}); then the
+//      columns of L^{-1} go to their permuted places in L^{-1} P.
+// Every CTA writes only its own column block (launch 2 reads the diagonal
+// blocks of the others, written by launch 1).
 template <class E>
-__global__ void __launch_bounds__(NT) k_lu_inv(const LuTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(NT) k_lu_dinv(const LuTask* __restrict__ tasks, int maxblk) {
+  using R = typename RealOf<E>::T;
+  __shared__ E Ls[NBMAX * NBMAX], Ds[NBMAX * NBMAX];
+  const LuTask t = tasks[blockIdx.x / (2 * maxblk)];
+  const int rest = blockIdx.x % (2 * maxblk);
+  const bool upper = (rest & 1) != 0;
+  const int J = rest >> 1, m = t.m, ld = t.lda;
+  const int J0 = J * NBMAX;
+  if (J0 >= m) return;
+  const int jb = min(NBMAX, m - J0);
+  const E* A = (const E*)t.A;
+  for (int idx = threadIdx.x; idx < jb * jb; idx += NT) {
+    const int r = idx % jb, c = idx / jb;
+    Ls[r + c * NBMAX] = A[(size_t)(J0 + r) + (size_t)(J0 + c) * ld];
+  }
+  __syncthreads();
+  diag_inverse<E, R>(Ls, jb, Ds, upper);
+  __syncthreads();
+  E* Y = upper ? (E*)t.Uinv : (E*)t.scratch;
+  for (int idx = threadIdx.x; idx < jb * jb; idx += NT) {
+    const int r = idx % jb, c = idx / jb;
+    Y[(size_t)(J0 + r) + (size_t)(J0 + c) * m] = Ds[r + c * NBMAX];
+  }
+}
+
+template <class E>
+__global__ void __launch_bounds__(NT) k_lu_inv_cols(const LuTask* __restrict__ tasks, int maxblk) {
   using R = typename RealOf<E>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   GemmSmem<R>& gs = *reinterpret_cast<GemmSmem<R>*>(smraw);
-  E* Ls = reinterpret_cast<E*>(smraw + sizeof(GemmSmem<R>));  // NBMAX x NBMAX, ld NBMAX
-  E* Ds = Ls + NBMAX * NBMAX;                                  // NBMAX x NBMAX, ld NBMAX
-  const LuTask t = tasks[blockIdx.x >> 1];
-  const bool lower = (blockIdx.x & 1) == 0;
-  const int m = t.m, ld = t.lda;
+  E* Ds = reinterpret_cast<E*>(smraw + sizeof(GemmSmem<R>));  // NBMAX x NBMAX, ld NBMAX
+  const LuTask t = tasks[blockIdx.x / (2 * maxblk)];
+  const int rest = blockIdx.x % (2 * maxblk);
+  const bool upper = (rest & 1) != 0;
+  const int J = rest >> 1, m = t.m, ld = t.lda;
+  const int J0 = J * NBMAX;
+  if (J0 >= m) return;
+  const int jb = min(NBMAX, m - J0), J1 = J0 + jb;
   const int tid = threadIdx.x;
   const E* A = (const E*)t.A;
-  if (lower) {
-    // ------------------------------------------------ L^{-1} (in scratch) --
-    // X[I, 0:I0] = -L[I,I]^{-1} L[I, 0:I0] X[0:I0, 0:I0]; X[I, I] = L[I,I]^{-1}
-    E* X = (E*)t.scratch;
-    for (int I0 = 0; I0 < m; I0 += NBMAX) {
+  E zero;
+  zero.re = 0;
+  zero.im = 0;
+  auto load_d = [&](const E* Y, int I0, int ib) {
+    for (int idx = tid; idx < ib * ib; idx += NT) {
+      const int r = idx % ib, c = idx / ib;
+      Ds[r + c * NBMAX] = Y[(size_t)(I0 + r) + (size_t)(I0 + c) * m];
+    }
+    __syncthreads();
+  };
+  if (!upper) {
+    E* X = (E*)t.scratch;  // L^{-1}, m x m
+    for (int idx = tid; idx < J0 * jb; idx += NT) X[(size_t)(idx % J0) + (size_t)(J0 + idx / J0) * m] = zero;
+    for (int I0 = J1; I0 < m; I0 += NBMAX) {
       const int ib = min(NBMAX, m - I0);
-      if (I0 > 0) cta_gemm<E, R>(X + I0, m, A + I0, ld, X, m, ib, I0, I0, (R)-1, true, gs);
-      for (int idx = tid; idx < ib * ib; idx += NT) {
-        const int r = idx % ib, c = idx / ib;
-        Ls[r + c * NBMAX] = A[(size_t)(I0 + r) + (size_t)(I0 + c) * ld];
-      }
+      cta_gemm<E, R>(X + I0 + (size_t)J0 * m, m, A + I0 + (size_t)J0 * ld, ld, X + J0 + (size_t)J0 * m, m, ib, jb,
+                     I0 - J0, (R)-1, true, gs);
       __syncthreads();
-      diag_inverse<E, R>(Ls, ib, Ds, false);
-      __syncthreads();
-      if (I0 > 0) cta_gemm<E, R>(X + I0, m, Ds, NBMAX, X + I0, m, ib, I0, ib, (R)1, true, gs);
-      for (int idx = tid; idx < ib * (m - I0); idx += NT) {
-        const int r = idx % ib, c = I0 + idx / ib;
-        E v;
-        if (c < I0 + ib) {
-          v = Ds[r + (c - I0) * NBMAX];
-        } else {
-          v.re = 0;
-          v.im = 0;
-        }
-        X[(size_t)(I0 + r) + (size_t)c * m] = v;
-      }
+      load_d(X, I0, ib);
+      cta_gemm<E, R>(X + I0 + (size_t)J0 * m, m, Ds, NBMAX, X + I0 + (size_t)J0 * m, m, ib, jb, ib, (R)1, true, gs);
       __syncthreads();
     }
     // L^{-1} P: column r of L^{-1} is column piv[r] of the result
     E* Lp = (E*)t.Linv;
-    for (int idx = tid; idx < m * m; idx += NT) {
-      const int i = idx % m, r = idx / m;
-      Lp[(size_t)i + (size_t)t.piv[r] * m] = X[idx];
+    for (int idx = tid; idx < m * jb; idx += NT) {
+      const int i = idx % m, r = J0 + idx / m;
+      Lp[(size_t)i + (size_t)t.piv[r] * m] = X[(size_t)i + (size_t)r * m];
     }
-    __syncthreads();
     return;
   }
-  // ------------------------------------------------ U^{-1} (odd CTA) ------
-  // Y[I, J0:m] = -U[I,I]^{-1} U[I, J0:m] Y[J0:m, J0:m]; Y[I, I] = U[I,I]^{-1}
   E* Y = (E*)t.Uinv;
-  const int nblk = (m + NBMAX - 1) / NBMAX;
-  for (int bI = nblk - 1; bI >= 0; --bI) {
-    const int I0 = bI * NBMAX, ib = min(NBMAX, m - I0), J0 = I0 + ib;
-    if (J0 < m)
-      cta_gemm<E, R>(Y + (size_t)I0 + (size_t)J0 * m, m, A + (size_t)I0 + (size_t)J0 * ld, ld,
-                     Y + (size_t)J0 + (size_t)J0 * m, m, ib, m - J0, m - J0, (R)-1, true, gs);
-    for (int idx = tid; idx < ib * ib; idx += NT) {
-      const int r = idx % ib, c = idx / ib;
-      Ls[r + c * NBMAX] = A[(size_t)(I0 + r) + (size_t)(I0 + c) * ld];
-    }
+  for (int idx = tid; idx < (m - J1) * jb; idx += NT)
+    Y[(size_t)(J1 + idx % (m - J1)) + (size_t)(J0 + idx / (m - J1)) * m] = zero;
+  for (int bI = J - 1; bI >= 0; --bI) {
+    const int I0 = bI * NBMAX, I1 = I0 + NBMAX;
+    cta_gemm<E, R>(Y + I0 + (size_t)J0 * m, m, A + I0 + (size_t)I1 * ld, ld, Y + I1 + (size_t)J0 * m, m, NBMAX, jb,
+                   J1 - I1, (R)-1, true, gs);
     __syncthreads();
-    diag_inverse<E, R>(Ls, ib, Ds, true);
-    __syncthreads();
-    if (J0 < m)
-      cta_gemm<E, R>(Y + (size_t)I0 + (size_t)J0 * m, m, Ds, NBMAX, Y + (size_t)I0 + (size_t)J0 * m, m, ib, m - J0,
-                     ib, (R)1, true, gs);
-    for (int idx = tid; idx < ib * J0; idx += NT) {
-      const int r = idx % ib, c = idx / ib;
-      E v;
-      if (c >= I0) {
-        v = Ds[r + (c - I0) * NBMAX];
-      } else {
-        v.re = 0;
-        v.im = 0;
-      }
-      Y[(size_t)(I0 + r) + (size_t)c * m] = v;
-    }
+    load_d(Y, I0, NBMAX);
+    cta_gemm<E, R>(Y + I0 + (size_t)J0 * m, m, Ds, NBMAX, Y + I0 + (size_t)J0 * m, m, NBMAX, jb, NBMAX, (R)1, true,
+                   gs);
     __syncthreads();
   }
 }
@@ -386,7 +463,7 @@ size_t lu_smem(int maxm, int nb) {
 template <class E>
 size_t lu_inv_smem() {
   using R = typename RealOf<E>::T;
-  return sizeof(GemmSmem<R>) + 2 * (size_t)NBMAX * NBMAX * sizeof(E) + 16;
+  return sizeof(GemmSmem<R>) + (size_t)NBMAX * NBMAX * sizeof(E) + 16;
 }
 
 template <class E>
@@ -397,13 +474,54 @@ cudaError_t launch_lu(const LuTask* d, int n, int maxm, int* st, cudaStream_t s)
   if (nb < 1) return cudaErrorInvalidValue;
   const size_t sm = lu_smem<E>(maxm, nb);
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
-  cudaFuncSetAttribute(k_lu_blk<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_lu_blk<E><<<n, NT, sm, s>>>(d, nb, maxm, st);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(k_lu_cl<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  // CTAs per task: about one per 64 x 64 tile of the first trailing update,
+  // at most 16, and the launch's clusters within the 152 SMs
+  const int tiles = (maxm + 63) / 64;
+  int csize = std::max(1, std::min(std::min(16, tiles * tiles), 152 / std::max(n, 1)));
+  if (csize > 8) {
+    cudaFuncSetAttribute(k_lu_cl<E>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(csize, 1, 1);
+    q.blockDim = dim3(NT, 1, 1);
+    q.dynamicSmemBytes = sm;
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = csize;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_lu_cl<E>, &q) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      csize = 8;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n * csize, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_lu_cl<E>, d, nb, maxm, st);
+  if (e != cudaSuccess) return e;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int maxblk = (maxm + NBMAX - 1) / NBMAX;
+  k_lu_dinv<E><<<2 * maxblk * n, NT, 0, s>>>(d, maxblk);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smi = lu_inv_smem<E>();
-  cudaFuncSetAttribute(k_lu_inv<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
-  k_lu_inv<E><<<2 * n, NT, smi, s>>>(d);
+  cudaFuncSetAttribute(k_lu_inv_cols<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
+  k_lu_inv_cols<E><<<2 * maxblk * n, NT, smi, s>>>(d, maxblk);
   return cudaGetLastError();
 }
 
