@@ -1,4 +1,5 @@
 // Device memory, task staging, and the FP64 device copy of the H^2 matrix.
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -101,6 +102,11 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
     cudaGetLastError();
     fail(H2_ENOMEM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
   }
+  // debugging aid: H2_POISON_ALLOC set in the environment fills every new
+  // buffer with 0xFF bytes (NaN in every floating-point type), so that a
+  // kernel reading memory nothing has written yet shows up as NaN results
+  static const bool poison = std::getenv("H2_POISON_ALLOC") != nullptr;
+  if (poison) ck(cudaMemsetAsync(p, 0xFF, want, c.stream), "poison");
   b.p = p;
   b.bytes = want;
   c.gen++;

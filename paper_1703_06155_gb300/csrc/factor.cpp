@@ -872,18 +872,26 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
   for (size_t q = 0; q < nj; ++q) {
     LevelF& F = *jobs[q].F;
     const std::vector<int>& bt = *jobs[q].bt;
-    std::set<int> inb(bt.begin(), bt.end());
-    std::map<int64_t, std::vector<int>> tg;
+    std::vector<char> inb(F.nc, 0);
+    for (int i : bt) inb[i] = 1;
+    // (target block (j, k), eliminated cluster i) for every i of the batch and
+    // j, k in its near list, grouped by target in increasing key order (the
+    // clusters of one target in batch order)
+    std::vector<std::pair<int64_t, int>> tgl;
     for (int i : bt) {
       if (F.m[i] <= 0) continue;
       for (int j : F.nbrs[i])
-        for (int k : F.nbrs[i]) tg[pkey(j, k)].push_back(i);
+        for (int k : F.nbrs[i]) tgl.emplace_back(pkey(j, k), i);
     }
+    std::stable_sort(tgl.begin(), tgl.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     const double fl0 = gs.flops;
-    for (auto& [key, cl] : tg) {
+    for (size_t g0 = 0; g0 < tgl.size();) {
+      size_t g1 = g0;
+      while (g1 < tgl.size() && tgl[g1].first == tgl[g0].first) ++g1;
+      const int64_t key = tgl[g0].first;
       const int j = (int)(key >> 32), k = (int)(uint32_t)key;
-      const int rlo = inb.count(j) ? F.m[j] : lo_of(q, j);
-      const int clo = inb.count(k) ? F.m[k] : lo_of(q, k);
+      const int rlo = inb[j] ? F.m[j] : lo_of(q, j);
+      const int clo = inb[k] ? F.m[k] : lo_of(q, k);
       const int nj_ = F.n[j], nk = F.n[k];
       char* C;
       auto it = F.near_id.find(key);
@@ -895,11 +903,13 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         F.fill_live[id] = 1;
       }
       gs.task(C + ((size_t)rlo + (size_t)clo * nj_) * es, nj_, nj_ - rlo, nk - clo, -1.0, 1.0);
-      for (int i : cl) {
+      for (size_t u = g0; u < g1; ++u) {
+        const int i = tgl[u].second;
         const int ni = F.n[i], mi = F.m[i];
         gs.pair(NB(q, j, i) + (size_t)rlo * es, nj_, OP_N, NB(q, i, k) + (size_t)clo * ni * es, ni, OP_N, mi);
       }
       gs.close();
+      g0 = g1;
     }
     jobs[q].c->stats.flops_factor += gs.flops - fl0 + f2 + f3;
   }
@@ -1049,6 +1059,7 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
     ApplyBatch ab;
     GemmBatch g;
     double fl = 0;
+    int maxrows = 0, maxkb = 0;
     for (Ctx* cp : cs) {
       Ctx& c = *cp;
       RootF& R = c.root;
@@ -1061,6 +1072,8 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
       const int k0 = pi * nb, kb = std::min(nb, n - k0);
       pt.push_back(PanelTask{Rm, Li + (size_t)pi * nb * nb * es, Ui + (size_t)pi * nb * nb * es, ipiv + k0, n, k0, k0,
                              n - k0, kb});
+      maxrows = std::max(maxrows, n - k0);
+      maxkb = std::max(maxkb, kb);
       sw.push_back(SwapTask{Rm, ipiv + k0, n, k0, kb, 0, k0, 0});
       sw.push_back(SwapTask{Rm, ipiv + k0, n, k0, kb, k0 + kb, n, 0});
       c.stats.flops_factor += 8.0 * (n - k0) * (double)kb * kb / 2;
@@ -1081,7 +1094,8 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
       lc.st.upload(lc);
       {
         ProfScope ps(lc, "root_panel", fl, prec == P64 ? "fp64" : "fp32");
-        ck(lu_panel(lc.st.ptr<PanelTask>(i0), (int)pt.size(), prec, (int*)lc.statusbuf.p, lc.stream), "root panel");
+        ck(lu_panel(lc.st.ptr<PanelTask>(i0), (int)pt.size(), prec, maxrows, maxkb, (int*)lc.statusbuf.p, lc.stream),
+           "root panel");
       }
       ck(swap_rows_batch(lc.st.ptr<SwapTask>(i1), (int)sw.size(), prec, lc.stream), "root swaps");
       lc.launches += 2;

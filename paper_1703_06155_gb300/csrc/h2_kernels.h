@@ -227,7 +227,9 @@ cudaError_t select_rank(const SelTask* d_tasks, int ntasks, cudaStream_t s);
 cudaError_t pchol_wy(const PcholTask* d_tasks, int ntasks, int maxp, int cmax, cudaStream_t s,
                      int* csize_used = nullptr);
 // one CTA per task
-cudaError_t lu_panel(const PanelTask* d_tasks, int ntasks, int prec, int* d_status,
+// maxrows / maxkb: the largest panel of the launch; launches whose largest
+// panel fits in 200 KB factorize their panels in shared memory
+cudaError_t lu_panel(const PanelTask* d_tasks, int ntasks, int prec, int maxrows, int maxkb, int* d_status,
                      cudaStream_t s);
 // the row interchanges of several panels, each on its own column range
 struct SwapTask {

@@ -421,6 +421,7 @@ __global__ void __launch_bounds__(NT) k_lu_inv_cols(const LuTask* __restrict__ t
   if (!upper) {
     E* X = (E*)t.scratch;  // L^{-1}, m x m
     for (int idx = tid; idx < J0 * jb; idx += NT) X[(size_t)(idx % J0) + (size_t)(J0 + idx / J0) * m] = zero;
+    __syncthreads();
     for (int I0 = J1; I0 < m; I0 += NBMAX) {
       const int ib = min(NBMAX, m - I0);
       cta_gemm<E, R>(X + I0 + (size_t)J0 * m, m, A + I0 + (size_t)J0 * ld, ld, X + J0 + (size_t)J0 * m, m, ib, jb,
@@ -430,7 +431,9 @@ __global__ void __launch_bounds__(NT) k_lu_inv_cols(const LuTask* __restrict__ t
       cta_gemm<E, R>(X + I0 + (size_t)J0 * m, m, Ds, NBMAX, X + I0 + (size_t)J0 * m, m, ib, jb, ib, (R)1, true, gs);
       __syncthreads();
     }
-    // L^{-1} P: column r of L^{-1} is column piv[r] of the result
+    // L^{-1} P: column r of L^{-1} is column piv[r] of the result (every
+    // thread's rows of the block, zeroed or computed, are written by now)
+    __syncthreads();
     E* Lp = (E*)t.Linv;
     for (int idx = tid; idx < m * jb; idx += NT) {
       const int i = idx % m, r = J0 + idx / m;
@@ -441,6 +444,7 @@ __global__ void __launch_bounds__(NT) k_lu_inv_cols(const LuTask* __restrict__ t
   E* Y = (E*)t.Uinv;
   for (int idx = tid; idx < (m - J1) * jb; idx += NT)
     Y[(size_t)(J1 + idx % (m - J1)) + (size_t)(J0 + idx / (m - J1)) * m] = zero;
+  __syncthreads();
   for (int bI = J - 1; bI >= 0; --bI) {
     const int I0 = bI * NBMAX, I1 = I0 + NBMAX;
     cta_gemm<E, R>(Y + I0 + (size_t)J0 * m, m, A + I0 + (size_t)I1 * ld, ld, Y + I1 + (size_t)J0 * m, m, NBMAX, jb,

@@ -147,7 +147,10 @@ __global__ void __launch_bounds__(NT, 1) k_osj_cl(const EigTask* __restrict__ ta
     }
   cluster_barrier();
 
-  const int T = max(1, NW / b);  // warps per team (one team per pair of a round)
+  // warps per team (one team per pair of a round): one warp unless the
+  // columns are long enough to give every lane of a larger team >= 4 entries
+  // (each warp of a team repeats the pair's reductions and parameters)
+  const int T = max(1, min(NW / b, r / 128));
   const int team = warp / T, wt = warp % T;
   int sweep = 0;
   bool done = false;
@@ -224,17 +227,22 @@ __global__ void __launch_bounds__(NT, 1) k_osj_cl(const EigTask* __restrict__ ta
           }
           gr = wsum(gr);
           gi = wsum(gi);
-          if (lane == 0) s_part[warp] = pack(gr, gi);
+          if (T > 1 && lane == 0) s_part[warp] = pack(gr, gi);
         }
-        __syncthreads();
-        if (act) {
-          gr = {0.0f, 0.0f};
-          gi = {0.0f, 0.0f};
-          for (int w = 0; w < T; ++w) {
-            const float4 v = s_part[team * T + w];
-            gr = dadd(gr, re_of(v));
-            gi = dadd(gi, im_of(v));
+        if (T > 1) {
+          // the team's warps combine their partial sums
+          __syncthreads();
+          if (act) {
+            gr = {0.0f, 0.0f};
+            gi = {0.0f, 0.0f};
+            for (int w = 0; w < T; ++w) {
+              const float4 v = s_part[team * T + w];
+              gr = dadd(gr, re_of(v));
+              gi = dadd(gi, im_of(v));
+            }
           }
+        }
+        if (act) {
           const float gf = hypotf(gr.h, gi.h);
           // entries below 1e-30 of the scaled matrix (max |R| ~ 1) are never
           // rotated: far below any truncation threshold, and keeps the
@@ -353,9 +361,10 @@ int64_t osj_cluster_scratch(int maxp) {
 }
 
 int osj_cluster_size(int ntasks, int maxp, int cmax) {
-  // about 8 columns per CTA pair of blocks, at most 16 CTAs, and the launch's
-  // clusters within the 152 SMs when the problems are many
-  int c = std::min(std::min(16, std::max(cmax, 1)), std::max(1, (maxp + 7) / 8));
+  // blocks of about 8 columns (8 pairs per round, two warps per SM
+  // sub-partition), at most 16 CTAs, and the launch's clusters within the 152
+  // SMs when the problems are many
+  int c = std::min(std::min(16, std::max(cmax, 1)), std::max(1, (maxp + 15) / 16));
   if (ntasks > 0) c = std::min(c, std::max(1, 152 / ntasks));
   while (c < 16 && smem_bytes(maxp, c) > kSmemMax) ++c;
   return c;

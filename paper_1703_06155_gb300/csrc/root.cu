@@ -6,6 +6,7 @@ namespace h2k {
 namespace {
 
 constexpr int NT = 256;
+constexpr size_t kPanelSmem = 200 * 1024;  // largest panel copied to shared memory
 
 template <class E> struct RealOf;
 template <> struct RealOf<cd> { using T = double; };
@@ -29,40 +30,58 @@ __global__ void __launch_bounds__(NT) k_select(const SelTask* __restrict__ tasks
   if (threadIdx.x == 0) *t.out = cnt[0];
 }
 
+// largest |z|^2 of the CTA, ties to the lowest row; result to every thread
+template <class R>
+__device__ void panel_argmax(R& v, int& i, R* wv, int* wi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const R ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { wv[threadIdx.x >> 5] = v; wi[threadIdx.x >> 5] = i; }
+  __syncthreads();
+  v = wv[0];
+  i = wi[0];
+  for (int w = 1; w < NT / 32; ++w)
+    if (wv[w] > v || (wv[w] == v && wi[w] < i)) { v = wv[w]; i = wi[w]; }
+  __syncthreads();
+}
+
+// One tall panel (nrows x kb) per CTA: pivot search, row swap, scaling and
+// rank-1 update column by column, then the inverses of its unit lower and
+// upper kb x kb triangles.  The panel is copied to shared memory when the
+// launch provides room for it (dynamic shared memory >= nrows x kb entries),
+// else it is worked on in place.
 template <class E>
-__global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ tasks, int* status) {
+__global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ tasks, int* status, int in_smem) {
   using R = typename RealOf<E>::T;
-  __shared__ R redv[NT];
-  __shared__ int redi[NT];
+  __shared__ R wv[NT / 32];
+  __shared__ int wi[NT / 32];
+  extern __shared__ __align__(16) unsigned char psm[];
   const PanelTask t = tasks[blockIdx.x];
-  E* A = (E*)t.A;
-  const int ld = t.lda, kb = t.kb;
-  auto at = [&](int r, int c) -> E& { return A[(size_t)(t.row0 + r) + (size_t)(t.col0 + c) * ld]; };
+  E* G = (E*)t.A + (size_t)t.row0 + (size_t)t.col0 * t.lda;
+  const int kb = t.kb, nr = t.nrows;
+  E* P = in_smem ? reinterpret_cast<E*>(psm) : G;
+  const int ldp = in_smem ? nr : t.lda;
+  if (in_smem) {
+    for (int idx = threadIdx.x; idx < nr * kb; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      P[idx] = G[(size_t)r + (size_t)c * t.lda];
+    }
+    __syncthreads();
+  }
+  auto at = [&](int r, int c) -> E& { return P[(size_t)r + (size_t)c * ldp]; };
   for (int j = 0; j < kb; ++j) {
     R best = -1;
-    int bi = t.nrows;
-    for (int i = j + threadIdx.x; i < t.nrows; i += NT) {
+    int bi = nr;
+    for (int i = j + threadIdx.x; i < nr; i += NT) {
       const E v = at(i, j);
       const R a = (R)v.re * (R)v.re + (R)v.im * (R)v.im;
       if (a > best || (a == best && i < bi)) { best = a; bi = i; }
     }
-    redv[threadIdx.x] = best;
-    redi[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        const R o = redv[threadIdx.x + s];
-        const int oi = redi[threadIdx.x + s];
-        if (o > redv[threadIdx.x] || (o == redv[threadIdx.x] && oi < redi[threadIdx.x])) {
-          redv[threadIdx.x] = o;
-          redi[threadIdx.x] = oi;
-        }
-      }
-      __syncthreads();
-    }
-    const int pr = redi[0];
-    const R pv = redv[0];
-    __syncthreads();
+    panel_argmax<R>(best, bi, wv, wi);
+    const int pr = bi;
+    const R pv = best;
     if (!(pv > (R)0)) {
       if (threadIdx.x == 0 && status) atomicMax(status, 1);
       return;
@@ -78,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ t
     const E d = at(j, j);
     const R dd = (R)d.re * (R)d.re + (R)d.im * (R)d.im;
     const R ir = (R)d.re / dd, ii = -(R)d.im / dd;
-    for (int i = j + 1 + threadIdx.x; i < t.nrows; i += NT) {
+    for (int i = j + 1 + threadIdx.x; i < nr; i += NT) {
       E v = at(i, j);
       const R vr = (R)v.re * ir - (R)v.im * ii, vi = (R)v.re * ii + (R)v.im * ir;
       v.re = vr;
@@ -86,7 +105,7 @@ __global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ t
       at(i, j) = v;
     }
     __syncthreads();
-    const int rem_r = t.nrows - j - 1, rem_c = kb - j - 1;
+    const int rem_r = nr - j - 1, rem_c = kb - j - 1;
     for (int idx = threadIdx.x; idx < rem_r * rem_c; idx += NT) {
       const int i = j + 1 + idx % rem_r, c = j + 1 + idx / rem_r;
       const E l = at(i, j), u = at(j, c);
@@ -97,6 +116,11 @@ __global__ void __launch_bounds__(NT) k_lu_panel(const PanelTask* __restrict__ t
     }
     __syncthreads();
   }
+  if (in_smem)
+    for (int idx = threadIdx.x; idx < nr * kb; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      G[(size_t)r + (size_t)c * t.lda] = P[idx];
+    }
   // (unit lower L11)^{-1}
   E* X = (E*)t.Linv;
   for (int idx = threadIdx.x; idx < kb * kb; idx += NT) {
@@ -199,10 +223,22 @@ cudaError_t select_rank(const SelTask* d, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t lu_panel(const PanelTask* d, int n, int prec, int* st, cudaStream_t s) {
+cudaError_t lu_panel(const PanelTask* d, int n, int prec, int maxrows, int maxkb, int* st, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (prec == P64) k_lu_panel<cd><<<n, NT, 0, s>>>(d, st);
-  else k_lu_panel<cf><<<n, NT, 0, s>>>(d, st);
+  const size_t es = prec == P64 ? sizeof(cd) : sizeof(cf);
+  const size_t need = (size_t)maxrows * maxkb * es;
+  const int in_smem = need <= kPanelSmem ? 1 : 0;
+  const size_t dyn = in_smem ? need : 0;
+  cudaError_t e = cudaSuccess;
+  if (prec == P64) {
+    if (dyn) e = cudaFuncSetAttribute(k_lu_panel<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    k_lu_panel<cd><<<n, NT, dyn, s>>>(d, st, in_smem);
+  } else {
+    if (dyn) e = cudaFuncSetAttribute(k_lu_panel<cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    k_lu_panel<cf><<<n, NT, dyn, s>>>(d, st, in_smem);
+  }
   return cudaGetLastError();
 }
 

@@ -298,3 +298,29 @@ def test_degenerate_sizes_solve(dev, N):
     xm = A.solve(torch.from_numpy(b).to(dev), refine=True, tol=1e-12, max_iter=30).cpu().numpy()
     assert rel(xm, xe) < 1e-6
     A.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_refactorization_is_bitwise_repeatable(dev, prec):
+    # the factorization has no order-dependent arithmetic (no atomics on
+    # values, fixed split-K reduction order): refactorizing one context, and
+    # factorizing a fresh one, must reproduce the solution bit for bit.  The
+    # scratch and factor arenas of a context are reused, so a kernel that read
+    # memory before writing it, or a missing barrier, would show up here as
+    # occasional differences
+    eps = 1e-6
+    H = h2_problem(16, 64, eps)
+    b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 2, 29)).to(dev)
+    A = gpu_ctx(H)
+    xs = []
+    for _ in range(8):
+        A.factorize(eps, prec)
+        xs.append(A.solve(b).cpu().numpy())
+    B = gpu_ctx(H)
+    B.factorize(eps, prec)
+    xs.append(B.solve(b).cpu().numpy())
+    diffs = [float(np.abs(x - xs[0]).max()) for x in xs[1:]]
+    print("%s refactorizations: largest difference to the first %s" % (prec, diffs))
+    assert max(diffs) == 0.0
+    A.close()
+    B.close()
