@@ -529,9 +529,9 @@ cudaError_t set_diag(void* A, int lda, int n, int prec, double v, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t copy2d(const CopyTask* d, int n, cudaStream_t s) {
+cudaError_t copy2d(const CopyTask* d, int n, cudaStream_t s, int ctas_per_task) {
   if (n <= 0) return cudaSuccess;
-  k_copy2d<<<dim3(n, 4), NT, 0, s>>>(d);
+  k_copy2d<<<dim3(n, std::max(1, std::min(32, ctas_per_task))), NT, 0, s>>>(d);
   return cudaGetLastError();
 }
 

@@ -141,13 +141,17 @@ void run_copy(Ctx& c, CopyBatch& b, const char* what) {
   HostScope hs(c, "run_copy");
   const int i0 = c.st.add(b.t);
   c.st.upload(c);
-  double bytes = 0;
+  double bytes = 0, elems = 0;
   for (const CopyTask& t : b.t) {
     const double n = (double)t.rows * t.cols, ns = (double)std::min(t.rows, t.srows) * std::min(t.cols, t.scols);
     bytes += n * esz(t.dst_prec) * (t.mode == 1 ? 2 : 1) + (t.src ? ns * esz(t.src_prec) : 0.0);
+    elems += n;
   }
+  // CTAs per task for about 8K entries each: large blocks get enough CTAs
+  // to keep many HBM requests in flight
+  const int per = (int)std::min(32.0, std::max(1.0, std::ceil(elems / (double)b.t.size() / 8192.0)));
   ProfScope ps(c, std::string("copy:") + what, 0.0, nullptr, bytes);
-  ck(copy2d(c.st.ptr<CopyTask>(i0), (int)b.t.size(), c.stream), what);
+  ck(copy2d(c.st.ptr<CopyTask>(i0), (int)b.t.size(), c.stream, per), what);
   c.launches++;
 }
 

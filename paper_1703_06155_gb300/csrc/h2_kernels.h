@@ -190,7 +190,8 @@ cudaError_t apply_right(const ApplyTask* d_tasks, const ApplyTile* d_tiles,
                         int ntiles, int prec, int maxp, int th, cudaStream_t s);
 int apply_tile_width(int prec, int maxp);
 
-cudaError_t copy2d(const CopyTask* d_tasks, int ntasks, cudaStream_t s);
+// ctas_per_task CTAs (1..32) share each task's columns
+cudaError_t copy2d(const CopyTask* d_tasks, int ntasks, cudaStream_t s, int ctas_per_task = 4);
 
 cudaError_t householder_complement(const HhTask* d_tasks, int ntasks,
                                    cudaStream_t s);

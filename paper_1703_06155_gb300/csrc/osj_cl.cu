@@ -51,6 +51,9 @@ constexpr int NT = 512;
 constexpr int NW = NT / 32;
 constexpr int kMaxSweeps = 40;
 constexpr int kMaxB = 16;  // columns per block
+#ifndef OSJ_TDIV
+#define OSJ_TDIV 128  // column entries per warp of a pair's team, at least
+#endif
 constexpr size_t kSmemMax = 225 * 1024;
 
 __device__ __forceinline__ void cluster_barrier() {
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(NT, 1) k_osj_cl(const EigTask* __restrict__ ta
   // warps per team (one team per pair of a round): one warp unless the
   // columns are long enough to give every lane of a larger team >= 4 entries
   // (each warp of a team repeats the pair's reductions and parameters)
-  const int T = max(1, min(NW / b, r / 128));
+  const int T = max(1, min(NW / b, r / OSJ_TDIV));
   const int team = warp / T, wt = warp % T;
   int sweep = 0;
   bool done = false;
