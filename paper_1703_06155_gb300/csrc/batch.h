@@ -40,7 +40,10 @@ struct GemmBatch {
   int pina = -1;         // precision of the A operands if it differs from B's
   // fp64: FP64-accumulating launch (the FP64 pipe bounds it, so padding is
   // what costs); FP32 launches keep 64-wide tiles unless padding dominates
-  int64_t plan(int target_ctas = 8 * 152, bool fp64 = true, int policy = 0, bool narrow_ok = true) {
+  // narrow_ok: the 64 x 8 / 64 x 4 shapes may be used; wide_ok: the 64 x 128
+  // shape (tcgen05 tiles of complex64 products only) may be used
+  int64_t plan(int target_ctas = 8 * 152, bool fp64 = true, int policy = 0, bool narrow_ok = true,
+               bool wide_ok = false) {
     tl.clear();
     alg_flops = 0;
     std::vector<int64_t> kt(t.size(), 0);
@@ -55,15 +58,16 @@ struct GemmBatch {
     // arithmetic intensity; Hermitian outputs need square tiles
     bool anyherm = false;
     for (auto& g : t) anyherm |= g.herm != 0;
-    static const double pen64[7] = {1.0, 1.08, 1.15, 1.3, 1.3, 1.2, 1.3},
-                        pen32[7] = {1.0, 1.6, 2.2, 3.5, 5.0, 2.5, 3.0};
+    static const double pen64[8] = {1.0, 1.08, 1.15, 1.3, 1.3, 1.2, 1.3, 1.0},
+                        pen32[8] = {1.0, 1.6, 2.2, 3.5, 5.0, 2.5, 3.0, 0.8};
     const double* penalty = fp64 ? pen64 : pen32;
     double best = -1;
     bool narrow = !anyherm;
     for (auto& g : t) narrow = narrow && g.N <= 16;
-    for (int sh = 0; sh < 7; ++sh) {
+    for (int sh = 0; sh < 8; ++sh) {
       if (anyherm && (sh == 1 || sh == 3 || sh >= 5)) continue;
-      if (sh >= 5 && !narrow_ok) continue;
+      if ((sh == 5 || sh == 6) && !narrow_ok) continue;
+      if (sh == 7 && !wide_ok) continue;
       if (policy == 1 && sh != (narrow ? 1 : 0)) continue;
       const int bm = h2k::gemm_tile_m(sh), bn = h2k::gemm_tile_n(sh);
       double w = 0;

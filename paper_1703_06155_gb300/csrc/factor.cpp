@@ -44,14 +44,15 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   const int emul = (c.opts.gram_emulation && pa == P32 && pin == P32 && pacc == P64 && pout == P64) ? 1
                    : (c.mv_emul && pa == P64 && pin == P64 && pacc == P64 && pout == P64)   ? 2
                                                                                             : 0;
+  const bool all32 = pa == P32 && pin == P32 && pacc == P32 && pout == P32;
   const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 8 * 152, pacc == P64, c.opts.tile_policy,
-                            !emul);
+                            !emul, all32 && c.opts.tensor_cores == 2);
   if (b.tl.empty()) return;
   void* wsp = nullptr;
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
   c.st.upload(c);
-  const int tc = (b.shape == 0 && pa == P32 && pin == P32 && pacc == P32 && pout == P32) ? c.opts.tensor_cores : 0;
+  const int tc = ((b.shape == 0 || b.shape == 7) && all32) ? c.opts.tensor_cores : 0;
   const char* pipe = emul == 1      ? "fp32_df"
                      : emul == 2    ? "fp64_dd"
                      : pacc == P64  ? "fp64"

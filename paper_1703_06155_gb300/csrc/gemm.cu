@@ -729,14 +729,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t a, uint32_t lbo) {
   return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) | ((uint64_t)(128 >> 4) << 32) |
          (1ull << 46);
 }
-// instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 K-major, M = 128, N = 64
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 K-major, M = 128, N = BN
+template <int BN>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
+template <int BN>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc<BN>()), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -768,17 +772,18 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ float tf(float x) { return __uint_as_float(to_tf32(x)); }
 
-template <int BKC, int S>
+template <int BKC, int S, int BN>
 struct Cfg {
   static constexpr int KC = BKC / 2;  // 16-byte K groups (2 complex) per operand row
-  static constexpr int LBO_A = 16 * 128 + 16, LBO_B = 8 * 128 + 16;
+  static constexpr int LBO_A = 16 * 128 + 16, LBO_B = (BN / 8) * 128 + 16;
   static constexpr int PLANE_A = KC * LBO_A, PLANE_B = KC * LBO_B;
   static constexpr int STAGE = 2 * PLANE_A + 2 * PLANE_B;  // A hi, A lo, B hi, B lo
-  static constexpr int DLD = 65;                           // epilogue staging row stride (floats)
+  static constexpr int DLD = BN + 1;                       // epilogue staging row stride (floats)
   static constexpr int BODY = S * STAGE > 128 * DLD * 4 ? S * STAGE : 128 * DLD * 4;
   static constexpr int SMEM = BODY + 1024;                 // + alignment slack
-  static constexpr int NI = 64 * KC / NT;                  // A (and B) items per thread and chunk
-  static_assert(BKC % 4 == 0 && NI >= 1 && 64 * KC % NT == 0, "chunk shape");
+  static constexpr int NI = 64 * KC / NT;                  // A items per thread and chunk
+  static constexpr int NIB = BN * KC / NT;                 // B items per thread and chunk
+  static_assert(BKC % 4 == 0 && NI >= 1 && 64 * KC % NT == 0 && BN * KC % NT == 0, "chunk shape");
 };
 
 // position in the concatenated K range of a tile's pairs, with the current
@@ -792,12 +797,13 @@ struct Cursor {
 };
 }  // namespace umma
 
-template <int BKC, int S>
-__global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict__ tasks,
-                                                 const GemmPair* __restrict__ pairs,
-                                                 const GemmTile* __restrict__ tiles, cf* __restrict__ ws) {
-  using C_ = umma::Cfg<BKC, S>;
-  constexpr int KC = C_::KC, NI = C_::NI;
+template <int BKC, int S, int BN>
+__global__ void __launch_bounds__(NT, BN == 64 ? 4 : 3) k_gemm_umma(const GemmTask* __restrict__ tasks,
+                                                                const GemmPair* __restrict__ pairs,
+                                                                const GemmTile* __restrict__ tiles,
+                                                                cf* __restrict__ ws) {
+  using C_ = umma::Cfg<BKC, S, BN>;
+  constexpr int KC = C_::KC, NI = C_::NI, NIB = C_::NIB;
   extern __shared__ unsigned char smraw[];
   __shared__ uint64_t bars[S];
   __shared__ uint32_t tslot;
@@ -805,7 +811,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   const GemmTile tl = tiles[blockIdx.x];
   const GemmTask tk = tasks[tl.task];
-  const int m0 = tl.tm * 64, n0 = tl.tn * 64;
+  const int m0 = tl.tm * 64, n0 = tl.tn * BN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t klo = tk.nk > 1 ? (int64_t)tl.kc * tk.ksz : 0;
   const int64_t khi = tk.nk > 1 ? klo + tk.ksz : ((int64_t)1 << 62);
@@ -837,7 +843,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
   // each, as loaded (no operation on the values, so the loads stay in flight
   // until the chunk is staged); out-of-range elements are read from a clamped
   // in-range address and zeroed at staging (validity bits am / bm)
-  float4 ra[NI], rb[NI];
+  float4 ra[NI], rb[NIB];
   unsigned am = 0, bm = 0;
   auto elem = [](const cf* X, int ld, bool tr, int r, int k) -> const cf& {
     return tr ? X[(size_t)k + (size_t)r * ld] : X[(size_t)r + (size_t)k * ld];
@@ -857,9 +863,9 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
       ra[r] = make_float4(x0.re, x0.im, x1.re, x1.im);
     }
 #pragma unroll
-    for (int r = 0; r < NI; ++r) {
+    for (int r = 0; r < NIB; ++r) {
       const int it = tid + r * NT;
-      const int n = bt ? (it & 63) : it / KC, kp = bt ? (it >> 6) : it % KC;
+      const int n = bt ? (it & (BN - 1)) : it / KC, kp = bt ? (it / BN) : it % KC;
       const int k = c.k0 + 2 * kp;
       const bool vn = n0 + n < tk.N, v0 = vn && k < c.kend, v1 = vn && k + 1 < c.kend;
       bm |= (v0 ? 1u : 0u) << (2 * r) | (v1 ? 1u : 0u) << (2 * r + 1);
@@ -890,9 +896,9 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
       *(float4*)(st + C_::PLANE_A + o1) = make_float4(l.y, l.x, l.w, l.z);
     }
 #pragma unroll
-    for (int r = 0; r < NI; ++r) {
+    for (int r = 0; r < NIB; ++r) {
       const int it = tid + r * NT;
-      const int n = bt ? (it & 63) : it / KC, kp = bt ? (it >> 6) : it % KC;
+      const int n = bt ? (it & (BN - 1)) : it / KC, kp = bt ? (it / BN) : it % KC;
       const bool v0 = (bm >> (2 * r)) & 1u, v1 = (bm >> (2 * r + 1)) & 1u;
       const float4 v = make_float4(v0 ? rb[r].x : 0.f, v0 ? sb * rb[r].y : 0.f, v1 ? rb[r].z : 0.f,
                                    v1 ? sb * rb[r].w : 0.f);
@@ -926,7 +932,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
 
   umma::Cursor cur{tk.p0 - 1, 0, 0, 0, nullptr, nullptr, 0, 0, 0, 0};
   if (!advance(cur)) {  // no K overlaps this tile: C = beta C (zero partial)
-    for (int e = tid; e < 64 * 64; e += NT) {
+    for (int e = tid; e < 64 * BN; e += NT) {
       const int m = m0 + (e & 63), n = n0 + (e >> 6);
       if (m < tk.M && n < tk.N) emit(m, n, 0.f, 0.f);
     }
@@ -934,7 +940,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::saddr(&tslot)),
-                 "r"(64));
+                 "r"(BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -967,9 +973,9 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
         const uint64_t al = umma::sdesc(a + C_::PLANE_A + 2 * ks * C_::LBO_A, C_::LBO_A);
         const uint64_t bh = umma::sdesc(bb + 2 * ks * C_::LBO_B, C_::LBO_B);
         const uint64_t bl = umma::sdesc(bb + C_::PLANE_B + 2 * ks * C_::LBO_B, C_::LBO_B);
-        umma::mma(tmem, al, bh, (c > 0 || ks > 0) ? 1u : 0u);
-        umma::mma(tmem, ah, bl, 1u);
-        umma::mma(tmem, ah, bh, 1u);
+        umma::mma<BN>(tmem, al, bh, (c > 0 || ks > 0) ? 1u : 0u);
+        umma::mma<BN>(tmem, ah, bl, 1u);
+        umma::mma<BN>(tmem, ah, bh, 1u);
       }
       umma::commit(umma::saddr(&bars[s]));
     }
@@ -986,7 +992,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
   __syncthreads();
   // C values of the beta term: all loads in flight together (rather than one
   // load-store round trip per element), overlapping the TMEM read-out
-  constexpr int EPT = 64 * 64 / NT;
+  constexpr int EPT = 64 * BN / NT;
   const bool useold = tk.nk <= 1 && tk.beta != 0.0;
   cf cold[EPT];
   if (useold) {
@@ -997,11 +1003,13 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
     }
   }
   const bool ok = fail == 0;
-  float* Ds = (float*)sm;  // 128 x 64 accumulator, row stride DLD
+  float* Ds = (float*)sm;  // 128 x BN accumulator, row stride DLD
   if (ok) {
-    const int row = 32 * (warp & 3) + lane, cb = 32 * (warp >> 2);
+    // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its sub-partition's), columns
+    // of half w / 4 of the tile
+    const int row = 32 * (warp & 3) + lane, cb = (BN / 2) * (warp >> 2);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < BN / 16; ++h) {
       uint32_t v[8];
       const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cb + 8 * h);
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -1016,7 +1024,7 @@ __global__ void __launch_bounds__(NT, 4) k_gemm_umma(const GemmTask* __restrict_
   }
   umma::fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
   for (int i = 0; i < EPT; ++i) {
@@ -1091,7 +1099,9 @@ __global__ void k_gemm_mirror(const GemmTask* __restrict__ tasks, int bm) {
 // shapes 0 64x64, 1 64x16, 2 32x32, 3 32x16, 4 16x16, 5 64x8, 6 64x4 (the
 // narrow ones for products with a few right-hand sides; plain FP tiles only)
 int gemm_tile_m(int shape) { return shape == 4 ? 16 : (shape == 2 || shape == 3) ? 32 : 64; }
-int gemm_tile_n(int shape) { return shape == 0 ? 64 : shape == 2 ? 32 : shape == 5 ? 8 : shape == 6 ? 4 : 16; }
+int gemm_tile_n(int shape) {
+  return shape == 0 ? 64 : shape == 2 ? 32 : shape == 5 ? 8 : shape == 6 ? 4 : shape == 7 ? 128 : 16;
+}
 
 template <int BM, int BN>
 static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
@@ -1124,17 +1134,17 @@ static cudaError_t gemm_tile(const GemmTask* d_tasks, const GemmPair* d_pairs, c
 #define UMMA_S 2
 #endif
 
-template <int BKC, int S>
+template <int BKC, int S, int BN>
 static cudaError_t gemm_umma(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTile* d_tiles, int ntiles,
                              cf* ws, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_gemm_umma<BKC, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               umma::Cfg<BKC, S>::SMEM);
+    const cudaError_t e = cudaFuncSetAttribute(k_gemm_umma<BKC, S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               umma::Cfg<BKC, S, BN>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gemm_umma<BKC, S><<<ntiles, NT, umma::Cfg<BKC, S>::SMEM, s>>>(d_tasks, d_pairs, d_tiles, ws);
+  k_gemm_umma<BKC, S, BN><<<ntiles, NT, umma::Cfg<BKC, S, BN>::SMEM, s>>>(d_tasks, d_pairs, d_tiles, ws);
   return cudaGetLastError();
 }
 
@@ -1148,8 +1158,12 @@ cudaError_t gemm(const GemmTask* d_tasks, const GemmPair* d_pairs, const GemmTil
                  int pout, int pacc, void* ws, cudaStream_t s, int shape, int pina, int tensor, int emul) {
   if (ntiles <= 0) return cudaSuccess;
   if (pina < 0) pina = pin;
+  if (shape == 7) {  // 64 x 128: tcgen05 tiles of complex64 products only
+    if (tensor != 2 || pina != P32 || pin != P32 || pacc != P32 || pout != P32) return cudaErrorInvalidValue;
+    return gemm_umma<UMMA_BKC, UMMA_S, 128>(d_tasks, d_pairs, d_tiles, ntiles, (cf*)ws, s);
+  }
   if (tensor && shape == 0 && pina == P32 && pin == P32 && pacc == P32 && pout == P32) {
-    if (tensor == 2) return gemm_umma<UMMA_BKC, UMMA_S>(d_tasks, d_pairs, d_tiles, ntiles, (cf*)ws, s);
+    if (tensor == 2) return gemm_umma<UMMA_BKC, UMMA_S, 64>(d_tasks, d_pairs, d_tiles, ntiles, (cf*)ws, s);
     k_gemm_tc<<<ntiles, NT, 0, s>>>(d_tasks, d_pairs, d_tiles, (cf*)ws);
     return cudaGetLastError();
   }

@@ -159,7 +159,8 @@ struct KGramTile { int task, tm, tn; };
 // split-K: tasks with nk > 1 write partial tiles to `ws` (accumulator
 // precision), then gemm_reduce sums them in a fixed order into C.
 // shape: output tile 0 = 64 x 64, 1 = 64 x 16, 2 = 32 x 32, 3 = 32 x 16, 4 = 16 x 16,
-// 5 = 64 x 8, 6 = 64 x 4 (5 and 6 not with emul)
+// 5 = 64 x 8, 6 = 64 x 4 (5 and 6 not with emul), 7 = 64 x 128 (tensor = 2
+// complex64 products only)
 // (gemm_tile_m / gemm_tile_n).  pina >= 0: precision of the A operands when
 // it differs from B's (pin); supported: A complex128 with B complex64, FP64
 // accumulation into complex128 or FP32 accumulation into complex64.

@@ -106,7 +106,7 @@ def test_parity_grid20(grid20, prec, solver):
     assert any(k.startswith("gemm_splitk:") for k in paths), paths
     if prec == "mixed":
         assert paths.get("gemm:fp32_df:32x32", 0) > 0, paths
-        assert paths.get("gemm:tcgen05_tf32x3:64x64", 0) > 0, paths
+        assert any(k.startswith("gemm:tcgen05_tf32x3:") for k in paths), paths
     A.close()
 
 
@@ -135,8 +135,10 @@ def test_headline_grid32_sampled_exact_rows():
     assert rho.max() <= 10 * EPS, rho
     paths = A.stats()["paths"]
     print("grid32 paths:", paths)
-    for p in ("pchol_wy:cta16", "gemm:fp32_df:32x32", "gemm:tcgen05_tf32x3:64x64"):
+    for p in ("pchol_wy:cta16", "gemm:fp32_df:32x32"):
         assert paths.get(p, 0) > 0, (p, paths)
+    # complex64 bulk on tcgen05 tiles of both widths (64 x 64 and 64 x 128)
+    assert paths.get("gemm:tcgen05_tf32x3:64x64", 0) > 0 and paths.get("gemm:tcgen05_tf32x3:64x128", 0) > 0, paths
     # the Step-0 eigen-decomposition of the largest Ritz problems on a cluster of >= 8 CTAs
     assert any(k.split(":cta")[0] in ("jacobi_cluster", "heev_cluster", "osj_cluster") and int(k.split(":cta")[1]) >= 8
                for k in paths), paths
