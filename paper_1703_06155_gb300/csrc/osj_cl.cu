@@ -107,6 +107,10 @@ __global__ void __launch_bounds__(NT, 1) k_osj_cl(const EigTask* __restrict__ ta
   int* flags = reinterpret_cast<int*>(lamd + r);  // per sweep: a rotation happened (zeroed by the host)
   const int nblk = 2 * C;
   const int b = (r + nblk - 1) / nblk;
+  if (b > kMaxB) {  // the launcher sizes clusters so that this never happens
+    if (rank == 0 && tid == 0 && status) atomicMax(status, 2);
+    return;
+  }
   extern __shared__ float4 osm[];
   float4* Ws = osm;                  // 2b columns of W (ld r)
   float4* Js = osm + (size_t)2 * b * r;  // the same columns of J
@@ -350,6 +354,14 @@ size_t smem_bytes(int r, int C) {
   return (size_t)4 * b * r * sizeof(float4);
 }
 
+// smallest cluster whose blocks hold at most kMaxB columns and whose staged
+// columns fit in shared memory (orders <= osj_max_order() fit with 16)
+int min_cluster(int r) {
+  int c = 1;
+  while (c < 16 && ((r + 2 * c - 1) / (2 * c) > kMaxB || smem_bytes(r, c) > kSmemMax)) ++c;
+  return c;
+}
+
 }  // namespace
 
 int osj_max_order() {
@@ -369,8 +381,7 @@ int osj_cluster_size(int ntasks, int maxp, int cmax) {
   // SMs when the problems are many
   int c = std::min(std::min(16, std::max(cmax, 1)), std::max(1, (maxp + 15) / 16));
   if (ntasks > 0) c = std::min(c, std::max(1, 152 / ntasks));
-  while (c < 16 && smem_bytes(maxp, c) > kSmemMax) ++c;
-  return c;
+  return std::max(c, min_cluster(maxp));
 }
 
 cudaError_t osj_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int csize, void* d_scratch, int* d_status,
@@ -380,8 +391,7 @@ cudaError_t osj_eig_cluster(const EigTask* d_tasks, int ntasks, int maxp, int cs
   const int64_t per = osj_cluster_scratch(maxp);
   cudaError_t e = cudaMemsetAsync(d_scratch, 0, (size_t)per * ntasks, s);
   if (e != cudaSuccess) return e;
-  csize = std::max(1, std::min(16, csize));
-  while (csize < 16 && smem_bytes(maxp, csize) > kSmemMax) ++csize;
+  csize = std::max(min_cluster(maxp), std::min(16, csize));
   const size_t smem = smem_bytes(maxp, csize);
   e = cudaFuncSetAttribute(k_osj_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -104,3 +104,30 @@ def test_batch_mixed_refinement(dev):
     assert info["resid"] <= 1e-10
     for q, (x, b) in enumerate(zip(xs, bs)):
         assert rel(x.cpu().numpy(), dense_solve(q, b)) < 1e-8, q
+
+
+def test_many_instances_share_launches(dev):
+    # 24 copies of one 16^3 problem in one batch: a Step-0 launch then holds
+    # about a hundred eigen-problems, so the per-problem clusters get small
+    # and the one-sided Jacobi's column blocks long (they must stay within
+    # the kernel's block limit); every instance must match the same problem
+    # factorized alone, to FP32 closeness before refinement and to 1e-10 after
+    from paper_1703_06155_gb300 import H2, factorize_batch, solve_batch
+    H = h2_problem(16, 64, EPS)
+    rep = oracle_to_rep(H)
+    cs = [H2.load(rep) for _ in range(24)]
+    factorize_batch(cs, EPS, "mixed")
+    one = H2.load(rep)
+    one.factorize(EPS, "mixed")
+    b = inputs.rhs_gaussian(H.tree.N, 2, 41)
+    bt = torch.from_numpy(b).to(dev)
+    x1 = one.solve(bt).cpu().numpy()
+    xs, _ = solve_batch(cs, [bt] * len(cs))
+    worst = max(rel(x.cpu().numpy(), x1) for x in xs)
+    xr, _ = solve_batch(cs, [bt] * len(cs), refine=True, tol=1e-10, max_iter=30)
+    xr1 = one.solve(bt, refine=True, tol=1e-10, max_iter=30).cpu().numpy()
+    worst_r = max(rel(x.cpu().numpy(), xr1) for x in xr)
+    print("24 instances: unrefined vs alone %.1e, refined vs alone %.1e" % (worst, worst_r))
+    assert worst < 1e-4 and worst_r < 1e-9
+    for c in cs + [one]:
+        c.close()
