@@ -154,4 +154,10 @@ inline void run_apply_narrow(Ctx& c, ApplyBatch& b, int prec, const char* what) 
 }
 void run_copy(Ctx& c, CopyBatch& b, const char* what);
 
+// host-side bounds checks of the task lists (checks.cpp, H2_CHECKS)
+void check_gemm(const GemmBatch& b, int pina, int pin, int pout, const char* what);
+void check_copy(const CopyBatch& b, const char* what);
+void check_apply(const ApplyBatch& b, bool left, int prec, const char* what);
+void check_lu(const std::vector<h2k::LuTask>& lu, int prec);
+
 }  // namespace h2

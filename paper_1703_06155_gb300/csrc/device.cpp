@@ -11,7 +11,10 @@
 namespace h2 {
 
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    alloc_unregister(p);
+    cudaFree(p);
+  }
   p = nullptr;
   bytes = 0;
 }
@@ -92,6 +95,7 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
   if (b.p) {
     ck(cudaStreamSynchronize(c.stream), "sync before realloc");
     if (c.side.s) ck(cudaStreamSynchronize(c.side.s), "sync before realloc");
+    alloc_unregister(b.p);
     cudaFree(b.p);
     b.p = nullptr;
     c.dev_bytes -= old;
@@ -107,6 +111,7 @@ void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes) {
   // kernel reading memory nothing has written yet shows up as NaN results
   static const bool poison = std::getenv("H2_POISON_ALLOC") != nullptr;
   if (poison) ck(cudaMemsetAsync(p, 0xFF, want, c.stream), "poison");
+  alloc_register(p, want);
   b.p = p;
   b.bytes = want;
   c.gen++;

@@ -48,6 +48,7 @@ void run_gemm(Ctx& c, GemmBatch& b, int pin, int pout, int pacc, const char* wha
   const int64_t ws = b.plan(c.opts.split_target > 0 ? c.opts.split_target : 8 * 152, pacc == P64, c.opts.tile_policy,
                             !emul, all32 && c.opts.tensor_cores == 2);
   if (b.tl.empty()) return;
+  if (checks_on()) check_gemm(b, b.pina, pin, pout, what);
   void* wsp = nullptr;
   if (ws > 0) wsp = dev_ensure(c, c.gemm_ws, (size_t)ws * (pacc == P64 ? sizeof(cd) : sizeof(cf)));
   const int i0 = c.st.add(b.t), i1 = c.st.add(b.p), i2 = c.st.add(b.tl);
@@ -140,6 +141,7 @@ void run_apply_gemm(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what
 void run_copy(Ctx& c, CopyBatch& b, const char* what) {
   if (b.empty()) return;
   HostScope hs(c, "run_copy");
+  if (checks_on()) check_copy(b, what);
   const int i0 = c.st.add(b.t);
   c.st.upload(c);
   double bytes = 0, elems = 0;
@@ -162,6 +164,7 @@ void ensure_covered(Ctx& lc, Ctx& c, int ls);
 
 // Step 2 / panel applications: in-place kernel or GEMM + copy (h2_opts.apply_path)
 void run_apply_auto(Ctx& c, ApplyBatch& b, bool left, int prec, const char* what) {
+  if (checks_on()) check_apply(b, left, prec, what);
   if (c.opts.apply_path == 1) run_apply(c, b, left, prec, what);
   else run_apply_gemm(c, b, left, prec, what);
 }
@@ -843,6 +846,7 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     }
   }
   if (!lu.empty()) {
+    if (checks_on()) check_lu(lu, prec);
     const int i0 = lc.st.add(lu);
     lc.st.upload(lc);
     double fl = 0;

@@ -114,6 +114,12 @@ void ck(cudaError_t e, const char* what);
 void* dev_ensure(Ctx& c, DevBuf& b, size_t bytes);
 // Frees a buffer of the context's arena accounting.
 void dev_free(Ctx& c, DevBuf& b);
+// allocation registry and the host-side bounds checks of the task lists
+// (checks.cpp; on when H2_CHECKS is set in the environment)
+bool checks_on();
+void alloc_register(const void* p, size_t bytes);
+void alloc_unregister(const void* p);
+void check_range(const void* p, size_t bytes, const std::string& what);
 // Frees the factors of the last factorization and the factorization scratch
 // (after a failed factorization: the context keeps its H^2 matrix only).
 void drop_factors(Ctx& c);

@@ -337,3 +337,46 @@ def test_matvec_emulation_against_fp64_and_oracle(dev):
     print("refined solve: emulated residual %.2e, FP64 residual %.2e" % (res_emul, res64))
     assert res_emul <= 1e-10 and res64 <= 2e-10
     A.close()
+
+
+_CHECKED_RUN = r"""
+import sys, numpy as np, torch
+sys.path[:0] = ["tests", "."]
+from _problems import h2_problem
+from _h2io import oracle_to_rep
+from paper_1703_06155_gb300 import H2, inputs, factorize_batch, solve_batch
+H = h2_problem(16, 64, 1e-6)
+b = torch.from_numpy(inputs.rhs_gaussian(H.tree.N, 3, 7)).cuda()
+A = H2.load(oracle_to_rep(H))
+A.factorize(1e-6, "mixed")
+A.solve(b, refine=True, tol=1e-10, max_iter=30)
+A.factorize(1e-6, "fp64")
+A.invert()
+A.solve(b, use_inverse=True)
+A.solve(b, adjoint=True)
+A.matvec(b)
+A.set_opts(stop_level=H.l0 + 1)
+A.factorize(1e-6, "mixed")
+A.solve(b)
+cs = [H2.load(oracle_to_rep(h2_problem(n, 64, 1e-6))) for n in (12, 16)]
+factorize_batch(cs, 1e-6, "mixed")
+solve_batch(cs, [torch.from_numpy(inputs.rhs_gaussian(c.stats()["N"], 2, 3)).cuda() for c in cs], refine=True)
+print("checked run ok")
+"""
+
+
+def test_bounds_checked_run(dev):
+    # the same library with H2_CHECKS set: every GEMM, copy, apply and
+    # partial-LU task list of a mixed and an FP64 factorization (full and
+    # early-stopped), refined / adjoint / inverse-based solves, a matvec and
+    # a two-instance batch is checked on the host against the allocations it
+    # touches before its launch; any overrun would fail the call
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, H2_CHECKS="1")
+    r = subprocess.run([sys.executable, "-c", _CHECKED_RUN], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    print(r.stdout[-2000:], r.stderr[-2000:])
+    assert r.returncode == 0 and "checked run ok" in r.stdout
