@@ -42,6 +42,18 @@ Readings of the paper where it is silent or ambiguous:
      neighbours, so this equals a sequential sweep up to the order in which
      fill-ins of non-neighbours are transformed.  'natural' (one cluster per
      batch) is the paper's left-to-right sweep.
+  R7 symmetric variant (`symmetric=True`, for a complex-symmetric Z_H2:
+     Z^T = Z, S_st = S_ts^T): a block LDL^T elimination.  The Step-2
+     transform keeps Z_cur symmetric (Q^H Z conj(Q) with one basis per
+     cluster), so only the blocks (a, b) with a <= b are stored and block
+     (b, a) is read as the transpose of (a, b).  Eliminating i' with
+     F = Z_i'i' (LU with partial pivoting inside F, R5) gives
+     Z = [I 0; B F^-1 I] [F 0; 0 S] [I F^-1 B^T; 0 I], S = C - B F^-1 B^T
+     with B = Z_(rest) i' = (Z_i' (rest))^T: the factor keeps the raw block
+     row Z_i'(rest) once instead of the two panels L^-1 P Z_i'c and
+     Z_ci' U^-1, and S is formed for one triangle of target pairs.  In exact
+     arithmetic the Schur complements, hence the rank decisions and the
+     solution, equal those of the LU form.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -54,7 +66,7 @@ class ClusterFactor:
     """Factor data of one cluster at one level (the non-identity parts of
     Q_i^l, L_i^l and U_i^l in eq. 34)."""
 
-    __slots__ = ("n", "kt", "m", "Q", "LU", "piv", "Up", "Lp")
+    __slots__ = ("n", "kt", "m", "Q", "LU", "piv", "Up", "Lp", "Zr", "Finv")
 
 
 class LevelFactor:
@@ -79,6 +91,12 @@ def _x_uinv(X, LU):
     return sla.solve_triangular(LU, X.T, lower=False, trans="T").T
 
 
+def _transpose(X):
+    """Plain transpose: block (b, a) of a complex-symmetric matrix is the
+    transpose, not the conjugate transpose, of block (a, b)."""
+    return X.T
+
+
 def _round(X, dtype):
     return X if dtype == np.complex128 else X.astype(dtype).astype(np.complex128)
 
@@ -98,7 +116,17 @@ def ancestor_map(H, l, a, lv):
     return E
 
 
-def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop_level=None):
+def _blk(store, a, b, sym):
+    """Block (a, b) of a block store; with one-sided storage (`sym`) the
+    pairs a > b are the transposed views of the stored (b, a)."""
+    return store[(a, b)] if (not sym or a <= b) else store[(b, a)].T
+
+
+def _has(store, a, b, sym):
+    return (a, b) in store if (not sym or a <= b) else (b, a) in store
+
+
+def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop_level=None, symmetric=False):
     """Factorize Z_H2 (Algorithm 1).  `bulk`=np.complex64 rounds the Schur /
     LU / transform products to FP32 complex, emulating the mixed-precision
     path; rank decisions (Step 0/1) always run in FP64.  `observe`, if given,
@@ -111,16 +139,24 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
     processed, and the remaining matrix of all pairs at stop_level is
     factorized as the final block; a pair that lies inside an ancestor's
     admissible block enters it as pad(E_a S E_b^T) + F, E from
-    `ancestor_map` (the coupling in the level's incoming bases, eq. 20)."""
+    `ancestor_map` (the coupling in the level's incoming bases, eq. 20).
+    `symmetric`: block LDL^T form with one-sided block storage (R7); Z_H2
+    must be complex symmetric."""
     tree, part, L, l0 = H.tree, H.part, H.L, H.l0
+    sym = bool(symmetric)
+    if sym:
+        for (t, s_), Dm in H.D.items():
+            assert np.allclose(Dm, H.D[(s_, t)].T, rtol=0, atol=1e-12 * (1 + np.abs(Dm).max())), "Z_H2 not symmetric"
+    blk = lambda store, a, b: _blk(store, a, b, sym)
+    has = lambda store, a, b: _has(store, a, b, sym)
     ls = l0 if stop_level is None else max(l0, min(L, int(stop_level)))
     Fz = Factorization()
-    Fz.H, Fz.eps, Fz.ordering = H, eps, ordering
+    Fz.H, Fz.eps, Fz.ordering, Fz.symmetric = H, eps, ordering, sym
     Fz.levels = []
     # level-L state
     n = np.array(tree.size[L], dtype=np.int64)
     B = {c: H.V[c].copy() for c in range(2 ** L)}
-    near = {p: H.D[p].copy() for p in part.inad[L]}
+    near = {p: H.D[p].copy() for p in part.inad[L] if not sym or p[0] <= p[1]}
     fill = {}
     for l in range(L, ls - 1, -1):
         near_set = set(part.inad[l])
@@ -148,6 +184,9 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
         for (a, b) in fill:
             fill_rows[a].append(b)
             fill_cols[b].append(a)
+            if sym:                                             # the (b, a) view
+                fill_rows[b].append(a)
+                fill_cols[a].append(b)
 
         def act(c):
             return slice(int(m[c]), int(n[c])) if done[c] else slice(0, int(n[c]))
@@ -170,8 +209,8 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 else:
                     Qf, _ = np.linalg.qr(Bi, mode="complete")
                     Vp = Qf[:, ki:]
-                rows = [(k, fill[(i, k)]) for k in fill_rows[i]]
-                cols = [(k, fill[(k, i)]) for k in fill_cols[i]]
+                rows = [(k, blk(fill, i, k)) for k in fill_rows[i]]
+                cols = [(k, blk(fill, k, i)) for k in fill_cols[i]]
                 Vadd = np.zeros((ni, 0), dtype=np.complex128)
                 Vrest = Vp
                 if (rows or cols) and ni > ki:
@@ -204,23 +243,29 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 kt[i] = B[i].shape[1]
             # ---- Step 2: Z_cur <- Q_i^H Z_cur conj(Q_i) (eq. 5, Alg. 3):
             # block rows of the batch first, then block columns ----
+            # With one-sided storage (R7) the row transform of a view (i, j),
+            # j < i, is the column transform of the stored (j, i): every
+            # off-diagonal block gets both of its transforms in the row pass,
+            # and only the diagonal blocks take the column pass.
             for i in bt:
                 Qh = step01[i][1].conj().T
                 for j in nbrs[i]:
-                    X = near[(i, j)]
+                    X = blk(near, i, j)
                     cj = slice(0, int(n[i])) if j == i else act(j)
                     X[:, cj] = _round(Qh @ X[:, cj], bulk)
                 for kk in fill_rows[i]:
-                    X = fill[(i, kk)]
+                    X = blk(fill, i, kk)
                     ck = act(kk)
                     X[:, ck] = _round(Qh @ X[:, ck], bulk)
             for i in bt:
                 Qb = step01[i][1].conj()
                 for j in nbrs[i]:
+                    if sym and j != i:
+                        continue
                     X = near[(j, i)]
                     cj = slice(0, int(n[i])) if j == i else act(j)
                     X[cj, :] = _round(X[cj, :] @ Qb, bulk)
-                for kk in fill_cols[i]:
+                for kk in ([] if sym else fill_cols[i]):
                     X = fill[(kk, i)]
                     ck = act(kk)
                     X[ck, :] = _round(X[ck, :] @ Qb, bulk)
@@ -232,12 +277,20 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 mi = ni - int(kt[i])
                 cf = ClusterFactor()
                 cf.n, cf.kt, cf.m, cf.Q = ni, int(kt[i]), mi, step01[i][1]
-                cf.Up, cf.Lp = {}, {}
+                cf.Up, cf.Lp, cf.Zr, cf.Finv = {}, {}, {}, None
                 cf.LU, cf.piv = None, None
                 if mi > 0:
                     LU, piv = dense.lu(near[(i, i)][:mi, :mi])  # eq. (11)
                     LU = _round(LU, bulk)
                     cf.LU, cf.piv = LU, piv
+                    if sym:
+                        # R7: F^-1 (from the pivoted LU) and the raw block row
+                        cf.Finv = _round(_uinv(LU, _linv_p(LU, piv, np.eye(mi, dtype=np.complex128))), bulk)
+                        for j in nbrs[i]:
+                            cs = slice(mi, ni) if j == i else act(j)
+                            cf.Zr[j] = (blk(near, i, j)[:mi, cs].copy(), cs)
+                        cfs[i] = cf
+                        continue
                     for j in nbrs[i]:
                         cs = slice(mi, ni) if j == i else act(j)
                         Uj = _round(_linv_p(LU, piv, near[(i, j)][:mi, cs]), bulk)   # Alg. 4 l.2
@@ -245,26 +298,41 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                         cf.Up[j] = (Uj, cs)
                         cf.Lp[j] = (Lj, cs)
                 cfs[i] = cf
+            def target(j, kk, rs, cs, upd):
+                if has(near, j, kk):
+                    near[(j, kk)][rs, cs] -= upd
+                else:                                           # eq. (15): store F_jk
+                    if (j, kk) not in fill:
+                        fill[(j, kk)] = np.zeros((int(n[j]), int(n[kk])), dtype=np.complex128)
+                        fill_rows[j].append(kk)
+                        fill_cols[kk].append(j)
+                        if sym and j != kk:
+                            fill_rows[kk].append(j)
+                            fill_cols[j].append(kk)
+                        stats["fill_blocks"] += 1
+                        if (j, kk) not in adm_set:
+                            stats["pushed_blocks"] += 1
+                    fill[(j, kk)][rs, cs] -= upd
+
             for i in bt:
                 cf = cfs[i]
-                if cf.m == 0:
+                if cf.m == 0 or not sym:
+                    continue
+                # R7: S_jk -= Z_ji' F^-1 Z_i'k for the stored pairs j <= k
+                W = {kk: _round(cf.Finv @ Zk, bulk) for kk, (Zk, _) in cf.Zr.items()}
+                for j, (Zj, rs) in cf.Zr.items():
+                    for kk, (Zk, cs) in cf.Zr.items():
+                        if j <= kk:
+                            target(j, kk, rs, cs, _round(_transpose(Zj) @ W[kk], bulk))
+            for i in bt:
+                cf = cfs[i]
+                if cf.m == 0 or sym:
                     continue
                 for j in nbrs[i]:                               # Alg. 4 l.4, eq. (12)
                     Lj, rs = cf.Lp[j]
                     for kk in nbrs[i]:
                         Uk, cs = cf.Up[kk]
-                        upd = _round(Lj @ Uk, bulk)
-                        if (j, kk) in near_set:
-                            near[(j, kk)][rs, cs] -= upd
-                        else:                                   # eq. (15): store F_jk
-                            if (j, kk) not in fill:
-                                fill[(j, kk)] = np.zeros((int(n[j]), int(n[kk])), dtype=np.complex128)
-                                fill_rows[j].append(kk)
-                                fill_cols[kk].append(j)
-                                stats["fill_blocks"] += 1
-                                if (j, kk) not in adm_set:
-                                    stats["pushed_blocks"] += 1
-                            fill[(j, kk)][rs, cs] -= upd
+                        target(j, kk, rs, cs, _round(Lj @ Uk, bulk))
             for i in bt:
                 m[i] = cfs[i].m
                 done[i] = True
@@ -279,7 +347,7 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
             """Kept (trailing) part of pair (a,b) after the level: the merged
             block of Fig. 2(h); admissible blocks give pad(S) + F (eqs. 20-22)."""
             if (a, b) in near_set:
-                return near[(a, b)][m[a]:, m[b]:].copy()
+                return blk(near, a, b)[m[a]:, m[b]:].copy()
             X = np.zeros((int(kt[a]), int(kt[b])), dtype=np.complex128)
             if (a, b) in adm_set:
                 S = H.S[l][(a, b)]
@@ -293,8 +361,8 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                         S = ancestor_map(H, l, a, lv) @ H.S[lv][(A_, B_)] @ ancestor_map(H, l, b, lv).T
                         X[:S.shape[0], :S.shape[1]] = S
                         break
-            if (a, b) in fill:
-                X += fill[(a, b)][m[a]:, m[b]:]                 # eq. (22)/(33)
+            if has(fill, a, b):
+                X += blk(fill, a, b)[m[a]:, m[b]:]              # eq. (22)/(33)
             return X
 
         if l > ls:
@@ -311,6 +379,8 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 Bn[p] = Tn
             near_n = {}
             for p, q in part.inad[l - 1]:
+                if sym and p > q:
+                    continue
                 top = np.hstack([kept(2 * p, 2 * q), kept(2 * p, 2 * q + 1)])
                 bot = np.hstack([kept(2 * p + 1, 2 * q), kept(2 * p + 1, 2 * q + 1)])
                 near_n[(p, q)] = np.vstack([top, bot])
@@ -320,7 +390,7 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 if (a, b) in adm_set:
                     continue
                 pa, pb = a // 2, b // 2
-                assert (pa, pb) not in near_par
+                assert (pa, pb) not in near_par                 # siblings are near: pa != pb
                 if (pa, pb) not in fill_n:
                     fill_n[(pa, pb)] = np.zeros((int(npar[pa]), int(npar[pb])), dtype=np.complex128)
                 ro = 0 if a % 2 == 0 else int(kt[a - 1])
@@ -388,13 +458,21 @@ def solve(Fz, b, inverse=None):
     one = b.ndim == 1
     if one:
         b = b[:, None]
+    sym = getattr(Fz, "symmetric", False)
     vec = _leaf_split(Fz, b)
     saved = []
     for li, lev in enumerate(Fz.levels):
         for i in lev.order:
             cf = lev.cl[i]
             vec[i] = cf.Q.conj().T @ vec[i]                      # Alg. 5 l.3
-            if cf.m > 0:
+            if cf.m > 0 and sym:
+                # L of the block LDL^T (R7): y_i' stays, the rest of the
+                # vector loses B F^-1 y_i' = Z_i'(rest)^T (F^-1 y_i')
+                Fi = cf.Finv if inverse is None else inverse.Finv[li][i]
+                t = Fi @ vec[i][:cf.m]
+                for j, (Zj, rs) in cf.Zr.items():
+                    vec[j][rs] -= _transpose(Zj) @ t
+            elif cf.m > 0:
                 if inverse is None:
                     bi = _linv_p(cf.LU, cf.piv, vec[i][:cf.m])   # Alg. 5 l.4, eq. (39)
                 else:
@@ -423,7 +501,19 @@ def solve(Fz, b, inverse=None):
             vec[c][int(lev.n[c]) - k:] = vp
         for i in reversed(lev.order):
             cf = lev.cl[i]
-            if cf.m > 0:
+            if cf.m > 0 and sym:
+                # D^-1 and L^T (R7): x_i' = F^-1 (y_i' - Z_i'(rest) x_rest)
+                t = vec[i][:cf.m].copy()
+                if inverse is None:
+                    for k_, (Zk, cs) in cf.Zr.items():
+                        t -= Zk @ vec[k_][cs]
+                    vec[i][:cf.m] = cf.Finv @ t
+                else:
+                    t = inverse.Finv[li][i] @ t
+                    for k_, (Ub, cs) in inverse.Ub[li][i].items():
+                        t += Ub @ vec[k_][cs]
+                    vec[i][:cf.m] = t
+            elif cf.m > 0:
                 if inverse is None:
                     t = vec[i][:cf.m].copy()
                     for k_, (Uk, cs) in cf.Up.items():
@@ -451,6 +541,9 @@ def solve_adjoint(Fz, r):
     """lambda = Z^{-H} r from the same factors: the adjoints of the solve's
     elementary operations applied in reverse order (U^H then L^H of eq. 34)."""
     r = np.asarray(r, dtype=np.complex128)
+    if getattr(Fz, "symmetric", False):
+        # Z^T = Z gives Z^-H r = conj(Z^-1 conj(r))
+        return np.conj(solve(Fz, np.conj(r)))
     one = r.ndim == 1
     if one:
         r = r[:, None]
@@ -516,11 +609,17 @@ def invert(Fz):
     -(U_i'i')^{-1} U_i'c panels and the inverse of the final block, so that
     applying Z^{-1} needs matrix-vector products only."""
     inv = Inverse()
-    inv.Linv, inv.Uinv, inv.Ub = [], [], []
+    inv.Linv, inv.Uinv, inv.Ub, inv.Finv = [], [], [], []
+    sym = getattr(Fz, "symmetric", False)
     for lev in Fz.levels:
-        Li, Ui, Ubl = {}, {}, {}
+        Li, Ui, Ubl, Fi = {}, {}, {}, {}
         for i, cf in lev.cl.items():
             if cf.m == 0:
+                continue
+            if sym:
+                # R7: F^-1 and -F^-1 Z_i'c
+                Fi[i] = _uinv(cf.LU, _linv_p(cf.LU, cf.piv, np.eye(cf.m, dtype=np.complex128)))
+                Ubl[i] = {k: (-Fi[i] @ Zk, cs) for k, (Zk, cs) in cf.Zr.items()}
                 continue
             I = np.eye(cf.m, dtype=np.complex128)
             Li[i] = _linv_p(cf.LU, cf.piv, I)
@@ -529,6 +628,7 @@ def invert(Fz):
         inv.Linv.append(Li)
         inv.Uinv.append(Ui)
         inv.Ub.append(Ubl)
+        inv.Finv.append(Fi)
     inv.Rinv = dense.lu_solve(Fz.root_LU, Fz.root_piv, np.eye(Fz.root_size, dtype=np.complex128)) if Fz.root_size else None
     return inv
 

@@ -282,6 +282,55 @@ def test_degenerate_sizes(N):
         assert np.linalg.norm(x - xe) <= tol * np.linalg.norm(xe), (eps, np.linalg.norm(x - xe))
 
 
+# ------------------------------------- block LDL^T (symmetric) variant ----
+
+
+@pytest.mark.parametrize("ordering", ["colored", "natural"])
+def test_ldlt_eps_zero_is_exact(ordering):
+    # eps_fill = 0: the block LDL^T of the symmetric Z_H2 with one-sided block
+    # storage is exact (Z = L D L^T), like the LU form (eq. 34); the adjoint
+    # (Z^-H = conj Z^-1 conj) and the factor-form inverse follow it
+    Hm = h2_problem(12, 64, 1e-6)
+    Zh = h2_dense(12, 64, 1e-6)
+    Fz = factor.factorize(Hm, 0.0, ordering, symmetric=True)
+    b = inputs.rhs_gaussian(Hm.tree.N, 2, 11)
+    xe = np.linalg.solve(Zh, b)
+    assert np.linalg.norm(factor.solve(Fz, b) - xe) / np.linalg.norm(xe) < 1e-11
+    le = np.linalg.solve(Zh.conj().T, b)
+    assert np.linalg.norm(factor.solve_adjoint(Fz, b) - le) / np.linalg.norm(le) < 1e-11
+    xi = factor.solve(Fz, b, inverse=factor.invert(Fz))
+    assert np.linalg.norm(xi - xe) / np.linalg.norm(xe) < 1e-11
+
+
+def test_ldlt_matches_lu_form_and_halves_the_blocks():
+    # eps_fill > 0: the two forms compute the same Schur complements in exact
+    # arithmetic, so every Step-0 decision (per-cluster kept ranks) and the
+    # solution agree to rounding; the symmetric form stores one block of each
+    # off-diagonal pair, half the fill-in blocks of the LU form
+    Hm = h2_problem(12, 64, 1e-6)
+    b = inputs.rhs_gaussian(Hm.tree.N, 1, 4)[:, 0]
+    for eps in (1e-6, 1e-4):
+        Flu = factorization(12, 64, 1e-6, eps, "colored")
+        Fs = factor.factorize(Hm, eps, "colored", symmetric=True)
+        for a, c in zip(Flu.levels, Fs.levels):
+            assert np.array_equal(a.kt, c.kt), (a.l, a.kt, c.kt)
+            assert 2 * c.stats["fill_blocks"] == a.stats["fill_blocks"]
+        x1, x2 = factor.solve(Flu, b), factor.solve(Fs, b)
+        assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-12
+
+
+def test_ldlt_refinement_from_complex64_bulk():
+    # the mixed-precision emulation (complex64 bulk) of the symmetric form,
+    # refined with the FP64 H^2 matvec, reaches the dense solution
+    Hm = h2_problem(12, 64, 1e-6)
+    Zh = h2_dense(12, 64, 1e-6)
+    Fz = factor.factorize(Hm, 1e-6, "colored", bulk=np.complex64, symmetric=True)
+    b = inputs.rhs_gaussian(Hm.tree.N, 1, 6)[:, 0]
+    x, hist = factor.refine(Fz, b, tol=1e-12, max_iter=10)
+    assert hist[-1] <= 1e-12 and len(hist) <= 8
+    assert np.linalg.norm(Zh @ x - b) / np.linalg.norm(b) < 1e-11
+
+
 # ---------------------------------------------- planted mistakes (CPU) ----
 
 
@@ -312,6 +361,12 @@ def test_planted_mistakes_are_caught(monkeypatch):
         test_self_term_quadrature()
     monkeypatch.undo()
     assert err_exact() < 1e-11
+    # (d) block LDL^T with the conjugate transpose where Z^T = Z asks for the
+    # plain transpose
+    monkeypatch.setattr(factor, "_transpose", lambda X: X.conj().T)
+    x = factor.solve(factor.factorize(Hm, 0.0, symmetric=True), b)
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) > 1e-6
+    monkeypatch.undo()
 
 
 # ------------------------------------------- derivative in the contrast ----
