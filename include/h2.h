@@ -134,6 +134,21 @@ typedef struct {
                             the residuals of refined solves with tol >=
                             1e-11, FP64 FMAs elsewhere; 2: also h2_matvec;
                             0: FP64 FMAs everywhere                        */
+  int ldlt;              /* elimination form: 1 (default) block LDL^T when
+                            the matrix is complex symmetric (Z^T = Z:
+                            always for h2_build, for h2_load when every
+                            block equals the transpose of its mirror; a
+                            batch uses it when all its instances qualify),
+                            block LU otherwise; 0 block LU always (eq. 34,
+                            both panels L^-1 P Z_i'c and Z_ci' U^-1 kept).
+                            LDL^T keeps one block of each off-diagonal
+                            pair, the raw block row Z_i'c and
+                            F^-1 = (Z_i'i')^-1 as the factor, and forms the
+                            Schur updates of one triangle of the target
+                            pairs: the same Step-0 decisions and solution
+                            as LU in exact arithmetic with about half the
+                            near-field factor memory; h2_stats "ldlt"
+                            reports the form of the last factorization    */
 } h2_opts;
 
 /* Fill `o` with the defaults listed above. */
@@ -330,7 +345,7 @@ h2_status h2_grad_chi(h2_ctx* ctx, const void* x, const void* mu,
 /*
  * h2_set_opts - change the run-time tunables of a context (apply_path,
  * solve_graph, split_target, cluster_max, tile_policy, tensor_cores,
- * gram_emulation, eig_solver, stop_level, matvec_emulation, profile) without
+ * gram_emulation, eig_solver, stop_level, matvec_emulation, ldlt, profile) without
  * rebuilding it; the other fields of *opts are ignored.  They take effect at
  * the next h2_factorize / h2_solve (captured solve graphs are retired).  No
  * counterpart in the paper: used by the autotuner.

@@ -37,7 +37,8 @@ class h2_opts(ctypes.Structure):
                 ("solve_graph", ctypes.c_int), ("split_target", ctypes.c_int), ("cluster_max", ctypes.c_int),
                 ("tile_policy", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("gram_emulation", ctypes.c_int), ("eig_solver", ctypes.c_int), ("stop_level", ctypes.c_int),
-                ("proxy_margin", ctypes.c_double), ("matvec_emulation", ctypes.c_int)]
+                ("proxy_margin", ctypes.c_double), ("matvec_emulation", ctypes.c_int),
+                ("ldlt", ctypes.c_int)]
 
 
 class H2Error(RuntimeError):

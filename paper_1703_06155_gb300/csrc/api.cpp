@@ -62,11 +62,13 @@ void apply_Ainv(h2_ctx* x, const cd* in, cd* out, int nrhs, bool adj, bool inv) 
   void* t = dev_ensure(c, x->tA, (size_t)N * nrhs * esz(c.prec));
   const double* sc = (const double*)c.dscale.p;
   const double* isc = (const double*)x->invscale.p;
-  // Z (S x) = S b ; adjoint: Z^H (S^{-1} x) = S^{-1} b
-  ck(permute_scale(in, t, (const int64_t*)c.dperm.p, adj ? isc : sc, N, nrhs, P64, c.prec, 0, 0, c.stream),
+  // Z (S x) = S b ; adjoint: Z^H (S^{-1} x) = S^{-1} b.  Block LDL^T factors
+  // of the symmetric Z solve the adjoint as Z^{-H} r = conj(Z^{-1} conj(r)).
+  const int cj = adj && c.fac_ldlt ? 1 : 0;
+  ck(permute_scale(in, t, (const int64_t*)c.dperm.p, adj ? isc : sc, N, nrhs, P64, c.prec, 0, cj, c.stream),
      "permute in");
-  solve_tree(c, t, nrhs, adj, inv);
-  ck(permute_scale(t, out, (const int64_t*)c.dperm.p, adj ? sc : isc, N, nrhs, c.prec, P64, 1, 0, c.stream),
+  solve_tree(c, t, nrhs, adj && !cj, inv);
+  ck(permute_scale(t, out, (const int64_t*)c.dperm.p, adj ? sc : isc, N, nrhs, c.prec, P64, 1, cj, c.stream),
      "permute out");
 }
 
@@ -106,22 +108,26 @@ void apply_Ainv_group(const std::vector<h2_ctx*>& xs, const std::vector<const cd
                       const std::vector<cd*>& outs, int nrhs, bool adj, bool inv) {
   Ctx& lc = xs[0]->c;
   std::vector<void*> ts;
+  // block LDL^T factors: Z^{-H} r = conj(Z^{-1} conj(r)) (as apply_Ainv)
+  for (h2_ctx* x : xs)
+    if (x->c.fac_ldlt != lc.fac_ldlt) fail(H2_EINVAL, "instances factorized in different forms (ldlt)");
+  const int cj = adj && lc.fac_ldlt ? 1 : 0;
   for (size_t q = 0; q < xs.size(); ++q) {
     Ctx& c = xs[q]->c;
     const int64_t N = c.H.tree.N;
     void* t = dev_ensure(c, xs[q]->tA, (size_t)N * nrhs * esz(c.prec));
     ck(permute_scale(ins[q], t, (const int64_t*)c.dperm.p,
-                     adj ? (const double*)xs[q]->invscale.p : (const double*)c.dscale.p, N, nrhs, P64, c.prec, 0, 0,
+                     adj ? (const double*)xs[q]->invscale.p : (const double*)c.dscale.p, N, nrhs, P64, c.prec, 0, cj,
                      lc.stream),
        "permute in");
     ts.push_back(t);
   }
-  solve_tree_group(cores(xs), ts, nrhs, adj, inv);
+  solve_tree_group(cores(xs), ts, nrhs, adj && !cj, inv);
   for (size_t q = 0; q < xs.size(); ++q) {
     Ctx& c = xs[q]->c;
     ck(permute_scale(ts[q], outs[q], (const int64_t*)c.dperm.p,
                      adj ? (const double*)c.dscale.p : (const double*)xs[q]->invscale.p, c.H.tree.N, nrhs, c.prec,
-                     P64, 1, 0, lc.stream),
+                     P64, 1, cj, lc.stream),
        "permute out");
   }
 }
@@ -249,6 +255,7 @@ void h2_default_opts(h2_opts* o) {
   o->stop_level = 0;
   o->proxy_margin = 0.3;
   o->matvec_emulation = 1;
+  o->ldlt = 1;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
@@ -256,7 +263,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
       o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
       o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1 ||
       o->eig_solver < 0 || o->eig_solver > 2 || o->stop_level < 0 || o->matvec_emulation < 0 ||
-      o->matvec_emulation > 2)
+      o->matvec_emulation > 2 || o->ldlt < 0 || o->ldlt > 1)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -269,6 +276,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
   c.eig_solver = o->eig_solver;
   c.stop_level = o->stop_level;
   c.matvec_emulation = o->matvec_emulation;
+  c.ldlt = o->ldlt;
   c.profile = o->profile;
   ctx->c.graphs.clear();
   return H2_OK;
@@ -305,7 +313,7 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2 ||
       x->c.opts.gram_emulation < 0 || x->c.opts.gram_emulation > 1 || x->c.opts.eig_solver < 0 ||
       x->c.opts.eig_solver > 2 || x->c.opts.stop_level < 0 || x->c.opts.matvec_emulation < 0 ||
-      x->c.opts.matvec_emulation > 2) {
+      x->c.opts.matvec_emulation > 2 || x->c.opts.ldlt < 0 || x->c.opts.ldlt > 1) {
     delete x;
     g_err = "h2_build: bad options";
     return H2_EINVAL;
@@ -980,7 +988,7 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
     << ",\"flops_factor\":" << c.stats.flops_factor
     << ",\"launches_factor\":" << c.stats.launches_factor << ",\"launches_solve\":" << c.stats.launches_solve
     << ",\"refine_iters\":" << c.stats.refine_iters << ",\"refine_resid\":" << c.stats.refine_resid
-    << ",\"symmetric\":" << (c.H.symmetric ? 1 : 0) << ",\"dev_bytes\":" << c.dev_bytes << ",\"dev_peak\":" << c.dev_peak << ",\"root_n\":" << c.root.n
+    << ",\"symmetric\":" << (c.H.symmetric ? 1 : 0) << ",\"ldlt\":" << (c.fac_ldlt ? 1 : 0) << ",\"dev_bytes\":" << c.dev_bytes << ",\"dev_peak\":" << c.dev_peak << ",\"root_n\":" << c.root.n
     << ",\"build_rank_max\":[";
   for (int l = c.H.l0; l <= c.H.L; ++l) {
     int mx = 0;
@@ -998,7 +1006,10 @@ h2_status h2_stats(const h2_ctx* ctx, char* json, size_t cap) {
     for (const DevBuf* b : {&c.root.R, &c.root.piv, &c.root.Linv, &c.root.Uinv, &c.root.Rinv}) kept += b->bytes;
     for (const DevBuf* b : {&c.fill_pp[0], &c.fill_pp[1], &c.B_pp[0], &c.B_pp[1], &c.Vp_pp[0], &c.Vp_pp[1]})
       work += b->bytes;
+    size_t near_bytes = 0;
+    for (const LevelF& F : c.lev) near_bytes += F.near_elems * esz(c.prec);
     o << "\"h2\":" << h2 << ",\"factors\":" << kept << ",\"level_work\":" << work
+      << ",\"near_blocks\":" << near_bytes
       << ",\"other\":" << (c.dev_bytes > h2 + kept + work ? c.dev_bytes - h2 - kept - work : 0);
   }
   o << "},\"levels\":[";

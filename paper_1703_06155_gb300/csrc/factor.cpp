@@ -185,6 +185,7 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   }
   F.l = l;
   F.nc = nc;
+  F.sym = c.fac_ldlt;
   F.n = n;
   F.k0 = H.rank[l];
   F.kt = F.k0;
@@ -210,12 +211,26 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
   // near-field blocks (inadmissible at this level)
   F.near_pairs = H.part.inad[l];
   size_t tot = 0;
+  // block LDL^T: the stored block of the pair {a, b} is (min, max)
+  auto alias_of = [&](const std::unordered_map<int64_t, int>& ids, int a, int b) {
+    auto it = ids.find(pkey(b, a));
+    if (it == ids.end()) fail(H2_EINTERNAL, "block LDL^T: pair without its transpose");
+    return it->second;
+  };
+  F.near_off.assign(F.near_pairs.size(), 0);
   for (size_t q = 0; q < F.near_pairs.size(); ++q) {
     const auto [a, b] = F.near_pairs[q];
     F.near_id[pkey(a, b)] = (int)q;
-    F.near_off.push_back(tot);
+    if (F.sym && a > b) continue;
+    F.near_off[q] = tot;
     tot += (size_t)n[a] * n[b];
   }
+  if (F.sym)
+    for (size_t q = 0; q < F.near_pairs.size(); ++q) {
+      const auto [a, b] = F.near_pairs[q];
+      if (a > b) F.near_off[q] = F.near_off[alias_of(F.near_id, a, b)];
+    }
+  F.near_elems = tot;
   dev_ensure(c, F.near_buf, tot * es);
   // fill-in blocks: every Schur target outside the near field, plus the
   // fill-ins carried up from the children of pushed blocks
@@ -233,8 +248,15 @@ void setup_level(Ctx& c, LevelF& F, int l, const std::vector<int>& n, const std:
     F.fill_off.push_back(tot);
     F.fill_live.push_back(cs.count(F.fill_pairs[q]) ? 1 : 0);
     F.fill_is_adm.push_back(c.adm_id[l].count(pkey(a, b)) ? 1 : 0);
+    if (F.sym && a > b) continue;
     tot += (size_t)n[a] * n[b];
   }
+  if (F.sym)
+    for (size_t q = 0; q < F.fill_pairs.size(); ++q) {
+      const auto [a, b] = F.fill_pairs[q];
+      if (a > b) F.fill_off[q] = F.fill_off[alias_of(F.fill_id, a, b)];
+    }
+  F.fill_elems = tot;
   F.fill_row.assign(nc, {});
   F.fill_col.assign(nc, {});
   for (size_t q = 0; q < F.fill_pairs.size(); ++q) {
@@ -436,9 +458,13 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         cd* Sq = S[q];
         // trace(M) = sum of ||F||_F^2 over the row (and column) fill-ins
         const int b0 = (int)fb.size();
+        // block LDL^T: a row fill-in (i, k), k < i, is the transposed stored
+        // (k, i) and enters in the column form
+        auto tr = [&](int k) { return F.sym && f.i > k; };
         for (int id : f.rowf) {
           const int k = F.fill_pairs[id].second, lo = lo_of(q, k);
-          fb.push_back(FrobBlock{FB(q, id) + (size_t)lo * n * es, n, n, F.n[k] - lo});
+          if (tr(k)) fb.push_back(FrobBlock{FB(q, id) + (size_t)lo * es, F.n[k], F.n[k] - lo, n});
+          else fb.push_back(FrobBlock{FB(q, id) + (size_t)lo * n * es, n, n, F.n[k] - lo});
         }
         if (!sym)
           for (int id : f.colf) {
@@ -458,7 +484,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           for (int id : f.rowf) {
             const int k = F.fill_pairs[id].second, lo = lo_of(q, k), w = F.n[k] - lo;
             gX.task(Xb + (size_t)off * p * es, p, p, w, 1.0, 0.0);
-            gX.pair(VA, n, OP_H, FB(q, id) + (size_t)lo * n * es, n, OP_N, n);
+            if (tr(k)) gX.pair(VA, n, OP_H, FB(q, id) + (size_t)lo * es, F.n[k], OP_T, n);
+            else gX.pair(VA, n, OP_H, FB(q, id) + (size_t)lo * n * es, n, OP_N, n);
             gX.close();
             off += w;
           }
@@ -485,8 +512,13 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
           gM.task(Sq + f.M, n, n, n, 1.0, 0.0);
           for (int id : f.rowf) {
             const int k = F.fill_pairs[id].second, lo = lo_of(q, k);
-            char* A = FB(q, id) + (size_t)lo * n * es;
-            gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
+            if (tr(k)) {
+              char* A = FB(q, id) + (size_t)lo * es;
+              gM.pair(A, F.n[k], OP_T, A, F.n[k], OP_C, F.n[k] - lo);
+            } else {
+              char* A = FB(q, id) + (size_t)lo * n * es;
+              gM.pair(A, n, OP_N, A, n, OP_H, F.n[k] - lo);
+            }
           }
           if (!sym)
             for (int id : f.colf) {
@@ -798,23 +830,26 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     for (int i : *jobs[q].bt) {
       const int n = F.n[i], m = F.m[i];
       const char* Q = P[q].Q + F.Q_off[i] * es;
+      // block LDL^T: only the stored block of each pair is transformed; the
+      // row transform of (i, j), j < i, is the column transform of (j, i)
       for (int j : F.nbrs[i]) {
         if (j == i) {
           L2.add(Q, n, OP_H, NB(q, i, i), n, n, n, 0);
           R2.add(Q, n, OP_C, NB(q, i, i), n, n, n, 0);
         } else {
           const int lo = lo_of(q, j);
-          L2.add(Q, n, OP_H, NB(q, i, j) + (size_t)lo * n * es, n, n, F.n[j] - lo, 0);
-          R2.add(Q, n, OP_C, NB(q, j, i) + (size_t)lo * es, F.n[j], n, F.n[j] - lo, 0);
+          if (!F.sym || i < j) L2.add(Q, n, OP_H, NB(q, i, j) + (size_t)lo * n * es, n, n, F.n[j] - lo, 0);
+          if (!F.sym || i > j) R2.add(Q, n, OP_C, NB(q, j, i) + (size_t)lo * es, F.n[j], n, F.n[j] - lo, 0);
         }
       }
       for (int id : F.fill_row[i]) {
         if (!F.fill_live[id]) continue;
         const int b = F.fill_pairs[id].second, lo = lo_of(q, b);
-        L2.add(Q, n, OP_H, FB(q, id) + (size_t)lo * n * es, n, n, F.n[b] - lo, m);
+        if (F.sym && i > b) R2.add(Q, n, OP_C, FB(q, id) + (size_t)lo * es, F.n[b], n, F.n[b] - lo, m);
+        else L2.add(Q, n, OP_H, FB(q, id) + (size_t)lo * n * es, n, n, F.n[b] - lo, m);
       }
       for (int id : F.fill_col[i]) {
-        if (!F.fill_live[id]) continue;
+        if (F.sym || !F.fill_live[id]) continue;
         const int a = F.fill_pairs[id].first, lo = lo_of(q, a);
         R2.add(Q, n, OP_C, FB(q, id) + (size_t)lo * es, F.n[a], n, F.n[a] - lo, m);
       }
@@ -857,24 +892,81 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     ck(lu_blocked(lc.st.ptr<LuTask>(i0), (int)lu.size(), maxm, prec, (int*)lc.statusbuf.p, lc.stream), "lu");
     lc.launches++;
   }
-  ApplyBatch PL, PR;
-  for (size_t q = 0; q < nj; ++q) {
-    const LevelF& F = *jobs[q].F;
-    for (int i : *jobs[q].bt) {
-      const int n = F.n[i], m = F.m[i];
-      if (m <= 0) continue;
-      const char* Linv = P[q].inv + F.inv_off[i] * es;
-      const char* Uinv = Linv + (size_t)n * n * es;
-      for (int j : F.nbrs[i]) {
-        const int lo = (j == i) ? m : lo_of(q, j);
-        PL.add(Linv, m, OP_N, NB(q, i, j) + (size_t)lo * n * es, n, m, F.n[j] - lo, 0);
-        PR.add(Uinv, m, OP_N, NB(q, j, i) + (size_t)lo * es, F.n[j], m, F.n[j] - lo, 0);
+  // Block LU: the panels L^{-1}P Z_i'c and Z_ci' U^{-1} in place (Alg. 4).
+  // Block LDL^T (all jobs of a group share the form): F^{-1} = U^{-1} L^{-1}P
+  // replaces L^{-1}P in its slot, the block row Z_i'c stays raw, and
+  // W_ik = F^{-1} Z_i'k (a workspace) is the right operand of the Schur
+  // updates S_jk -= Z_ji' W_ik, formed for the stored pairs j <= k only.
+  const bool sym = jobs[0].F->sym;
+  double f3 = 0;
+  std::vector<std::unordered_map<int64_t, size_t>> woff(nj);
+  char* Wb = nullptr;
+  if (sym) {
+    GemmBatch gf, gw;
+    CopyBatch cf;
+    lscr = 0;
+    size_t wt = 0;
+    for (size_t q = 0; q < nj; ++q) {
+      const LevelF& F = *jobs[q].F;
+      for (int i : *jobs[q].bt) {
+        const int n = F.n[i], m = F.m[i];
+        if (m <= 0) continue;
+        char* Linv = P[q].inv + F.inv_off[i] * es;
+        const char* Uinv = Linv + (size_t)n * n * es;
+        gf.task(lsc + lscr * es, m, m, m, 1.0, 0.0);
+        gf.pair(Uinv, m, OP_N, Linv, m, OP_N, m);
+        gf.close();
+        cf.add(lsc + lscr * es, prec, m, m, m, Linv, prec, m, m, m);
+        lscr += (size_t)m * m;
+        for (int k : F.nbrs[i]) {
+          const int clo = (k == i) ? m : lo_of(q, k);
+          woff[q][pkey(i, k)] = wt;
+          wt += (size_t)m * (F.n[k] - clo);
+        }
       }
     }
+    run_gemm(lc, gf, prec, prec, prec, "F^-1");
+    run_copy(lc, cf, "F^-1 copy");
+    Wb = (char*)dev_ensure(lc, lc.ldlt_w, (wt + 1) * es);
+    for (size_t q = 0; q < nj; ++q) {
+      const LevelF& F = *jobs[q].F;
+      for (int i : *jobs[q].bt) {
+        const int n = F.n[i], m = F.m[i];
+        if (m <= 0) continue;
+        const char* Fi = P[q].inv + F.inv_off[i] * es;
+        for (int k : F.nbrs[i]) {
+          const int clo = (k == i) ? m : lo_of(q, k);
+          gw.task(Wb + woff[q].at(pkey(i, k)) * es, m, m, F.n[k] - clo, 1.0, 0.0);
+          if (i > k)  // Z_i'k = rows clo.. of the stored (k, i), transposed
+            gw.pair(Fi, m, OP_N, NB(q, i, k) + (size_t)clo * es, F.n[k], OP_T, m);
+          else
+            gw.pair(Fi, m, OP_N, NB(q, i, k) + (size_t)clo * n * es, n, OP_N, m);
+          gw.close();
+        }
+      }
+    }
+    run_gemm(lc, gw, prec, prec, prec, "F^-1 Z");
+    f3 = (gf.flops + gw.flops) / (double)nj;
+  } else {
+    ApplyBatch PL, PR;
+    for (size_t q = 0; q < nj; ++q) {
+      const LevelF& F = *jobs[q].F;
+      for (int i : *jobs[q].bt) {
+        const int n = F.n[i], m = F.m[i];
+        if (m <= 0) continue;
+        const char* Linv = P[q].inv + F.inv_off[i] * es;
+        const char* Uinv = Linv + (size_t)n * n * es;
+        for (int j : F.nbrs[i]) {
+          const int lo = (j == i) ? m : lo_of(q, j);
+          PL.add(Linv, m, OP_N, NB(q, i, j) + (size_t)lo * n * es, n, m, F.n[j] - lo, 0);
+          PR.add(Uinv, m, OP_N, NB(q, j, i) + (size_t)lo * es, F.n[j], m, F.n[j] - lo, 0);
+        }
+      }
+    }
+    run_apply_auto(lc, PL, true, prec, "U panels");
+    run_apply_auto(lc, PR, false, prec, "L panels");
+    f3 = (PL.flops + PR.flops) / (double)nj;
   }
-  run_apply_auto(lc, PL, true, prec, "U panels");
-  run_apply_auto(lc, PR, false, prec, "L panels");
-  const double f3 = (PL.flops + PR.flops) / (double)nj;
 
   GemmBatch gs;
   auto hsS = std::make_unique<HostScope>(lc, "schur-plan");
@@ -890,7 +982,8 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     for (int i : bt) {
       if (F.m[i] <= 0) continue;
       for (int j : F.nbrs[i])
-        for (int k : F.nbrs[i]) tgl.emplace_back(pkey(j, k), i);
+        for (int k : F.nbrs[i])
+          if (!sym || j <= k) tgl.emplace_back(pkey(j, k), i);
     }
     std::stable_sort(tgl.begin(), tgl.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     const double fl0 = gs.flops;
@@ -910,12 +1003,20 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         const int id = F.fill_id.at(key);
         C = FB(q, id);
         F.fill_live[id] = 1;
+        if (sym) F.fill_live[F.fill_id.at(pkey(k, j))] = 1;
       }
       gs.task(C + ((size_t)rlo + (size_t)clo * nj_) * es, nj_, nj_ - rlo, nk - clo, -1.0, 1.0);
       for (size_t u = g0; u < g1; ++u) {
         const int i = tgl[u].second;
         const int ni = F.n[i], mi = F.m[i];
-        gs.pair(NB(q, j, i) + (size_t)rlo * es, nj_, OP_N, NB(q, i, k) + (size_t)clo * ni * es, ni, OP_N, mi);
+        if (!sym) {
+          gs.pair(NB(q, j, i) + (size_t)rlo * es, nj_, OP_N, NB(q, i, k) + (size_t)clo * ni * es, ni, OP_N, mi);
+        } else {
+          // Z_ji' = rows rlo.. of the logical (j, i): the stored (i, j) transposed when j > i
+          const char* W = Wb + woff[q].at(pkey(i, k)) * es;
+          if (j > i) gs.pair(NB(q, i, j) + (size_t)rlo * ni * es, ni, OP_T, W, mi, OP_N, mi);
+          else gs.pair(NB(q, j, i) + (size_t)rlo * es, nj_, OP_N, W, mi, OP_N, mi);
+        }
       }
       gs.close();
       g0 = g1;
@@ -944,8 +1045,22 @@ void merge_level(Ctx& c, LevelF& F, LevelF& Pn, CopyBatch& as, CopyBatch& ac) {
   Ptrs S = ptrs(c, F), D = ptrs(c, Pn);
   auto NBs = [&](int a, int b) { return S.near + F.near_off.at(F.near_id.at(pkey(a, b))) * es; };
   auto ro = [&](int a) { return (a & 1) ? F.kt[a - 1] : 0; };
+  // kept part of the level's block (a, b) into dst (kt_a x kt_b, leading
+  // dimension ld), assigned or accumulated; block LDL^T: (a, b), a > b, is
+  // the stored (b, a) transposed
+  auto kept_copy = [&](CopyBatch& cb, const char* base, size_t off, int a, int b, char* d, int ld, int mode) {
+    if (F.sym && a > b) {
+      cb.add(base + (off + (size_t)F.m[b] + (size_t)F.m[a] * F.n[b]) * es, prec, F.n[b], F.kt[a], F.kt[b], d, prec,
+             ld, F.kt[a], F.kt[b], mode);
+      cb.t.back().transpose = 1;
+    } else {
+      cb.add(base + (off + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a], F.kt[a], F.kt[b], d, prec,
+             ld, F.kt[a], F.kt[b], mode);
+    }
+  };
   for (size_t q = 0; q < Pn.near_pairs.size(); ++q) {
     const auto [p, r] = Pn.near_pairs[q];
+    if (Pn.sym && p > r) continue;
     char* dst = D.near + Pn.near_off[q] * es;
     const int ld = Pn.n[p];
     for (int a = 2 * p; a <= 2 * p + 1; ++a)
@@ -953,22 +1068,22 @@ void merge_level(Ctx& c, LevelF& F, LevelF& Pn, CopyBatch& as, CopyBatch& ac) {
         char* d = dst + ((size_t)ro(a) + (size_t)ro(b) * ld) * es;
         const int64_t key = pkey(a, b);
         if (F.near_id.count(key)) {
-          as.add(NBs(a, b) + ((size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a], F.kt[a], F.kt[b], d, prec,
-                 ld, F.kt[a], F.kt[b]);
+          kept_copy(as, S.near, F.near_off[F.near_id.at(key)], a, b, d, ld, 0);
         } else {
           const int idx = c.adm_id[l].at(key);
           as.add((char*)c.dS.p + c.S_off[l][idx] * sizeof(cd), P64, F.k0[a], F.k0[a], F.k0[b], d, prec, ld, F.kt[a],
                  F.kt[b]);
           auto it = F.fill_id.find(key);
           if (it != F.fill_id.end() && F.fill_live[it->second])
-            ac.add(S.fill + (F.fill_off[it->second] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a],
-                   F.kt[a], F.kt[b], d, prec, ld, F.kt[a], F.kt[b], 1);
+            kept_copy(ac, S.fill, F.fill_off[it->second], a, b, d, ld, 1);
         }
       }
   }
   for (size_t q = 0; q < F.fill_pairs.size(); ++q) {
     if (!F.fill_live[q] || F.fill_is_adm[q]) continue;
     const auto [a, b] = F.fill_pairs[q];
+    if (F.sym && a > b) continue;  // the stored (b, a) carries it
+    if (F.sym && a / 2 == b / 2) fail(H2_EINTERNAL, "block LDL^T: pushed fill-in between siblings");
     const int id = Pn.fill_id.at(pkey(a / 2, b / 2));
     const int ld = Pn.n[a / 2];
     char* d = D.fill + (Pn.fill_off[id] + (size_t)ro(a) + (size_t)ro(b) * ld) * es;
@@ -1031,9 +1146,19 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
       for (int b = 0; b < F.nc; ++b) {
         char* d = Rm + ((size_t)off[a] + (size_t)off[b] * n) * es;
         const int64_t key = pkey(a, b);
+        // kept part of (a, b); block LDL^T: (a, b), a > b, is the stored (b, a) transposed
+        auto kept_copy = [&](CopyBatch& cb, const char* base, size_t o, int mode) {
+          if (F.sym && a > b) {
+            cb.add(base + (o + (size_t)F.m[b] + (size_t)F.m[a] * F.n[b]) * es, prec, F.n[b], F.kt[a], F.kt[b], d,
+                   prec, n, F.kt[a], F.kt[b], mode);
+            cb.t.back().transpose = 1;
+          } else {
+            cb.add(base + (o + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a], F.kt[a], F.kt[b], d,
+                   prec, n, F.kt[a], F.kt[b], mode);
+          }
+        };
         if (F.near_id.count(key)) {
-          as.add(S.near + (F.near_off[F.near_id.at(key)] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec,
-                 F.n[a], F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b]);
+          kept_copy(as, S.near, F.near_off[F.near_id.at(key)], 0);
         } else {
           auto ai = c.adm_id[l].find(key);
           if (ai != c.adm_id[l].end()) {
@@ -1048,9 +1173,7 @@ void root_factor_group(Ctx& lc, const std::vector<Ctx*>& cs) {
                    F.kt[a], F.kt[b]);
           }
           auto it = F.fill_id.find(key);
-          if (it != F.fill_id.end() && F.fill_live[it->second])
-            ac.add(S.fill + (F.fill_off[it->second] + (size_t)F.m[a] + (size_t)F.m[b] * F.n[a]) * es, prec, F.n[a],
-                   F.kt[a], F.kt[b], d, prec, n, F.kt[a], F.kt[b], 1);
+          if (it != F.fill_id.end() && F.fill_live[it->second]) kept_copy(ac, S.fill, F.fill_off[it->second], 1);
         }
       }
     const int nb = R.nb;
@@ -1264,7 +1387,12 @@ void check_status(Ctx& c) {
 void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
   const auto t0 = std::chrono::steady_clock::now();
   Ctx& lc = *cs[0];
+  // block LDL^T (h2_opts.ldlt) when every instance asks for it and is
+  // complex symmetric (the launches of a group share one form), else block LU
+  bool ldlt = true;
+  for (Ctx* c : cs) ldlt = ldlt && c->opts.ldlt != 0 && c->H.symmetric;
   for (Ctx* c : cs) {
+    c->fac_ldlt = ldlt;
     c->stream = lc.stream;
     c->epoch++;
     c->factored = false;
@@ -1303,6 +1431,7 @@ void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
       const size_t es = esz(prec);
       for (size_t q = 0; q < F.near_pairs.size(); ++q) {
         const auto [a, b] = F.near_pairs[q];
+        if (F.sym && a > b) continue;
         cb.add((const cd*)c.dD.p + c.D_off[q], P64, n[a], n[a], n[b], (char*)F.near_buf.p + F.near_off[q] * es, prec,
                n[a], n[a], n[b]);
       }

@@ -163,6 +163,10 @@ struct Stager {
 // Factor data of one level.
 struct LevelF {
   int l = 0, nc = 0;
+  // block LDL^T form (h2_opts.ldlt): pairs (a, b) with a > b are not stored;
+  // their offsets point at the stored (b, a), read transposed
+  bool sym = false;
+  size_t near_elems = 0, fill_elems = 0;      // stored entries
   std::vector<int> n, k0, kt, m;
   std::vector<std::vector<int>> nbrs;          // near lists incl. self
   std::vector<std::vector<int>> batches;       // elimination batches
@@ -262,6 +266,7 @@ struct Ctx {
   std::vector<std::unordered_map<int64_t, int>> adm_id;  // [l] pair -> idx
   // factorization
   bool factored = false, inverted = false;
+  bool fac_ldlt = false;  // the factors are in block LDL^T form (h2_opts.ldlt)
   int prec = 0;
   double eps_fill = 0;
   // CUDA-graph replay of solves: a graph is valid while no device buffer of
@@ -275,6 +280,7 @@ struct Ctx {
   DevBuf scratch, scratch2, vecbuf, vecbuf2, vecbuf3, normbuf, statusbuf, gemm_ws, jac_buf, applybuf, frobbuf;
   DevBuf fill_pp[2], B_pp[2], Vp_pp[2];  // per-level working arenas, by level parity
   DevBuf lu_scr;                         // partial-LU inversion scratch of one batch
+  DevBuf ldlt_w;                         // block LDL^T: F^-1 Z_i'k of one batch
   Stager st;
   Stats stats;
   int64_t launches = 0;

@@ -175,8 +175,8 @@ void matvec_tree(Ctx& c, const cd* x, cd* y, int nrhs, bool adj) { matvec_tree_g
 
 // Explicit factor-form inverse (eq. 35): the diagonal inverses L^{-1}P and
 // U^{-1} and the inverse of the final block exist after the factorization;
-// add -U^{-1} U_ik for every U panel, so the backward sweep is matrix-vector
-// products only.
+// add -U^{-1} U_ik for every U panel (-F^{-1} Z_i'k for block LDL^T factors),
+// so the backward sweep is matrix-vector products only.
 
 void invert(Ctx& c) {
   if (!c.factored) fail(H2_ESTATE, "invert before factorize");
@@ -198,13 +198,17 @@ void invert(Ctx& c) {
     for (int i = 0; i < F.nc; ++i) {
       const int mi = F.m[i], ni = F.n[i];
       if (mi <= 0) continue;
-      const char* Uinv = (char*)F.inv_buf.p + (F.inv_off[i] + (size_t)ni * ni) * es;
+      // LU: -U^{-1} (L^{-1}P Z_i'k); block LDL^T: -F^{-1} Z_i'k (F^{-1} in the L^{-1}P slot)
+      const char* Uinv = (char*)F.inv_buf.p + (F.inv_off[i] + (F.sym ? 0 : (size_t)ni * ni)) * es;
       for (size_t q = 0; q < F.nbrs[i].size(); ++q) {
         const int k = F.nbrs[i][q];
         const int clo = (k == i) ? F.m[i] : (F.batch_of[k] < F.batch_of[i] ? F.m[k] : 0);
+        const char* blk = (char*)F.near_buf.p + F.near_off.at(F.near_id.at(pkey(i, k))) * es;
         g.task(Ub + F.Ub_off[F.nbr_first[i] + q] * es, mi, mi, F.n[k] - clo, -1.0, 0.0);
-        g.pair(Uinv, mi, OP_N,
-               (char*)F.near_buf.p + (F.near_off.at(F.near_id.at(pkey(i, k))) + (size_t)clo * ni) * es, ni, OP_N, mi);
+        if (F.sym && i > k)  // Z_i'k = rows clo.. of the stored (k, i), transposed
+          g.pair(Uinv, mi, OP_N, blk + (size_t)clo * es, F.n[k], OP_T, mi);
+        else
+          g.pair(Uinv, mi, OP_N, blk + (size_t)clo * ni * es, ni, OP_N, mi);
         g.close();
       }
     }

@@ -161,6 +161,7 @@ void root_solve_grouped(Ctx& lc, const std::vector<Ctx*>& cs, const std::vector<
 struct SolveVecs {
   std::vector<Vec> vec;  // vec[0] = x itself (tree order, ld N)
   Vec vr;                // final-block vector
+  Vec vt;                // block LDL^T: F^{-1} y of the batch's clusters
 };
 
 // Forward (Algorithm 5) / backward (Algorithm 6) substitution, or the adjoint
@@ -189,11 +190,19 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
     }
     const size_t roff = tot;
     tot += (size_t)c.root.n * nrhs;
+    // block LDL^T: F^{-1} y_i' of a batch, laid out like a level vector
+    int64_t tld = 0;
+    if (c.fac_ldlt)
+      for (const LevelF& F : c.lev) tld = std::max(tld, F.vlen);
+    const size_t toff = tot;
+    tot += (size_t)tld * nrhs;
     char* buf = (char*)dev_ensure(c, c.vecbuf, (tot + 1) * es);
     sv[q].vec.resize(nlev);
     sv[q].vec[0] = Vec{(char*)xs[q], c.H.tree.N};
     for (int li = 1; li < nlev; ++li) sv[q].vec[li] = Vec{buf + off[li] * es, c.lev[li].vlen};
     sv[q].vr = Vec{buf + roff * es, c.root.n};
+    sv[q].vt = Vec{buf + toff * es, tld};
+    if (adjoint && c.fac_ldlt) fail(H2_EINTERNAL, "block LDL^T factors: adjoint sweeps are not used");
   }
   auto has = [&](size_t q, int d) { return d < (int)cs[q]->lev.size(); };
   auto top = [&](size_t q) { return (int)cs[q]->lev.size() - 1; };
@@ -269,16 +278,24 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
     for (int d = 0; d < depth; ++d) {
       for (int b = 0; b < nbat(d); ++b) {
         ApplyBatch a1, a2;
-        GemmBatch g;
+        GemmBatch g, gt;
         for (size_t q = 0; q < nq; ++q) {
           if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
           Ctx& c = *cs[q];
           const LevelF& F = c.lev[d];
-          const Vec v = sv[q].vec[d];
+          const Vec v = sv[q].vec[d], vt = sv[q].vt;
           const auto& bt = F.batches[b];
           for (int i : bt) {
             a1.add(Q(F, i), F.n[i], OP_H, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
-            if (F.m[i] > 0) a2.add(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
+            if (F.m[i] <= 0) continue;
+            if (!F.sym) {
+              a2.add(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
+            } else {
+              // block LDL^T: t_i = F^{-1} y_i' (the slot of L^{-1}P holds F^{-1}); y_i' stays
+              gt.task(seg(vt, F, i, 0), (int)vt.ld, F.m[i], nrhs, 1.0, 0.0);
+              gt.pair(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
+              gt.close();
+            }
           }
           std::map<int, std::vector<int>> tg;
           for (int i : bt)
@@ -287,13 +304,22 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
           for (auto& [j, cl] : tg) {
             const int rlo = lo_at(F, j, cl[0]);
             g.task(seg(v, F, j, rlo), (int)v.ld, F.n[j] - rlo, nrhs, -1.0, 1.0);
-            for (int i : cl)
-              g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_N, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
+            for (int i : cl) {
+              if (!F.sym)
+                g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_N, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
+              else if (j > i)  // Z_ji' = the stored (i, j) transposed
+                g.pair(NBp(c, F, j, i) + (size_t)rlo * F.n[i] * es, F.n[i], OP_T, seg(vt, F, i, 0), (int)vt.ld,
+                       OP_N, F.m[i]);
+              else
+                g.pair(NBp(c, F, j, i) + (size_t)rlo * es, F.n[j], OP_N, seg(vt, F, i, 0), (int)vt.ld, OP_N,
+                       F.m[i]);
+            }
             g.close();
           }
         }
         run_apply_narrow(lc, a1, prec, "fwd Q^H");
         run_apply_narrow(lc, a2, prec, "fwd L^-1");
+        run_gemm(lc, gt, prec, prec, prec, "fwd F^-1");
         run_gemm(lc, g, prec, prec, prec, "fwd update");
       }
       merge(d, true);
@@ -316,11 +342,16 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
             const int mi = F.m[i];
             if (mi <= 0) continue;
             if (!use_inverse) {
+              // LU: y_i' -= (L^{-1}P Z_i'k) x_k; block LDL^T: y_i' -= Z_i'k x_k
               g.task(seg(v, F, i, 0), (int)v.ld, mi, nrhs, -1.0, 1.0);
               for (int k : F.nbrs[i]) {
                 const int clo = lo_at(F, k, i);
-                g.pair(NBp(c, F, i, k) + (size_t)clo * F.n[i] * es, F.n[i], OP_N, seg(v, F, k, clo), (int)v.ld, OP_N,
-                       F.n[k] - clo);
+                if (F.sym && i > k)  // the stored (k, i) transposed
+                  g.pair(NBp(c, F, i, k) + (size_t)clo * es, F.n[k], OP_T, seg(v, F, k, clo), (int)v.ld, OP_N,
+                         F.n[k] - clo);
+                else
+                  g.pair(NBp(c, F, i, k) + (size_t)clo * F.n[i] * es, F.n[i], OP_N, seg(v, F, k, clo), (int)v.ld,
+                         OP_N, F.n[k] - clo);
               }
               g.close();
             } else {
@@ -334,7 +365,8 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
               }
               g.close();
             }
-            a1.add(Uinv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+            // x_i' = U^{-1} (...) (LU) or F^{-1} (...) (block LDL^T, F^{-1} in the L^{-1}P slot)
+            a1.add(F.sym ? Linv(F, i) : Uinv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
           }
           for (int i : bt) a2.add(Q(F, i), F.n[i], OP_C, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
         }
