@@ -319,6 +319,18 @@ def test_ldlt_matches_lu_form_and_halves_the_blocks():
         assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-12
 
 
+def test_ldlt_early_stop_and_percell_contrast_exact():
+    # per-cell contrast keeps Z = D^1/2 A D^-1/2 symmetric (R12), and an early
+    # stop (Sec. III-C) assembles its final block from the one-sided store:
+    # both stay exact at eps_fill = 0
+    for Hm, Zh, stop in ((h2_problem(12, 64, 1e-6, percell_seed=3), h2_dense(12, 64, 1e-6, percell_seed=3), None),
+                         (h2_problem(12, 64, 1e-6), h2_dense(12, 64, 1e-6), 4)):
+        Fz = factor.factorize(Hm, 0.0, "colored", stop_level=stop, symmetric=True)
+        b = inputs.rhs_gaussian(Hm.tree.N, 1, 7)[:, 0]
+        xe = np.linalg.solve(Zh, b)
+        assert np.linalg.norm(factor.solve(Fz, b) - xe) / np.linalg.norm(xe) < 1e-11
+
+
 def test_ldlt_refinement_from_complex64_bulk():
     # the mixed-precision emulation (complex64 bulk) of the symmetric form,
     # refined with the FP64 H^2 matvec, reaches the dense solution
