@@ -142,10 +142,11 @@ typedef struct {
                             block LU otherwise; 0 block LU always (eq. 34,
                             both panels L^-1 P Z_i'c and Z_ci' U^-1 kept).
                             LDL^T keeps one block of each off-diagonal
-                            pair, the raw block row Z_i'c and
-                            F^-1 = (Z_i'i')^-1 as the factor, and forms the
-                            Schur updates of one triangle of the target
-                            pairs: the same Step-0 decisions and solution
+                            pair, the raw block row Z_i'c and the pivoted
+                            LU of F = Z_i'i' as the factor (F^-1 applied
+                            as U^-1 L^-1 P), and forms the Schur updates of
+                            one triangle of the target pairs: the same
+                            Step-0 decisions and solution
                             as LU in exact arithmetic with about half the
                             near-field factor memory; h2_stats "ldlt"
                             reports the form of the last factorization    */

@@ -51,7 +51,8 @@ Readings of the paper where it is silent or ambiguous:
      Z = [I 0; B F^-1 I] [F 0; 0 S] [I F^-1 B^T; 0 I], S = C - B F^-1 B^T
      with B = Z_(rest) i' = (Z_i' (rest))^T: the factor keeps the raw block
      row Z_i'(rest) once instead of the two panels L^-1 P Z_i'c and
-     Z_ci' U^-1, and S is formed for one triangle of target pairs.  In exact
+     Z_ci' U^-1, F^-1 is applied through the pivoted LU of F (L^-1 P, then
+     U^-1), and S is formed for one triangle of target pairs.  In exact
      arithmetic the Schur complements, hence the rank decisions and the
      solution, equal those of the LU form.
 """
@@ -66,7 +67,7 @@ class ClusterFactor:
     """Factor data of one cluster at one level (the non-identity parts of
     Q_i^l, L_i^l and U_i^l in eq. 34)."""
 
-    __slots__ = ("n", "kt", "m", "Q", "LU", "piv", "Up", "Lp", "Zr", "Finv")
+    __slots__ = ("n", "kt", "m", "Q", "LU", "piv", "Up", "Lp", "Zr")
 
 
 class LevelFactor:
@@ -277,15 +278,15 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 mi = ni - int(kt[i])
                 cf = ClusterFactor()
                 cf.n, cf.kt, cf.m, cf.Q = ni, int(kt[i]), mi, step01[i][1]
-                cf.Up, cf.Lp, cf.Zr, cf.Finv = {}, {}, {}, None
+                cf.Up, cf.Lp, cf.Zr = {}, {}, {}
                 cf.LU, cf.piv = None, None
                 if mi > 0:
                     LU, piv = dense.lu(near[(i, i)][:mi, :mi])  # eq. (11)
                     LU = _round(LU, bulk)
                     cf.LU, cf.piv = LU, piv
                     if sym:
-                        # R7: F^-1 (from the pivoted LU) and the raw block row
-                        cf.Finv = _round(_uinv(LU, _linv_p(LU, piv, np.eye(mi, dtype=np.complex128))), bulk)
+                        # R7: the raw block row; F^-1 is applied through the
+                        # pivoted LU (L^-1 P, then U^-1)
                         for j in nbrs[i]:
                             cs = slice(mi, ni) if j == i else act(j)
                             cf.Zr[j] = (blk(near, i, j)[:mi, cs].copy(), cs)
@@ -319,7 +320,8 @@ def factorize(H, eps, ordering="colored", bulk=np.complex128, observe=None, stop
                 if cf.m == 0 or not sym:
                     continue
                 # R7: S_jk -= Z_ji' F^-1 Z_i'k for the stored pairs j <= k
-                W = {kk: _round(cf.Finv @ Zk, bulk) for kk, (Zk, _) in cf.Zr.items()}
+                W = {kk: _round(_uinv(cf.LU, _round(_linv_p(cf.LU, cf.piv, Zk), bulk)), bulk)
+                     for kk, (Zk, _) in cf.Zr.items()}
                 for j, (Zj, rs) in cf.Zr.items():
                     for kk, (Zk, cs) in cf.Zr.items():
                         if j <= kk:
@@ -468,8 +470,8 @@ def solve(Fz, b, inverse=None):
             if cf.m > 0 and sym:
                 # L of the block LDL^T (R7): y_i' stays, the rest of the
                 # vector loses B F^-1 y_i' = Z_i'(rest)^T (F^-1 y_i')
-                Fi = cf.Finv if inverse is None else inverse.Finv[li][i]
-                t = Fi @ vec[i][:cf.m]
+                y = vec[i][:cf.m]
+                t = _uinv(cf.LU, _linv_p(cf.LU, cf.piv, y)) if inverse is None else inverse.Finv[li][i] @ y
                 for j, (Zj, rs) in cf.Zr.items():
                     vec[j][rs] -= _transpose(Zj) @ t
             elif cf.m > 0:
@@ -507,7 +509,7 @@ def solve(Fz, b, inverse=None):
                 if inverse is None:
                     for k_, (Zk, cs) in cf.Zr.items():
                         t -= Zk @ vec[k_][cs]
-                    vec[i][:cf.m] = cf.Finv @ t
+                    vec[i][:cf.m] = _uinv(cf.LU, _linv_p(cf.LU, cf.piv, t))
                 else:
                     t = inverse.Finv[li][i] @ t
                     for k_, (Ub, cs) in inverse.Ub[li][i].items():

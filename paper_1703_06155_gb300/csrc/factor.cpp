@@ -893,31 +893,25 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
     lc.launches++;
   }
   // Block LU: the panels L^{-1}P Z_i'c and Z_ci' U^{-1} in place (Alg. 4).
-  // Block LDL^T (all jobs of a group share the form): F^{-1} = U^{-1} L^{-1}P
-  // replaces L^{-1}P in its slot, the block row Z_i'c stays raw, and
-  // W_ik = F^{-1} Z_i'k (a workspace) is the right operand of the Schur
-  // updates S_jk -= Z_ji' W_ik, formed for the stored pairs j <= k only.
+  // Block LDL^T (all jobs of a group share the form): the block row Z_i'c
+  // stays raw, and W_ik = F^{-1} Z_i'k = U^{-1} (L^{-1}P Z_i'k) (a workspace;
+  // the triangular factors applied in turn, as the LU panels apply them: a
+  // product U^{-1} L^{-1}P formed first loses accuracy in complex64 where
+  // the two factors cancel) is the right operand of the Schur updates
+  // S_jk -= Z_ji' W_ik, formed for the stored pairs j <= k only.
   const bool sym = jobs[0].F->sym;
   double f3 = 0;
   std::vector<std::unordered_map<int64_t, size_t>> woff(nj);
   char* Wb = nullptr;
   if (sym) {
-    GemmBatch gf, gw;
-    CopyBatch cf;
-    lscr = 0;
+    GemmBatch gw;
+    ApplyBatch pw;
     size_t wt = 0;
     for (size_t q = 0; q < nj; ++q) {
       const LevelF& F = *jobs[q].F;
       for (int i : *jobs[q].bt) {
-        const int n = F.n[i], m = F.m[i];
+        const int m = F.m[i];
         if (m <= 0) continue;
-        char* Linv = P[q].inv + F.inv_off[i] * es;
-        const char* Uinv = Linv + (size_t)n * n * es;
-        gf.task(lsc + lscr * es, m, m, m, 1.0, 0.0);
-        gf.pair(Uinv, m, OP_N, Linv, m, OP_N, m);
-        gf.close();
-        cf.add(lsc + lscr * es, prec, m, m, m, Linv, prec, m, m, m);
-        lscr += (size_t)m * m;
         for (int k : F.nbrs[i]) {
           const int clo = (k == i) ? m : lo_of(q, k);
           woff[q][pkey(i, k)] = wt;
@@ -925,28 +919,30 @@ void process_batches(Ctx& lc, std::vector<Job>& jobs, double eps) {
         }
       }
     }
-    run_gemm(lc, gf, prec, prec, prec, "F^-1");
-    run_copy(lc, cf, "F^-1 copy");
     Wb = (char*)dev_ensure(lc, lc.ldlt_w, (wt + 1) * es);
     for (size_t q = 0; q < nj; ++q) {
       const LevelF& F = *jobs[q].F;
       for (int i : *jobs[q].bt) {
         const int n = F.n[i], m = F.m[i];
         if (m <= 0) continue;
-        const char* Fi = P[q].inv + F.inv_off[i] * es;
+        const char* Linv = P[q].inv + F.inv_off[i] * es;
+        const char* Uinv = Linv + (size_t)n * n * es;
         for (int k : F.nbrs[i]) {
           const int clo = (k == i) ? m : lo_of(q, k);
-          gw.task(Wb + woff[q].at(pkey(i, k)) * es, m, m, F.n[k] - clo, 1.0, 0.0);
+          char* W = Wb + woff[q].at(pkey(i, k)) * es;
+          gw.task(W, m, m, F.n[k] - clo, 1.0, 0.0);
           if (i > k)  // Z_i'k = rows clo.. of the stored (k, i), transposed
-            gw.pair(Fi, m, OP_N, NB(q, i, k) + (size_t)clo * es, F.n[k], OP_T, m);
+            gw.pair(Linv, m, OP_N, NB(q, i, k) + (size_t)clo * es, F.n[k], OP_T, m);
           else
-            gw.pair(Fi, m, OP_N, NB(q, i, k) + (size_t)clo * n * es, n, OP_N, m);
+            gw.pair(Linv, m, OP_N, NB(q, i, k) + (size_t)clo * n * es, n, OP_N, m);
           gw.close();
+          pw.add(Uinv, m, OP_N, W, m, m, F.n[k] - clo, 0);
         }
       }
     }
-    run_gemm(lc, gw, prec, prec, prec, "F^-1 Z");
-    f3 = (gf.flops + gw.flops) / (double)nj;
+    run_gemm(lc, gw, prec, prec, prec, "L^-1 Z");
+    run_apply_auto(lc, pw, true, prec, "U^-1 W");
+    f3 = (gw.flops + pw.flops) / (double)nj;
   } else {
     ApplyBatch PL, PR;
     for (size_t q = 0; q < nj; ++q) {

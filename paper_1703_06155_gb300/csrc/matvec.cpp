@@ -195,24 +195,32 @@ void invert(Ctx& c) {
       }
     char* Ub = (char*)dev_ensure(c, F.Ub_buf, (tot + 1) * es);
     GemmBatch g;
+    ApplyBatch ua;
     for (int i = 0; i < F.nc; ++i) {
       const int mi = F.m[i], ni = F.n[i];
       if (mi <= 0) continue;
-      // LU: -U^{-1} (L^{-1}P Z_i'k); block LDL^T: -F^{-1} Z_i'k (F^{-1} in the L^{-1}P slot)
-      const char* Uinv = (char*)F.inv_buf.p + (F.inv_off[i] + (F.sym ? 0 : (size_t)ni * ni)) * es;
+      // LU: -U^{-1} (L^{-1}P Z_i'k), the U panel holding L^{-1}P Z_i'k;
+      // block LDL^T: -F^{-1} Z_i'k = -U^{-1} (L^{-1}P Z_i'k) from the raw block
+      const char* Linv = (char*)F.inv_buf.p + F.inv_off[i] * es;
+      const char* Uinv = Linv + (size_t)ni * ni * es;
       for (size_t q = 0; q < F.nbrs[i].size(); ++q) {
         const int k = F.nbrs[i][q];
         const int clo = (k == i) ? F.m[i] : (F.batch_of[k] < F.batch_of[i] ? F.m[k] : 0);
         const char* blk = (char*)F.near_buf.p + F.near_off.at(F.near_id.at(pkey(i, k))) * es;
-        g.task(Ub + F.Ub_off[F.nbr_first[i] + q] * es, mi, mi, F.n[k] - clo, -1.0, 0.0);
-        if (F.sym && i > k)  // Z_i'k = rows clo.. of the stored (k, i), transposed
-          g.pair(Uinv, mi, OP_N, blk + (size_t)clo * es, F.n[k], OP_T, mi);
-        else
+        char* Ubq = Ub + F.Ub_off[F.nbr_first[i] + q] * es;
+        g.task(Ubq, mi, mi, F.n[k] - clo, -1.0, 0.0);
+        if (!F.sym)
           g.pair(Uinv, mi, OP_N, blk + (size_t)clo * ni * es, ni, OP_N, mi);
+        else if (i > k)  // Z_i'k = rows clo.. of the stored (k, i), transposed
+          g.pair(Linv, mi, OP_N, blk + (size_t)clo * es, F.n[k], OP_T, mi);
+        else
+          g.pair(Linv, mi, OP_N, blk + (size_t)clo * ni * es, ni, OP_N, mi);
         g.close();
+        if (F.sym) ua.add(Uinv, mi, OP_N, Ubq, mi, mi, F.n[k] - clo, 0);
       }
     }
     run_gemm(c, g, prec, prec, prec, "inverse panels");
+    run_apply(c, ua, true, prec, "inverse panels U^-1");
   }
   ck(cudaStreamSynchronize(c.stream), "invert sync");
   c.inverted = true;

@@ -277,7 +277,7 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
     // ---------------- forward: L y = b (Algorithm 5) ----------------
     for (int d = 0; d < depth; ++d) {
       for (int b = 0; b < nbat(d); ++b) {
-        ApplyBatch a1, a2;
+        ApplyBatch a1, a2, at;
         GemmBatch g, gt;
         for (size_t q = 0; q < nq; ++q) {
           if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
@@ -291,10 +291,11 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
             if (!F.sym) {
               a2.add(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, F.m[i], nrhs, 0);
             } else {
-              // block LDL^T: t_i = F^{-1} y_i' (the slot of L^{-1}P holds F^{-1}); y_i' stays
+              // block LDL^T: t_i = F^{-1} y_i' = U^{-1} (L^{-1}P y_i'); y_i' stays
               gt.task(seg(vt, F, i, 0), (int)vt.ld, F.m[i], nrhs, 1.0, 0.0);
               gt.pair(Linv(F, i), F.m[i], OP_N, seg(v, F, i, 0), (int)v.ld, OP_N, F.m[i]);
               gt.close();
+              at.add(Uinv(F, i), F.m[i], OP_N, seg(vt, F, i, 0), (int)vt.ld, F.m[i], nrhs, 0);
             }
           }
           std::map<int, std::vector<int>> tg;
@@ -319,7 +320,8 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
         }
         run_apply_narrow(lc, a1, prec, "fwd Q^H");
         run_apply_narrow(lc, a2, prec, "fwd L^-1");
-        run_gemm(lc, gt, prec, prec, prec, "fwd F^-1");
+        run_gemm(lc, gt, prec, prec, prec, "fwd L^-1 y");
+        run_apply_narrow(lc, at, prec, "fwd U^-1 y");
         run_gemm(lc, g, prec, prec, prec, "fwd update");
       }
       merge(d, true);
@@ -331,7 +333,7 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
     for (int d = depth - 1; d >= 0; --d) {
       for (int b = nbat(d) - 1; b >= 0; --b) {
         GemmBatch g;
-        ApplyBatch a1, a2;
+        ApplyBatch a0, a1, a2;
         for (size_t q = 0; q < nq; ++q) {
           if (!has(q, d) || b >= (int)cs[q]->lev[d].batches.size()) continue;
           Ctx& c = *cs[q];
@@ -365,15 +367,18 @@ static void solve_tree_sweeps(const std::vector<Ctx*>& cs, const std::vector<voi
               }
               g.close();
             }
-            // x_i' = U^{-1} (...) (LU) or F^{-1} (...) (block LDL^T, F^{-1} in the L^{-1}P slot)
-            a1.add(F.sym ? Linv(F, i) : Uinv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+            // x_i' = U^{-1} (...) (LU) or F^{-1} (...) = U^{-1} L^{-1}P (...) (block LDL^T)
+            if (F.sym) a0.add(Linv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
+            a1.add(Uinv(F, i), mi, OP_N, seg(v, F, i, 0), (int)v.ld, mi, nrhs, 0);
           }
           for (int i : bt) a2.add(Q(F, i), F.n[i], OP_C, seg(v, F, i, 0), (int)v.ld, F.n[i], nrhs, 0);
         }
         if (!use_inverse) {
           run_gemm(lc, g, prec, prec, prec, "bwd update");
+          run_apply_narrow(lc, a0, prec, "bwd L^-1");
           run_apply_narrow(lc, a1, prec, "bwd U^-1");
         } else {
+          run_apply_narrow(lc, a0, prec, "inv L^-1");
           run_apply_narrow(lc, a1, prec, "inv U^-1");
           run_gemm(lc, g, prec, prec, prec, "inv update");
         }
