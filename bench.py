@@ -63,8 +63,9 @@ def parse():
     p.add_argument("--eig-solver", type=int, default=None, choices=[0, 1, 2],
                    help="Step-0 eigen-decomposition: 0 cyclic Jacobi, 1 tridiagonal + QL, "
                         "2 one-sided Jacobi SVD of the Cholesky factor (default: library's)")
-    p.add_argument("--ldlt", type=int, default=None, choices=[0, 1],
-                   help="elimination form: 0 block LU, 1 block LDL^T of the symmetric matrix (default: library's)")
+    p.add_argument("--ldlt", type=int, default=None, choices=[0, 1, 2],
+                   help="elimination form: 0 block LU, 1 block LDL^T of the symmetric matrix, 2 LDL^T for FP64 "
+                        "factorizations only (default: library's)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison factorization (large grids)")
     p.add_argument("--proxy", type=int, default=0,
                    help="construction with proxy points (h2_opts.proxy_min; 0 = exact far-field sample)")

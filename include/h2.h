@@ -134,13 +134,19 @@ typedef struct {
                             the residuals of refined solves with tol >=
                             1e-11, FP64 FMAs elsewhere; 2: also h2_matvec;
                             0: FP64 FMAs everywhere                        */
-  int ldlt;              /* elimination form: 1 (default) block LDL^T when
-                            the matrix is complex symmetric (Z^T = Z:
-                            always for h2_build, for h2_load when every
-                            block equals the transpose of its mirror; a
-                            batch uses it when all its instances qualify),
-                            block LU otherwise; 0 block LU always (eq. 34,
-                            both panels L^-1 P Z_i'c and Z_ci' U^-1 kept).
+  int ldlt;              /* elimination form: 2 (default) block LDL^T for
+                            FP64 factorizations of a complex-symmetric
+                            matrix, block LU for mixed-precision ones; 1
+                            block LDL^T for both precisions; 0 block LU
+                            always (eq. 34, both panels L^-1 P Z_i'c and
+                            Z_ci' U^-1 kept).  LDL^T needs Z^T = Z (always
+                            for h2_build, for h2_load when every block
+                            equals the transpose of its mirror); a batch
+                            uses it when all its instances qualify.  With
+                            a complex64 bulk its rounding error is larger
+                            than LU's (1.4x at 262,144 unknowns; at
+                            884,736 unknowns, eps 1e-4, the refinement did
+                            not converge), hence the default.
                             LDL^T keeps one block of each off-diagonal
                             pair, the raw block row Z_i'c and the pivoted
                             LU of F = Z_i'i' as the factor (F^-1 applied

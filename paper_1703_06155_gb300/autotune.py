@@ -15,7 +15,8 @@ for candidate settings of
                 one-sided Jacobi SVD of the Cholesky factor,
   stop_level    early stop of the factorization (Sec. III-C): l0 (0) or one
                 to three levels below it, the rest as one dense final block,
-  ldlt          block LDL^T / block LU elimination (symmetric matrices),
+  ldlt          block LDL^T in FP64 only / in both precisions (symmetric
+                matrices; block LU otherwise),
 
 one parameter at a time from the defaults (coordinate descent), keeps the
 fastest setting of each and leaves it set on the context.  Every timing runs
@@ -31,7 +32,7 @@ DEFAULT_SPACE = {
     "cluster_max": [16, 8],
     "apply_path": [2, 1],
     "eig_solver": [2, 0, 1],
-    "ldlt": [1, 0],
+    "ldlt": [2, 1],
 }
 
 
@@ -62,7 +63,7 @@ def autotune(ctx, b, eps, precision="mixed", tol=1e-6, space=None, repeats=2, st
         space = dict(DEFAULT_SPACE)
         space["stop_level"] = stop_levels(ctx)
         if not ctx.stats()["symmetric"]:
-            space["ldlt"] = [1]  # block LU either way: the LDL^T form needs a symmetric matrix
+            space["ldlt"] = [2]  # block LU either way: the LDL^T form needs a symmetric matrix
     space = dict(space)
     stream = stream or torch.cuda.current_stream()
     best = {k: v[0] for k, v in space.items()}

@@ -255,7 +255,7 @@ void h2_default_opts(h2_opts* o) {
   o->stop_level = 0;
   o->proxy_margin = 0.3;
   o->matvec_emulation = 1;
-  o->ldlt = 1;
+  o->ldlt = 2;
 }
 
 h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
@@ -263,7 +263,7 @@ h2_status h2_set_opts(h2_ctx* ctx, const h2_opts* o) {
       o->cluster_max > 16 || o->tile_policy < 0 || o->tile_policy > 1 || o->profile < 0 || o->profile > 2 ||
       o->tensor_cores < 0 || o->tensor_cores > 2 || o->gram_emulation < 0 || o->gram_emulation > 1 ||
       o->eig_solver < 0 || o->eig_solver > 2 || o->stop_level < 0 || o->matvec_emulation < 0 ||
-      o->matvec_emulation > 2 || o->ldlt < 0 || o->ldlt > 1)
+      o->matvec_emulation > 2 || o->ldlt < 0 || o->ldlt > 2)
     return H2_EINVAL;
   h2_opts& c = ctx->c.opts;
   c.apply_path = o->apply_path;
@@ -313,7 +313,7 @@ h2_status h2_build(const double* pts, int64_t N, double k, double h, const doubl
   if (x->c.opts.leafsize < 1 || !(x->c.opts.eta > 0) || x->c.opts.tensor_cores < 0 || x->c.opts.tensor_cores > 2 ||
       x->c.opts.gram_emulation < 0 || x->c.opts.gram_emulation > 1 || x->c.opts.eig_solver < 0 ||
       x->c.opts.eig_solver > 2 || x->c.opts.stop_level < 0 || x->c.opts.matvec_emulation < 0 ||
-      x->c.opts.matvec_emulation > 2 || x->c.opts.ldlt < 0 || x->c.opts.ldlt > 1) {
+      x->c.opts.matvec_emulation > 2 || x->c.opts.ldlt < 0 || x->c.opts.ldlt > 2) {
     delete x;
     g_err = "h2_build: bad options";
     return H2_EINVAL;

@@ -1383,10 +1383,12 @@ void check_status(Ctx& c) {
 void factorize_group(const std::vector<Ctx*>& cs, double eps, int prec) {
   const auto t0 = std::chrono::steady_clock::now();
   Ctx& lc = *cs[0];
-  // block LDL^T (h2_opts.ldlt) when every instance asks for it and is
-  // complex symmetric (the launches of a group share one form), else block LU
+  // block LDL^T (h2_opts.ldlt: 1, or 2 for an FP64 factorization) when every
+  // instance asks for it and is complex symmetric (the launches of a group
+  // share one form), else block LU
   bool ldlt = true;
-  for (Ctx* c : cs) ldlt = ldlt && c->opts.ldlt != 0 && c->H.symmetric;
+  for (Ctx* c : cs)
+    ldlt = ldlt && (c->opts.ldlt == 1 || (c->opts.ldlt == 2 && prec == P64)) && c->H.symmetric;
   for (Ctx* c : cs) {
     c->fac_ldlt = ldlt;
     c->stream = lc.stream;

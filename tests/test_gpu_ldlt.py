@@ -1,5 +1,5 @@
-"""Block LDL^T form of the elimination (h2_opts.ldlt = 1, the default for a
-complex-symmetric matrix) on the GPU against
+"""Block LDL^T form of the elimination (h2_opts.ldlt = 1; the default 2 takes
+it for FP64 factorizations of a complex-symmetric matrix) on the GPU against
 the oracle's block LDL^T (factor.factorize(..., symmetric=True)) on the same
 H^2 matrices (h2_load), and against the block LU form (ldlt = 0).
 
@@ -46,7 +46,10 @@ def load(Hm, **kw):
 def test_ldlt_exact(dev):
     Hm = h2_problem(12, 64, EPS)
     Zd = h2_dense(12, 64, EPS)
-    A = load(Hm, ldlt=1)
+    # the default takes block LDL^T for FP64 and block LU for the mixed bulk
+    A = load(Hm)
+    A.factorize(EPS, "mixed")
+    assert A.stats()["ldlt"] == 0
     A.factorize(0.0, "fp64")
     assert A.stats()["ldlt"] == 1
     b = inputs.rhs_gaussian(Hm.tree.N, 2, 11)
