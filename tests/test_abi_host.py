@@ -101,13 +101,19 @@ def test_set_opts_validates(libh2):
     a = H2.build(pts, K, H, 3.0, 1e-6, host_only=1)
     a.set_opts(apply_path=1, split_target=300, cluster_max=8, tile_policy=1)
     for bad in (dict(apply_path=3), dict(cluster_max=17), dict(tile_policy=2), dict(split_target=-1),
-                dict(tensor_cores=3), dict(tensor_cores=-1), dict(gram_emulation=2)):
+                dict(tensor_cores=3), dict(tensor_cores=-1), dict(gram_emulation=2), dict(eig_solver=3),
+                dict(matvec_emulation=3), dict(ldlt=3), dict(ldlt=-1)):
         with pytest.raises(H2Error):
             a.set_opts(**bad)
     assert libh2.h2_set_opts(None, ctypes.byref(default_opts())) == -1
     # the ctypes mirror of h2_opts reads the library's defaults field by field
     o = default_opts()
     assert (o.leafsize, o.tensor_cores, o.gram_emulation, o.profile) == (64, 2, 1, 0)
+    # the last fields of the struct (a layout mismatch would misread them)
+    assert (o.eig_solver, o.matvec_emulation, o.ldlt) == (2, 1, 2)
+    a.set_opts(ldlt=0)
+    a.set_opts(ldlt=1)
+    assert a.stats()["ldlt"] == 0  # no factorization yet
     a.close()
 
 
