@@ -68,3 +68,36 @@ def test_reference_arm_names_our_config():
     class A:
         grid, chi, eps, nrhs = 32, 3.0, 1e-6, 16
     assert bench.workload_name(A) == "grid32 (N=32768), chi=3, eps=1e-06, nrhs=16, leaf 64, eta 1"
+
+
+def test_autotune_coordinate_descent_and_ldlt_space(monkeypatch):
+    # host logic of the autotuner: one parameter at a time from the defaults,
+    # the fastest value kept; the block LDL^T choice is only offered for a
+    # symmetric matrix (a fake context and timer: no GPU)
+    from paper_1703_06155_gb300 import autotune
+
+    class Fake:
+        def __init__(self, sym):
+            self.sym, self.opts = sym, {}
+
+        def _sizes(self):
+            return (0, 9, 2)
+
+        def stats(self):
+            return {"symmetric": self.sym}
+
+        def set_opts(self, **kw):
+            self.opts = dict(kw)
+
+    def timer(ctx, b, eps, precision, tol, stream, repeats):
+        o = ctx.opts
+        return 100.0 - 5.0 * (o.get("ldlt") == 1) - 3.0 * (o.get("tile_policy") == 1) + 2.0 * (o.get("stop_level", 0) > 0)
+
+    monkeypatch.setattr(autotune, "_time_step", timer)
+    for sym, want in ((1, 1), (0, 2)):
+        ctx = Fake(sym)
+        best, log = autotune.autotune(ctx, None, 1e-6, stream=object())
+        assert best["ldlt"] == want and best["tile_policy"] == 1 and best["stop_level"] == 0
+        assert ctx.opts["ldlt"] == want
+        tried = {c["ldlt"] for c, _ in log}
+        assert tried == ({2, 1} if sym else {2})
